@@ -1,0 +1,94 @@
+"""The seeded generator: optimality conditions hold by construction, the
+active constraints have full rank, layouts are consistent, and draws are
+reproducible."""
+import numpy as np
+import pytest
+
+import qcpgen as g
+from qcpgen.problems import _constraint_rows
+
+
+def _check(p):
+    Pu = p.P.to_scipy()
+    assert np.all(p.P.row_ids() <= p.P.indices), "P must be upper"
+    for M in (p.P, p.A, p.AT):
+        assert np.all(np.diff(M.indptr) >= 0)
+        for r in range(min(M.nrows, 300)):
+            c = M.indices[M.indptr[r]:M.indptr[r + 1]]
+            assert np.all(np.diff(c) > 0)
+    np.testing.assert_array_equal(p.AT.data, p.A.data[p.AT_perm])
+    assert np.array_equal(p.A.to_scipy().T.toarray() if p.m * p.n < 4e6 else 0,
+                          p.AT.to_scipy().toarray() if p.m * p.n < 4e6 else 0)
+    assert int(p.cone_dim.sum()) == p.m
+    Pf = Pu + __import__("scipy.sparse", fromlist=["triu"]).triu(Pu, k=1).T
+    A = p.A.to_scipy()
+    np.testing.assert_allclose(A @ p.x + p.s, p.b, atol=1e-12 * max(1, np.abs(p.b).max(initial=0)))
+    np.testing.assert_allclose(Pf @ p.x + A.T @ p.y, -p.q, atol=1e-11 * max(1, np.abs(p.q).max(initial=0)))
+    assert abs(p.s @ p.y) < 1e-12 * max(1.0, np.linalg.norm(p.s) * np.linalg.norm(p.y))
+    r = 0
+    for t, d in p.cones:
+        yb, sb = p.y[r:r + d], p.s[r:r + d]
+        if t == g.ZERO:
+            assert np.all(sb == 0)
+        elif t == g.NONNEG:
+            assert np.all(yb >= 0) and np.all(sb >= 0)
+            assert np.all((yb > 0) ^ (sb > 0)), "strict complementarity"
+        else:
+            assert np.linalg.norm(yb[1:]) <= yb[0] + 1e-12
+            assert np.linalg.norm(sb[1:]) <= sb[0] + 1e-12
+            assert (yb[0] > 0) or (sb[0] > 0)
+        r += d
+
+
+def test_config1():
+    p = g.config1(0)
+    assert (p.n, p.m, p.P.nnz) == (50, 80, 1275)
+    _check(p)
+    C = _constraint_rows(p.A, p.cones, p.y, p.s)
+    assert C.shape[0] == 50 and np.linalg.matrix_rank(C.toarray()) == 50
+    q = g.config1(0)
+    np.testing.assert_array_equal(p.A.data, q.A.data)
+    np.testing.assert_array_equal(p.q, q.q)
+
+
+@pytest.mark.slow
+def test_config2():
+    p = g.config2(0)
+    assert (p.n, p.m) == (2000, 5500) and p.A.nnz == 44000
+    assert len(p.cones) == 302
+    _check(p)
+
+
+def test_config3_scaled_and_small():
+    p = g.config3(0, scale=0.02)
+    _check(p)
+    assert max(d for t, d in p.cones if t == g.SOC) <= 200
+    assert min(d for t, d in p.cones if t == g.SOC) >= 3
+    for p in [g.small_qcp(1, 12, 3, 6, (3, 4, 5)), g.unconstrained_qp(0, 5), g.equality_qp(2, 8, 3)]:
+        _check(p)
+
+
+def test_config4_subset():
+    ps = g.config4(0, n_problems=3, n_range=(50, 120))
+    for p in ps:
+        _check(p)
+        assert 1.5 * p.n - 1 <= p.m <= 3 * p.n + 1
+    # problem i is drawn from its own stream
+    q = g.config4(0, n_problems=1, n_range=(50, 120), first=1)[0]
+    np.testing.assert_array_equal(q.q, ps[1].q)
+
+
+def test_config5_family_small():
+    fam = g.config5_family(0, scale=0.02)
+    a, b = fam.instance(0), fam.instance(1)
+    _check(a)
+    _check(b)
+    assert a.P is b.P and a.A is b.A
+    assert not np.array_equal(a.q, b.q)
+
+
+def test_fp32_rounding():
+    p = g.config1(0)
+    r = g.round_to_fp32(p)
+    assert np.all(r.A.data == r.A.data.astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(r.q - p.q)) <= 1e-6 * np.max(np.abs(p.q))
