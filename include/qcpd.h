@@ -1,0 +1,243 @@
+/*
+ * qcpd.h -- C ABI of the GB300 library for derivatives of a quadratic cone
+ * program's solution map (arXiv 2508.17522).
+ *
+ * The conic pair (Sec. 2.1, eq. conic-pair):
+ *     minimize (1/2) x^T P x + q^T x  s.t.  A x + s = b,  s in K,
+ * with dual variable y in K*.  Given a solution (x, y, s), the library
+ * evaluates
+ *   * the forward product (JVP, Sec. 3.1):
+ *       (dx, dy, ds) = D S(theta)[dP, dA, dq, db]
+ *   * the adjoint product (VJP, Sec. 3.2):
+ *       (dP, dA, dq, db) = D S(theta)^T [dx, dy, ds], kept on the stored
+ *       patterns of P and A (Sec. 3.2, last paragraph),
+ * through the implicit function theorem on the homogeneous embedding
+ * (Sec. 2.4): z = (x, y - s, 1), F = D_z N(z), dz solves F dz = -D_theta N,
+ * and the outputs go through D phi(z).  The linear systems are solved
+ * matrix-free by an LSQR Krylov iteration (Sec. 3.1 prescribes LSMR; both
+ * need only products with F and F^T, which is what the kernels provide).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Memory     Every array argument is a DEVICE pointer owned by the caller
+ *             (for example a torch tensor's data_ptr), except the cone
+ *             description (qcp_cone), which lives in HOST memory, and the
+ *             qcp_info outputs, which are host structs.  The library copies
+ *             what it needs at plan creation; inputs may be freed after
+ *             qcp_plan_create returns.  A plan owns its device workspace,
+ *             allocated once at creation and freed by qcp_plan_destroy.
+ *  Types      Floating-point arrays are all float64 (QCP_F64) or all
+ *             float32 (QCP_F32, "FP32 storage": problem data, the combined
+ *             matrix, perturbations and outputs in binary32; Krylov vectors
+ *             and every dot product and norm in float64).
+ *             Index arrays: row pointers int64, column indices int32,
+ *             sorted and unique within each row.
+ *  P          Symmetric; only its upper triangle (diagonal included) is
+ *             stored, in CSR.  Explicit zeros are part of the pattern.
+ *  dP         JVP input: values on P's stored upper pattern, read as the
+ *             upper triangle of a symmetric perturbation.  VJP output: the
+ *             entries of the symmetric matrix D_theta N^T[r]_P at the stored
+ *             upper positions (so the gradient with respect to a stored
+ *             off-diagonal value is twice the returned entry).
+ *  A, AT      A is m x n CSR; AT is its transpose in CSR (n x m).  AT_perm
+ *             (int64, nnz(A)) maps AT's k-th stored value to its position in
+ *             A's value array; it may be NULL, in which case the plan derives
+ *             it from A.
+ *  Cones      K is a product of blocks listed in row order: QCP_CONE_ZERO
+ *             (the cone {0}), QCP_CONE_NONNEG (R+^d) and QCP_CONE_SOC
+ *             (second-order cone, stored (t, u) with t first, Appendix A).
+ *  Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *             All work of a plan is enqueued on the stream given at creation.
+ *             JVP/VJP calls return when the outputs are written: they
+ *             synchronize the stream every opts->check_every iterations to
+ *             test convergence (check_every = 0: run exactly opts->maxiter
+ *             iterations without synchronizing; finished systems skip their
+ *             work).
+ *  Errors     Every entry point returns a qcp_status.  On an error the
+ *             outputs are unspecified and qcp_last_error() describes it.
+ *             QCP_NOT_CONVERGED still writes the outputs (the last iterate).
+ *  Threads    A plan must not be used by two host threads at once.
+ */
+#ifndef QCPD_H
+#define QCPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QCP_OK = 0,
+    QCP_ERR_ARG = 1,          /* null pointer, bad size, unsorted CSR, P not upper, AT inconsistent, ... */
+    QCP_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    QCP_ERR_ALLOC = 3,        /* device allocation failed */
+    QCP_NOT_CONVERGED = 4,    /* rtol not reached (maxiter hit, or the true residual stalled above
+                                 rtol at the attainable accuracy); outputs hold the last iterate */
+    QCP_BREAKDOWN = 5,        /* a non-finite Krylov scalar appeared */
+    QCP_ERR_TIMEOUT = 6,      /* reserved for bounded device waits */
+    QCP_WARN_NEAR_KINK = 7    /* solution within opts->kink_tol of a point where D Pi is undefined */
+} qcp_status;
+
+typedef enum { QCP_F64 = 0, QCP_F32 = 1 } qcp_dtype;
+
+typedef enum { QCP_CONE_ZERO = 0, QCP_CONE_NONNEG = 1, QCP_CONE_SOC = 2 } qcp_cone_type;
+
+/* CSR matrix; all pointers are device pointers. */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int64_t* indptr;    /* nrows + 1 */
+    const int32_t* indices;   /* nnz */
+    const void* values;       /* nnz, float64 or float32 */
+} qcp_csr;
+
+/* Cone blocks in row order; HOST arrays of length nblocks. */
+typedef struct {
+    int32_t nblocks;
+    const int32_t* type;      /* qcp_cone_type */
+    const int32_t* dim;       /* block sizes, each >= 1, summing to m */
+} qcp_cone;
+
+typedef struct {
+    int64_t n, m;             /* n >= 1 variables, m >= 0 constraint rows */
+    qcp_csr P_upper;          /* n x n, upper triangle incl. diagonal */
+    qcp_csr A;                /* m x n */
+    qcp_csr AT;               /* n x m, the transpose of A */
+    const int64_t* AT_perm;   /* nnz(A) or NULL */
+    const void* q;            /* n */
+    const void* b;            /* m */
+    qcp_cone K;
+} qcp_problem;
+
+/* A solution of the conic pair: x (n), y (m) in K*, s (m) in K. */
+typedef struct {
+    const void* x;
+    const void* y;
+    const void* s;
+} qcp_solution;
+
+typedef enum {
+    QCP_PRECOND_NONE = 0,     /* LSQR on F itself: the plain method of Sec. 3.1 */
+    QCP_PRECOND_EQUILIBRATE = 1 /* LSQR on W F C: W = 1/(row norms of F), C = 1/(column norms of W F),
+                                   C constant on each SOC block; D Pi's off-diagonal SOC terms are
+                                   left out of the norms (any positive diagonal is a valid choice) */
+} qcp_precond;
+
+typedef struct {
+    int32_t solver;           /* 0 = LSQR (the only solver built) */
+    double rtol;              /* target for ||F dz + dN|| / ||dN|| (JVP) or ||F^T r + g|| / ||g|| (VJP) */
+    int64_t maxiter;          /* iteration cap per system (counted over all restarts) */
+    int32_t check_every;      /* iterations between host convergence checks; 0 = none */
+    int32_t use_graph;        /* 1 = replay the iteration chunk as a CUDA graph */
+    int32_t compute_residual; /* 1 = recompute the true (unscaled) relative residual at exit and,
+                                 if it is above rtol, continue iterating with a tighter internal
+                                 tolerance (at most 4 times, while it keeps halving); 0 = trust the
+                                 Krylov estimate */
+    int32_t precond;          /* qcp_precond */
+    double kink_tol;          /* QCP_WARN_NEAR_KINK threshold on info.kink_margin */
+} qcp_options;
+
+typedef struct {
+    int32_t status;           /* qcp_status of this system */
+    int64_t iters;            /* Krylov iterations taken */
+    double rel_residual;      /* true ||F dz + dN|| / ||dN|| at exit (if computed, else -1) */
+    double rel_residual_est;  /* the Krylov recurrence's estimate of the same ratio */
+    double kink_margin;       /* min over rows of the distance to a kink of D Pi (Appendix A) */
+} qcp_info;
+
+typedef struct qcp_plan qcp_plan;
+
+/* Text of the last error on this host thread (never NULL). */
+const char* qcp_last_error(void);
+
+/* Fill *opts with defaults: LSQR, rtol 1e-10, maxiter 100000, check_every 32,
+   use_graph 1, compute_residual 1, precond QCP_PRECOND_NONE, kink_tol 0. */
+void qcp_default_options(qcp_options* opts);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t qcp_version(void);
+
+/*
+ * Build a plan for one problem at one solution (Sec. 3.1, first step: form z
+ * and Pi z; Sec. 2.4: the data of F).  Precomputes on the device P x,
+ * g = 2 P x + q, kappa = x^T P x, z_y = y - s and the per-block state of
+ * D Pi_{K*}(z_y) (Appendix A), lays out the combined matrix
+ * [[P, A^T], [A, 0]] used by every product with F and F^T, and allocates
+ * Krylov workspace for up to max_rhs simultaneous directions.
+ * Errors: QCP_ERR_ARG (see qcp_status), QCP_ERR_ALLOC, QCP_ERR_CUDA.
+ */
+int qcp_plan_create(const qcp_problem* prob, const qcp_solution* sol, qcp_dtype dtype,
+                    int32_t max_rhs, void* stream, qcp_plan** out);
+
+/*
+ * A plan over nprob independent problems of any sizes (probs[i], sols[i]),
+ * run together in every launch (one direction per problem).  Vector and
+ * value arguments of the batched calls are the per-problem arrays
+ * concatenated in problem order.
+ */
+int qcp_batch_plan_create(int32_t nprob, const qcp_problem* probs, const qcp_solution* sols,
+                          qcp_dtype dtype, void* stream, qcp_plan** out);
+
+int qcp_plan_destroy(qcp_plan* plan);
+
+/* Number of problems in the plan and total lengths of the concatenated
+   arrays (n, m, nnz of P's upper pattern, nnz of A). */
+int qcp_plan_sizes(const qcp_plan* plan, int64_t* nprob, int64_t* n_total, int64_t* m_total,
+                   int64_t* nnzP_total, int64_t* nnzA_total);
+
+/*
+ * Forward product (Sec. 3.1): dN = D_theta N(z)[dP, dA, dq, db]
+ * = (dP x + dA^T y + dq, -dA x + db, -x^T dP x - dq^T x - db^T y);
+ * dz solves min ||F dz + dN||; (dx, dy, ds) = D phi(z) dz
+ * = (dz_x - dz_N x, D dz_y - dz_N y, D dz_y - dz_y - dz_N s), D = D Pi_{K*}(z_y).
+ * Inputs dP (nnz P), dA (nnz A), dq (n), db (m); outputs dx (n), dy (m), ds (m).
+ * For a batched plan all arrays are concatenations over problems and info
+ * points to nprob structs.  info may be NULL.
+ */
+int qcp_derivative_jvp(qcp_plan* plan, const qcp_options* opts, const void* dP, const void* dA,
+                       const void* dq, const void* db, void* dx, void* dy, void* ds,
+                       qcp_info* info);
+
+/*
+ * Adjoint product (Sec. 3.2): g = D phi(z)^T (wx, wy, ws)
+ * = (wx, D (wy + ws) - ws, -x^T wx - y^T wy - s^T ws); r solves
+ * min ||F^T r + g||; (dP, dA, dq, db) = D_theta N(z)^T [r] on the patterns:
+ * dP_ij = (r1_i x_j + x_i r1_j)/2 - r_N x_i x_j, dA_ij = y_i r1_j - r2_i x_j,
+ * dq = r1 - r_N x, db = r2 - r_N y.
+ */
+int qcp_derivative_vjp(qcp_plan* plan, const qcp_options* opts, const void* wx, const void* wy,
+                       const void* ws, void* dP, void* dA, void* dq, void* db, qcp_info* info);
+
+/*
+ * k directions of a single-problem plan in one solve (k <= max_rhs): every
+ * launch carries all k systems.  Arrays hold the k directions back to back
+ * (direction i of dP at offset i * nnz(P), of dx at i * n, ...); info holds k
+ * structs.
+ */
+int qcp_derivative_jvp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k, const void* dP,
+                             const void* dA, const void* dq, const void* db, void* dx, void* dy,
+                             void* ds, qcp_info* info);
+int qcp_derivative_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k, const void* wx,
+                             const void* wy, const void* ws, void* dP, void* dA, void* dq, void* db,
+                             qcp_info* info);
+
+/*
+ * Tile schedule of a plan: tile_nnz is the target number of nonzeros of M
+ * per tile (rows are grouped into tiles, never splitting an SOC block); a row
+ * with more than long_row nonzeros leaves its tile and is cut into pieces of
+ * long_chunk nonzeros, one CTA each.  Rebuilds the schedule and the Krylov
+ * workspace (and drops captured graphs).  Defaults 4096, 512, 4096.  Used by
+ * the autotuner.  Errors: QCP_ERR_ARG (tile_nnz < 64, long_row < 1,
+ * long_chunk < 32), QCP_ERR_ALLOC.
+ */
+int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, int32_t long_chunk);
+
+/* Number of kernel launches made by the most recent JVP/VJP call of the plan
+   (graph replays counted per kernel node). */
+int64_t qcp_plan_last_launches(const qcp_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCPD_H */

@@ -74,12 +74,16 @@ def jvp_dense(prob, d, fac=None):
     """(dx, dy, ds) = D phi(z) (-F^{-1}) D_theta N(z)[d theta]  (Sec. 3.1)."""
     fac = fac or DenseFactor(prob)
     z = fac.z
-    dN = d_theta_N(prob, z, d.dP, d.dA, d.dq, d.db)
+    big = fac.N > 3000
+    dN = (d_theta_N_sparse if big else d_theta_N)(prob, z, d.dP, d.dA, d.dq, d.db)
     dz, lam = fac.solve(-dN)
-    out = E.Dphi(prob, z) @ dz
-    n, m = prob.n, prob.m
     res = np.linalg.norm(fac.F @ dz + dN) / max(np.linalg.norm(dN), 1e-300)
     info = {"lambda": lam, "pivot_ratio": fac.pivot_ratio, "rel_residual": float(res)}
+    if big:   # D phi applied without forming it (pinned equal to the dense D phi)
+        dx, dy, ds = _phi_apply(prob, z, dz)
+        return dx, dy, ds, info
+    out = E.Dphi(prob, z) @ dz
+    n, m = prob.n, prob.m
     return out[:n], out[n:n + m], out[n + m:], info
 
 
@@ -87,11 +91,14 @@ def vjp_dense(prob, d, fac=None):
     """d theta = D_theta N(z)^T (-F^{-T}) D phi(z)^T w  (Sec. 3.2)."""
     fac = fac or DenseFactor(prob)
     z = fac.z
-    w = np.concatenate([d.wx, d.wy, d.ws])
-    g = E.Dphi(prob, z).T @ w
+    big = fac.N > 3000
+    if big:
+        g = _phi_apply_T(prob, z, d.wx, d.wy, d.ws)
+    else:
+        g = E.Dphi(prob, z).T @ np.concatenate([d.wx, d.wy, d.ws])
     r, mu = fac.solve(-g, trans=1)
     res = np.linalg.norm(fac.F.T @ r + g) / max(np.linalg.norm(g), 1e-300)
-    dPv, dAv, dq, db = d_theta_N_T(prob, z, r)
+    dPv, dAv, dq, db = (d_theta_N_T_sparse if big else d_theta_N_T)(prob, z, r)
     info = {"mu": mu, "pivot_ratio": fac.pivot_ratio, "rel_residual": float(res)}
     return dPv, dAv, dq, db, info
 

@@ -136,7 +136,12 @@ def F_dense(prob, z):
     pz = proj_K(prob, z)
     DP = dproj_K(prob, z)
     N = z.shape[0]
-    return (DuQ(prob, pz) @ DP - DP + np.eye(N)) / z[-1]
+    if N <= 3000:
+        prod = DuQ(prob, pz) @ DP
+    else:
+        # the same product, with D Pi held sparse (it is block diagonal)
+        prod = np.asarray((sp.csr_matrix(DP).T @ DuQ(prob, pz).T).T)
+    return (prod - DP + np.eye(N)) / z[-1]
 
 
 # ---------------------------------------------------------------- D_theta Q

@@ -1,0 +1,501 @@
+// Entry points of the C ABI (include/qcpd.h) and the LSQR driver.
+//
+// One JVP/VJP solve (Sec. 3.1 / 3.2) is, on the plan's stream:
+//   right-hand side kernel (dN or D phi^T w, and ||b||)
+//   one G^T- (JVP) or G-pass (VJP) starting the bidiagonalisation
+//   repeated iterations: [G-pass, G^T-pass] (JVP) or [G^T-pass, G-pass]
+//     (VJP), each a single launch over all tiles of all systems, replayed
+//     from a captured CUDA graph in chunks of check_every iterations
+//   output kernel (D phi dz, or the pattern-restricted D_theta N^T r)
+//   optionally one more pass for the true residual.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "qcpd_kernels.cuh"
+#include "qcpd_plan.h"
+
+namespace qcpd {
+const char* last_error();
+int create_plan(qcp_plan* p, const qcp_problem* probs, const qcp_solution* sols);
+
+template <typename T>
+static PlanView<T> view(qcp_plan* p, bool scaled) {
+    PlanView<T> v;
+    v.tiles = p->d_tiles.as<Tile>();
+    v.sys = p->d_sys.as<Sys>();
+    v.probs = p->d_prob.as<Prob>();
+    v.state = p->d_state.as<LsqrState>();
+    v.R = Reduce{p->d_tpart.as<Part>(), p->d_gpart.as<Part>(), p->d_gcnt.as<int32_t>(), p->d_scnt.as<int32_t>(),
+                 p->d_groups.as<Group>()};
+    v.active = p->d_active.as<int>();
+    v.split_cnt = p->d_split_cnt.as<int32_t>();
+    v.row_part = p->d_row_part.as<double>();
+    v.mrowptr = p->d_mrowptr.as<int64_t>();
+    v.mcol = p->d_mcol.as<int32_t>();
+    v.mval = p->d_mval.as<T>();
+    v.mvalG = scaled ? p->d_mvalG.as<T>() : p->d_mval.as<T>();
+    v.mvalT = scaled ? p->d_mvalT.as<T>() : p->d_mval.as<T>();
+    v.rw = p->d_rw.as<double>();
+    v.cd = p->d_cd.as<double>();
+    v.scaled = scaled ? 1 : 0;
+    v.mvmap = p->d_mvmap.as<int32_t>();
+    v.coefA = p->d_coefA.as<double>();
+    v.coefB = p->d_coefB.as<double>();
+    v.pz = p->d_pz.as<double>();
+    v.zy = p->d_zy.as<double>();
+    v.flag = p->d_flag.as<int8_t>();
+    v.blocks = p->d_blocks.as<SocBlock>();
+    v.U = p->d_U.as<double>();
+    v.V = p->d_V.as<double>();
+    v.W = p->d_W.as<double>();
+    v.X = p->d_X.as<double>();
+    v.XI = p->d_XI.as<double>();
+    v.RHS = p->d_RHS.as<double>();
+    v.rmax = p->rmax;
+    v.long_chunk = p->long_chunk;
+    return v;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+    // static + dynamic shared memory above 48 KB needs the opt-in
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, bool SC>
+static int set_smem_attrs_sc(size_t smem) {
+    QCP_CUDA(allow_smem(k_pass<PASS_G, ROLE_U, SC, T>, smem));
+    QCP_CUDA(allow_smem(k_pass<PASS_G, ROLE_V, SC, T>, smem));
+    QCP_CUDA(allow_smem(k_pass<PASS_G, ROLE_RES, SC, T>, smem));
+    QCP_CUDA(allow_smem(k_pass<PASS_GT, ROLE_U, SC, T>, smem));
+    QCP_CUDA(allow_smem(k_pass<PASS_GT, ROLE_V, SC, T>, smem));
+    QCP_CUDA(allow_smem(k_pass<PASS_GT, ROLE_RES, SC, T>, smem));
+    return QCP_OK;
+}
+
+template <typename T>
+static int set_smem_attrs(size_t smem) {
+    QCP_TRY((set_smem_attrs_sc<T, false>(smem)));
+    QCP_TRY((set_smem_attrs_sc<T, true>(smem)));
+    QCP_CUDA(allow_smem(k_vjp_rhs<T>, smem));
+    QCP_CUDA(allow_smem(k_jvp_out<T>, smem));
+    return QCP_OK;
+}
+
+// Launch one pass kernel: PASS x ROLE, scaled or not.
+template <int PASS, int ROLE, typename T>
+static void launch_pass(const PlanView<T>& v, int ntiles, size_t smem, cudaStream_t st) {
+    if (v.scaled) k_pass<PASS, ROLE, true, T><<<ntiles, kThreads, smem, st>>>(v);
+    else k_pass<PASS, ROLE, false, T><<<ntiles, kThreads, smem, st>>>(v);
+}
+
+// Launch one LSQR iteration: u-update pass then v-update pass.
+template <typename T>
+static void launch_iter(int mode, const PlanView<T>& v, int ntiles, size_t smem, cudaStream_t st) {
+    if (mode == 0) {
+        launch_pass<PASS_G, ROLE_U, T>(v, ntiles, smem, st);
+        launch_pass<PASS_GT, ROLE_V, T>(v, ntiles, smem, st);
+    } else {
+        launch_pass<PASS_GT, ROLE_U, T>(v, ntiles, smem, st);
+        launch_pass<PASS_G, ROLE_V, T>(v, ntiles, smem, st);
+    }
+}
+
+template <typename T>
+static int run_chunk(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int ntiles, size_t smem, int chunk,
+                     bool use_graph) {
+    cudaStream_t st = p->stream;
+    if (!use_graph || chunk < 2) {
+        for (int c = 0; c < chunk; ++c) launch_iter<T>(mode, v, ntiles, smem, st);
+        QCP_CUDA(cudaGetLastError());
+        p->last_launches += 2 * chunk;
+        return QCP_OK;
+    }
+    GraphKey key{mode, nsys, chunk, v.scaled};
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        QCP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int c = 0; c < chunk; ++c) launch_iter<T>(mode, v, ntiles, smem, st);
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ee = cudaStreamEndCapture(st, &g);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            set_error("graph capture failed: %s", cudaGetErrorString(le != cudaSuccess ? le : ee));
+            return QCP_ERR_CUDA;
+        }
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            set_error("graph instantiation failed: %s", cudaGetErrorString(ie));
+            return QCP_ERR_CUDA;
+        }
+        it = p->graphs.emplace(key, ge).first;
+    }
+    QCP_CUDA(cudaGraphLaunch(it->second, st));
+    p->last_launches += 2 * chunk;
+    return QCP_OK;
+}
+
+static int status_of(const LsqrState& s, double kink, double kink_tol) {
+    if (s.outcome == O_BREAKDOWN) return QCP_BREAKDOWN;
+    if (s.outcome == O_MAXITER) return QCP_NOT_CONVERGED;
+    if (kink < kink_tol) return QCP_WARN_NEAR_KINK;
+    return QCP_OK;
+}
+
+static int worse(int a, int b) {
+    auto rank = [](int s) {
+        switch (s) {
+            case QCP_BREAKDOWN: return 3;
+            case QCP_NOT_CONVERGED: return 2;
+            case QCP_WARN_NEAR_KINK: return 1;
+            default: return 0;
+        }
+    };
+    return rank(b) > rank(a) ? b : a;
+}
+
+// Iterate until no system is active (host checks every check_every
+// iterations) or the iteration budget of this round is spent.
+template <typename T>
+static int iterate(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int ntiles, size_t smem,
+                   const qcp_options& opts) {
+    int64_t done_iters = 0;
+    const int64_t cap = opts.maxiter + 1;
+    while (done_iters < cap) {
+        int64_t chunk = opts.check_every > 0 ? opts.check_every : cap;
+        chunk = std::min<int64_t>(chunk, cap - done_iters);
+        const bool graph_ok = opts.use_graph && opts.check_every > 0 && chunk == opts.check_every;
+        QCP_TRY(run_chunk<T>(p, mode, nsys, v, ntiles, smem, (int)chunk, graph_ok));
+        done_iters += chunk;
+        if (opts.check_every > 0) {
+            QCP_CUDA(cudaMemcpyAsync(p->h_active, p->d_active.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+            QCP_CUDA(cudaStreamSynchronize(p->stream));
+            if (*p->h_active <= 0) break;
+        }
+    }
+    return QCP_OK;
+}
+
+// The v-update pass of the operator: starts the bidiagonalisation and resumes it.
+template <typename T>
+static void launch_v_pass(int mode, const PlanView<T>& v, int ntiles, size_t smem, cudaStream_t st) {
+    if (mode == 0) launch_pass<PASS_GT, ROLE_V, T>(v, ntiles, smem, st);
+    else launch_pass<PASS_G, ROLE_V, T>(v, ntiles, smem, st);
+}
+
+template <typename T>
+static void launch_output(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int ntiles, size_t smem,
+                          const OutArgs<T>& out, bool residual) {
+    cudaStream_t st = p->stream;
+    if (mode == 0) {
+        k_jvp_out<T><<<ntiles, kThreads, smem, st>>>(v, out);
+        if (residual) launch_pass<PASS_G, ROLE_RES, T>(v, ntiles, smem, st);
+    } else {
+        int maxrows = 0;
+        for (int s = 0; s < nsys; ++s) {
+            const Prob& pr = p->hprob[p->hsys[s].prob];
+            maxrows = std::max(maxrows, pr.n + pr.m);
+        }
+        dim3 grid((unsigned)std::max(1, std::min(4096, (maxrows + kWarps - 1) / kWarps)), (unsigned)nsys);
+        k_vjp_out<T><<<grid, kThreads, 0, st>>>(v, out, p->d_pip.as<int64_t>(), p->d_pix.as<int32_t>(),
+                                                p->d_aip.as<int64_t>(), p->d_aix.as<int32_t>());
+        if (residual) launch_pass<PASS_GT, ROLE_RES, T>(v, ntiles, smem, st);
+    }
+    p->last_launches += 1 + (residual ? 1 : 0);
+}
+
+// mode 0: JVP, 1: VJP.  nsys systems (the first nsys of the plan).
+template <typename T>
+static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, const RhsArgs<T>& rin,
+                 const OutArgs<T>& out, qcp_info* info) {
+    qcp_options opts;
+    if (opts_in) opts = *opts_in;
+    else qcp_default_options(&opts);
+    if (!(opts.rtol >= 0.0) || opts.maxiter < 1 || opts.check_every < 0) {
+        set_error("bad options: rtol >= 0, maxiter >= 1, check_every >= 0 required");
+        return QCP_ERR_ARG;
+    }
+    if (opts.solver != 0) {
+        set_error("only solver 0 (LSQR) is built");
+        return QCP_ERR_ARG;
+    }
+    if (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE) {
+        set_error("precond must be QCP_PRECOND_NONE or QCP_PRECOND_EQUILIBRATE");
+        return QCP_ERR_ARG;
+    }
+    cudaStream_t st = p->stream;
+    const bool scaled = opts.precond == QCP_PRECOND_EQUILIBRATE;
+    const PlanView<T> v = view<T>(p, scaled);
+    const int ntiles = p->batched ? p->ntiles : nsys * p->tiles_per_sys;
+    const size_t smem = tile_smem_bytes(p->rmax);
+    QCP_TRY(set_smem_attrs<T>(smem));
+    p->last_launches = 0;
+    QCP_CUDA(cudaMemsetAsync(p->d_active.p, 0, sizeof(int), st));
+    RhsArgs<T> ra = rin;
+    ra.rtol = opts.rtol;
+    ra.maxiter = opts.maxiter;
+    if (mode == 0) k_jvp_rhs<T><<<ntiles, kThreads, 0, st>>>(v, ra);
+    else k_vjp_rhs<T><<<ntiles, kThreads, smem, st>>>(v, ra);
+    launch_v_pass<T>(mode, v, ntiles, smem, st);
+    QCP_CUDA(cudaGetLastError());
+    p->last_launches += 2;
+    QCP_TRY(iterate<T>(p, mode, nsys, v, ntiles, smem, opts));
+    std::vector<LsqrState> hs(nsys);
+    std::vector<double> prev_res(nsys, INFINITY);
+    const bool residual = opts.compute_residual != 0;
+    for (int round = 0;; ++round) {
+        launch_output<T>(p, mode, nsys, v, ntiles, smem, out, residual);
+        QCP_CUDA(cudaGetLastError());
+        QCP_CUDA(cudaMemcpyAsync(hs.data(), p->d_state.p, nsys * sizeof(LsqrState), cudaMemcpyDeviceToHost, st));
+        QCP_CUDA(cudaStreamSynchronize(st));
+        if (!residual || round == 4) break;
+        // The Krylov estimate measures the scaled residual; where the true
+        // one misses the target, continue the same recurrence with a tighter
+        // internal tolerance.
+        int resumed = 0;
+        for (int s = 0; s < nsys; ++s) {
+            LsqrState& q = hs[s];
+            const bool improving = q.resid_true < 0.5 * prev_res[s];  // else rounding has stalled it
+            prev_res[s] = q.resid_true;
+            if (q.outcome != O_CONVERGED || !(q.resid_true > opts.rtol) || !(q.alpha > 0.0) ||
+                !isfinite(q.resid_true) || q.iters >= q.maxiter || q.bnorm_true <= 0.0 || !improving)
+                continue;
+            q.rtol *= std::max(0.01, 0.5 * opts.rtol / q.resid_true);
+            q.status = S_ACTIVE;
+            q.outcome = O_RUNNING;
+            q.xcoef = 0.0;
+            ++resumed;
+        }
+        if (!resumed) break;
+        QCP_CUDA(cudaMemcpyAsync(p->d_state.p, hs.data(), nsys * sizeof(LsqrState), cudaMemcpyHostToDevice, st));
+        QCP_CUDA(cudaMemcpyAsync(p->d_active.p, &resumed, sizeof(int), cudaMemcpyHostToDevice, st));
+        QCP_CUDA(cudaStreamSynchronize(st));
+        launch_v_pass<T>(mode, v, ntiles, smem, st);
+        p->last_launches += 1;
+        QCP_TRY(iterate<T>(p, mode, nsys, v, ntiles, smem, opts));
+    }
+    int rc = QCP_OK;
+    for (int s = 0; s < nsys; ++s) {
+        const double kink = p->kink[p->hsys[s].prob];
+        int ss = status_of(hs[s], kink, opts.kink_tol);
+        if (residual && ss != QCP_BREAKDOWN && hs[s].resid_true > opts.rtol) ss = QCP_NOT_CONVERGED;
+        rc = worse(rc, ss);
+        if (info) {
+            info[s].status = ss;
+            info[s].iters = hs[s].iters;
+            info[s].rel_residual = residual ? hs[s].resid_true : -1.0;
+            info[s].rel_residual_est = hs[s].bnorm > 0 ? hs[s].phibar / hs[s].bnorm : 0.0;
+            info[s].kink_margin = kink;
+        }
+    }
+    return rc;
+}
+
+static bool ptr_ok(const void* p, int64_t count) { return count == 0 || p != nullptr; }
+
+static int jvp_entry(qcp_plan* plan, const qcp_options* opts, int k, const void* dP, const void* dA,
+                     const void* dq, const void* db, void* dx, void* dy, void* ds, qcp_info* info) {
+    if (!plan) {
+        set_error("null plan");
+        return QCP_ERR_ARG;
+    }
+    const int nsys = plan->batched ? plan->nprob : k;
+    if (!plan->batched && (k < 1 || k > plan->max_rhs)) {
+        set_error("k = %d directions, plan built for 1..%d", k, plan->max_rhs);
+        return QCP_ERR_ARG;
+    }
+    const int64_t kk = plan->batched ? 1 : k;
+    if (!ptr_ok(dP, plan->pnz_tot * kk) || !ptr_ok(dA, plan->anz_tot * kk) || !ptr_ok(dq, plan->n_tot * kk) ||
+        !ptr_ok(db, plan->m_tot * kk) || !ptr_ok(dx, plan->n_tot * kk) || !ptr_ok(dy, plan->m_tot * kk) ||
+        !ptr_ok(ds, plan->m_tot * kk)) {
+        set_error("null array argument");
+        return QCP_ERR_ARG;
+    }
+    if (plan->dtype == QCP_F64) {
+        using T = double;
+        RhsArgs<T> r{(const T*)dP, (const T*)dA, (const T*)dq, (const T*)db, nullptr, nullptr, nullptr, 0, 0};
+        OutArgs<T> o{(T*)dx, (T*)dy, (T*)ds, nullptr};
+        return solve<T>(plan, 0, nsys, opts, r, o, info);
+    }
+    using T = float;
+    RhsArgs<T> r{(const T*)dP, (const T*)dA, (const T*)dq, (const T*)db, nullptr, nullptr, nullptr, 0, 0};
+    OutArgs<T> o{(T*)dx, (T*)dy, (T*)ds, nullptr};
+    return solve<T>(plan, 0, nsys, opts, r, o, info);
+}
+
+static int vjp_entry(qcp_plan* plan, const qcp_options* opts, int k, const void* wx, const void* wy,
+                     const void* ws, void* dP, void* dA, void* dq, void* db, qcp_info* info) {
+    if (!plan) {
+        set_error("null plan");
+        return QCP_ERR_ARG;
+    }
+    const int nsys = plan->batched ? plan->nprob : k;
+    if (!plan->batched && (k < 1 || k > plan->max_rhs)) {
+        set_error("k = %d directions, plan built for 1..%d", k, plan->max_rhs);
+        return QCP_ERR_ARG;
+    }
+    const int64_t kk = plan->batched ? 1 : k;
+    if (!ptr_ok(wx, plan->n_tot * kk) || !ptr_ok(wy, plan->m_tot * kk) || !ptr_ok(ws, plan->m_tot * kk) ||
+        !ptr_ok(dP, plan->pnz_tot * kk) || !ptr_ok(dA, plan->anz_tot * kk) || !ptr_ok(dq, plan->n_tot * kk) ||
+        !ptr_ok(db, plan->m_tot * kk)) {
+        set_error("null array argument");
+        return QCP_ERR_ARG;
+    }
+    if (plan->dtype == QCP_F64) {
+        using T = double;
+        RhsArgs<T> r{nullptr, nullptr, nullptr, nullptr, (const T*)wx, (const T*)wy, (const T*)ws, 0, 0};
+        OutArgs<T> o{(T*)dP, (T*)dA, (T*)dq, (T*)db};
+        return solve<T>(plan, 1, nsys, opts, r, o, info);
+    }
+    using T = float;
+    RhsArgs<T> r{nullptr, nullptr, nullptr, nullptr, (const T*)wx, (const T*)wy, (const T*)ws, 0, 0};
+    OutArgs<T> o{(T*)dP, (T*)dA, (T*)dq, (T*)db};
+    return solve<T>(plan, 1, nsys, opts, r, o, info);
+}
+
+static int make_plan(int np, const qcp_problem* probs, const qcp_solution* sols, qcp_dtype dtype, int max_rhs,
+                     bool batched, void* stream, qcp_plan** out) {
+    if (!out || !probs || !sols || np < 1 || max_rhs < 1) {
+        set_error("bad arguments to plan creation");
+        return QCP_ERR_ARG;
+    }
+    *out = nullptr;
+    if (dtype != QCP_F64 && dtype != QCP_F32) {
+        set_error("dtype must be QCP_F64 or QCP_F32");
+        return QCP_ERR_ARG;
+    }
+    qcp_plan* p = new qcp_plan();
+    p->dtype = dtype;
+    p->esz = dtype == QCP_F64 ? 8 : 4;
+    p->nprob = np;
+    p->max_rhs = max_rhs;
+    p->batched = batched;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    if (user == nullptr) {
+        // stream capture needs a stream other than the legacy default one;
+        // a blocking stream keeps ordering with work on the default stream
+        if (cudaStreamCreate(&p->stream) != cudaSuccess) {
+            set_error("cudaStreamCreate failed");
+            delete p;
+            return QCP_ERR_CUDA;
+        }
+        p->owns_stream = true;
+    } else {
+        p->stream = user;
+    }
+    if (cudaMallocHost(&p->h_active, sizeof(int)) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        qcp_plan_destroy(p);
+        return QCP_ERR_ALLOC;
+    }
+    const int rc = create_plan(p, probs, sols);
+    if (rc != QCP_OK) {
+        qcp_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return QCP_OK;
+}
+
+}  // namespace qcpd
+
+using namespace qcpd;
+
+extern "C" {
+
+const char* qcp_last_error(void) { return qcpd::last_error(); }
+
+void qcp_default_options(qcp_options* o) {
+    if (!o) return;
+    o->solver = 0;
+    o->rtol = 1e-10;
+    o->maxiter = 100000;
+    o->check_every = 32;
+    o->use_graph = 1;
+    o->compute_residual = 1;
+    o->precond = QCP_PRECOND_NONE;
+    o->kink_tol = 0.0;
+}
+
+int32_t qcp_version(void) { return 100; }
+
+int qcp_plan_create(const qcp_problem* prob, const qcp_solution* sol, qcp_dtype dtype, int32_t max_rhs,
+                    void* stream, qcp_plan** out) {
+    return make_plan(1, prob, sol, dtype, max_rhs, false, stream, out);
+}
+
+int qcp_batch_plan_create(int32_t nprob, const qcp_problem* probs, const qcp_solution* sols, qcp_dtype dtype,
+                          void* stream, qcp_plan** out) {
+    return make_plan(nprob, probs, sols, dtype, 1, true, stream, out);
+}
+
+int qcp_plan_destroy(qcp_plan* plan) {
+    if (!plan) return QCP_OK;
+    if (plan->stream) cudaStreamSynchronize(plan->stream);
+    const bool own = plan->owns_stream;
+    cudaStream_t s = plan->stream;
+    delete plan;
+    if (own && s) cudaStreamDestroy(s);
+    return QCP_OK;
+}
+
+int qcp_plan_sizes(const qcp_plan* p, int64_t* nprob, int64_t* n_total, int64_t* m_total, int64_t* nnzP_total,
+                   int64_t* nnzA_total) {
+    if (!p) {
+        set_error("null plan");
+        return QCP_ERR_ARG;
+    }
+    if (nprob) *nprob = p->nprob;
+    if (n_total) *n_total = p->n_tot;
+    if (m_total) *m_total = p->m_tot;
+    if (nnzP_total) *nnzP_total = p->pnz_tot;
+    if (nnzA_total) *nnzA_total = p->anz_tot;
+    return QCP_OK;
+}
+
+int qcp_derivative_jvp(qcp_plan* plan, const qcp_options* opts, const void* dP, const void* dA, const void* dq,
+                       const void* db, void* dx, void* dy, void* ds, qcp_info* info) {
+    return jvp_entry(plan, opts, 1, dP, dA, dq, db, dx, dy, ds, info);
+}
+
+int qcp_derivative_vjp(qcp_plan* plan, const qcp_options* opts, const void* wx, const void* wy, const void* ws,
+                       void* dP, void* dA, void* dq, void* db, qcp_info* info) {
+    return vjp_entry(plan, opts, 1, wx, wy, ws, dP, dA, dq, db, info);
+}
+
+int qcp_derivative_jvp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k, const void* dP, const void* dA,
+                             const void* dq, const void* db, void* dx, void* dy, void* ds, qcp_info* info) {
+    if (plan && plan->batched) {
+        set_error("the _multi entry points take single-problem plans");
+        return QCP_ERR_ARG;
+    }
+    return jvp_entry(plan, opts, k, dP, dA, dq, db, dx, dy, ds, info);
+}
+
+int qcp_derivative_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k, const void* wx, const void* wy,
+                             const void* ws, void* dP, void* dA, void* dq, void* db, qcp_info* info) {
+    if (plan && plan->batched) {
+        set_error("the _multi entry points take single-problem plans");
+        return QCP_ERR_ARG;
+    }
+    return vjp_entry(plan, opts, k, wx, wy, ws, dP, dA, dq, db, info);
+}
+
+int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, int32_t long_chunk) {
+    if (!plan || tile_nnz < 64 || long_row < 1 || long_chunk < 32) {
+        set_error("bad schedule: tile_nnz >= 64, long_row >= 1 and long_chunk >= 32 required");
+        return QCP_ERR_ARG;
+    }
+    plan->tile_nnz = tile_nnz;
+    plan->long_row = long_row;
+    plan->long_chunk = long_chunk;
+    return build_schedule(plan);
+}
+
+int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }
+
+}  // extern "C"

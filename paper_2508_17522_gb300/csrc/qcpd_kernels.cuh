@@ -1,0 +1,817 @@
+// Tile kernels of the Krylov hot loop and of the JVP/VJP right-hand sides
+// and outputs (arXiv 2508.17522, Sec. 3.1-3.2).  See qcpd_common.cuh for the
+// G = S F formulation that every kernel here follows.
+//
+// Diagonal scaling.  LSQR runs on Op = W G C, W = diag(w) (rows), C = diag(c)
+// (columns, constant on each second-order-cone block so that C commutes with
+// D Pi).  W = C = I is the plain method.  Because both linear systems are
+// consistent, row scaling does not change their solutions; column scaling is
+// undone on output (dz = C x, r' = W x).  The column scalings are folded into
+// two copies of M's values, MG = M diag(c) for G-passes and MT = M diag(w)
+// for G^T-passes, so a scaled pass moves the same bytes as a plain one.
+//
+// Precision.  M's values and the caller's arrays are T (float64 or float32);
+// the per-row data derived at plan time (q, b, g, x, y, y - s), the Krylov
+// vectors and every sum are float64, so FP32 storage only rounds the inputs.
+#pragma once
+
+#include "qcpd_common.cuh"
+
+namespace qcpd {
+
+enum PassKind { PASS_G = 0, PASS_GT = 1 };
+enum RoleKind { ROLE_U = 0, ROLE_V = 1, ROLE_RES = 2 };
+
+template <typename T>
+struct PlanView {
+    const Tile* tiles;
+    const Sys* sys;
+    const Prob* probs;
+    LsqrState* state;
+    Reduce R;
+    int* active;             // number of systems still iterating
+    int32_t* split_cnt;      // per split row: chunks finished in this launch
+    double* row_part;        // per LONG tile: its chunk's partial row sum
+    const int64_t* mrowptr;  // global row pointers of M
+    const int32_t* mcol;     // local column indices of M
+    const T* mval;           // values of M
+    const T* mvalG;          // M diag(c)   (== mval when unscaled)
+    const T* mvalT;          // M diag(w)   (== mval when unscaled)
+    const int32_t* mvmap;    // position of each M value in the problem's [P values; A values]
+    const double* coefA;     // N-indexed: q (x-rows), b (y-rows)
+    const double* coefB;     // N-indexed: g = 2 P x + q (x-rows), b (y-rows)
+    const double* pz;        // N-indexed: x (x-rows), y (y-rows)  -- Pi z without tau
+    const double* zy;        // N-indexed: y - s on y-rows
+    const int8_t* flag;      // N-indexed RowFlag on y-rows
+    const SocBlock* blocks;
+    const double* rw;        // N-indexed row scaling w
+    const double* cd;        // N-indexed column scaling c
+    int scaled;              // 0: plain method (w = c = 1)
+    double* U;               // Krylov u (unnormalised: u * beta)
+    double* V;               // Krylov v (unnormalised: v * alpha)
+    double* W;               // LSQR direction w
+    double* X;               // LSQR iterate
+    double* XI;              // D Pi applied to the vector the G-pass gathers
+    double* RHS;             // right-hand side b of min ||Op x - b||
+    int rmax;                // most rows in any tile (shared-memory sizing)
+    int long_chunk;          // nonzeros per LONG tile
+};
+
+// Dynamic shared memory of the tile kernels:
+//   cA, cB     kThreads doubles each: boundary partial sums per thread
+//   s0, s1, s2 rmax doubles each: per-row buffers of the epilogue
+//   srp        rmax + 1 int64: the tile's row pointers
+//   ra, rb     kThreads int32 each: rows of the boundary partials
+struct TileSmem {
+    double *cA, *cB, *s0, *s1, *s2;
+    int64_t* srp;
+    int32_t *ra, *rb;
+};
+
+__host__ __device__ inline size_t tile_smem_bytes(int rmax) {
+    return sizeof(double) * (size_t)(2 * kThreads + 3 * rmax) + sizeof(int64_t) * (size_t)(rmax + 1) +
+           sizeof(int32_t) * 2 * kThreads;
+}
+
+__device__ __forceinline__ TileSmem tile_smem(double* base, int rmax) {
+    TileSmem t;
+    t.cA = base;
+    t.cB = t.cA + kThreads;
+    t.s0 = t.cB + kThreads;
+    t.s1 = t.s0 + rmax;
+    t.s2 = t.s1 + rmax;
+    t.srp = reinterpret_cast<int64_t*>(t.s2 + rmax);
+    t.ra = reinterpret_cast<int32_t*>(t.srp + rmax + 1);
+    t.rb = t.ra + kThreads;
+    return t;
+}
+
+// Eight consecutive stored entries starting at an index that is a multiple
+// of 8 (the arrays are padded to a multiple of 8 entries): two 16-byte loads
+// of column indices and 16-byte loads of values.
+__device__ __forceinline__ void load8(const int32_t* col, const double* val, int64_t e, int32_t (&c)[kE],
+                                      double (&v)[kE]) {
+    const int4 c0 = __ldg(reinterpret_cast<const int4*>(col + e));
+    const int4 c1 = __ldg(reinterpret_cast<const int4*>(col + e) + 1);
+    c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
+    c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
+    const double2* vp = reinterpret_cast<const double2*>(val + e);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const double2 t = __ldg(vp + j);
+        v[2 * j] = t.x;
+        v[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ void load8(const int32_t* col, const float* val, int64_t e, int32_t (&c)[kE],
+                                      double (&v)[kE]) {
+    const int4 c0 = __ldg(reinterpret_cast<const int4*>(col + e));
+    const int4 c1 = __ldg(reinterpret_cast<const int4*>(col + e) + 1);
+    c[0] = c0.x; c[1] = c0.y; c[2] = c0.z; c[3] = c0.w;
+    c[4] = c1.x; c[5] = c1.y; c[6] = c1.z; c[7] = c1.w;
+    const float4* vp = reinterpret_cast<const float4*>(val + e);
+    const float4 t0 = __ldg(vp), t1 = __ldg(vp + 1);
+    v[0] = t0.x; v[1] = t0.y; v[2] = t0.z; v[3] = t0.w;
+    v[4] = t1.x; v[5] = t1.y; v[6] = t1.z; v[7] = t1.w;
+}
+
+// Row sums h_i = sum_k val_k * gv[col_k] of the tile's rows into sm.s0[].
+//
+// STREAM tiles (merge-style segmented SpMV): the tile's nonzeros are walked
+// in aligned groups of kE = 8; thread t takes one group per sweep, loads its
+// eight column indices and values with vector loads and issues the eight
+// gathers at once (about 24 loads in flight per thread), then multiplies the
+// eight entries in one FMA chain, cutting it at row ends.  Rows that start
+// and end inside a thread's group are written directly; the first and last
+// segment of each group go to boundary slots that one thread per row adds
+// up in thread order.  Exactly one FP64 FMA per nonzero, and the result does
+// not depend on scheduling.
+//
+// LONG tiles sum one chunk of one long row over the whole CTA (same aligned
+// loads); the last chunk of the row to finish adds the chunk sums in order.
+//
+// Returns the number of rows whose sums are complete (0 for a LONG tile
+// that is not the row's last chunk).
+template <typename VT, typename GT>
+__device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_t* rp, const int32_t* mcol,
+                                            const VT* vals, const GT* gv, const TileSmem& sm, Scratch* scratch,
+                                            int32_t* split_cnt, double* row_part, int long_chunk) {
+    const int tid = threadIdx.x;
+    const int rows = tl.r1 - tl.r0;
+    if (tl.kind == TILE_LONG) {
+        const int64_t rs = rp[tl.r0], re = rp[tl.r0 + 1];
+        const int64_t k0 = rs + (int64_t)tl.cb0 * long_chunk;
+        const int64_t k1 = (k0 + long_chunk < re) ? k0 + long_chunk : re;
+        double acc = 0.0;
+        for (int64_t e = (k0 & ~(int64_t)(kE - 1)) + (int64_t)tid * kE; e < k1; e += (int64_t)kChunk) {
+            int32_t c[kE];
+            double v[kE];
+            load8(mcol, vals, e, c, v);
+            double x[kE];
+#pragma unroll
+            for (int j = 0; j < kE; ++j) {
+                const bool ok = (e + j >= k0) && (e + j < k1);
+                x[j] = ok ? ld(gv + c[j]) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < kE; ++j) acc = fma(v[j], x[j], acc);
+        }
+        const double s = block_sum(acc, scratch);
+        __shared__ int s_last;
+        if (tid == 0) {
+            if (tl.cb1 == 1) {
+                sm.s0[0] = s;
+                s_last = 1;
+            } else {
+                row_part[ti] = s;
+                __threadfence();
+                const int prev = atomicAdd(split_cnt + tl.split, 1);
+                s_last = (prev == tl.cb1 - 1);
+                if (s_last) {
+                    __threadfence();
+                    double t = 0.0;
+                    const int first = ti - tl.cb0;
+                    for (int c = 0; c < tl.cb1; ++c) t += __ldcg(row_part + first + c);
+                    sm.s0[0] = t;
+                    split_cnt[tl.split] = 0;
+                }
+            }
+        }
+        __syncthreads();
+        return s_last ? 1 : 0;
+    }
+    for (int i = tid; i < rows; i += kThreads) sm.s0[i] = 0.0;
+    for (int i = tid; i <= rows; i += kThreads) sm.srp[i] = rp[tl.r0 + i];
+    const int64_t K0 = rp[tl.r0], K1 = rp[tl.r1];
+    __syncthreads();
+    for (int64_t c0 = K0 & ~(int64_t)(kE - 1); c0 < K1; c0 += kChunk) {
+        const int64_t e0 = c0 + (int64_t)tid * kE;
+        int ra = -1, rb = -1;
+        double pa = 0.0, pb = 0.0;
+        if (e0 < K1 && e0 + kE > K0) {
+            int32_t c[kE];
+            double v[kE], x[kE];
+            load8(mcol, vals, e0, c, v);
+#pragma unroll
+            for (int j = 0; j < kE; ++j) {
+                const bool ok = (e0 + j >= K0) && (e0 + j < K1);
+                x[j] = ok ? ld(gv + c[j]) : 0.0;
+            }
+            const int64_t kfirst = e0 > K0 ? e0 : K0;
+            int lo = 0, hi = rows;  // last row whose start is <= kfirst
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sm.srp[mid] <= kfirst) lo = mid;
+                else hi = mid;
+            }
+            // row of each of the eight entries (-1: outside the tile)
+            int rr[kE];
+            int i = lo;
+            int64_t rend = sm.srp[i + 1];
+#pragma unroll
+            for (int j = 0; j < kE; ++j) {
+                const int64_t k = e0 + j;
+                if (k < kfirst || k >= K1) {
+                    rr[j] = -1;
+                } else {
+                    while (k >= rend) {
+                        ++i;
+                        rend = sm.srp[i + 1];
+                    }
+                    rr[j] = i;
+                }
+            }
+            // branch-free FMA chain: restart at every row change
+            double acc = 0.0, part[kE];
+#pragma unroll
+            for (int j = 0; j < kE; ++j) {
+                const bool cont = (j > 0) && (rr[j] == rr[j - 1]);
+                acc = fma(v[j], x[j], cont ? acc : 0.0);
+                part[j] = acc;
+            }
+            int firstrow = -1, lastrow = -1;
+#pragma unroll
+            for (int j = 0; j < kE; ++j) {
+                if (rr[j] >= 0) {
+                    if (firstrow < 0) firstrow = rr[j];
+                    lastrow = rr[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kE; ++j) {
+                const bool end = rr[j] >= 0 && (j == kE - 1 || rr[j + 1] != rr[j]);
+                if (end) {
+                    if (rr[j] == firstrow) {
+                        ra = rr[j];
+                        pa = part[j];
+                    } else if (rr[j] == lastrow) {
+                        rb = rr[j];
+                        pb = part[j];
+                    } else {
+                        sm.s0[rr[j]] += part[j];  // a row inside this thread's group: no other writer
+                    }
+                }
+            }
+        }
+        sm.ra[tid] = ra;
+        sm.rb[tid] = rb;
+        sm.cA[tid] = pa;
+        sm.cB[tid] = pb;
+        __syncthreads();
+        // boundary partials, one thread per row, in thread order
+        const int64_t cend = c0 + kChunk;
+        for (int i = tid; i < rows; i += kThreads) {
+            int64_t a0 = sm.srp[i], a1 = sm.srp[i + 1];
+            a0 = a0 > c0 ? a0 : c0;
+            a1 = a1 < cend ? a1 : cend;
+            if (a1 <= a0) continue;
+            const int ta = (int)((a0 - c0) / kE), tb = (int)((a1 - 1 - c0) / kE);
+            double add = 0.0;
+            for (int t = ta; t <= tb; ++t) {
+                if (sm.ra[t] == i) add += sm.cA[t];
+                else if (sm.rb[t] == i) add += sm.cB[t];
+            }
+            sm.s0[i] += add;
+        }
+        __syncthreads();
+    }
+    return rows;
+}
+
+// One half-iteration of LSQR over all tiles of all systems.
+//   PASS_G : out = W G C in     (gathers XI = D Pi in, values M diag(c))
+//   PASS_GT: out = C G^T W in   (gathers in, values M diag(w); D Pi on the output side)
+//   ROLE_U : u <- (Op v)/alpha - (alpha/beta) u,  w <- v/alpha - wcoef w   (in = V, out = U)
+//   ROLE_V : v <- (Op^T u)/beta - (beta/alpha) v, x <- x + xcoef w         (in = U, out = V)
+//   ROLE_RES: unscaled residual of the current iterate                    (in = X)
+//   SC     : diagonal scaling on (compile-time, so the plain method pays no
+//            multiplications by 1 on the scarce FP64 pipe)
+// The CTA that completes a system also updates its tau entry and the LSQR
+// scalars (Paige & Saunders 1982, algorithm LSQR).
+template <int PASS, int ROLE, bool SC, typename T>
+__global__ void __launch_bounds__(kThreads, 4) k_pass(PlanView<T> a) {
+    extern __shared__ double smem[];
+    __shared__ Scratch scratch;
+    const int ti = blockIdx.x;
+    const Tile tl = a.tiles[ti];
+    const Sys sy = a.sys[tl.sys];
+    LsqrState* st = a.state + tl.sys;
+    const int status = st->status;
+    if (ROLE != ROLE_RES && status == S_DONE) return;
+    const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
+    const Prob pr = a.probs[sy.prob];
+    const int n = pr.n;
+    const int N = pr.n + pr.m + 1;
+    const TileSmem sm = tile_smem(smem, a.rmax);
+    double* s0 = sm.s0;
+    double* s1 = sm.s1;
+    double* s2 = sm.s2;
+
+    const double* in = (ROLE == ROLE_U) ? a.V + sy.voff : (ROLE == ROLE_V ? a.U + sy.voff : a.X + sy.voff);
+    double* outv = (ROLE == ROLE_U) ? a.U + sy.voff : (ROLE == ROLE_V ? a.V + sy.voff : nullptr);
+    const double* cA = a.coefA + pr.doff;
+    const double* cB = a.coefB + pr.doff;
+    const double* rw = a.rw + pr.doff;
+    const double* cd = a.cd + pr.doff;
+    double* W = a.W + sy.voff;
+    double* X = a.X + sy.voff;
+    double* XI = a.XI + sy.voff;
+    const double alpha = st->alpha, beta = st->beta;
+    double c1, c2;
+    if (ROLE == ROLE_U) {
+        c1 = 1.0 / alpha;
+        c2 = alpha / beta;
+    } else if (ROLE == ROLE_V) {
+        c1 = beta > 0.0 ? 1.0 / beta : 0.0;
+        c2 = st->first ? 0.0 : beta / alpha;
+    } else {
+        c1 = 1.0;
+        c2 = 0.0;
+    }
+    const double wcoef = st->wcoef, xcoef = st->xcoef;
+    const double tin = in[N - 1];  // tau entry of the input vector
+    // the t-column term: (scaled) tau entry of the input
+    const double tt = SC ? (PASS == PASS_G ? cd[N - 1] : rw[N - 1]) * tin : tin;
+
+    Part part = pzero();
+    int rows = tl.r1 - tl.r0;
+    if (only_x) {
+        if (tl.kind == TILE_LONG && tl.cb0 != 0) rows = 0;  // one chunk updates the row
+        for (int i = threadIdx.x; i < rows; i += kThreads) {
+            const int r = tl.r0 + i;
+            X[r] = fma(xcoef, W[r], X[r]);
+        }
+    } else {
+        const int64_t* rp = a.mrowptr + pr.mrow;
+        if (PASS == PASS_G)
+            rows = tile_rowsums(tl, ti, rp, a.mcol, a.mvalG, XI, sm, &scratch, a.split_cnt, a.row_part,
+                                a.long_chunk);
+        else
+            rows = tile_rowsums(tl, ti, rp, a.mcol, a.mvalT, in, sm, &scratch, a.split_cnt, a.row_part,
+                                a.long_chunk);
+        double ss = 0.0, dtop = 0.0, dbot = 0.0;
+        if (PASS == PASS_G) {
+            for (int i = threadIdx.x; i < rows; i += kThreads) {
+                const int r = tl.r0 + i;
+                const double iv = in[r];
+                double o;
+                if (r < n) {
+                    o = fma(ld(cA + r), tt, s0[i]);
+                    dtop = fma(ld(cB + r), SC ? cd[r] * iv : iv, dtop);
+                } else {
+                    const double xi = XI[r];
+                    const double dxi = SC ? cd[r] * (xi - iv) : xi - iv;
+                    o = fma(-ld(cA + r), tt, s0[i]) + dxi;
+                    dbot = fma(ld(cB + r), SC ? cd[r] * xi : xi, dbot);
+                }
+                if (SC) o *= rw[r];
+                if (ROLE == ROLE_RES) {
+                    double e = o - a.RHS[sy.voff + r];
+                    if (SC) e /= rw[r];
+                    ss = fma(e, e, ss);
+                } else {
+                    const double nv = fma(c1, o, -c2 * outv[r]);
+                    outv[r] = nv;
+                    ss = fma(nv, nv, ss);
+                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * W[r]);
+                    else X[r] = fma(xcoef, W[r], X[r]);
+                }
+            }
+        } else {
+            // G^T: top rows M rho - g r3; bottom rows D(M rho - b r3 + r2) - r2 (rho = W in)
+            for (int i = threadIdx.x; i < rows; i += kThreads) {
+                const int r = tl.r0 + i;
+                const double iv = SC ? rw[r] * in[r] : in[r];
+                const double h = fma(-ld(cB + r), tt, s0[i]);
+                if (r < n) {
+                    s1[i] = h;
+                    dtop = fma(ld(cA + r), iv, dtop);
+                } else {
+                    s1[i] = h + iv;
+                    dbot = fma(ld(cA + r), iv, dbot);
+                }
+            }
+            __syncthreads();
+            const int cb0 = tl.kind == TILE_STREAM ? tl.cb0 : 0, cb1 = tl.kind == TILE_STREAM ? tl.cb1 : 0;
+            apply_D_tile<double>(s1, s2, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1,
+                            a.zy + pr.doff);
+            __syncthreads();
+            for (int i = threadIdx.x; i < rows; i += kThreads) {
+                const int r = tl.r0 + i;
+                const double iv = in[r];
+                double o = (r < n) ? s2[i] : s2[i] - (SC ? rw[r] * iv : iv);
+                if (SC) o *= cd[r];
+                if (ROLE == ROLE_RES) {
+                    double e = o - a.RHS[sy.voff + r];
+                    if (SC) e /= cd[r];
+                    ss = fma(e, e, ss);
+                } else {
+                    const double nv = fma(c1, o, -c2 * outv[r]);
+                    outv[r] = nv;
+                    s1[i] = nv;
+                    ss = fma(nv, nv, ss);
+                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * W[r]);
+                    else X[r] = fma(xcoef, W[r], X[r]);
+                }
+            }
+            if (ROLE != ROLE_RES) {
+                __syncthreads();
+                apply_D_tile<double>(s1, s2, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1,
+                                a.zy + pr.doff);
+                __syncthreads();
+                for (int i = threadIdx.x; i < rows; i += kThreads) XI[tl.r0 + i] = s2[i];
+            }
+        }
+        part = block_sum3(ss, dtop, dbot, &scratch);
+    }
+
+    Part tot;
+    if (!finish_tile(a.R, tl, sy.g0, sy.g1, ti, part, &tot, &scratch)) return;
+    if (threadIdx.x != 0) return;
+
+    // ---- the system's finisher: tau entry and LSQR scalars ----
+    const int rN = N - 1;
+    if (only_x) {
+        X[rN] = fma(xcoef, W[rN], X[rN]);
+        st->status = S_DONE;
+        atomicSub(a.active, 1);
+        return;
+    }
+    const double kappa = pr.kappa;
+    double oN;
+    if (PASS == PASS_G) {
+        oN = -tot.b - tot.c + kappa * tt;
+        if (SC) oN *= rw[rN];
+    } else {
+        oN = tot.b - tot.c + kappa * tt;
+        if (SC) oN *= cd[rN];
+    }
+    if (ROLE == ROLE_RES) {
+        double e = oN - a.RHS[sy.voff + rN];
+        if (SC) e /= (PASS == PASS_G ? rw[rN] : cd[rN]);
+        const double ss = tot.a + e * e;
+        st->resid_true = st->bnorm_true > 0.0 ? sqrt(ss) / st->bnorm_true : 0.0;
+        return;
+    }
+    const double nvN = c1 * oN - c2 * outv[rN];
+    outv[rN] = nvN;
+    if (PASS == PASS_GT) XI[rN] = nvN;
+    const double nrm = sqrt(tot.a + nvN * nvN);
+    if (ROLE == ROLE_U) {
+        W[rN] = tin * c1 - wcoef * W[rN];
+        // rotation eliminating beta_{k+1}
+        const double rhobar = st->rhobar;
+        const double rho = hypot(rhobar, nrm);
+        const double c = rhobar / rho, s = nrm / rho;
+        const double phi = c * st->phibar;
+        st->phibar = s * st->phibar;
+        st->rho = rho;
+        st->c = c;
+        st->s = s;
+        st->xcoef = phi / rho;
+        st->beta = nrm;
+        st->iters += 1;
+        if (!isfinite(rho) || !isfinite(phi) || rho == 0.0) {
+            st->outcome = O_BREAKDOWN;
+            st->xcoef = 0.0;
+            st->status = S_FINAL;
+        } else if (st->phibar <= st->rtol * st->bnorm || nrm == 0.0) {
+            st->outcome = O_CONVERGED;
+            st->status = S_FINAL;
+        } else if (st->iters >= st->maxiter) {
+            st->outcome = O_MAXITER;
+            st->status = S_FINAL;
+        }
+    } else {
+        X[rN] = fma(xcoef, W[rN], X[rN]);
+        if (st->first) {
+            st->rhobar = nrm;
+            st->phibar = st->beta;
+            st->wcoef = 0.0;
+            st->first = 0;
+        } else {
+            st->rhobar = -st->c * nrm;
+            st->wcoef = (st->s * nrm) / st->rho;
+        }
+        st->alpha = nrm;
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+            // A^T r = 0: the current x solves the least-squares problem
+            if (!isfinite(nrm)) st->outcome = O_BREAKDOWN;
+            else st->outcome = O_CONVERGED;
+            st->status = S_DONE;
+            atomicSub(a.active, 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RhsArgs {
+    const T* dP;
+    const T* dA;
+    const T* dq;
+    const T* db;
+    const T* wx;
+    const T* wy;
+    const T* ws;
+    double rtol;
+    int64_t maxiter;
+};
+
+__device__ __forceinline__ void init_state(LsqrState* st, int* active, double bn, double bn_true, double rtol,
+                                           int64_t maxiter) {
+    LsqrState q{};
+    q.beta = bn;
+    q.bnorm = bn;
+    q.bnorm_true = bn_true;
+    q.rtol = rtol;
+    q.maxiter = maxiter;
+    q.first = 1;
+    q.resid_true = -1.0;
+    if (bn > 0.0 && isfinite(bn)) {
+        q.status = S_ACTIVE;
+        q.outcome = O_RUNNING;
+        atomicAdd(active, 1);
+    } else {
+        q.status = S_DONE;
+        q.outcome = isfinite(bn) ? O_CONVERGED : O_BREAKDOWN;
+        q.resid_true = 0.0;
+    }
+    *st = q;
+}
+
+// JVP right-hand side (Sec. 3.1): dN = D_theta N(z)[d theta]
+//   = (dP x + dA^T y + dq, -dA x + db, -x^T dP x - dq^T x - db^T y).
+// LSQR solves min ||W G C x - b|| with b = -W S dN:
+//   S dN negated = (-(dP x + dA^T y + dq), -dA x + db, x^T dP x + dq^T x + db^T y).
+// The perturbation values are read through the M -> [P; A] value map, so
+// the same pass yields dP x (both triangles) and dA^T y.  One warp per row.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_jvp_rhs(PlanView<T> a, RhsArgs<T> in) {
+    __shared__ Scratch scratch;
+    const int ti = blockIdx.x;
+    const Tile tl = a.tiles[ti];
+    const Sys sy = a.sys[tl.sys];
+    const Prob pr = a.probs[sy.prob];
+    const int n = pr.n;
+    const int N = pr.n + pr.m + 1;
+    const int64_t* rp = a.mrowptr + pr.mrow;
+    const double* pz = a.pz + pr.doff;
+    const T* dP = in.dP + sy.po;
+    const T* dA = in.dA + sy.ao;
+    const double* rw = a.rw + pr.doff;
+    const bool sc = a.scaled != 0;
+    const int64_t pnz = pr.pnz;
+    double* U = a.U + sy.voff;
+    double* RHS = a.RHS + sy.voff;
+    double* X = a.X + sy.voff;
+    double* W = a.W + sy.voff;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // A LONG tile's chunks all cover the same row: chunk 0 does the whole row
+    // with the CTA, the other chunks only join the reduction.
+    const bool is_long = tl.kind == TILE_LONG;
+    const bool skip = is_long && tl.cb0 != 0;
+    double ss = 0.0, sst = 0.0, dtop = 0.0, dbot = 0.0;
+    const int rstep = is_long ? 1 : kWarps;
+    for (int r = tl.r0 + (is_long ? 0 : warp); r < tl.r1 && !skip; r += rstep) {
+        double hp = 0.0, ha = 0.0;
+        const int64_t kb = rp[r] + (is_long ? threadIdx.x : lane);
+        const int stride = is_long ? kThreads : 32;
+        for (int64_t k = kb; k < rp[r + 1]; k += stride) {
+            const int32_t vm = a.mvmap[k];
+            const double gx = ld(pz + a.mcol[k]);
+            if (vm < pnz) hp += ld(dP + vm) * gx;
+            else ha += ld(dA + (vm - pnz)) * gx;
+        }
+        if (is_long) {
+            const Part h2 = block_sum_part(Part{hp, ha, 0.0, 0.0}, &scratch);
+            hp = h2.a;
+            ha = h2.b;
+        } else {
+            hp = warp_sum(hp);
+            ha = warp_sum(ha);
+        }
+        if ((is_long ? threadIdx.x : lane) == 0) {
+            double bval;
+            if (r < n) {
+                const double dq = ld(in.dq + sy.xo + r), x = ld(pz + r);
+                bval = -(hp + ha + dq);
+                dtop += x * hp + dq * x;
+            } else {
+                const int j = r - n;
+                const double db = ld(in.db + sy.yo + j);
+                bval = -ha + db;
+                dbot += db * ld(pz + r);
+            }
+            sst += bval * bval;
+            if (sc) bval *= rw[r];
+            U[r] = bval;
+            RHS[r] = bval;
+            X[r] = 0.0;
+            W[r] = 0.0;
+            ss += bval * bval;
+        }
+    }
+    const Part part = block_sum_part(Part{ss, dtop, dbot, sst}, &scratch);
+    Part tot;
+    if (!finish_tile(a.R, tl, sy.g0, sy.g1, ti, part, &tot, &scratch)) return;
+    if (threadIdx.x != 0) return;
+    const double bNt = tot.b + tot.c;
+    const double bN = sc ? rw[N - 1] * bNt : bNt;
+    U[N - 1] = bN;
+    RHS[N - 1] = bN;
+    X[N - 1] = 0.0;
+    W[N - 1] = 0.0;
+    init_state(a.state + tl.sys, a.active, sqrt(tot.a + bN * bN), sqrt(tot.d + bNt * bNt), in.rtol, in.maxiter);
+}
+
+// VJP right-hand side (Sec. 3.2): g = D phi(z)^T (wx, wy, ws)
+//   = (wx, D (wy + ws) - ws, -x^T wx - y^T wy - s^T ws);
+// LSQR solves min ||C G^T W r~ - b|| with b = -C g, and the G-pass of its
+// first half-iteration gathers D Pi b, written here to XI.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> in) {
+    extern __shared__ double smem[];
+    __shared__ Scratch scratch;
+    const int ti = blockIdx.x;
+    const Tile tl = a.tiles[ti];
+    const Sys sy = a.sys[tl.sys];
+    const Prob pr = a.probs[sy.prob];
+    const int n = pr.n;
+    const int N = pr.n + pr.m + 1;
+    const bool skip = (tl.kind == TILE_LONG && tl.cb0 != 0);
+    const int rows = skip ? 0 : tl.r1 - tl.r0;
+    const int cb0 = tl.kind == TILE_STREAM ? tl.cb0 : 0, cb1 = tl.kind == TILE_STREAM ? tl.cb1 : 0;
+    const double* pz = a.pz + pr.doff;
+    const double* zy = a.zy + pr.doff;
+    const double* cd = a.cd + pr.doff;
+    const bool sc = a.scaled != 0;
+    double* U = a.U + sy.voff;
+    double* RHS = a.RHS + sy.voff;
+    double* X = a.X + sy.voff;
+    double* W = a.W + sy.voff;
+    double* XI = a.XI + sy.voff;
+    const TileSmem sm = tile_smem(smem, a.rmax);
+    double* s0 = sm.s0;
+    double* s1 = sm.s1;
+    double* s2 = sm.s2;
+    double dtop = 0.0, dbot = 0.0;
+    for (int i = threadIdx.x; i < rows; i += kThreads) {
+        const int r = tl.r0 + i;
+        if (r < n) {
+            const double w = ld(in.wx + sy.xo + r);
+            s0[i] = w;
+            dtop += ld(pz + r) * w;
+        } else {
+            const int j = r - n;
+            const double wy = ld(in.wy + sy.yo + j), ws = ld(in.ws + sy.yo + j);
+            s0[i] = wy + ws;
+            const double y = ld(pz + r);
+            dbot += y * wy + (y - ld(zy + r)) * ws;
+        }
+    }
+    __syncthreads();
+    apply_D_tile<double>(s0, s1, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy);
+    __syncthreads();
+    double ss = 0.0, sst = 0.0;
+    for (int i = threadIdx.x; i < rows; i += kThreads) {
+        const int r = tl.r0 + i;
+        double g = s1[i];
+        if (r >= n) g -= ld(in.ws + sy.yo + (r - n));
+        double bval = -g;
+        sst += bval * bval;
+        if (sc) bval *= cd[r];
+        U[r] = bval;
+        RHS[r] = bval;
+        X[r] = 0.0;
+        W[r] = 0.0;
+        s0[i] = bval;
+        ss += bval * bval;
+    }
+    __syncthreads();
+    apply_D_tile<double>(s0, s2, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += kThreads) XI[tl.r0 + i] = s2[i];
+    const Part part = block_sum_part(Part{ss, dtop, dbot, sst}, &scratch);
+    Part tot;
+    if (!finish_tile(a.R, tl, sy.g0, sy.g1, ti, part, &tot, &scratch)) return;
+    if (threadIdx.x != 0) return;
+    const double bNt = tot.b + tot.c;
+    const double bN = sc ? cd[N - 1] * bNt : bNt;
+    U[N - 1] = bN;
+    RHS[N - 1] = bN;
+    XI[N - 1] = bN;
+    X[N - 1] = 0.0;
+    W[N - 1] = 0.0;
+    init_state(a.state + tl.sys, a.active, sqrt(tot.a + bN * bN), sqrt(tot.d + bNt * bNt), in.rtol, in.maxiter);
+}
+
+// JVP output (Sec. 3.1): dz = C x, then (dx, dy, ds) = (dz_x - dz_N x,
+// D dz_y - dz_N y, D dz_y - dz_y - dz_N s), s = y - z_y.  Also writes
+// XI = D Pi x for the optional residual pass.
+template <typename T>
+struct OutArgs {
+    T* o1;  // dx  | dP
+    T* o2;  // dy  | dA
+    T* o3;  // ds  | dq
+    T* o4;  //     | db
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_jvp_out(PlanView<T> a, OutArgs<T> o) {
+    extern __shared__ double smem[];
+    const Tile tl = a.tiles[blockIdx.x];
+    const Sys sy = a.sys[tl.sys];
+    const Prob pr = a.probs[sy.prob];
+    const int n = pr.n;
+    const int N = pr.n + pr.m + 1;
+    const bool skip = (tl.kind == TILE_LONG && tl.cb0 != 0);
+    const int rows = skip ? 0 : tl.r1 - tl.r0;
+    const int cb0 = tl.kind == TILE_STREAM ? tl.cb0 : 0, cb1 = tl.kind == TILE_STREAM ? tl.cb1 : 0;
+    const double* pz = a.pz + pr.doff;
+    const double* zy = a.zy + pr.doff;
+    const double* cd = a.cd + pr.doff;
+    const bool sc = a.scaled != 0;
+    const double* X = a.X + sy.voff;
+    double* XI = a.XI + sy.voff;
+    const TileSmem sm = tile_smem(smem, a.rmax);
+    double* s0 = sm.s0;
+    double* s1 = sm.s1;
+    double* s2 = sm.s2;
+    const double dzN = X[N - 1] * (sc ? cd[N - 1] : 1.0);
+    for (int i = threadIdx.x; i < rows; i += kThreads) {
+        const int r = tl.r0 + i;
+        s0[i] = X[r];
+        s2[i] = sc ? X[r] * cd[r] : X[r];  // dz = C x
+    }
+    __syncthreads();
+    apply_D_tile<double>(s0, s1, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += kThreads) {
+        const int r = tl.r0 + i;
+        XI[r] = s1[i];
+        const double cr = sc ? cd[r] : 1.0;  // D commutes with C (C is constant on SOC blocks)
+        if (r < n) {
+            o.o1[sy.xo + r] = (T)(s2[i] - dzN * ld(pz + r));
+        } else {
+            const int j = r - n;
+            const double y = ld(pz + r);
+            const double s = y - ld(zy + r);
+            const double Ddz = cr * s1[i];
+            o.o2[sy.yo + j] = (T)(Ddz - dzN * y);
+            o.o3[sy.yo + j] = (T)(Ddz - s2[i] - dzN * s);
+        }
+    }
+}
+
+// VJP output (Sec. 3.2, computed only on the stored patterns): with
+// r = S W x = (r1, r2, r_N) = (w_x X_x, -w_y X_y, w_N X_N),
+//   dP_ij = (r1_i x_j + x_i r1_j)/2 - r_N x_i x_j   on P's upper pattern
+//   dA_ij = y_i r1_j - r2_i x_j                       on A's pattern
+//   dq = r1 - r_N x,  db = r2 - r_N y.
+// One warp per (system, row); blockIdx.y selects the system.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_vjp_out(PlanView<T> a, OutArgs<T> o, const int64_t* pip,
+                                                     const int32_t* pix, const int64_t* aip,
+                                                     const int32_t* aix) {
+    const Sys sy = a.sys[blockIdx.y];
+    const Prob pr = a.probs[sy.prob];
+    const int n = pr.n, m = pr.m;
+    const int N = n + m + 1;
+    const double* pz = a.pz + pr.doff;
+    const double* X = a.X + sy.voff;
+    const double* rw = a.rw + pr.doff;
+    const bool sc = a.scaled != 0;
+    const double rN = X[N - 1] * (sc ? rw[N - 1] : 1.0);
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * kThreads) >> 5;
+    const int64_t* pp = pip + pr.prow;
+    const int64_t* ap = aip + pr.arow;
+    const int32_t* px = pix + pr.poff;
+    const int32_t* ax = aix + pr.aoff;
+    for (int row = gw; row < n + m; row += nw) {
+        if (row < n) {
+            const int i = row;
+            const double xi = ld(pz + i), r1i = X[i] * (sc ? rw[i] : 1.0);
+            for (int64_t k = pp[i] + lane; k < pp[i + 1]; k += 32) {
+                const int j = px[k];
+                const double xj = ld(pz + j), r1j = X[j] * (sc ? rw[j] : 1.0);
+                o.o1[sy.po + k] = (T)(0.5 * (r1i * xj + xi * r1j) - rN * xi * xj);
+            }
+            if (lane == 0) o.o3[sy.xo + i] = (T)(r1i - rN * xi);
+        } else {
+            const int i = row - n;
+            const double yi = ld(pz + n + i), r2i = -X[n + i] * (sc ? rw[n + i] : 1.0);
+            for (int64_t k = ap[i] + lane; k < ap[i + 1]; k += 32) {
+                const int j = ax[k];
+                const double r1j = X[j] * (sc ? rw[j] : 1.0);
+                o.o2[sy.ao + k] = (T)(yi * r1j - r2i * ld(pz + j));
+            }
+            if (lane == 0) o.o4[sy.yo + i] = (T)(r2i - rN * yi);
+        }
+    }
+}
+
+}  // namespace qcpd

@@ -1,0 +1,130 @@
+// Host-side plan object and helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "qcpd_common.cuh"
+
+namespace qcpd {
+
+void set_error(const char* fmt, ...);
+
+#define QCP_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ::qcpd::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                              __LINE__);                                                     \
+            return e_ == cudaErrorMemoryAllocation ? QCP_ERR_ALLOC : QCP_ERR_CUDA;           \
+        }                                                                                    \
+    } while (0)
+
+#define QCP_TRY(expr)              \
+    do {                           \
+        int rc_ = (expr);          \
+        if (rc_ != QCP_OK) return rc_; \
+    } while (0)
+
+// A device allocation freed on destruction.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t nbytes) {
+        release();
+        if (nbytes == 0) nbytes = 16;
+        cudaError_t e = cudaMalloc(&p, nbytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMalloc(%zu) failed: %s", nbytes, cudaGetErrorString(e));
+            return QCP_ERR_ALLOC;
+        }
+        bytes = nbytes;
+        return QCP_OK;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct GraphKey {
+    int mode;    // 0 JVP, 1 VJP
+    int nsys;
+    int chunk;
+    int scaled;  // diagonal scaling on (different kernels)
+    bool operator<(const GraphKey& o) const {
+        if (mode != o.mode) return mode < o.mode;
+        if (nsys != o.nsys) return nsys < o.nsys;
+        if (scaled != o.scaled) return scaled < o.scaled;
+        return chunk < o.chunk;
+    }
+};
+
+}  // namespace qcpd
+
+struct qcp_plan {
+    qcp_dtype dtype = QCP_F64;
+    size_t esz = 8;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    int nprob = 0;
+    int max_rhs = 1;
+    bool batched = false;
+
+    // host copies of the per-problem layout
+    std::vector<qcpd::Prob> hprob;
+    std::vector<std::vector<int32_t>> cone_type, cone_dim;
+    std::vector<double> kink;  // per problem
+    int64_t n_tot = 0, m_tot = 0, pnz_tot = 0, anz_tot = 0, N_tot = 0, nsoc_tot = 0, mnnz = 0;
+
+    // problem data (device)
+    qcpd::DevBuf d_prob, d_mrowptr, d_mcol, d_mvmap, d_mval;
+    qcpd::DevBuf d_coefA, d_coefB, d_pz, d_zy, d_flag, d_blocks;
+    qcpd::DevBuf d_rw, d_cd, d_mvalG, d_mvalT;   // equilibration: row/column scalings, scaled values
+    qcpd::DevBuf d_pip, d_pix, d_aip, d_aix;
+
+    // schedule
+    int tile_nnz = 4096;
+    int long_row = 512;
+    int long_chunk = 4096;
+    int rmax = 1;
+    std::vector<std::vector<qcpd::Tile>> ptiles;  // per problem, sys = problem
+    std::vector<int64_t> h_mrowptr;               // host copy (schedule building)
+    qcpd::DevBuf d_ptiles, d_pgroups, d_ppart, d_pgpart, d_pgcnt, d_pscnt, d_psys;
+
+    // systems
+    int nsys_cap = 0;
+    int tiles_per_sys = 0;   // single-problem plans: tiles of one system
+    int groups_per_sys = 0;
+    std::vector<qcpd::Sys> hsys;
+    int ntiles = 0, ngroups = 0;
+    int nsplit = 0;          // rows cut into several LONG chunks (over all systems)
+    qcpd::DevBuf d_sys, d_tiles, d_groups, d_state, d_tpart, d_gpart, d_gcnt, d_scnt, d_active;
+    qcpd::DevBuf d_split_cnt, d_row_part;
+    qcpd::DevBuf d_U, d_V, d_W, d_X, d_XI, d_RHS;
+    int* h_active = nullptr;  // pinned
+
+    std::map<qcpd::GraphKey, cudaGraphExec_t> graphs;
+    int64_t last_launches = 0;
+
+    ~qcp_plan();
+};
+
+namespace qcpd {
+// Build (or rebuild) the tile schedule, systems and workspace of a plan.
+int build_schedule(qcp_plan* p);
+// Free captured graphs.
+void drop_graphs(qcp_plan* p);
+}  // namespace qcpd

@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every function that include/qcpd.h declares; the ctypes structs match the
+header's layout.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(qcp_[a-z0-9_]+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_17522_gb300.buildlib import build
+    build()
+    from paper_2508_17522_gb300 import _native
+    return _native.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 12, names
+    for n in names:
+        assert hasattr(lib, n), f"{n} missing from libqcpd.so"
+
+
+def test_options_defaults_without_gpu(lib):
+    from paper_2508_17522_gb300 import _native as N
+    o = N.qcp_options()
+    lib.qcp_default_options(ctypes.byref(o))
+    assert o.solver == 0 and o.rtol == 1e-10 and o.maxiter == 100000 and o.check_every == 32
+    assert lib.qcp_version() >= 100
+    assert lib.qcp_plan_destroy(None) == 0
+
+
+def test_struct_layout():
+    from paper_2508_17522_gb300 import _native as N
+    assert ctypes.sizeof(N.qcp_csr) == 48
+    assert ctypes.sizeof(N.qcp_cone) == 24
+    assert ctypes.sizeof(N.qcp_problem) == 16 + 3 * 48 + 24 + 24
+    assert ctypes.sizeof(N.qcp_options) == 48  # precond fills the padding after compute_residual
+    assert ctypes.sizeof(N.qcp_info) == 40
+
+
+def test_built_for_sm103a_only():
+    from paper_2508_17522_gb300 import buildlib
+    assert buildlib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

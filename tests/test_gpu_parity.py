@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances: FP64 storage, relative error <= 1e-6 over the concatenated
+outputs; FP32 storage, <= 1e-4 against the oracle run on the FP32-rounded
+problem promoted to FP64 (rounding the data moves theta by ~6e-8, which a
+conditioned solve can amplify, so the oracle sees the same rounded data).
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import adjoint_gap, g, gpu_jvp, gpu_vjp, lib, rel_err, to_np, torch
+from oracle import derivative as D
+from oracle import kkt_linearized as KL
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-6
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def q():
+    return lib()
+
+
+def _plan(q, prob, dtype=torch.float64, max_rhs=1):
+    return q.qcp_plan_create(q.problem_tensors(prob, "cuda", dtype), dtype, max_rhs=max_rhs)
+
+
+SMALL = [
+    ("config1", lambda: g.config1(0)),
+    ("config1_seed3", lambda: g.config1(3)),
+    ("soc_mix", lambda: g.small_qcp(21, 10, 2, 5, (3, 4, 5))),
+    ("soc_rays", lambda: g.small_qcp(22, 16, 0, 6, (3, 3, 6, 8), soc_mix=(0.5, 0.25))),
+    ("soc_dims_1_2", lambda: g.small_qcp(24, 14, 1, 3, (1, 2, 2, 7, 1), soc_mix=(0.4, 0.3))),
+    ("soc_big_block", lambda: g.small_qcp(25, 60, 3, 10, (40, 5), soc_mix=(0.5, 0.0))),
+    ("unconstrained", lambda: g.unconstrained_qp(2, 9)),
+    ("equality", lambda: g.equality_qp(4, 12, 7)),
+    ("config3_scaled", lambda: g.config3(0, scale=0.004)),
+    ("config5_scaled", lambda: g.config5_family(0, scale=0.01).instance(0)),
+]
+
+
+@pytest.mark.parametrize("precond", ["none", "equilibrate"])
+@pytest.mark.parametrize("name,mk", SMALL, ids=[s[0] for s in SMALL])
+def test_jvp_vjp_fp64_small(q, name, mk, precond):
+    prob = mk()
+    d = g.make_directions(prob, 11)
+    fac = D.DenseFactor(prob)
+    ref_j = D.jvp_dense(prob, d, fac)[:3]
+    ref_v = D.vjp_dense(prob, d, fac)[:4]
+    plan = _plan(q, prob)
+    opts = q.options(rtol=1e-11, maxiter=100000, precond=precond)
+    jv, ji = gpu_jvp(q, plan, d, opts)
+    vv, vi = gpu_vjp(q, plan, d, opts)
+    assert rel_err(jv, ref_j) < TOL64, (rel_err(jv, ref_j), ji)
+    assert rel_err(vv, ref_v) < TOL64, (rel_err(vv, ref_v), vi)
+    # the status is OK unless rounding stalls the true residual above rtol,
+    # in which case it says so and the residual is still small
+    for inf in (ji[0], vi[0]):
+        assert inf["status"] in ("QCP_OK", "QCP_NOT_CONVERGED"), inf
+        assert inf["rel_residual"] <= (1e-11 if inf["status"] == "QCP_OK" else 1e-8), inf
+    assert adjoint_gap(prob, d, jv, vv) < 1e-8
+    plan.close()
+
+
+@pytest.mark.parametrize("precond", ["none", "equilibrate"])
+@pytest.mark.parametrize("name,mk", SMALL[:6], ids=[s[0] for s in SMALL[:6]])
+def test_jvp_vjp_fp32_storage(q, name, mk, precond):
+    prob = mk()
+    r = g.round_to_fp32(prob)
+    d = g.make_directions(prob, 12)
+    d32 = g.Directions(*[np.asarray(a, np.float32).astype(np.float64) for a in
+                         (d.dP, d.dA, d.dq, d.db, d.wx, d.wy, d.ws)])
+    fac = D.DenseFactor(r)
+    ref_j = D.jvp_dense(r, d32, fac)[:3]
+    ref_v = D.vjp_dense(r, d32, fac)[:4]
+    plan = _plan(q, prob, torch.float32)
+    opts = q.options(rtol=1e-8, maxiter=100000, precond=precond)
+    jv, ji = gpu_jvp(q, plan, d32, opts)
+    vv, vi = gpu_vjp(q, plan, d32, opts)
+    assert rel_err(jv, ref_j) < TOL32, (rel_err(jv, ref_j), ji)
+    assert rel_err(vv, ref_v) < TOL32, (rel_err(vv, ref_v), vi)
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    prob = g.config2(0)
+    dirs = g.make_directions_batch(prob, 5, 16)
+    fac = D.DenseFactor(prob)
+    ref_j = [D.jvp_dense(prob, d, fac)[:3] for d in dirs]
+    ref_v = [D.vjp_dense(prob, d, fac)[:4] for d in dirs]
+    return prob, dirs, ref_j, ref_v
+
+
+def test_config2_sixteen_directions(q, cfg2):
+    """Configuration 2 as stated: 16 JVP and 16 VJP directions, rtol 1e-10."""
+    prob, dirs, ref_j, ref_v = cfg2
+    k = len(dirs)
+    plan = _plan(q, prob, max_rhs=k)
+    opts = q.options(rtol=1e-10, maxiter=100000)
+    cat = lambda name: np.concatenate([getattr(d, name) for d in dirs])
+    dx, dy, ds, ji = q.qcp_derivative_jvp_multi(plan, k, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
+    dx, dy, ds = to_np(dx, dy, ds)
+    n, m = prob.n, prob.m
+    for i in range(k):
+        got = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
+        assert rel_err(got, ref_j[i]) < TOL64, (i, rel_err(got, ref_j[i]), ji[i])
+        assert ji[i]["status"] == "QCP_OK"
+    gP, gA, gq, gb, vi = q.qcp_derivative_vjp_multi(plan, k, cat("wx"), cat("wy"), cat("ws"), opts)
+    gP, gA, gq, gb = to_np(gP, gA, gq, gb)
+    nP, nA = prob.P.nnz, prob.A.nnz
+    for i in range(k):
+        got = (gP[i * nP:(i + 1) * nP], gA[i * nA:(i + 1) * nA], gq[i * n:(i + 1) * n], gb[i * m:(i + 1) * m])
+        assert rel_err(got, ref_v[i]) < TOL64, (i, rel_err(got, ref_v[i]), vi[i])
+    # a single-direction solve reproduces direction 0 of the multi solve bit for bit
+    j0, _ = gpu_jvp(q, plan, dirs[0], opts)
+    assert np.array_equal(j0[0], dx[:n]) and np.array_equal(j0[1], dy[:m])
+    plan.close()
+
+
+def test_config2_schedules_agree(q, cfg2):
+    """Different tile sizes (multi-chunk tiles, CTA-per-row tiles) agree."""
+    prob, dirs, ref_j, ref_v = cfg2
+    plan = _plan(q, prob)
+    outs = []
+    # (16384, ...) stages several chunks per tile; long_row 8 / long_chunk 32
+    # cuts most x-rows into several one-CTA pieces
+    for tile_nnz, long_row, long_chunk in [(4096, 512, 4096), (16384, 4096, 4096), (256, 8, 32), (1024, 16, 64)]:
+        plan.set_schedule(tile_nnz, long_row, long_chunk)
+        for precond in ("none", "equilibrate"):
+            jv, ji = gpu_jvp(q, plan, dirs[0], q.options(rtol=1e-10, precond=precond))
+            assert rel_err(jv, ref_j[0]) < TOL64, (tile_nnz, long_row, precond, rel_err(jv, ref_j[0]))
+            vv, vi = gpu_vjp(q, plan, dirs[0], q.options(rtol=1e-10, precond=precond))
+            assert rel_err(vv, ref_v[0]) < TOL64, (tile_nnz, long_row, precond, rel_err(vv, ref_v[0]))
+            outs.append(jv)
+    plan.close()
+
+
+def test_determinism_and_graph(q):
+    prob = g.small_qcp(30, 40, 5, 30, (3, 5, 9))
+    d = g.make_directions(prob, 3)
+    plan = _plan(q, prob)
+    a, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12))
+    b, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12))
+    c, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12, use_graph=False))
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+    plan.close()
+
+
+def test_batched_uneven_problems(q):
+    probs = [g.config1(0), g.small_qcp(41, 17, 2, 8, (3, 6)), g.unconstrained_qp(5, 4),
+             g.small_qcp(42, 33, 0, 20, (4, 4, 12), soc_mix=(0.5, 0.2)), g.config3(1, scale=0.003)]
+    dirs = [g.make_directions(p, 9) for p in probs]
+    plan = q.qcp_batch_plan_create([q.problem_tensors(p, "cuda") for p in probs], torch.float64)
+    cat = lambda name: np.concatenate([getattr(d, name) for d in dirs])
+    opts = q.options(rtol=1e-13)
+    dx, dy, ds, ji = q.qcp_derivative_jvp(plan, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
+    gP, gA, gq, gb, vi = q.qcp_derivative_vjp(plan, cat("wx"), cat("wy"), cat("ws"), opts)
+    dx, dy, ds, gP, gA, gq, gb = to_np(dx, dy, ds, gP, gA, gq, gb)
+    on = om = op = oa = 0
+    for p, d, a, b in zip(probs, dirs, ji, vi):
+        fac = D.DenseFactor(p)
+        rj = D.jvp_dense(p, d, fac)[:3]
+        rv = D.vjp_dense(p, d, fac)[:4]
+        got_j = (dx[on:on + p.n], dy[om:om + p.m], ds[om:om + p.m])
+        got_v = (gP[op:op + p.P.nnz], gA[oa:oa + p.A.nnz], gq[on:on + p.n], gb[om:om + p.m])
+        assert rel_err(got_j, rj) < TOL64, (rel_err(got_j, rj), a)
+        assert rel_err(got_v, rv) < TOL64, (rel_err(got_v, rv), b)
+        on, om, op, oa = on + p.n, om + p.m, op + p.P.nnz, oa + p.A.nnz
+    plan.close()
+
+
+def test_zero_direction_and_maxiter(q):
+    prob = g.config1(0)
+    plan = _plan(q, prob)
+    z = g.Directions(*[np.zeros_like(a) for a in g.make_directions(prob, 1).__dict__.values()])
+    jv, ji = gpu_jvp(q, plan, z, q.options())
+    assert all(np.all(x == 0) for x in jv) and ji[0]["iters"] == 0 and ji[0]["status"] == "QCP_OK"
+    d = g.make_directions(prob, 1)
+    jv, ji = gpu_jvp(q, plan, d, q.options(rtol=1e-14, maxiter=3))
+    assert ji[0]["status"] == "QCP_NOT_CONVERGED" and ji[0]["iters"] == 3
+    plan.close()
+
+
+def test_invalid_inputs_rejected(q):
+    from paper_2508_17522_gb300._native import QCPError
+    prob = g.config1(0)
+    bad = q.problem_tensors(prob, "cuda")
+    bad.A_indices = bad.A_indices.flip(0).contiguous()           # unsorted and out of row order
+    with pytest.raises(QCPError, match="ERR_ARG"):
+        q.qcp_plan_create(bad, torch.float64)
+    bad = q.problem_tensors(prob, "cuda")
+    bad.AT_data = bad.AT_data * 1.5                              # A^T is not A's transpose
+    with pytest.raises(QCPError, match="ERR_ARG"):
+        q.qcp_plan_create(bad, torch.float64)
+    bad = q.problem_tensors(prob, "cuda")
+    bad.cone_dim = bad.cone_dim.copy()
+    bad.cone_dim[-1] -= 1                                        # cones do not cover m rows
+    with pytest.raises(QCPError, match="ERR_ARG"):
+        q.qcp_plan_create(bad, torch.float64)
+    # a lower-triangular entry in P
+    import dataclasses
+    Pl = dataclasses.replace(prob.P, indices=prob.P.indices.copy())
+    Pl.indices[Pl.indptr[3]] = 0
+    bad = q.problem_tensors(dataclasses.replace(prob, P=Pl), "cuda")
+    with pytest.raises(QCPError, match="ERR_ARG"):
+        q.qcp_plan_create(bad, torch.float64)
+
+
+def test_at_perm_optional(q):
+    prob = g.small_qcp(50, 20, 3, 12, (3, 4))
+    d = g.make_directions(prob, 2)
+    a = q.qcp_plan_create(q.problem_tensors(prob, "cuda", with_perm=False), torch.float64)
+    b = _plan(q, prob)
+    ja, _ = gpu_jvp(q, a, d, q.options(rtol=1e-12))
+    jb, _ = gpu_jvp(q, b, d, q.options(rtol=1e-12))
+    for x, y in zip(ja, jb):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
+@pytest.mark.slow
+def test_config3_full_size_properties(q):
+    """The large sparse QCP at its stated size, in the benchmark's launch
+    configuration: the JVP satisfies the differentiated optimality
+    conditions, the reported true residual meets the tolerance, and JVP and
+    VJP are adjoint."""
+    prob = g.config3(0)
+    d = g.make_directions(prob, 1)
+    plan = _plan(q, prob)
+    opts = q.options(rtol=1e-9, maxiter=400000, precond="equilibrate")
+    jv, ji = gpu_jvp(q, plan, d, opts)
+    vv, vi = gpu_vjp(q, plan, d, opts)
+    assert ji[0]["status"] == "QCP_OK" and vi[0]["status"] == "QCP_OK", (ji, vi)
+    assert ji[0]["rel_residual"] < 1e-9 and vi[0]["rel_residual"] < 1e-9, (ji, vi)
+    assert KL.relative_residual(prob, d, *jv) < 1e-7
+    assert adjoint_gap(prob, d, jv, vv) < 1e-7
+    plan.close()

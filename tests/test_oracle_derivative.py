@@ -151,3 +151,17 @@ def test_planted_transposed_operand_is_caught(monkeypatch):
 
     monkeypatch.setattr(E, "F_dense", bad_F)
     assert rel_err(D.jvp_dense(p, d)[:3], ref) > 1e-3
+
+
+@pytest.mark.parametrize("mk", QPS[:2] + SOCS)
+def test_linearized_kkt_pins_dense_jvp(mk):
+    """The dense JVP satisfies the differentiated optimality conditions, and
+    a perturbed answer does not (so the check has teeth)."""
+    from oracle import kkt_linearized as KL
+    p = mk()
+    d = g.make_directions(p, 17)
+    dx, dy, ds, _ = D.jvp_dense(p, d)
+    assert KL.relative_residual(p, d, dx, dy, ds) < 1e-11
+    rng = np.random.default_rng(0)
+    bad = dy + 1e-4 * np.linalg.norm(dy) * rng.standard_normal(dy.size) / np.sqrt(dy.size)
+    assert KL.relative_residual(p, d, dx, bad, ds) > 1e-7
