@@ -58,31 +58,23 @@ struct PlanView {
 };
 
 // Dynamic shared memory of the tile kernels:
-//   cA, cB     kThreads doubles each: boundary partial sums per thread
-//   s0, s1, s2 rmax doubles each: per-row buffers of the epilogue
+//   s0, s1, s2 rmax doubles each: per-row buffers (row sums, epilogue)
 //   srp        rmax + 1 int64: the tile's row pointers
-//   ra, rb     kThreads int32 each: rows of the boundary partials
 struct TileSmem {
-    double *cA, *cB, *s0, *s1, *s2;
+    double *s0, *s1, *s2;
     int64_t* srp;
-    int32_t *ra, *rb;
 };
 
 __host__ __device__ inline size_t tile_smem_bytes(int rmax) {
-    return sizeof(double) * (size_t)(2 * kThreads + 3 * rmax) + sizeof(int64_t) * (size_t)(rmax + 1) +
-           sizeof(int32_t) * 2 * kThreads;
+    return sizeof(double) * (size_t)(3 * rmax) + sizeof(int64_t) * (size_t)(rmax + 1);
 }
 
 __device__ __forceinline__ TileSmem tile_smem(double* base, int rmax) {
     TileSmem t;
-    t.cA = base;
-    t.cB = t.cA + kThreads;
-    t.s0 = t.cB + kThreads;
+    t.s0 = base;
     t.s1 = t.s0 + rmax;
     t.s2 = t.s1 + rmax;
     t.srp = reinterpret_cast<int64_t*>(t.s2 + rmax);
-    t.ra = reinterpret_cast<int32_t*>(t.srp + rmax + 1);
-    t.rb = t.ra + kThreads;
     return t;
 }
 
@@ -185,97 +177,119 @@ __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_
     for (int i = tid; i <= rows; i += kThreads) sm.srp[i] = rp[tl.r0 + i];
     const int64_t K0 = rp[tl.r0], K1 = rp[tl.r1];
     __syncthreads();
-    for (int64_t c0 = K0 & ~(int64_t)(kE - 1); c0 < K1; c0 += kChunk) {
-        const int64_t e0 = c0 + (int64_t)tid * kE;
-        int ra = -1, rb = -1;
-        double pa = 0.0, pb = 0.0;
-        if (e0 < K1 && e0 + kE > K0) {
-            int32_t c[kE];
-            double v[kE], x[kE];
-            load8(mcol, vals, e0, c, v);
+    // Each warp owns the rows that start in its eighth of the tile's
+    // nonzeros, so no partial sum crosses a warp and the sweeps below need
+    // only warp-level synchronisation.
+    const int lane = tid & 31, warp = tid >> 5;
+    const int64_t q = (K1 - K0 + kWarps - 1) / kWarps;
+    auto lower = [&](int64_t key) {  // first row whose start is >= key
+        int lo = 0, hi = rows;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.srp[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int w0 = (warp == 0) ? 0 : lower(K0 + warp * q);
+    const int w1 = (warp == kWarps - 1) ? rows : lower(K0 + (warp + 1) * q);
+    if (w1 > w0) {
+        const int64_t WK0 = sm.srp[w0], WK1 = sm.srp[w1];
+        for (int64_t c0 = WK0 & ~(int64_t)(kE - 1); c0 < WK1; c0 += 32 * kE) {
+            const int64_t e0 = c0 + (int64_t)lane * kE;
+            // head: the lane's first row segment; tail: its last (the same
+            // segment when the lane's eight entries lie in one row)
+            int hk = -1, tk = -1;
+            double hv = 0.0, tv = 0.0;
+            if (e0 < WK1 && e0 + kE > WK0) {
+                int32_t c[kE];
+                double v[kE], x[kE];
+                load8(mcol, vals, e0, c, v);
 #pragma unroll
-            for (int j = 0; j < kE; ++j) {
-                const bool ok = (e0 + j >= K0) && (e0 + j < K1);
-                x[j] = ok ? ld(gv + c[j]) : 0.0;
-            }
-            const int64_t kfirst = e0 > K0 ? e0 : K0;
-            int lo = 0, hi = rows;  // last row whose start is <= kfirst
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (sm.srp[mid] <= kfirst) lo = mid;
-                else hi = mid;
-            }
-            // row of each of the eight entries (-1: outside the tile)
-            int rr[kE];
-            int i = lo;
-            int64_t rend = sm.srp[i + 1];
-#pragma unroll
-            for (int j = 0; j < kE; ++j) {
-                const int64_t k = e0 + j;
-                if (k < kfirst || k >= K1) {
-                    rr[j] = -1;
-                } else {
-                    while (k >= rend) {
-                        ++i;
-                        rend = sm.srp[i + 1];
-                    }
-                    rr[j] = i;
+                for (int j = 0; j < kE; ++j) {
+                    const bool ok = (e0 + j >= WK0) && (e0 + j < WK1);
+                    x[j] = ok ? ld(gv + c[j]) : 0.0;
                 }
-            }
-            // branch-free FMA chain: restart at every row change
-            double acc = 0.0, part[kE];
-#pragma unroll
-            for (int j = 0; j < kE; ++j) {
-                const bool cont = (j > 0) && (rr[j] == rr[j - 1]);
-                acc = fma(v[j], x[j], cont ? acc : 0.0);
-                part[j] = acc;
-            }
-            int firstrow = -1, lastrow = -1;
-#pragma unroll
-            for (int j = 0; j < kE; ++j) {
-                if (rr[j] >= 0) {
-                    if (firstrow < 0) firstrow = rr[j];
-                    lastrow = rr[j];
+                const int64_t kfirst = e0 > WK0 ? e0 : WK0;
+                int lo = w0, hi = w1;  // last row whose start is <= kfirst
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.srp[mid] <= kfirst) lo = mid;
+                    else hi = mid;
                 }
-            }
+                // row of each of the eight entries (-1: outside the warp's range)
+                int rr[kE];
+                int i = lo;
+                int64_t rend = sm.srp[i + 1];
 #pragma unroll
-            for (int j = 0; j < kE; ++j) {
-                const bool end = rr[j] >= 0 && (j == kE - 1 || rr[j + 1] != rr[j]);
-                if (end) {
-                    if (rr[j] == firstrow) {
-                        ra = rr[j];
-                        pa = part[j];
-                    } else if (rr[j] == lastrow) {
-                        rb = rr[j];
-                        pb = part[j];
+                for (int j = 0; j < kE; ++j) {
+                    const int64_t k = e0 + j;
+                    if (k < kfirst || k >= WK1) {
+                        rr[j] = -1;
                     } else {
-                        sm.s0[rr[j]] += part[j];  // a row inside this thread's group: no other writer
+                        while (k >= rend) {
+                            ++i;
+                            rend = sm.srp[i + 1];
+                        }
+                        rr[j] = i;
+                    }
+                }
+                // branch-free FMA chain: restart at every row change
+                double acc = 0.0, part[kE];
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    const bool cont = (j > 0) && (rr[j] == rr[j - 1]);
+                    acc = fma(v[j], x[j], cont ? acc : 0.0);
+                    part[j] = acc;
+                }
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    if (rr[j] >= 0) {
+                        if (hk < 0) hk = rr[j];
+                        tk = rr[j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    const bool end = rr[j] >= 0 && (j == kE - 1 || rr[j + 1] != rr[j]);
+                    if (end) {
+                        if (rr[j] == hk) hv = part[j];
+                        if (rr[j] == tk) tv = part[j];
+                        // a row that starts and ends inside this lane's group
+                        if (rr[j] != hk && rr[j] != tk) sm.s0[rr[j]] = part[j];
                     }
                 }
             }
-        }
-        sm.ra[tid] = ra;
-        sm.rb[tid] = rb;
-        sm.cA[tid] = pa;
-        sm.cB[tid] = pb;
-        __syncthreads();
-        // boundary partials, one thread per row, in thread order
-        const int64_t cend = c0 + kChunk;
-        for (int i = tid; i < rows; i += kThreads) {
-            int64_t a0 = sm.srp[i], a1 = sm.srp[i + 1];
-            a0 = a0 > c0 ? a0 : c0;
-            a1 = a1 < cend ? a1 : cend;
-            if (a1 <= a0) continue;
-            const int ta = (int)((a0 - c0) / kE), tb = (int)((a1 - 1 - c0) / kE);
-            double add = 0.0;
-            for (int t = ta; t <= tb; ++t) {
-                if (sm.ra[t] == i) add += sm.cA[t];
-                else if (sm.rb[t] == i) add += sm.cB[t];
+            // Rows crossing lanes: a segmented inclusive scan of the tails
+            // along the lanes.  A chain passes through lanes that hold one
+            // segment of the same row and restarts at a lane with two or
+            // more segments (or a new row); the lane whose head continues a
+            // chain adds the chain's sum to its head.
+            const unsigned full = 0xffffffffu;
+            const bool single = (hk == tk);
+            const int ptk = __shfl_up_sync(full, tk, 1);
+            int f = (lane == 0) || !single || tk != ptk || tk < 0;
+            double S = tv;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const double oS = __shfl_up_sync(full, S, d);
+                const int of = __shfl_up_sync(full, f, d);
+                if (lane >= d && !f) {
+                    S = oS + S;
+                    f = of;
+                }
             }
-            sm.s0[i] += add;
+            const double pS = __shfl_up_sync(full, S, 1);
+            const int nhk = __shfl_down_sync(full, hk, 1);
+            if (!single && hk >= 0) {
+                const double h = (lane > 0 && hk == ptk) ? pS + hv : hv;
+                sm.s0[hk] += h;  // the head row closes here
+            }
+            if (tk >= 0 && (lane == 31 || nhk != tk)) sm.s0[tk] += S;  // the tail row's chain ends here
+            __syncwarp();
         }
-        __syncthreads();
     }
+    __syncthreads();
     return rows;
 }
 
@@ -290,7 +304,7 @@ __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_
 // The CTA that completes a system also updates its tau entry and the LSQR
 // scalars (Paige & Saunders 1982, algorithm LSQR).
 template <int PASS, int ROLE, bool SC, typename T>
-__global__ void __launch_bounds__(kThreads, 4) k_pass(PlanView<T> a) {
+__global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
     extern __shared__ double smem[];
     __shared__ Scratch scratch;
     const int ti = blockIdx.x;
@@ -447,16 +461,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass(PlanView<T> a) {
         oN = tot.b - tot.c + kappa * tt;
         if (SC) oN *= cd[rN];
     }
+    // Gauge: dz_N = 0.  F z = 0 at a root, so F's last column is a
+    // combination of the others and dropping it (the tau entry of every
+    // x-space vector stays 0) keeps the solution set's image under D phi;
+    // it also keeps the system well posed when rounding of the data has
+    // moved z off the root.  G^T-passes therefore leave the tau entry of
+    // their output at 0 and leave it out of norms and residuals.
     if (ROLE == ROLE_RES) {
-        double e = oN - a.RHS[sy.voff + rN];
-        if (SC) e /= (PASS == PASS_G ? rw[rN] : cd[rN]);
-        const double ss = tot.a + e * e;
+        double ss = tot.a;
+        if (PASS == PASS_G) {
+            double e = oN - a.RHS[sy.voff + rN];
+            if (SC) e /= rw[rN];
+            ss += e * e;
+        }
         st->resid_true = st->bnorm_true > 0.0 ? sqrt(ss) / st->bnorm_true : 0.0;
         return;
     }
-    const double nvN = c1 * oN - c2 * outv[rN];
+    const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * outv[rN];
     outv[rN] = nvN;
-    if (PASS == PASS_GT) XI[rN] = nvN;
+    if (PASS == PASS_GT) XI[rN] = 0.0;
     const double nrm = sqrt(tot.a + nvN * nvN);
     if (ROLE == ROLE_U) {
         W[rN] = tin * c1 - wcoef * W[rN];
@@ -697,14 +720,14 @@ __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> 
     Part tot;
     if (!finish_tile(a.R, tl, sy.g0, sy.g1, ti, part, &tot, &scratch)) return;
     if (threadIdx.x != 0) return;
-    const double bNt = tot.b + tot.c;
-    const double bN = sc ? cd[N - 1] * bNt : bNt;
-    U[N - 1] = bN;
-    RHS[N - 1] = bN;
-    XI[N - 1] = bN;
+    // The tau equation of F^T r = -g is dropped (gauge dz_N = 0, see k_pass):
+    // the right-hand side lives in the x-space of the JVP, whose tau entry is 0.
+    U[N - 1] = 0.0;
+    RHS[N - 1] = 0.0;
+    XI[N - 1] = 0.0;
     X[N - 1] = 0.0;
     W[N - 1] = 0.0;
-    init_state(a.state + tl.sys, a.active, sqrt(tot.a + bN * bN), sqrt(tot.d + bNt * bNt), in.rtol, in.maxiter);
+    init_state(a.state + tl.sys, a.active, sqrt(tot.a), sqrt(tot.d), in.rtol, in.maxiter);
 }
 
 // JVP output (Sec. 3.1): dz = C x, then (dx, dy, ds) = (dz_x - dz_N x,

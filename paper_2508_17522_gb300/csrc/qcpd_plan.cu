@@ -563,7 +563,7 @@ int build_schedule(qcp_plan* p) {
     p->rmax = 1;
     p->ptiles.assign(p->nprob, {});
     for (int i = 0; i < p->nprob; ++i) cut_tiles(p, i, p->ptiles[i], p->rmax);
-    if (sizeof(double) * (4 * (size_t)p->rmax + 3 * kThreads) > 200 * 1024) {
+    if (sizeof(double) * (4 * (size_t)p->rmax + 1) > 200 * 1024) {
         set_error("a tile needs %d rows (a second-order-cone block that large does not fit in shared memory)",
                   p->rmax);
         return QCP_ERR_ARG;
