@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the QCP solution-map derivative (JVP + VJP).
+
+Workload (default): the single second-order-cone QCP with n=2000, m=5500
+(cone {0}^500 x R+^2000 x SOC(10)^300), 16 forward and 16 adjoint directions,
+relative residual tolerance 1e-10, FP64, synthetic seeded data with an
+optimum built by construction.  One step = the 16 JVPs plus the 16 VJPs,
+each group solved together in one multi-direction call.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--precond equilibrate|none] [--workload config2|config3]
+
+Prints one JSON line (rank 0).  `value` counts JVP+VJP solves per second
+over all ranks with inputs resident in device memory; `e2e` measures the
+same through the public API with the inputs copied from pinned host memory
+and the outputs copied back inside the timed region.  With N > 1 (torchrun)
+every rank solves its own instance (replicas, weak scaling); there is no
+collective on the data path.  `--impl reference` times the CPU FP64 oracle
+(dense LU of the bordered derivative system) on the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# --------------------------------------------------------------------------- workloads
+def workload(name, rank):
+    import qcpgen as g
+    if name == "config2":
+        prob = g.config2(seed=rank)
+        dirs = g.make_directions_batch(prob, 5 + 1000 * rank, 16)
+        return prob, dirs, 1e-10, ("single SOC QCP n=2000 m=5500 {0}^500 x R+^2000 x SOC(10)^300, "
+                                   "16 JVP + 16 VJP directions")
+    if name == "config3":
+        prob = g.config3(seed=rank)
+        dirs = g.make_directions_batch(prob, 5 + 1000 * rank, 1)
+        return prob, dirs, 1e-6, ("large sparse QCP n=100000 m=220000 {0}^20000 x R+^150000 x lognormal SOC "
+                                  "blocks on 50000 rows, 1 JVP + 1 VJP direction")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes_per_pass(prob):
+    """Bytes one product with F or F^T must move (FP64 values 8 B, indices
+    4 B): half of B_iter = 2 [12 (2 nnz(A) + nnz_up(P)) + 4 (m + 2n + 3)]
+    + 8 (8n + 14m + 9N), the per-iteration traffic of one F and one F^T
+    product plus the LSQR vector updates."""
+    n, m, N = prob.n, prob.m, prob.N
+    b_iter = 2 * (12 * (2 * prob.A.nnz + prob.P.nnz) + 4 * (m + 2 * n + 3)) + 8 * (8 * n + 14 * m + 9 * N)
+    return b_iter / 2.0
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("qcpd_kernels.cuh", "qcpd_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2508_17522_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name, bytes_per_pass):
+    """dram read+write bytes per pass launch from a committed ncu summary
+    (profiles/*.json), if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_pass_{workload_name}_dram.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_pass")
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, col in (("hw_slowdown", 5), ("hw_thermal_slowdown", 6), ("sw_thermal_slowdown", 7),
+                              ("sw_power_cap", 8)):
+                if f[col].lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- oracle (CPU)
+def oracle_step(prob, dirs):
+    """The CPU FP64 oracle on one step of the workload: dense LU of the
+    bordered derivative system, then every JVP and VJP direction."""
+    from oracle import derivative as D
+    fac = D.DenseFactor(prob)
+    for d in dirs:
+        D.jvp_dense(prob, d, fac)
+        D.vjp_dense(prob, d, fac)
+    return 2 * len(dirs)
+
+
+def oracle_sample(prob, dirs, budget_s=30.0):
+    """A bounded sample of the oracle on this workload (rank 0 only)."""
+    t0 = time.perf_counter()
+    solves = oracle_step(prob, dirs[:16])
+    dt = time.perf_counter() - t0
+    return {"value": solves / dt, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one full step on the host: dense LU of the bordered (N+1)x(N+1) derivative "
+                       f"system (N={prob.N}) plus {len(dirs[:16])} JVP and {len(dirs[:16])} VJP solves, "
+                       f"{dt:.1f} s; numpy/scipy FP64 with the BLAS threads of all {os.cpu_count()} cores")}
+
+
+# --------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
+    ap.add_argument("--workload", default="config2", choices=["config2", "config3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    metric = "JVP+VJP solves/sec at <=1e-6 rel err"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        prob, dirs, rtol, desc = workload(args.workload, 0)
+        if args.workload != "config2":
+            raise SystemExit("the oracle reference arm covers the config2 workload (dense LU)")
+        for _ in range(args.warmup):
+            oracle_step(prob, dirs)
+        t0 = time.perf_counter()
+        solves = 0
+        for _ in range(args.steps):
+            solves += oracle_step(prob, dirs)
+        dt = time.perf_counter() - t0
+        val = solves / dt
+        print(json.dumps({
+            "impl": "reference", "metric": metric, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "rtol": rtol},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} full steps of the dense-LU oracle on the host"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_2508_17522_gb300 as q
+    from paper_2508_17522_gb300.buildlib import build
+    build()
+
+    prob, dirs, rtol, desc = workload(args.workload, rank)
+    k = len(dirs)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and args.workload == "config2":
+        log("timing the CPU oracle sample ...")
+        cpu = oracle_sample(prob, dirs)
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    plan = q.qcp_plan_create(q.problem_tensors(prob, dev), torch.float64, max_rhs=k, stream=stream)
+    opts = q.options(rtol=rtol, maxiter=400000, precond=args.precond)
+    cat = lambda nm: np.concatenate([getattr(d, nm) for d in dirs])
+    host = {nm: torch.as_tensor(cat(nm)).pin_memory() for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
+    with torch.cuda.stream(stream):
+        devin = {nm: t.to(dev, non_blocking=True) for nm, t in host.items()}
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream.synchronize()
+
+    launches = [0]
+    pass_ms = [0.0]
+    passes = [0]
+    infos = []
+
+    def step(inputs):
+        jout = q.qcp_derivative_jvp_multi(plan, k, inputs["dP"], inputs["dA"], inputs["dq"], inputs["db"], opts)
+        launches[0] += plan.last_launches()
+        ms, n_ = plan.last_timing()
+        pass_ms[0] += ms
+        passes[0] += n_
+        vout = q.qcp_derivative_vjp_multi(plan, k, inputs["wx"], inputs["wy"], inputs["ws"], opts)
+        launches[0] += plan.last_launches()
+        ms, n_ = plan.last_timing()
+        pass_ms[0] += ms
+        passes[0] += n_
+        infos.append((jout[-1], vout[-1]))
+        return jout[:-1] + vout[:-1]
+
+    for _ in range(args.warmup):
+        step(devin)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region (L2 flushed before every step)
+    launches[0], pass_ms[0], passes[0] = 0, 0.0, 0
+    infos.clear()
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        step(devin)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    dev_launches = launches[0]
+    statuses = sorted({i["status"] for pair in infos for grp in pair for i in grp})
+    max_res = max(i["rel_residual"] for pair in infos for grp in pair for i in grp)
+
+    # ---- end to end through the public API with host buffers
+    e2e_ms = 0.0
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = 0
+    outs_host = None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ins = {nm: t.to(dev, non_blocking=True) for nm, t in host.items()}
+        outs = step(ins)
+        with torch.cuda.stream(stream):
+            if outs_host is None:
+                outs_host = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+                d2h = sum(o.numel() * o.element_size() for o in outs)
+            for hdst, o in zip(outs_host, outs):
+                hdst.copy_(o, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+
+    # ---- max over ranks
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t[0]), float(t[1])
+    solves_per_step = 2 * k * world
+    value = solves_per_step * args.steps / (total_ms / 1e3)
+    e2e = solves_per_step * args.steps / (e2e_ms / 1e3)
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_note = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    bpp = algorithmic_bytes_per_pass(prob) * k
+    avg_pass_s = (pass_ms[0] / 1e3) / max(passes[0], 1)
+    achieved = bpp / avg_pass_s / 1e9
+    traffic = recorded_traffic(args.workload, bpp)
+
+    if rank == 0:
+        line = {
+            "metric": metric, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "solver": "LSQR",
+                       "parallelism": f"replicas x{world}", "l2": "flushed before every timed step "
+                       f"({L2_FLUSH_BYTES >> 20} MiB write)", "status": statuses,
+                       "max_true_rel_residual": max_res},
+            "roofline": {"bound": "hbm", "kernel": "k_pass (one product with F or F^T, all systems)",
+                         "achieved": achieved, "peak": peak, "peak_source": peak_note, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "bytes_per_launch": bpp, "avg_launch_us": avg_pass_s * 1e6},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": dev_launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

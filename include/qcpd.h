@@ -236,6 +236,12 @@ int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, in
    (graph replays counted per kernel node). */
 int64_t qcp_plan_last_launches(const qcp_plan* plan);
 
+/* Device time (CUDA events on the plan's stream) of the Krylov iteration
+   chunks of the most recent JVP/VJP call, and the number of pass launches
+   (products with F or F^T over all systems) they contain; their ratio is
+   the average duration of one pass.  Errors: QCP_ERR_ARG (null plan). */
+int qcp_plan_last_timing(const qcp_plan* plan, double* pass_ms, int64_t* passes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,8 @@ def lib():
     L.qcp_plan_set_schedule.argtypes = [c_void_p, c_int32, c_int32, c_int32]
     L.qcp_plan_last_launches.restype = c_int64
     L.qcp_plan_last_launches.argtypes = [c_void_p]
+    L.qcp_plan_last_timing.restype = ctypes.c_int
+    L.qcp_plan_last_timing.argtypes = [c_void_p, P(c_double), P(c_int64)]
     _lib = L
     return L
 

@@ -162,6 +162,12 @@ class Plan:
     def last_launches(self) -> int:
         return int(N.lib().qcp_plan_last_launches(self._h))
 
+    def last_timing(self):
+        """(device ms of the iteration chunks, pass launches in them) of the last call."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(N.lib().qcp_plan_last_timing(self._h, ctypes.byref(ms), ctypes.byref(n)), "qcp_plan_last_timing")
+        return ms.value, n.value
+
     def set_schedule(self, tile_nnz: int = 4096, long_row: int = 512, long_chunk: int = 4096):
         _check(N.lib().qcp_plan_set_schedule(self._h, int(tile_nnz), int(long_row), int(long_chunk)),
                "qcp_plan_set_schedule")

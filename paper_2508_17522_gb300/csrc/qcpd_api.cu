@@ -169,13 +169,21 @@ static int iterate(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int nt
         int64_t chunk = opts.check_every > 0 ? opts.check_every : cap;
         chunk = std::min<int64_t>(chunk, cap - done_iters);
         const bool graph_ok = opts.use_graph && opts.check_every > 0 && chunk == opts.check_every;
+        QCP_CUDA(cudaEventRecord(p->ev0, p->stream));
         QCP_TRY(run_chunk<T>(p, mode, nsys, v, ntiles, smem, (int)chunk, graph_ok));
+        QCP_CUDA(cudaEventRecord(p->ev1, p->stream));
         done_iters += chunk;
+        p->pass_launches += 2 * chunk;
         if (opts.check_every > 0) {
             QCP_CUDA(cudaMemcpyAsync(p->h_active, p->d_active.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
             QCP_CUDA(cudaStreamSynchronize(p->stream));
-            if (*p->h_active <= 0) break;
+        } else {
+            QCP_CUDA(cudaEventSynchronize(p->ev1));
         }
+        float ms = 0.0f;
+        QCP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->pass_ms += ms;
+        if (opts.check_every > 0 && *p->h_active <= 0) break;
     }
     return QCP_OK;
 }
@@ -234,6 +242,8 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
     const size_t smem = tile_smem_bytes(p->rmax);
     QCP_TRY(set_smem_attrs<T>(smem));
     p->last_launches = 0;
+    p->pass_ms = 0.0;
+    p->pass_launches = 0;
     QCP_CUDA(cudaMemsetAsync(p->d_active.p, 0, sizeof(int), st));
     RhsArgs<T> ra = rin;
     ra.rtol = opts.rtol;
@@ -387,6 +397,11 @@ static int make_plan(int np, const qcp_problem* probs, const qcp_solution* sols,
     } else {
         p->stream = user;
     }
+    if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
+        set_error("cudaEventCreate failed");
+        qcp_plan_destroy(p);
+        return QCP_ERR_CUDA;
+    }
     if (cudaMallocHost(&p->h_active, sizeof(int)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         qcp_plan_destroy(p);
@@ -497,5 +512,15 @@ int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, in
 }
 
 int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }
+
+int qcp_plan_last_timing(const qcp_plan* plan, double* pass_ms, int64_t* passes) {
+    if (!plan) {
+        set_error("null plan");
+        return QCP_ERR_ARG;
+    }
+    if (pass_ms) *pass_ms = plan->pass_ms;
+    if (passes) *passes = plan->pass_launches;
+    return QCP_OK;
+}
 
 }  // extern "C"

@@ -1086,5 +1086,7 @@ int create_plan(qcp_plan* p, const qcp_problem* probs, const qcp_solution* sols)
 
 qcp_plan::~qcp_plan() {
     qcpd::drop_graphs(this);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
     if (h_active) cudaFreeHost(h_active);
 }

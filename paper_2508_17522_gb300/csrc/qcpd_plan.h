@@ -118,6 +118,11 @@ struct qcp_plan {
 
     std::map<qcpd::GraphKey, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;
+    // device time of the iteration chunks of the last call (CUDA events on
+    // the plan's stream) and the number of pass launches they contain
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double pass_ms = 0.0;
+    int64_t pass_launches = 0;
 
     ~qcp_plan();
 };
