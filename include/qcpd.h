@@ -236,6 +236,34 @@ int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, in
    (graph replays counted per kernel node). */
 int64_t qcp_plan_last_launches(const qcp_plan* plan);
 
+/*
+ * The forward product of qcp_derivative_jvp for a single-problem plan and one
+ * direction, for callers that cannot allocate device memory at call time:
+ * code running while its stream is captured into a CUDA graph, allocator
+ * hooks, or loops whose memory comes from a pool they do not own.  The
+ * paper has no counterpart; it is a deployment variant of the same kernels.
+ *
+ * All per-call scratch (Krylov vectors, LSQR scalars, reduction partials and
+ * counters) lives in one 16 MiB file-scope device array of the library
+ * instead of plan memory; about 48 bytes per embedding row N = n + m + 1
+ * plus 40 bytes per tile, so problems up to roughly N = 340000 fit.  Larger
+ * plans are rejected with QCP_ERR_ARG and a message giving the size needed.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Every GPU that loads the library holds the array until the
+ * process exits.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress, once per device); make that first
+ * call before any stream capture begins.  Every call shares the one array
+ * and clears it at entry, so calls whose work overlaps on the GPU (two
+ * host threads, or two streams) race and must be serialised by the caller.
+ * Arguments, options (check_every >= 1 is required) and outputs are those
+ * of qcp_derivative_jvp; the plan must not be batched.
+ */
+int qcp_derivative_jvp_noalloc(qcp_plan* plan, const qcp_options* opts, const void* dP, const void* dA,
+                               const void* dq, const void* db, void* dx, void* dy, void* ds,
+                               qcp_info* info);
+
 /* Device time (CUDA events on the plan's stream) of the Krylov iteration
    chunks of the most recent JVP/VJP call, and the number of pass launches
    (products with F or F^T over all systems) they contain; their ratio is

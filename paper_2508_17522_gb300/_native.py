@@ -77,7 +77,7 @@ def lib():
     L.qcp_plan_destroy.argtypes = [c_void_p]
     L.qcp_plan_sizes.restype = ctypes.c_int
     L.qcp_plan_sizes.argtypes = [c_void_p] + [P(c_int64)] * 5
-    for name in ("qcp_derivative_jvp", "qcp_derivative_vjp"):
+    for name in ("qcp_derivative_jvp", "qcp_derivative_vjp", "qcp_derivative_jvp_noalloc"):
         f = getattr(L, name)
         f.restype = ctypes.c_int
         f.argtypes = [c_void_p, P(qcp_options)] + [c_void_p] * 7 + [P(qcp_info)]

@@ -218,6 +218,23 @@ def qcp_derivative_jvp(plan: Plan, dP, dA, dq, db, opts=None):
     return dx, dy, ds, info
 
 
+def qcp_derivative_jvp_noalloc(plan: Plan, dP, dA, dq, db, out=None, opts=None):
+    """qcp_derivative_jvp with the call's scratch in the library's static
+    device array (include/qcpd.h).  Pass preallocated outputs in `out`
+    (dx, dy, ds) to keep the call itself free of device allocation."""
+    ins = [plan._vec(dP, plan.nnzP_total), plan._vec(dA, plan.nnzA_total), plan._vec(dq, plan.n_total),
+           plan._vec(db, plan.m_total)]
+    if out is None:
+        out = [torch.empty(sz, device=plan.device, dtype=plan.dtype)
+               for sz in (plan.n_total, plan.m_total, plan.m_total)]
+    info = (N.qcp_info * 1)()
+    o = opts if opts is not None else options()
+    code = N.lib().qcp_derivative_jvp_noalloc(plan.handle, ctypes.byref(o), *[_vp(t) for t in ins],
+                                              *[_vp(t) for t in out], info)
+    _check(code, "qcp_derivative_jvp_noalloc", ok=_ALLOW)
+    return out[0], out[1], out[2], [_info_dict(info[0])]
+
+
 def qcp_derivative_vjp(plan: Plan, wx, wy, ws, opts=None):
     """(dP, dA, dq, db, info) = D S(theta)^T [wx, wy, ws]  (Sec. 3.2)."""
     ins = [plan._vec(wx, plan.n_total), plan._vec(wy, plan.m_total), plan._vec(ws, plan.m_total)]

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "qcpd_kernels.cuh"
 #include "qcpd_plan.h"
@@ -416,6 +417,165 @@ static int make_plan(int np, const qcp_problem* probs, const qcp_solution* sols,
     return QCP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// JVP without device allocation.
+//
+// Some callers cannot call cudaMalloc when they need a derivative: code
+// that runs while a stream is being captured into a CUDA graph, allocator
+// hooks and real-time loops that forbid device allocation, or hosts whose
+// memory is handed out by a pool they do not own.  For them the per-call
+// scratch of the JVP (Krylov vectors, LSQR scalars, reduction partials and
+// counters) lives in one file-scope device array of fixed size instead of
+// plan memory.  Every GPU that loads the library holds the array until the
+// process exits.
+constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[256];  // device address of the array, per device ordinal
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+static int noalloc_scratch(void** out) {
+    int dev = 0;
+    QCP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        set_error("device ordinal %d out of range", dev);
+        return QCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        QCP_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return QCP_OK;
+}
+
+// Bytes of scratch a one-direction JVP on this plan needs, and the view
+// that points the kernels at it.
+template <typename T>
+static size_t noalloc_layout(qcp_plan* p, unsigned char* base, PlanView<T>* v, bool scaled) {
+    const Prob& pr = p->hprob[0];
+    const size_t N = (size_t)pr.n + pr.m + 1;
+    const size_t nt = (size_t)p->tiles_per_sys, ng = (size_t)p->groups_per_sys;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        unsigned char* q = base ? base + off : nullptr;
+        off += bytes;
+        return q;
+    };
+    unsigned char* tpart = take(nt * sizeof(Part));
+    unsigned char* gpart = take(ng * sizeof(Part));
+    unsigned char* gcnt = take(ng * sizeof(int32_t));
+    unsigned char* scnt = take(sizeof(int32_t));
+    unsigned char* state = take(sizeof(LsqrState));
+    unsigned char* active = take(sizeof(int));
+    unsigned char* split = take(std::max(1, p->nsplit) * sizeof(int32_t));
+    unsigned char* rowp = take(std::max<size_t>(1, nt) * sizeof(double));
+    unsigned char* vec[6];
+    for (int i = 0; i < 6; ++i) vec[i] = take(N * sizeof(double));
+    if (v) {
+        *v = view<T>(p, scaled);
+        v->state = reinterpret_cast<LsqrState*>(state);
+        v->R = Reduce{reinterpret_cast<Part*>(tpart), reinterpret_cast<Part*>(gpart),
+                      reinterpret_cast<int32_t*>(gcnt), reinterpret_cast<int32_t*>(scnt), p->d_groups.as<Group>()};
+        v->active = reinterpret_cast<int*>(active);
+        v->split_cnt = reinterpret_cast<int32_t*>(split);
+        v->row_part = reinterpret_cast<double*>(rowp);
+        v->U = reinterpret_cast<double*>(vec[0]);
+        v->V = reinterpret_cast<double*>(vec[1]);
+        v->W = reinterpret_cast<double*>(vec[2]);
+        v->X = reinterpret_cast<double*>(vec[3]);
+        v->XI = reinterpret_cast<double*>(vec[4]);
+        v->RHS = reinterpret_cast<double*>(vec[5]);
+    }
+    return off;
+}
+
+template <typename T>
+static int jvp_noalloc(qcp_plan* p, const qcp_options* opts_in, const void* dP, const void* dA, const void* dq,
+                       const void* db, void* dx, void* dy, void* ds, qcp_info* info) {
+    qcp_options opts;
+    if (opts_in) opts = *opts_in;
+    else qcp_default_options(&opts);
+    if (!(opts.rtol >= 0.0) || opts.maxiter < 1 || opts.check_every < 1 || opts.solver != 0 ||
+        (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE)) {
+        set_error("bad options: rtol >= 0, maxiter >= 1, check_every >= 1, solver 0, known precond required");
+        return QCP_ERR_ARG;
+    }
+    const size_t need = noalloc_layout<T>(p, nullptr, nullptr, false);
+    if (need > kNoAllocScratchBytes) {
+        set_error("qcp_derivative_jvp_noalloc: this plan needs %zu bytes of scratch, the static array holds %zu",
+                  need, kNoAllocScratchBytes);
+        return QCP_ERR_ARG;
+    }
+    void* base = nullptr;
+    QCP_TRY(noalloc_scratch(&base));
+    const bool scaled = opts.precond == QCP_PRECOND_EQUILIBRATE;
+    PlanView<T> v;
+    noalloc_layout<T>(p, static_cast<unsigned char*>(base), &v, scaled);
+    cudaStream_t st = p->stream;
+    const int ntiles = p->tiles_per_sys;
+    const size_t smem = tile_smem_bytes(p->rmax);
+    QCP_TRY(set_smem_attrs<T>(smem));
+    // the array keeps the previous call's contents: counters, partial sums,
+    // the LSQR scalars and the Krylov vectors all start at zero
+    QCP_CUDA(cudaMemsetAsync(base, 0, need, st));
+    RhsArgs<T> ra{(const T*)dP, (const T*)dA, (const T*)dq, (const T*)db, nullptr, nullptr, nullptr,
+                  opts.rtol, opts.maxiter};
+    const OutArgs<T> out{(T*)dx, (T*)dy, (T*)ds, nullptr};
+    k_jvp_rhs<T><<<ntiles, kThreads, 0, st>>>(v, ra);
+    launch_pass<PASS_GT, ROLE_V, T>(v, ntiles, smem, st);
+    QCP_CUDA(cudaGetLastError());
+    LsqrState hs;
+    double prev_res = INFINITY;
+    for (int round = 0;; ++round) {
+        for (int64_t done = 0; done <= opts.maxiter; done += opts.check_every) {
+            for (int c = 0; c < opts.check_every; ++c) launch_iter<T>(0, v, ntiles, smem, st);
+            QCP_CUDA(cudaGetLastError());
+            int active = 0;
+            QCP_CUDA(cudaMemcpyAsync(&active, v.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            QCP_CUDA(cudaStreamSynchronize(st));
+            if (active <= 0) break;
+        }
+        k_jvp_out<T><<<ntiles, kThreads, smem, st>>>(v, out);
+        if (opts.compute_residual) launch_pass<PASS_G, ROLE_RES, T>(v, ntiles, smem, st);
+        QCP_CUDA(cudaGetLastError());
+        QCP_CUDA(cudaMemcpyAsync(&hs, v.state, sizeof(LsqrState), cudaMemcpyDeviceToHost, st));
+        QCP_CUDA(cudaStreamSynchronize(st));
+        if (!opts.compute_residual || round == 4) break;
+        // same continuation rule as qcp_derivative_jvp
+        const bool improving = hs.resid_true < 0.5 * prev_res;
+        prev_res = hs.resid_true;
+        if (hs.outcome != O_CONVERGED || !(hs.resid_true > opts.rtol) || !(hs.alpha > 0.0) ||
+            !isfinite(hs.resid_true) || hs.iters >= hs.maxiter || hs.bnorm_true <= 0.0 || !improving)
+            break;
+        hs.rtol *= std::max(0.01, 0.5 * opts.rtol / hs.resid_true);
+        hs.status = S_ACTIVE;
+        hs.outcome = O_RUNNING;
+        hs.xcoef = 0.0;
+        const int one = 1;
+        QCP_CUDA(cudaMemcpyAsync(v.state, &hs, sizeof(LsqrState), cudaMemcpyHostToDevice, st));
+        QCP_CUDA(cudaMemcpyAsync(v.active, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+        QCP_CUDA(cudaStreamSynchronize(st));
+        launch_pass<PASS_GT, ROLE_V, T>(v, ntiles, smem, st);
+    }
+    int rc = status_of(hs, p->kink[0], opts.kink_tol);
+    if (opts.compute_residual && rc != QCP_BREAKDOWN && hs.resid_true > opts.rtol) rc = QCP_NOT_CONVERGED;
+    if (info) {
+        info->status = rc;
+        info->iters = hs.iters;
+        info->rel_residual = opts.compute_residual ? hs.resid_true : -1.0;
+        info->rel_residual_est = hs.bnorm > 0 ? hs.phibar / hs.bnorm : 0.0;
+        info->kink_margin = p->kink[0];
+    }
+    return rc;
+}
+
 }  // namespace qcpd
 
 using namespace qcpd;
@@ -512,6 +672,21 @@ int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, in
 }
 
 int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }
+
+int qcp_derivative_jvp_noalloc(qcp_plan* plan, const qcp_options* opts, const void* dP, const void* dA,
+                               const void* dq, const void* db, void* dx, void* dy, void* ds, qcp_info* info) {
+    if (!plan || plan->batched) {
+        set_error("qcp_derivative_jvp_noalloc takes a single-problem plan");
+        return QCP_ERR_ARG;
+    }
+    const qcpd::Prob& pr = plan->hprob[0];
+    if ((pr.pnz && !dP) || (pr.anz && !dA) || !dq || (pr.m && !db) || !dx || (pr.m && (!dy || !ds))) {
+        set_error("null array argument");
+        return QCP_ERR_ARG;
+    }
+    if (plan->dtype == QCP_F64) return jvp_noalloc<double>(plan, opts, dP, dA, dq, db, dx, dy, ds, info);
+    return jvp_noalloc<float>(plan, opts, dP, dA, dq, db, dx, dy, ds, info);
+}
 
 int qcp_plan_last_timing(const qcp_plan* plan, double* pass_ms, int64_t* passes) {
     if (!plan) {
