@@ -75,7 +75,7 @@ typedef enum {
     QCP_NOT_CONVERGED = 4,    /* rtol not reached (maxiter hit, or the true residual stalled above
                                  rtol at the attainable accuracy); outputs hold the last iterate */
     QCP_BREAKDOWN = 5,        /* a non-finite Krylov scalar appeared */
-    QCP_ERR_TIMEOUT = 6,      /* reserved for bounded device waits */
+    QCP_ERR_TIMEOUT = 6,      /* a bounded device wait (persistent mode's grid barrier) gave up */
     QCP_WARN_NEAR_KINK = 7    /* solution within opts->kink_tol of a point where D Pi is undefined */
 } qcp_status;
 
@@ -134,6 +134,10 @@ typedef struct {
                                  tolerance (at most 4 times, while it keeps halving); 0 = trust the
                                  Krylov estimate */
     int32_t precond;          /* qcp_precond */
+    int32_t persistent;       /* 1 = run the Krylov iterations of all systems in one cooperative
+                                 launch (grid-wide barriers between passes, every wait bounded;
+                                 a barrier that times out returns QCP_ERR_TIMEOUT); 0 = one launch
+                                 per pass, replayed from CUDA graphs */
     double kink_tol;          /* QCP_WARN_NEAR_KINK threshold on info.kink_margin */
 } qcp_options;
 
@@ -151,7 +155,8 @@ typedef struct qcp_plan qcp_plan;
 const char* qcp_last_error(void);
 
 /* Fill *opts with defaults: LSQR, rtol 1e-10, maxiter 100000, check_every 32,
-   use_graph 1, compute_residual 1, precond QCP_PRECOND_NONE, kink_tol 0. */
+   use_graph 1, compute_residual 1, precond QCP_PRECOND_NONE, persistent 0,
+   kink_tol 0. */
 void qcp_default_options(qcp_options* opts);
 
 /* Library version as an integer (major * 10000 + minor * 100 + patch). */

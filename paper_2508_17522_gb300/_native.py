@@ -40,7 +40,7 @@ class qcp_solution(ctypes.Structure):
 class qcp_options(ctypes.Structure):
     _fields_ = [("solver", c_int32), ("rtol", c_double), ("maxiter", c_int64), ("check_every", c_int32),
                 ("use_graph", c_int32), ("compute_residual", c_int32), ("precond", c_int32),
-                ("kink_tol", c_double)]
+                ("persistent", c_int32), ("kink_tol", c_double)]
 
 
 class qcp_info(ctypes.Structure):

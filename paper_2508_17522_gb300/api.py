@@ -97,13 +97,15 @@ _PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE
 
 
 def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_residual=True, precond="none",
-            kink_tol=0.0):
-    """qcp_options; precond is "none" (the plain method) or "equilibrate"."""
+            kink_tol=0.0, persistent=False):
+    """qcp_options; precond is "none" (the plain method) or "equilibrate";
+    persistent=True runs the Krylov loop in one cooperative launch."""
     o = N.qcp_options()
     N.lib().qcp_default_options(ctypes.byref(o))
     o.rtol, o.maxiter, o.check_every = float(rtol), int(maxiter), int(check_every)
     o.use_graph, o.compute_residual, o.kink_tol = int(bool(use_graph)), int(bool(compute_residual)), float(kink_tol)
     o.precond = _PRECOND[precond] if isinstance(precond, str) else int(precond)
+    o.persistent = int(bool(persistent))
     return o
 
 

@@ -189,6 +189,51 @@ static int iterate(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int nt
     return QCP_OK;
 }
 
+// All remaining iterations in one cooperative launch (qcp_options.persistent).
+template <typename T>
+static int iterate_persistent(qcp_plan* p, int mode, const PlanView<T>& v, int ntiles, size_t smem,
+                              const qcp_options& opts) {
+    cudaStream_t st = p->stream;
+    int dev = 0, nsm = 0, per_sm = 0;
+    QCP_CUDA(cudaGetDevice(&dev));
+    QCP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    void* fn = nullptr;
+    if (mode == 0) fn = v.scaled ? (void*)k_persist<0, true, T> : (void*)k_persist<0, false, T>;
+    else fn = v.scaled ? (void*)k_persist<1, true, T> : (void*)k_persist<1, false, T>;
+    QCP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+    if (per_sm < 1) {
+        set_error("persistent mode: a CTA of this plan does not fit on an SM");
+        return QCP_ERR_ARG;
+    }
+    int grid = std::min(ntiles, per_sm * nsm);
+    PersistCtl c;
+    int32_t* ctl = p->d_pctl.as<int32_t>();
+    c.bar_count = reinterpret_cast<unsigned*>(ctl);
+    c.bar_gen = reinterpret_cast<unsigned*>(ctl + 1);
+    c.stop = ctl + 2;
+    c.err = ctl + 3;
+    c.max_iters = opts.maxiter + 2;
+    QCP_CUDA(cudaMemsetAsync(ctl, 0, 4 * sizeof(int32_t), st));
+    PlanView<T> va = v;
+    void* args[] = {(void*)&va, (void*)&c, (void*)&ntiles};
+    QCP_CUDA(cudaEventRecord(p->ev0, st));
+    QCP_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, st));
+    QCP_CUDA(cudaEventRecord(p->ev1, st));
+    QCP_CUDA(cudaEventSynchronize(p->ev1));
+    float ms = 0.0f;
+    QCP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    p->pass_ms += ms;
+    p->last_launches += 1;
+    int32_t hc[4];
+    QCP_CUDA(cudaMemcpy(hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost));
+    if (hc[3]) {
+        set_error("persistent mode: a grid barrier gave up waiting (bounded spin)");
+        return QCP_ERR_TIMEOUT;
+    }
+    return QCP_OK;
+}
+
 // The v-update pass of the operator: starts the bidiagonalisation and resumes it.
 template <typename T>
 static void launch_v_pass(int mode, const PlanView<T>& v, int ntiles, size_t smem, cudaStream_t st) {
@@ -254,7 +299,11 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
     launch_v_pass<T>(mode, v, ntiles, smem, st);
     QCP_CUDA(cudaGetLastError());
     p->last_launches += 2;
-    QCP_TRY(iterate<T>(p, mode, nsys, v, ntiles, smem, opts));
+    auto run_iterations = [&]() -> int {
+        if (opts.persistent) return iterate_persistent<T>(p, mode, v, ntiles, smem, opts);
+        return iterate<T>(p, mode, nsys, v, ntiles, smem, opts);
+    };
+    QCP_TRY(run_iterations());
     std::vector<LsqrState> hs(nsys);
     std::vector<double> prev_res(nsys, INFINITY);
     const bool residual = opts.compute_residual != 0;
@@ -287,7 +336,12 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         QCP_CUDA(cudaStreamSynchronize(st));
         launch_v_pass<T>(mode, v, ntiles, smem, st);
         p->last_launches += 1;
-        QCP_TRY(iterate<T>(p, mode, nsys, v, ntiles, smem, opts));
+        QCP_TRY(run_iterations());
+    }
+    if (opts.persistent) {
+        int64_t it = 0;
+        for (int s = 0; s < nsys; ++s) it = std::max<int64_t>(it, hs[s].iters);
+        p->pass_launches = 2 * it;  // passes the persistent launches ran
     }
     int rc = QCP_OK;
     for (int s = 0; s < nsys; ++s) {
@@ -593,6 +647,7 @@ void qcp_default_options(qcp_options* o) {
     o->use_graph = 1;
     o->compute_residual = 1;
     o->precond = QCP_PRECOND_NONE;
+    o->persistent = 0;
     o->kink_tol = 0.0;
 }
 

@@ -99,7 +99,9 @@ struct SocBlock {
 struct LsqrState {
     double alpha, beta;     // current normalisers of v and u
     double rhobar, phibar;
-    double rho;             // rho of the last rotation
+    double inv_rho;         // 1 / rho of the last rotation
+    double uc1, uc2;        // next u-update: 1/alpha, alpha/beta
+    double vc1, vc2;        // next v-update: 1/beta, beta/alpha (0 at the first one)
     double wcoef;           // theta_{k+1} / rho_k  (w <- v - wcoef w)
     double xcoef;           // phi_k / rho_k        (x <- x + xcoef w)
     double c, s;
@@ -202,12 +204,16 @@ __device__ __forceinline__ Part ld_part(const Part* p) {
 
 // Two-level last-CTA-done reduction of one Part per tile into one per
 // system.  Called by every thread of the CTA with the tile's partial (valid
-// in thread 0).  Returns true in the single CTA that completes the system,
-// with the system total in *total (valid in thread 0).
-// Sums run in a fixed order, so results do not depend on CTA scheduling.
-// No CTA ever waits on another: the last one to arrive does the work.
+// in thread 0).  Returns true in warp 0 of the single CTA that completes the
+// system, with the system total in *total; every other warp and CTA gets
+// false.  After the arrival barrier only warp 0 works (shuffles, no block
+// barriers): FP64 adds are scarce and every barrier and dependent add sits on
+// the pass's critical path.  Sums run in a fixed order, so results do not
+// depend on CTA scheduling.  No CTA ever waits on another: the last one to
+// arrive does the work.
 __device__ __forceinline__ bool finish_tile(const Reduce& R, const Tile& tl, int32_t g0, int32_t g1,
                                             int tile, Part part, Part* total, Scratch* scratch) {
+    (void)scratch;
     __shared__ int s_last;
     if (threadIdx.x == 0) {
         R.tile_part[tile] = part;
@@ -217,26 +223,33 @@ __device__ __forceinline__ bool finish_tile(const Reduce& R, const Tile& tl, int
         s_last = (prev == g.t1 - g.t0 - 1);
     }
     __syncthreads();
-    if (!s_last) return false;
+    if (!s_last || threadIdx.x >= 32) return false;
+    const int lane = threadIdx.x;
     __threadfence();
     const Group g = R.groups[tl.group];
     Part acc = pzero();
-    for (int i = g.t0 + (int)threadIdx.x; i < g.t1; i += blockDim.x) acc = padd(acc, ld_part(R.tile_part + i));
-    acc = block_sum_part(acc, scratch);
-    if (threadIdx.x == 0) {
+    for (int i = g.t0 + lane; i < g.t1; i += 32) acc = padd(acc, ld_part(R.tile_part + i));
+    acc = warp_sum_part(acc);
+    if (g1 - g0 == 1) {  // the group is the whole system
+        if (lane == 0) R.group_cnt[tl.group] = 0;
+        *total = acc;
+        return true;
+    }
+    int last = 0;
+    if (lane == 0) {
         R.group_cnt[tl.group] = 0;
         R.group_part[tl.group] = acc;
         __threadfence();
         const int prev = atomicAdd(&R.sys_cnt[tl.sys], 1);
-        s_last = (prev == g1 - g0 - 1);
+        last = (prev == g1 - g0 - 1);
     }
-    __syncthreads();
-    if (!s_last) return false;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return false;
     __threadfence();
     acc = pzero();
-    for (int i = g0 + (int)threadIdx.x; i < g1; i += blockDim.x) acc = padd(acc, ld_part(R.group_part + i));
-    acc = block_sum_part(acc, scratch);
-    if (threadIdx.x == 0) R.sys_cnt[tl.sys] = 0;
+    for (int i = g0 + lane; i < g1; i += 32) acc = padd(acc, ld_part(R.group_part + i));
+    acc = warp_sum_part(acc);
+    if (lane == 0) R.sys_cnt[tl.sys] = 0;
     *total = acc;
     return true;
 }

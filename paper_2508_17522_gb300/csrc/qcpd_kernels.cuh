@@ -78,6 +78,14 @@ __device__ __forceinline__ TileSmem tile_smem(double* base, int rmax) {
     return t;
 }
 
+// Loads of vectors that other CTAs write during the same launch.  In a
+// persistent launch they must bypass the (non-coherent) L1: L1 = false.
+template <bool L1>
+__device__ __forceinline__ double ldv(const double* p) {
+    if (L1) return *p;
+    return __ldcg(p);
+}
+
 // Eight consecutive stored entries starting at an index that is a multiple
 // of 8 (the arrays are padded to a multiple of 8 entries): two 16-byte loads
 // of column indices and 16-byte loads of values.
@@ -108,6 +116,131 @@ __device__ __forceinline__ void load8(const int32_t* col, const float* val, int6
     v[4] = t1.x; v[5] = t1.y; v[6] = t1.z; v[7] = t1.w;
 }
 
+// Row sums of rows [0, rows) whose row pointers (global nonzero indices)
+// are srp[0..rows] in shared memory, into s0[] (zeroed by the caller, all
+// threads synchronised).  The merge-style segmented SpMV described at
+// tile_rowsums; gather(j) returns the vector entry of column j.  Ends with a
+// block barrier.
+template <typename VT, typename GF>
+__device__ __forceinline__ void stream_rowsums(const int64_t* srp, const int rows, const int32_t* mcol,
+                                               const VT* vals, GF gather, double* s0) {
+    const int tid = threadIdx.x;
+    const int64_t K0 = srp[0], K1 = srp[rows];
+    // Each warp owns the rows that start in its eighth of the tile's
+    // nonzeros, so no partial sum crosses a warp and the sweeps below need
+    // only warp-level synchronisation.
+    const int lane = tid & 31, warp = tid >> 5;
+    const int64_t q = (K1 - K0 + kWarps - 1) / kWarps;
+    auto lower = [&](int64_t key) {  // first row whose start is >= key
+        int lo = 0, hi = rows;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (srp[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int w0 = (warp == 0) ? 0 : lower(K0 + warp * q);
+    const int w1 = (warp == kWarps - 1) ? rows : lower(K0 + (warp + 1) * q);
+    if (w1 > w0) {
+        const int64_t WK0 = srp[w0], WK1 = srp[w1];
+        for (int64_t c0 = WK0 & ~(int64_t)(kE - 1); c0 < WK1; c0 += 32 * kE) {
+            const int64_t e0 = c0 + (int64_t)lane * kE;
+            // head: the lane's first row segment; tail: its last (the same
+            // segment when the lane's eight entries lie in one row)
+            int hk = -1, tk = -1;
+            double hv = 0.0, tv = 0.0;
+            if (e0 < WK1 && e0 + kE > WK0) {
+                int32_t c[kE];
+                double v[kE], x[kE];
+                load8(mcol, vals, e0, c, v);
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    const bool ok = (e0 + j >= WK0) && (e0 + j < WK1);
+                    x[j] = ok ? gather(c[j]) : 0.0;
+                }
+                const int64_t kfirst = e0 > WK0 ? e0 : WK0;
+                int lo = w0, hi = w1;  // last row whose start is <= kfirst
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (srp[mid] <= kfirst) lo = mid;
+                    else hi = mid;
+                }
+                // row of each of the eight entries (-1: outside the warp's range)
+                int rr[kE];
+                int i = lo;
+                int64_t rend = srp[i + 1];
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    const int64_t k = e0 + j;
+                    if (k < kfirst || k >= WK1) {
+                        rr[j] = -1;
+                    } else {
+                        while (k >= rend) {
+                            ++i;
+                            rend = srp[i + 1];
+                        }
+                        rr[j] = i;
+                    }
+                }
+                // branch-free FMA chain: restart at every row change
+                double acc = 0.0, part[kE];
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    const bool cont = (j > 0) && (rr[j] == rr[j - 1]);
+                    acc = fma(v[j], x[j], cont ? acc : 0.0);
+                    part[j] = acc;
+                }
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    if (rr[j] >= 0) {
+                        if (hk < 0) hk = rr[j];
+                        tk = rr[j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kE; ++j) {
+                    const bool end = rr[j] >= 0 && (j == kE - 1 || rr[j + 1] != rr[j]);
+                    if (end) {
+                        if (rr[j] == hk) hv = part[j];
+                        if (rr[j] == tk) tv = part[j];
+                        // a row that starts and ends inside this lane's group
+                        if (rr[j] != hk && rr[j] != tk) s0[rr[j]] = part[j];
+                    }
+                }
+            }
+            // Rows crossing lanes: a segmented inclusive scan of the tails
+            // along the lanes.  A chain passes through lanes that hold one
+            // segment of the same row and restarts at a lane with two or
+            // more segments (or a new row); the lane whose head continues a
+            // chain adds the chain's sum to its head.
+            const unsigned full = 0xffffffffu;
+            const bool single = (hk == tk);
+            const int ptk = __shfl_up_sync(full, tk, 1);
+            int f = (lane == 0) || !single || tk != ptk || tk < 0;
+            double S = tv;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const double oS = __shfl_up_sync(full, S, d);
+                const int of = __shfl_up_sync(full, f, d);
+                if (lane >= d && !f) {
+                    S = oS + S;
+                    f = of;
+                }
+            }
+            const double pS = __shfl_up_sync(full, S, 1);
+            const int nhk = __shfl_down_sync(full, hk, 1);
+            if (!single && hk >= 0) {
+                const double h = (lane > 0 && hk == ptk) ? pS + hv : hv;
+                s0[hk] += h;  // the head row closes here
+            }
+            if (tk >= 0 && (lane == 31 || nhk != tk)) s0[tk] += S;  // the tail row's chain ends here
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
 // Row sums h_i = sum_k val_k * gv[col_k] of the tile's rows into sm.s0[].
 //
 // STREAM tiles (merge-style segmented SpMV): the tile's nonzeros are walked
@@ -125,9 +258,9 @@ __device__ __forceinline__ void load8(const int32_t* col, const float* val, int6
 //
 // Returns the number of rows whose sums are complete (0 for a LONG tile
 // that is not the row's last chunk).
-template <typename VT, typename GT>
+template <bool L1, typename VT>
 __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_t* rp, const int32_t* mcol,
-                                            const VT* vals, const GT* gv, const TileSmem& sm, Scratch* scratch,
+                                            const VT* vals, const double* gv, const TileSmem& sm, Scratch* scratch,
                                             int32_t* split_cnt, double* row_part, int long_chunk) {
     const int tid = threadIdx.x;
     const int rows = tl.r1 - tl.r0;
@@ -144,7 +277,7 @@ __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_
 #pragma unroll
             for (int j = 0; j < kE; ++j) {
                 const bool ok = (e + j >= k0) && (e + j < k1);
-                x[j] = ok ? ld(gv + c[j]) : 0.0;
+                x[j] = ok ? ldv<L1>(gv + c[j]) : 0.0;
             }
 #pragma unroll
             for (int j = 0; j < kE; ++j) acc = fma(v[j], x[j], acc);
@@ -175,121 +308,8 @@ __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_
     }
     for (int i = tid; i < rows; i += kThreads) sm.s0[i] = 0.0;
     for (int i = tid; i <= rows; i += kThreads) sm.srp[i] = rp[tl.r0 + i];
-    const int64_t K0 = rp[tl.r0], K1 = rp[tl.r1];
     __syncthreads();
-    // Each warp owns the rows that start in its eighth of the tile's
-    // nonzeros, so no partial sum crosses a warp and the sweeps below need
-    // only warp-level synchronisation.
-    const int lane = tid & 31, warp = tid >> 5;
-    const int64_t q = (K1 - K0 + kWarps - 1) / kWarps;
-    auto lower = [&](int64_t key) {  // first row whose start is >= key
-        int lo = 0, hi = rows;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (sm.srp[mid] < key) lo = mid + 1;
-            else hi = mid;
-        }
-        return lo;
-    };
-    const int w0 = (warp == 0) ? 0 : lower(K0 + warp * q);
-    const int w1 = (warp == kWarps - 1) ? rows : lower(K0 + (warp + 1) * q);
-    if (w1 > w0) {
-        const int64_t WK0 = sm.srp[w0], WK1 = sm.srp[w1];
-        for (int64_t c0 = WK0 & ~(int64_t)(kE - 1); c0 < WK1; c0 += 32 * kE) {
-            const int64_t e0 = c0 + (int64_t)lane * kE;
-            // head: the lane's first row segment; tail: its last (the same
-            // segment when the lane's eight entries lie in one row)
-            int hk = -1, tk = -1;
-            double hv = 0.0, tv = 0.0;
-            if (e0 < WK1 && e0 + kE > WK0) {
-                int32_t c[kE];
-                double v[kE], x[kE];
-                load8(mcol, vals, e0, c, v);
-#pragma unroll
-                for (int j = 0; j < kE; ++j) {
-                    const bool ok = (e0 + j >= WK0) && (e0 + j < WK1);
-                    x[j] = ok ? ld(gv + c[j]) : 0.0;
-                }
-                const int64_t kfirst = e0 > WK0 ? e0 : WK0;
-                int lo = w0, hi = w1;  // last row whose start is <= kfirst
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (sm.srp[mid] <= kfirst) lo = mid;
-                    else hi = mid;
-                }
-                // row of each of the eight entries (-1: outside the warp's range)
-                int rr[kE];
-                int i = lo;
-                int64_t rend = sm.srp[i + 1];
-#pragma unroll
-                for (int j = 0; j < kE; ++j) {
-                    const int64_t k = e0 + j;
-                    if (k < kfirst || k >= WK1) {
-                        rr[j] = -1;
-                    } else {
-                        while (k >= rend) {
-                            ++i;
-                            rend = sm.srp[i + 1];
-                        }
-                        rr[j] = i;
-                    }
-                }
-                // branch-free FMA chain: restart at every row change
-                double acc = 0.0, part[kE];
-#pragma unroll
-                for (int j = 0; j < kE; ++j) {
-                    const bool cont = (j > 0) && (rr[j] == rr[j - 1]);
-                    acc = fma(v[j], x[j], cont ? acc : 0.0);
-                    part[j] = acc;
-                }
-#pragma unroll
-                for (int j = 0; j < kE; ++j) {
-                    if (rr[j] >= 0) {
-                        if (hk < 0) hk = rr[j];
-                        tk = rr[j];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kE; ++j) {
-                    const bool end = rr[j] >= 0 && (j == kE - 1 || rr[j + 1] != rr[j]);
-                    if (end) {
-                        if (rr[j] == hk) hv = part[j];
-                        if (rr[j] == tk) tv = part[j];
-                        // a row that starts and ends inside this lane's group
-                        if (rr[j] != hk && rr[j] != tk) sm.s0[rr[j]] = part[j];
-                    }
-                }
-            }
-            // Rows crossing lanes: a segmented inclusive scan of the tails
-            // along the lanes.  A chain passes through lanes that hold one
-            // segment of the same row and restarts at a lane with two or
-            // more segments (or a new row); the lane whose head continues a
-            // chain adds the chain's sum to its head.
-            const unsigned full = 0xffffffffu;
-            const bool single = (hk == tk);
-            const int ptk = __shfl_up_sync(full, tk, 1);
-            int f = (lane == 0) || !single || tk != ptk || tk < 0;
-            double S = tv;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const double oS = __shfl_up_sync(full, S, d);
-                const int of = __shfl_up_sync(full, f, d);
-                if (lane >= d && !f) {
-                    S = oS + S;
-                    f = of;
-                }
-            }
-            const double pS = __shfl_up_sync(full, S, 1);
-            const int nhk = __shfl_down_sync(full, hk, 1);
-            if (!single && hk >= 0) {
-                const double h = (lane > 0 && hk == ptk) ? pS + hv : hv;
-                sm.s0[hk] += h;  // the head row closes here
-            }
-            if (tk >= 0 && (lane == 31 || nhk != tk)) sm.s0[tk] += S;  // the tail row's chain ends here
-            __syncwarp();
-        }
-    }
-    __syncthreads();
+    stream_rowsums(sm.srp, rows, mcol, vals, [&](int32_t c) { return ldv<L1>(gv + c); }, sm.s0);
     return rows;
 }
 
@@ -303,14 +323,15 @@ __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_
 //            multiplications by 1 on the scarce FP64 pipe)
 // The CTA that completes a system also updates its tau entry and the LSQR
 // scalars (Paige & Saunders 1982, algorithm LSQR).
-template <int PASS, int ROLE, bool SC, typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
-    extern __shared__ double smem[];
-    __shared__ Scratch scratch;
-    const int ti = blockIdx.x;
+// The work of one tile in one pass (and, in the CTA that completes its
+// system, the system's finisher).  Every thread of the CTA calls it; it
+// returns in a CTA-uniform way except for the finisher, which only thread 0
+// runs, so callers synchronise before touching shared memory again.
+template <int PASS, int ROLE, bool SC, bool L1, typename T>
+__device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, double* smem, Scratch& scratch) {
     const Tile tl = a.tiles[ti];
     const Sys sy = a.sys[tl.sys];
-    LsqrState* st = a.state + tl.sys;
+    volatile LsqrState* st = a.state + tl.sys;
     const int status = st->status;
     if (ROLE != ROLE_RES && status == S_DONE) return;
     const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
@@ -331,20 +352,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
     double* W = a.W + sy.voff;
     double* X = a.X + sy.voff;
     double* XI = a.XI + sy.voff;
-    const double alpha = st->alpha, beta = st->beta;
+    // the finisher of the previous pass stored this pass's coefficients, so
+    // no tile divides (FP64 division is a long dependent chain here)
     double c1, c2;
     if (ROLE == ROLE_U) {
-        c1 = 1.0 / alpha;
-        c2 = alpha / beta;
+        c1 = st->uc1;
+        c2 = st->uc2;
     } else if (ROLE == ROLE_V) {
-        c1 = beta > 0.0 ? 1.0 / beta : 0.0;
-        c2 = st->first ? 0.0 : beta / alpha;
+        c1 = st->vc1;
+        c2 = st->vc2;
     } else {
         c1 = 1.0;
         c2 = 0.0;
     }
     const double wcoef = st->wcoef, xcoef = st->xcoef;
-    const double tin = in[N - 1];  // tau entry of the input vector
+    const double tin = ldv<L1>(in + N - 1);  // tau entry of the input vector
     // the t-column term: (scaled) tau entry of the input
     const double tt = SC ? (PASS == PASS_G ? cd[N - 1] : rw[N - 1]) * tin : tin;
 
@@ -354,49 +376,49 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
         if (tl.kind == TILE_LONG && tl.cb0 != 0) rows = 0;  // one chunk updates the row
         for (int i = threadIdx.x; i < rows; i += kThreads) {
             const int r = tl.r0 + i;
-            X[r] = fma(xcoef, W[r], X[r]);
+            X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
         }
     } else {
         const int64_t* rp = a.mrowptr + pr.mrow;
         if (PASS == PASS_G)
-            rows = tile_rowsums(tl, ti, rp, a.mcol, a.mvalG, XI, sm, &scratch, a.split_cnt, a.row_part,
-                                a.long_chunk);
+            rows = tile_rowsums<L1>(tl, ti, rp, a.mcol, a.mvalG, XI, sm, &scratch, a.split_cnt, a.row_part,
+                                    a.long_chunk);
         else
-            rows = tile_rowsums(tl, ti, rp, a.mcol, a.mvalT, in, sm, &scratch, a.split_cnt, a.row_part,
-                                a.long_chunk);
+            rows = tile_rowsums<L1>(tl, ti, rp, a.mcol, a.mvalT, in, sm, &scratch, a.split_cnt, a.row_part,
+                                    a.long_chunk);
         double ss = 0.0, dtop = 0.0, dbot = 0.0;
         if (PASS == PASS_G) {
             for (int i = threadIdx.x; i < rows; i += kThreads) {
                 const int r = tl.r0 + i;
-                const double iv = in[r];
+                const double iv = ldv<L1>(in + r);
                 double o;
                 if (r < n) {
                     o = fma(ld(cA + r), tt, s0[i]);
                     dtop = fma(ld(cB + r), SC ? cd[r] * iv : iv, dtop);
                 } else {
-                    const double xi = XI[r];
+                    const double xi = ldv<L1>(XI + r);
                     const double dxi = SC ? cd[r] * (xi - iv) : xi - iv;
                     o = fma(-ld(cA + r), tt, s0[i]) + dxi;
                     dbot = fma(ld(cB + r), SC ? cd[r] * xi : xi, dbot);
                 }
                 if (SC) o *= rw[r];
                 if (ROLE == ROLE_RES) {
-                    double e = o - a.RHS[sy.voff + r];
+                    double e = o - ldv<L1>(a.RHS + sy.voff + r);
                     if (SC) e /= rw[r];
                     ss = fma(e, e, ss);
                 } else {
-                    const double nv = fma(c1, o, -c2 * outv[r]);
+                    const double nv = fma(c1, o, -c2 * ldv<L1>(outv + r));
                     outv[r] = nv;
                     ss = fma(nv, nv, ss);
-                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * W[r]);
-                    else X[r] = fma(xcoef, W[r], X[r]);
+                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * ldv<L1>(W + r));
+                    else X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
                 }
             }
         } else {
             // G^T: top rows M rho - g r3; bottom rows D(M rho - b r3 + r2) - r2 (rho = W in)
             for (int i = threadIdx.x; i < rows; i += kThreads) {
                 const int r = tl.r0 + i;
-                const double iv = SC ? rw[r] * in[r] : in[r];
+                const double iv = SC ? rw[r] * ldv<L1>(in + r) : ldv<L1>(in + r);
                 const double h = fma(-ld(cB + r), tt, s0[i]);
                 if (r < n) {
                     s1[i] = h;
@@ -413,20 +435,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
             __syncthreads();
             for (int i = threadIdx.x; i < rows; i += kThreads) {
                 const int r = tl.r0 + i;
-                const double iv = in[r];
+                const double iv = ldv<L1>(in + r);
                 double o = (r < n) ? s2[i] : s2[i] - (SC ? rw[r] * iv : iv);
                 if (SC) o *= cd[r];
                 if (ROLE == ROLE_RES) {
-                    double e = o - a.RHS[sy.voff + r];
+                    double e = o - ldv<L1>(a.RHS + sy.voff + r);
                     if (SC) e /= cd[r];
                     ss = fma(e, e, ss);
                 } else {
-                    const double nv = fma(c1, o, -c2 * outv[r]);
+                    const double nv = fma(c1, o, -c2 * ldv<L1>(outv + r));
                     outv[r] = nv;
                     s1[i] = nv;
                     ss = fma(nv, nv, ss);
-                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * W[r]);
-                    else X[r] = fma(xcoef, W[r], X[r]);
+                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * ldv<L1>(W + r));
+                    else X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
                 }
             }
             if (ROLE != ROLE_RES) {
@@ -445,9 +467,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
     if (threadIdx.x != 0) return;
 
     // ---- the system's finisher: tau entry and LSQR scalars ----
+    __threadfence();
     const int rN = N - 1;
     if (only_x) {
-        X[rN] = fma(xcoef, W[rN], X[rN]);
+        X[rN] = fma(xcoef, ldv<L1>(W + rN), ldv<L1>(X + rN));
         st->status = S_DONE;
         atomicSub(a.active, 1);
         return;
@@ -470,30 +493,34 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
     if (ROLE == ROLE_RES) {
         double ss = tot.a;
         if (PASS == PASS_G) {
-            double e = oN - a.RHS[sy.voff + rN];
+            double e = oN - ldv<L1>(a.RHS + sy.voff + rN);
             if (SC) e /= rw[rN];
             ss += e * e;
         }
         st->resid_true = st->bnorm_true > 0.0 ? sqrt(ss) / st->bnorm_true : 0.0;
         return;
     }
-    const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * outv[rN];
+    const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * ldv<L1>(outv + rN);
     outv[rN] = nvN;
     if (PASS == PASS_GT) XI[rN] = 0.0;
     const double nrm = sqrt(tot.a + nvN * nvN);
     if (ROLE == ROLE_U) {
-        W[rN] = tin * c1 - wcoef * W[rN];
+        W[rN] = tin * c1 - wcoef * ldv<L1>(W + rN);
         // rotation eliminating beta_{k+1}
         const double rhobar = st->rhobar;
-        const double rho = hypot(rhobar, nrm);
-        const double c = rhobar / rho, s = nrm / rho;
-        const double phi = c * st->phibar;
-        st->phibar = s * st->phibar;
-        st->rho = rho;
+        const double rho = sqrt(rhobar * rhobar + nrm * nrm);
+        const double inv = 1.0 / rho;
+        const double c = rhobar * inv, s = nrm * inv;
+        const double phibar = st->phibar;
+        const double phi = c * phibar;
+        st->phibar = s * phibar;
+        st->inv_rho = inv;
         st->c = c;
         st->s = s;
-        st->xcoef = phi / rho;
+        st->xcoef = phi * inv;
         st->beta = nrm;
+        st->vc1 = nrm > 0.0 ? 1.0 / nrm : 0.0;  // next v-update: 1/beta, beta/alpha
+        st->vc2 = nrm * st->uc1;
         st->iters += 1;
         if (!isfinite(rho) || !isfinite(phi) || rho == 0.0) {
             st->outcome = O_BREAKDOWN;
@@ -507,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
             st->status = S_FINAL;
         }
     } else {
-        X[rN] = fma(xcoef, W[rN], X[rN]);
+        X[rN] = fma(xcoef, ldv<L1>(W + rN), ldv<L1>(X + rN));
         if (st->first) {
             st->rhobar = nrm;
             st->phibar = st->beta;
@@ -515,9 +542,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
             st->first = 0;
         } else {
             st->rhobar = -st->c * nrm;
-            st->wcoef = (st->s * nrm) / st->rho;
+            st->wcoef = (st->s * nrm) * st->inv_rho;
         }
         st->alpha = nrm;
+        st->uc1 = nrm > 0.0 ? 1.0 / nrm : 0.0;  // next u-update: 1/alpha, alpha/beta
+        st->uc2 = nrm * st->vc1;
         if (!(nrm > 0.0) || !isfinite(nrm)) {
             // A^T r = 0: the current x solves the least-squares problem
             if (!isfinite(nrm)) st->outcome = O_BREAKDOWN;
@@ -525,6 +554,82 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
             st->status = S_DONE;
             atomicSub(a.active, 1);
         }
+    }
+}
+
+template <int PASS, int ROLE, bool SC, typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
+    extern __shared__ double smem[];
+    __shared__ Scratch scratch;
+    run_tile<PASS, ROLE, SC, true, T>(a, blockIdx.x, smem, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form: all LSQR iterations of all systems in one cooperative
+// launch.  Each CTA owns the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// and runs them pass after pass; a grid barrier separates the passes (the
+// CTA that completes a system still updates its scalars inside the pass).
+// Every wait is bounded: after kSpinLimit polls the waiting CTA records a
+// timeout in *err and returns, and so do the others at their next barrier.
+struct PersistCtl {
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* stop;
+    int* err;
+    int64_t max_iters;
+};
+
+constexpr unsigned long long kSpinLimit = 1ull << 24;  // about 1 s with 64 ns naps
+
+__device__ __forceinline__ bool grid_sync(const PersistCtl& c, const int* active) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = c.bar_gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned prev = atomicAdd(c.bar_count, 1u);
+        if (prev == gridDim.x - 1) {
+            *c.bar_count = 0;  // nobody arrives again before the release below
+            *(volatile int*)c.stop = (*(volatile const int*)active <= 0) ? 1 : 0;
+            __threadfence();
+            atomicAdd(c.bar_gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > kSpinLimit) {
+                    atomicExch(c.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*(volatile int*)c.err == 0) && (*(volatile int*)c.stop == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int MODE, bool SC, typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_persist(PlanView<T> a, PersistCtl c, int ntiles) {
+    extern __shared__ double smem[];
+    __shared__ Scratch scratch;
+    constexpr int PU = MODE == 0 ? PASS_G : PASS_GT;   // u-update pass
+    constexpr int PV = MODE == 0 ? PASS_GT : PASS_G;   // v-update pass
+    for (int64_t it = 0; it < c.max_iters; ++it) {
+        for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+            run_tile<PU, ROLE_U, SC, false, T>(a, ti, smem, scratch);
+            __syncthreads();
+        }
+        if (!grid_sync(c, a.active)) return;
+        for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+            run_tile<PV, ROLE_V, SC, false, T>(a, ti, smem, scratch);
+            __syncthreads();
+        }
+        if (!grid_sync(c, a.active)) return;
     }
 }
 
@@ -552,6 +657,8 @@ __device__ __forceinline__ void init_state(LsqrState* st, int* active, double bn
     q.maxiter = maxiter;
     q.first = 1;
     q.resid_true = -1.0;
+    q.vc1 = bn > 0.0 ? 1.0 / bn : 0.0;  // the first v-update: v = G^T u / beta
+    q.vc2 = 0.0;
     if (bn > 0.0 && isfinite(bn)) {
         q.status = S_ACTIVE;
         q.outcome = O_RUNNING;

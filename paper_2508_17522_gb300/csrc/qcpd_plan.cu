@@ -654,6 +654,7 @@ int build_schedule(qcp_plan* p) {
     p->nsys_cap = nsys;
     p->nsplit = nsplit;
     QCP_TRY(p->d_split_cnt.alloc(std::max(1, nsplit) * sizeof(int32_t)));
+    QCP_TRY(p->d_pctl.alloc(4 * sizeof(int32_t)));
     QCP_TRY(p->d_row_part.alloc(std::max<size_t>(1, all.size()) * sizeof(double)));
     QCP_CUDA(cudaMemsetAsync(p->d_split_cnt.p, 0, std::max(1, nsplit) * sizeof(int32_t), p->stream));
     p->ntiles = (int)all.size();

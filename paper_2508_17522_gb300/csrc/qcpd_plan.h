@@ -113,6 +113,7 @@ struct qcp_plan {
     int nsplit = 0;          // rows cut into several LONG chunks (over all systems)
     qcpd::DevBuf d_sys, d_tiles, d_groups, d_state, d_tpart, d_gpart, d_gcnt, d_scnt, d_active;
     qcpd::DevBuf d_split_cnt, d_row_part;
+    qcpd::DevBuf d_pctl;     // persistent mode: barrier count, generation, stop flag, error flag
     qcpd::DevBuf d_U, d_V, d_W, d_X, d_XI, d_RHS;
     int* h_active = nullptr;  // pinned
 

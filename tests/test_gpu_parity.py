@@ -138,6 +138,32 @@ def test_config2_schedules_agree(q, cfg2):
     plan.close()
 
 
+@pytest.mark.parametrize("precond", ["none", "equilibrate"])
+def test_persistent_matches_launch_per_pass(q, cfg2, precond):
+    """One cooperative launch for the whole Krylov loop gives the same
+    results as one launch per pass (same kernels, same reduction order)."""
+    prob, dirs, ref_j, ref_v = cfg2
+    k = 4
+    plan = _plan(q, prob, max_rhs=k)
+    cat = lambda name: np.concatenate([getattr(d, name) for d in dirs[:k]])
+    res = {}
+    for persistent in (False, True):
+        opts = q.options(rtol=1e-10, precond=precond, persistent=persistent)
+        dx, dy, ds, ji = q.qcp_derivative_jvp_multi(plan, k, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
+        gP, gA, gq, gb, vi = q.qcp_derivative_vjp_multi(plan, k, cat("wx"), cat("wy"), cat("ws"), opts)
+        res[persistent] = (to_np(dx, dy, ds, gP, gA, gq, gb), ji, vi)
+        assert all(i["status"] == "QCP_OK" for i in ji + vi), (ji, vi)
+    a, b = res[False][0], res[True][0]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    n, m = prob.n, prob.m
+    dx, dy, ds = res[True][0][:3]
+    for i in range(k):
+        got = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
+        assert rel_err(got, ref_j[i]) < TOL64
+    plan.close()
+
+
 def test_determinism_and_graph(q):
     prob = g.small_qcp(30, 40, 5, 30, (3, 5, 9))
     d = g.make_directions(prob, 3)
@@ -161,6 +187,11 @@ def test_batched_uneven_problems(q):
     gP, gA, gq, gb, vi = q.qcp_derivative_vjp(plan, cat("wx"), cat("wy"), cat("ws"), opts)
     dx, dy, ds, gP, gA, gq, gb = to_np(dx, dy, ds, gP, gA, gq, gb)
     on = om = op = oa = 0
+    # the persistent form gives the same answers on uneven problems
+    po = q.options(rtol=1e-13, persistent=True)
+    pdx, pdy, pds, pji = q.qcp_derivative_jvp(plan, cat("dP"), cat("dA"), cat("dq"), cat("db"), po)
+    for x, y in zip(to_np(pdx, pdy, pds), (dx, dy, ds)):
+        assert np.array_equal(x, y)
     for p, d, a, b in zip(probs, dirs, ji, vi):
         fac = D.DenseFactor(p)
         rj = D.jvp_dense(p, d, fac)[:3]
