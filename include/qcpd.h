@@ -123,6 +123,23 @@ typedef enum {
                                    left out of the norms (any positive diagonal is a valid choice) */
 } qcp_precond;
 
+/* How the Krylov iterations are run on the GPU (all give the same iterates up
+   to rounding order; QCP_ENGINE_PASSES and QCP_ENGINE_PERSISTENT give
+   bit-identical ones). */
+typedef enum {
+    QCP_ENGINE_PASSES = 0,      /* one launch per half-iteration over all tiles of all systems,
+                                   replayed from CUDA graphs in chunks of check_every */
+    QCP_ENGINE_PERSISTENT = 1,  /* every iteration of all systems in one cooperative launch,
+                                   grid-wide barriers between passes, each wait bounded (a barrier
+                                   that times out returns QCP_ERR_TIMEOUT) */
+    QCP_ENGINE_CLUSTER = 2,     /* one thread-block cluster per system runs all of its iterations
+                                   in one launch; the Krylov vectors live in the cluster's shared
+                                   memory and only hardware cluster barriers separate passes.
+                                   Needs every system to fit (about 8 N + 56 N / C bytes per CTA
+                                   for C CTAs); QCP_ERR_ARG otherwise */
+    QCP_ENGINE_AUTO = 3         /* QCP_ENGINE_CLUSTER when every system fits, else PASSES */
+} qcp_engine;
+
 typedef struct {
     int32_t solver;           /* 0 = LSQR (the only solver built) */
     double rtol;              /* target for ||F dz + dN|| / ||dN|| (JVP) or ||F^T r + g|| / ||g|| (VJP) */
@@ -134,10 +151,7 @@ typedef struct {
                                  tolerance (at most 4 times, while it keeps halving); 0 = trust the
                                  Krylov estimate */
     int32_t precond;          /* qcp_precond */
-    int32_t persistent;       /* 1 = run the Krylov iterations of all systems in one cooperative
-                                 launch (grid-wide barriers between passes, every wait bounded;
-                                 a barrier that times out returns QCP_ERR_TIMEOUT); 0 = one launch
-                                 per pass, replayed from CUDA graphs */
+    int32_t engine;           /* qcp_engine */
     double kink_tol;          /* QCP_WARN_NEAR_KINK threshold on info.kink_margin */
 } qcp_options;
 
@@ -155,8 +169,8 @@ typedef struct qcp_plan qcp_plan;
 const char* qcp_last_error(void);
 
 /* Fill *opts with defaults: LSQR, rtol 1e-10, maxiter 100000, check_every 32,
-   use_graph 1, compute_residual 1, precond QCP_PRECOND_NONE, persistent 0,
-   kink_tol 0. */
+   use_graph 1, compute_residual 1, precond QCP_PRECOND_NONE,
+   engine QCP_ENGINE_AUTO, kink_tol 0. */
 void qcp_default_options(qcp_options* opts);
 
 /* Library version as an integer (major * 10000 + minor * 100 + patch). */
@@ -227,15 +241,27 @@ int qcp_derivative_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k,
                              qcp_info* info);
 
 /*
- * Tile schedule of a plan: tile_nnz is the target number of nonzeros of M
- * per tile (rows are grouped into tiles, never splitting an SOC block); a row
- * with more than long_row nonzeros leaves its tile and is cut into pieces of
- * long_chunk nonzeros, one CTA each.  Rebuilds the schedule and the Krylov
- * workspace (and drops captured graphs).  Defaults 4096, 512, 4096.  Used by
- * the autotuner.  Errors: QCP_ERR_ARG (tile_nnz < 64, long_row < 1,
+ * Tile schedule of a plan (QCP_ENGINE_PASSES and _PERSISTENT): tile_nnz is
+ * the target number of nonzeros of M per tile (rows are grouped into tiles,
+ * never splitting an SOC block); a row with more than long_row nonzeros
+ * leaves its tile and is cut into pieces of long_chunk nonzeros, one CTA
+ * each.  Rebuilds the schedule and the Krylov workspace (and drops captured
+ * graphs).  Defaults 4096, 512, 1 << 20.  Results are bit-reproducible from
+ * run to run unless a row is cut into several pieces: the piece that
+ * finishes last adds the row's terms to the pass's sums, so their position
+ * in the summation (and the last bit of the result) depends on scheduling.
+ * Used by the autotuner.  Errors: QCP_ERR_ARG (tile_nnz < 64, long_row < 1,
  * long_chunk < 32), QCP_ERR_ALLOC.
  */
 int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, int32_t long_chunk);
+
+/* CTAs per system under QCP_ENGINE_CLUSTER: 1 to 16 (above 8 is a
+   non-portable cluster size), or 0 (the default) to choose per call: the
+   most CTAs, up to 8, with which every system's cluster is resident at once
+   (as the occupancy calculator reports it for this GPU).  A problem whose
+   vectors need more CTAs' shared memory gets the smallest size that holds
+   them.  Returns QCP_ERR_ARG for other values. */
+int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas);
 
 /* Number of kernel launches made by the most recent JVP/VJP call of the plan
    (graph replays counted per kernel node). */

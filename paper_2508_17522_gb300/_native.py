@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "QCP_OK", 1: "QCP_ERR_ARG", 2: "QCP_ERR_CUDA", 3: "QCP_ERR_AL
                 7: "QCP_WARN_NEAR_KINK"}
 QCP_F64, QCP_F32 = 0, 1
 QCP_PRECOND_NONE, QCP_PRECOND_EQUILIBRATE = 0, 1
+QCP_ENGINE_PASSES, QCP_ENGINE_PERSISTENT, QCP_ENGINE_CLUSTER, QCP_ENGINE_AUTO = 0, 1, 2, 3
 
 
 class qcp_csr(ctypes.Structure):
@@ -40,7 +41,7 @@ class qcp_solution(ctypes.Structure):
 class qcp_options(ctypes.Structure):
     _fields_ = [("solver", c_int32), ("rtol", c_double), ("maxiter", c_int64), ("check_every", c_int32),
                 ("use_graph", c_int32), ("compute_residual", c_int32), ("precond", c_int32),
-                ("persistent", c_int32), ("kink_tol", c_double)]
+                ("engine", c_int32), ("kink_tol", c_double)]
 
 
 class qcp_info(ctypes.Structure):
@@ -87,6 +88,8 @@ def lib():
         f.argtypes = [c_void_p, P(qcp_options), c_int32] + [c_void_p] * 7 + [P(qcp_info)]
     L.qcp_plan_set_schedule.restype = ctypes.c_int
     L.qcp_plan_set_schedule.argtypes = [c_void_p, c_int32, c_int32, c_int32]
+    L.qcp_plan_set_cluster.restype = ctypes.c_int
+    L.qcp_plan_set_cluster.argtypes = [c_void_p, c_int32]
     L.qcp_plan_last_launches.restype = c_int64
     L.qcp_plan_last_launches.argtypes = [c_void_p]
     L.qcp_plan_last_timing.restype = ctypes.c_int

@@ -96,16 +96,21 @@ def _c_problem(pt: ProblemTensors):
 _PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE}
 
 
+_ENGINE = {"passes": N.QCP_ENGINE_PASSES, "persistent": N.QCP_ENGINE_PERSISTENT,
+           "cluster": N.QCP_ENGINE_CLUSTER, "auto": N.QCP_ENGINE_AUTO}
+
+
 def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_residual=True, precond="none",
-            kink_tol=0.0, persistent=False):
+            kink_tol=0.0, engine="auto"):
     """qcp_options; precond is "none" (the plain method) or "equilibrate";
-    persistent=True runs the Krylov loop in one cooperative launch."""
+    engine is "passes" (one launch per pass), "persistent" (one cooperative
+    launch), "cluster" (one thread-block cluster per system) or "auto"."""
     o = N.qcp_options()
     N.lib().qcp_default_options(ctypes.byref(o))
     o.rtol, o.maxiter, o.check_every = float(rtol), int(maxiter), int(check_every)
     o.use_graph, o.compute_residual, o.kink_tol = int(bool(use_graph)), int(bool(compute_residual)), float(kink_tol)
     o.precond = _PRECOND[precond] if isinstance(precond, str) else int(precond)
-    o.persistent = int(bool(persistent))
+    o.engine = _ENGINE[engine] if isinstance(engine, str) else int(engine)
     return o
 
 
@@ -170,7 +175,11 @@ class Plan:
         _check(N.lib().qcp_plan_last_timing(self._h, ctypes.byref(ms), ctypes.byref(n)), "qcp_plan_last_timing")
         return ms.value, n.value
 
-    def set_schedule(self, tile_nnz: int = 4096, long_row: int = 512, long_chunk: int = 4096):
+    def set_cluster(self, max_ctas: int = 0):
+        """CTAs per system of the cluster engine (0: chosen per call)."""
+        _check(N.lib().qcp_plan_set_cluster(self._h, int(max_ctas)), "qcp_plan_set_cluster")
+
+    def set_schedule(self, tile_nnz: int = 4096, long_row: int = 512, long_chunk: int = 1 << 20):
         _check(N.lib().qcp_plan_set_schedule(self._h, int(tile_nnz), int(long_row), int(long_chunk)),
                "qcp_plan_set_schedule")
 

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "qcpd_cluster.h"
 #include "qcpd_kernels.cuh"
 #include "qcpd_plan.h"
 
@@ -189,7 +190,7 @@ static int iterate(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int nt
     return QCP_OK;
 }
 
-// All remaining iterations in one cooperative launch (qcp_options.persistent).
+// All remaining iterations in one cooperative launch (QCP_ENGINE_PERSISTENT).
 template <typename T>
 static int iterate_persistent(qcp_plan* p, int mode, const PlanView<T>& v, int ntiles, size_t smem,
                               const qcp_options& opts) {
@@ -281,6 +282,23 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         set_error("precond must be QCP_PRECOND_NONE or QCP_PRECOND_EQUILIBRATE");
         return QCP_ERR_ARG;
     }
+    if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_AUTO) {
+        set_error("engine must be one of QCP_ENGINE_PASSES, _PERSISTENT, _CLUSTER, _AUTO");
+        return QCP_ERR_ARG;
+    }
+    int engine = opts.engine;
+    if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO) {
+        bool fits = false;
+        QCP_TRY(cluster_ready(p, nsys, &fits));
+        if (fits) {
+            engine = QCP_ENGINE_CLUSTER;
+        } else if (engine == QCP_ENGINE_CLUSTER) {
+            set_error("cluster engine: a problem's vectors do not fit in the shared memory of 16 CTAs");
+            return QCP_ERR_ARG;
+        } else {
+            engine = QCP_ENGINE_PASSES;
+        }
+    }
     cudaStream_t st = p->stream;
     const bool scaled = opts.precond == QCP_PRECOND_EQUILIBRATE;
     const PlanView<T> v = view<T>(p, scaled);
@@ -300,7 +318,8 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
     QCP_CUDA(cudaGetLastError());
     p->last_launches += 2;
     auto run_iterations = [&]() -> int {
-        if (opts.persistent) return iterate_persistent<T>(p, mode, v, ntiles, smem, opts);
+        if (engine == QCP_ENGINE_PERSISTENT) return iterate_persistent<T>(p, mode, v, ntiles, smem, opts);
+        if (engine == QCP_ENGINE_CLUSTER) return iterate_cluster<T>(p, mode, nsys, v, opts);
         return iterate<T>(p, mode, nsys, v, ntiles, smem, opts);
     };
     QCP_TRY(run_iterations());
@@ -338,10 +357,10 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         p->last_launches += 1;
         QCP_TRY(run_iterations());
     }
-    if (opts.persistent) {
+    if (engine != QCP_ENGINE_PASSES) {
         int64_t it = 0;
         for (int s = 0; s < nsys; ++s) it = std::max<int64_t>(it, hs[s].iters);
-        p->pass_launches = 2 * it;  // passes the persistent launches ran
+        p->pass_launches = 2 * it;  // passes the single-launch engines ran
     }
     int rc = QCP_OK;
     for (int s = 0; s < nsys; ++s) {
@@ -647,7 +666,7 @@ void qcp_default_options(qcp_options* o) {
     o->use_graph = 1;
     o->compute_residual = 1;
     o->precond = QCP_PRECOND_NONE;
-    o->persistent = 0;
+    o->engine = QCP_ENGINE_AUTO;
     o->kink_tol = 0.0;
 }
 
@@ -724,6 +743,15 @@ int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, in
     plan->long_row = long_row;
     plan->long_chunk = long_chunk;
     return build_schedule(plan);
+}
+
+int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas) {
+    if (!plan || max_ctas < 0 || max_ctas > kMaxCluster) {
+        set_error("cluster size must be 0 (automatic) or 1 to 16");
+        return QCP_ERR_ARG;
+    }
+    plan->cluster_cap = max_ctas;
+    return QCP_OK;
 }
 
 int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }

@@ -1,0 +1,413 @@
+// Host side of the cluster engine: per-problem row splits, the gather-buffer
+// column map, and the launches (one per cluster size present in a call).
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "qcpd_cluster.h"
+
+namespace qcpd {
+
+// Weight of one row against one stored entry when balancing CTAs: the
+// epilogue spends about eight FP64 operations per row, the row sums one per
+// stored entry.
+constexpr double kRowWeight = 8.0;
+
+// Slot -> (gather-buffer column, values) of the SELL-32 copy: column j of M
+// lives at poff[r] + j - split[r] of the gather buffer, r the CTA owning row
+// j; padding slots point at the zero slot FN with value 0.
+template <typename T>
+__device__ __forceinline__ void sell_put(int64_t slot, int64_t src, const ClusterProb& cp, const int32_t* mcol,
+                                         const T* mval, const T* mvalG, const T* mvalT, int32_t* scol, T* sval,
+                                         T* svalG, T* svalT) {
+    if (src < 0) {
+        scol[slot] = cp.FN;
+        sval[slot] = (T)0;
+        svalG[slot] = (T)0;
+        svalT[slot] = (T)0;
+        return;
+    }
+    const int j = mcol[src];
+    int lo = 0, hi = cp.C;  // the last r with split[r] <= j
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cp.split[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    scol[slot] = cp.poff[lo] + (j - cp.split[lo]);
+    sval[slot] = mval[src];
+    svalG[slot] = mvalG[src];
+    svalT[slot] = mvalT[src];
+}
+
+// One warp per slice.
+template <typename T>
+__global__ void k_sell_fill(const SellSlice* sl, int64_t nsl, const int32_t* perm, const int32_t* sl_prob,
+                            const int32_t* sl_r0, const ClusterProb* cps, const Prob* probs, const int64_t* mrowptr,
+                            const int32_t* mcol, const T* mval, const T* mvalG, const T* mvalT, int32_t* scol,
+                            T* sval, T* svalG, T* svalT) {
+    const int lane = threadIdx.x & 31;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nsl) return;
+    const SellSlice d = sl[s];
+    const ClusterProb cp = cps[sl_prob[s]];
+    const int64_t* rp = mrowptr + probs[sl_prob[s]].mrow;
+    const int R0 = sl_r0[s];
+    if (d.row >= 0) {
+        const int64_t k0 = rp[R0 + d.row], len = rp[R0 + d.row + 1] - k0;
+        for (int64_t j = lane; j < (int64_t)d.width * 32; j += 32)
+            sell_put(d.base + j, j < len ? k0 + j : -1, cp, mcol, mval, mvalG, mvalT, scol, sval, svalG, svalT);
+    } else {
+        const int row = perm[d.pidx + lane];
+        int64_t k0 = 0, len = 0;
+        if (row >= 0) {
+            k0 = rp[R0 + row];
+            len = rp[R0 + row + 1] - k0;
+        }
+        for (int k = 0; k < d.width; ++k)
+            sell_put(d.base + 32 * (int64_t)k + lane, k < len ? k0 + k : -1, cp, mcol, mval, mvalG, mvalT, scol,
+                     sval, svalG, svalT);
+    }
+}
+
+// Cut problem pi's n + m rows into C ranges of about equal weight, never
+// inside a second-order-cone block and of at most lcap rows each.  Returns
+// false when C such ranges cannot hold the rows.
+static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterProb& cp) {
+    const Prob& pr = p->hprob[pi];
+    const int n = pr.n, Nx = pr.n + pr.m;
+    const int64_t* rp = p->h_mrowptr.data() + pr.mrow;
+    // cut candidates: the end of every row outside SOC blocks and of every SOC block
+    std::vector<int> ends, socs;
+    ends.reserve(Nx);
+    socs.reserve(Nx);
+    int row = 0, nsb = 0;
+    for (; row < n; ++row) {
+        ends.push_back(row + 1);
+        socs.push_back(0);
+    }
+    for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
+        const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
+        if (t == QCP_CONE_SOC) {
+            row += d;
+            ++nsb;
+            ends.push_back(row);
+            socs.push_back(nsb);
+        } else {
+            for (int k = 0; k < d; ++k) {
+                ends.push_back(++row);
+                socs.push_back(nsb);
+            }
+        }
+    }
+    std::memset(&cp, 0, sizeof(cp));
+    cp.C = C;
+    const double total = (double)(rp[Nx] - rp[0]) + kRowWeight * Nx;
+    int k = 1, start = 0;
+    for (size_t u = 0; u < ends.size() && k < C; ++u) {
+        const int e = ends[u];
+        // a range also closes before its next unit would take it past lcap rows
+        const int next = (u + 1 < ends.size()) ? ends[u + 1] : e;
+        const double acc = (double)(rp[e] - rp[0]) + kRowWeight * e;
+        while (k < C && (acc >= total * k / C || next - start > lcap)) {
+            cp.split[k] = e;
+            cp.cb[k] = socs[u];
+            start = e;
+            ++k;
+        }
+    }
+    for (; k <= kMaxCluster; ++k) {
+        cp.split[k] = Nx;
+        cp.cb[k] = nsb;
+    }
+    int L = 0;
+    cp.poff[0] = 0;
+    for (int r = 0; r < kMaxCluster; ++r) {
+        const int len = (r < C) ? cp.split[r + 1] - cp.split[r] : 0;
+        L = std::max(L, len);
+        cp.poff[r + 1] = cp.poff[r] + even_up(len);
+    }
+    cp.FN = cp.poff[C];
+    cp.L = L;
+    return L <= lcap;
+}
+
+template <typename K>
+static void max_static_smem(K k, size_t& s) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) s = std::max(s, fa.sharedSizeBytes);
+}
+
+// Dynamic shared memory one CTA of the cluster kernels may use.
+static int cluster_smem_limit(size_t* out) {
+    int dev = 0, optin = 0;
+    QCP_CUDA(cudaGetDevice(&dev));
+    QCP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    size_t st = 0;
+    max_static_smem(k_cluster<0, false, double>, st);
+    max_static_smem(k_cluster<0, true, double>, st);
+    max_static_smem(k_cluster<1, false, double>, st);
+    max_static_smem(k_cluster<1, true, double>, st);
+    max_static_smem(k_cluster<0, false, float>, st);
+    max_static_smem(k_cluster<0, true, float>, st);
+    max_static_smem(k_cluster<1, false, float>, st);
+    max_static_smem(k_cluster<1, true, float>, st);
+    *out = (size_t)optin > st ? (size_t)optin - st : 0;
+    return QCP_OK;
+}
+
+// Clusters of C CTAs of the cluster kernel that can be resident at once.
+static int max_active_clusters(int C) {
+    static int cache[kMaxCluster + 1][64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cache[C][dev]) return cache[C][dev] - 1;
+    auto fn = k_cluster<0, false, double>;
+    const int smem = 64 * 1024;
+    int n = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+        (C <= 8 || cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3(kCThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();
+    cache[C][dev] = n + 1;
+    return n;
+}
+
+// The most CTAs per system, up to 8, with which every system's cluster is
+// resident at once (clusters cannot straddle GPCs, so this is not simply
+// SMs / systems); 1 when even single CTAs do not all fit.
+static int auto_cap(int nsys) {
+    for (int C = 8; C > 1; --C)
+        if (max_active_clusters(C) >= nsys) return C;
+    return 1;
+}
+
+// The SELL-32 copy of every problem's rows, CTA by CTA: rows longer than
+// kSellLong get a lane-strided slice each; the others are sorted by length
+// (longest first, so a slice's rows have similar lengths) and cut into
+// slices of 32.
+template <typename T>
+static int fill_sell(qcp_plan* p, ClusterLayout* lay, const std::vector<SellSlice>& hs,
+                     const std::vector<int32_t>& hsp, const std::vector<int32_t>& hsr, int64_t slots) {
+    QCP_TRY(lay->d_scol.alloc(sizeof(int32_t) * (size_t)slots));
+    QCP_TRY(lay->d_sval.alloc(sizeof(T) * (size_t)slots));
+    QCP_TRY(lay->d_svalG.alloc(sizeof(T) * (size_t)slots));
+    QCP_TRY(lay->d_svalT.alloc(sizeof(T) * (size_t)slots));
+    DevBuf d_sp, d_sr;
+    QCP_TRY(d_sp.alloc(sizeof(int32_t) * hsp.size()));
+    QCP_TRY(d_sr.alloc(sizeof(int32_t) * hsr.size()));
+    QCP_CUDA(cudaMemcpyAsync(d_sp.p, hsp.data(), sizeof(int32_t) * hsp.size(), cudaMemcpyHostToDevice, p->stream));
+    QCP_CUDA(cudaMemcpyAsync(d_sr.p, hsr.data(), sizeof(int32_t) * hsr.size(), cudaMemcpyHostToDevice, p->stream));
+    const int64_t nsl = (int64_t)hs.size();
+    if (nsl > 0) {
+        const int64_t blocks = (nsl * 32 + 255) / 256;
+        k_sell_fill<T><<<(unsigned)blocks, 256, 0, p->stream>>>(
+            lay->d_slices.as<SellSlice>(), nsl, lay->d_perm.as<int32_t>(), d_sp.as<int32_t>(), d_sr.as<int32_t>(),
+            lay->d_cprob.as<ClusterProb>(), p->d_prob.as<Prob>(), p->d_mrowptr.as<int64_t>(), p->d_mcol.as<int32_t>(),
+            p->d_mval.as<T>(), p->d_mvalG.as<T>(), p->d_mvalT.as<T>(), lay->d_scol.as<int32_t>(), lay->d_sval.as<T>(),
+            lay->d_svalG.as<T>(), lay->d_svalT.as<T>());
+        QCP_CUDA(cudaGetLastError());
+    }
+    QCP_CUDA(cudaStreamSynchronize(p->stream));
+    return QCP_OK;
+}
+
+static int build_sell(qcp_plan* p, ClusterLayout* lay) {
+    std::vector<SellSlice> hs;
+    std::vector<int32_t> hperm, hsp, hsr;
+    int64_t slots = 0;
+    std::vector<int> order;
+    for (int pi = 0; pi < p->nprob; ++pi) {
+        ClusterProb& cp = lay->hp[pi];
+        const Prob& pr = p->hprob[pi];
+        const int64_t* rp = p->h_mrowptr.data() + pr.mrow;
+        for (int r = 0; r < cp.C; ++r) {
+            cp.sl[r] = (int32_t)hs.size();
+            const int R0 = cp.split[r], R1 = cp.split[r + 1];
+            order.clear();
+            for (int i = R0; i < R1; ++i) {
+                const int64_t len = rp[i + 1] - rp[i];
+                if (len > kSellLong) {
+                    const int w = (int)((len + 31) / 32);
+                    hs.push_back(SellSlice{slots, w, i - R0, 0, 0});
+                    hsp.push_back(pi);
+                    hsr.push_back(R0);
+                    slots += 32 * (int64_t)w;
+                } else {
+                    order.push_back(i);
+                }
+            }
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int x, int y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+            for (size_t q = 0; q < order.size(); q += 32) {
+                const int w = (int)(rp[order[q] + 1] - rp[order[q]]);
+                hs.push_back(SellSlice{slots, w, -1, (int32_t)hperm.size(), 0});
+                hsp.push_back(pi);
+                hsr.push_back(R0);
+                for (size_t l = 0; l < 32; ++l) hperm.push_back(q + l < order.size() ? order[q + l] - R0 : -1);
+                slots += 32 * (int64_t)w;
+            }
+        }
+        for (int r = cp.C; r <= kMaxCluster; ++r) cp.sl[r] = (int32_t)hs.size();
+    }
+    if (hs.size() > (size_t)INT32_MAX || hperm.size() > (size_t)INT32_MAX) {
+        set_error("cluster engine: too many row slices");
+        return QCP_ERR_ARG;
+    }
+    QCP_TRY(lay->d_cprob.alloc(sizeof(ClusterProb) * p->nprob));
+    QCP_CUDA(cudaMemcpyAsync(lay->d_cprob.p, lay->hp.data(), sizeof(ClusterProb) * p->nprob, cudaMemcpyHostToDevice,
+                             p->stream));
+    QCP_TRY(lay->d_slices.alloc(sizeof(SellSlice) * hs.size()));
+    QCP_TRY(lay->d_perm.alloc(sizeof(int32_t) * hperm.size()));
+    QCP_CUDA(cudaMemcpyAsync(lay->d_slices.p, hs.data(), sizeof(SellSlice) * hs.size(), cudaMemcpyHostToDevice,
+                             p->stream));
+    QCP_CUDA(cudaMemcpyAsync(lay->d_perm.p, hperm.data(), sizeof(int32_t) * hperm.size(), cudaMemcpyHostToDevice,
+                             p->stream));
+    if (p->dtype == QCP_F64) return fill_sell<double>(p, lay, hs, hsp, hsr, slots);
+    return fill_sell<float>(p, lay, hs, hsp, hsr, slots);
+}
+
+static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
+    auto it = p->clusters.find(cap);
+    if (it != p->clusters.end()) {
+        *out = it->second.get();
+        return QCP_OK;
+    }
+    size_t limit = 0;
+    QCP_TRY(cluster_smem_limit(&limit));
+    std::unique_ptr<ClusterLayout> lay(new ClusterLayout());
+    lay->hp.resize(p->nprob);
+    lay->fits = true;
+    for (int pi = 0; pi < p->nprob; ++pi) {
+        bool ok = false;
+        const Prob& pr = p->hprob[pi];
+        for (int C = cap; C <= kMaxCluster && !ok; ++C) {
+            // most rows per CTA next to a gather buffer of n + m + C entries
+            int lcap = 0;
+            const int FN = pr.n + pr.m + C;
+            while (cluster_smem_bytes(FN, lcap + 2) <= limit) lcap += 2;
+            if (lcap < 1) continue;
+            ok = cluster_split(p, pi, C, lcap, lay->hp[pi]) &&
+                 cluster_smem_bytes(lay->hp[pi].FN, lay->hp[pi].L) <= limit;
+        }
+        if (!ok) lay->fits = false;
+    }
+    if (lay->fits) QCP_TRY(build_sell(p, lay.get()));
+    *out = lay.get();
+    p->clusters.emplace(cap, std::move(lay));
+    return QCP_OK;
+}
+
+static int cap_for(const qcp_plan* p, int nsys) { return p->cluster_cap > 0 ? p->cluster_cap : auto_cap(nsys); }
+
+int cluster_ready(qcp_plan* p, int nsys, bool* ok) {
+    ClusterLayout* lay = nullptr;
+    QCP_TRY(get_layout(p, cap_for(p, nsys), &lay));
+    *ok = lay->fits;
+    return QCP_OK;
+}
+
+template <int MODE, typename T>
+static auto cluster_kernel(bool scaled) -> void (*)(PlanView<T>, ClusterArgs) {
+    return scaled ? k_cluster<MODE, true, T> : k_cluster<MODE, false, T>;
+}
+
+template <typename T>
+int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const qcp_options& opts) {
+    ClusterLayout* lay = nullptr;
+    QCP_TRY(get_layout(p, cap_for(p, nsys), &lay));
+    if (!lay->fits) {
+        set_error("cluster engine: a problem's vectors do not fit in the shared memory of 16 CTAs");
+        return QCP_ERR_ARG;
+    }
+    cudaStream_t st = p->stream;
+    // systems grouped by cluster size, one launch per size
+    p->h_csys.clear();
+    std::vector<int> gsize, gstart;
+    for (int C = 1; C <= kMaxCluster; ++C) {
+        const int start = (int)p->h_csys.size();
+        for (int s = 0; s < nsys; ++s)
+            if (lay->hp[p->hsys[s].prob].C == C) p->h_csys.push_back(s);
+        if ((int)p->h_csys.size() > start) {
+            gsize.push_back(C);
+            gstart.push_back(start);
+        }
+    }
+    gstart.push_back((int)p->h_csys.size());
+    if (p->d_csys.bytes < sizeof(int32_t) * p->h_csys.size()) QCP_TRY(p->d_csys.alloc(sizeof(int32_t) * nsys));
+    QCP_CUDA(cudaMemcpyAsync(p->d_csys.p, p->h_csys.data(), sizeof(int32_t) * p->h_csys.size(),
+                             cudaMemcpyHostToDevice, st));
+    QCP_CUDA(cudaEventRecord(p->ev0, st));
+    for (size_t g = 0; g < gsize.size(); ++g) {
+        const int C = gsize[g];
+        int FN = 0, L = 0;
+        for (int i = gstart[g]; i < gstart[g + 1]; ++i) {
+            const ClusterProb& cp = lay->hp[p->hsys[p->h_csys[i]].prob];
+            FN = std::max(FN, cp.FN);
+            L = std::max(L, cp.L);
+        }
+        const size_t bytes = cluster_smem_bytes(FN, L);
+        auto fn = mode == 0 ? cluster_kernel<0, T>(v.scaled != 0) : cluster_kernel<1, T>(v.scaled != 0);
+        QCP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        if (C > 8) QCP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        const int nclus = gstart[g + 1] - gstart[g];
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(nclus * C));
+        cfg.blockDim = dim3(kCThreads);
+        cfg.dynamicSmemBytes = bytes;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int active = 0;
+        QCP_CUDA(cudaOccupancyMaxActiveClusters(&active, fn, &cfg));
+        if (active < 1) {
+            set_error("cluster engine: a cluster of %d CTAs with %zu bytes of shared memory each cannot run", C,
+                      bytes);
+            return QCP_ERR_ARG;
+        }
+        ClusterArgs ca;
+        ca.cprob = lay->d_cprob.as<ClusterProb>();
+        ca.slices = lay->d_slices.as<SellSlice>();
+        ca.perm = lay->d_perm.as<int32_t>();
+        ca.scol = lay->d_scol.as<int32_t>();
+        ca.sval = lay->d_sval.p;
+        ca.svalG = lay->d_svalG.p;
+        ca.svalT = lay->d_svalT.p;
+        ca.sys_list = p->d_csys.as<int32_t>() + gstart[g];
+        ca.C = C;
+        ca.FN = FN;
+        ca.L = L;
+        ca.pad = 0;
+        ca.max_passes = 2 * (opts.maxiter + 2);
+        QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, v, ca));
+        p->last_launches += 1;
+    }
+    QCP_CUDA(cudaEventRecord(p->ev1, st));
+    QCP_CUDA(cudaEventSynchronize(p->ev1));
+    float ms = 0.0f;
+    QCP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    p->pass_ms += ms;
+    return QCP_OK;
+}
+
+template int iterate_cluster<double>(qcp_plan*, int, int, const PlanView<double>&, const qcp_options&);
+template int iterate_cluster<float>(qcp_plan*, int, int, const PlanView<float>&, const qcp_options&);
+
+}  // namespace qcpd

@@ -93,6 +93,7 @@ struct SocBlock {
     int32_t kase;    // 0: ||u|| <= -t (D = 0), 1: ||u|| <= t (D = I), 2: formula
     int32_t pad;
     double t, r;     // t and ||u|| of z_y on the block
+    double h, tq;    // 1 / (2 r) and t / r^2 (kase 2), so no kernel divides
 };
 
 // LSQR scalars of one system (Paige & Saunders' recurrences).
@@ -111,6 +112,22 @@ struct LsqrState {
     double rtol;
     int64_t iters, maxiter;
     int32_t status, outcome, first, pad;
+};
+
+// Thread-block-cluster layout of one problem: CTA r of a system's cluster
+// owns the local rows [split[r], split[r+1]) (never cutting a second-order-
+// cone block) and keeps its slice of the gathered vector at poff[r] of the
+// gather buffer (poff even, so every slice starts on a 16-byte boundary).
+constexpr int kMaxCluster = 16;
+struct ClusterProb {
+    int32_t C;                        // CTAs per system
+    int32_t FN;                       // gather-buffer length (poff[C])
+    int32_t L;                        // most rows of one CTA
+    int32_t pad;
+    int32_t split[kMaxCluster + 1];
+    int32_t poff[kMaxCluster + 1];
+    int32_t cb[kMaxCluster + 1];      // CTA r's SOC blocks [cb[r], cb[r+1]) (problem-relative)
+    int32_t sl[kMaxCluster + 1];      // CTA r's row-sum slices [sl[r], sl[r+1]) (global indices)
 };
 
 // Four partial sums carried through the reductions.
@@ -148,27 +165,75 @@ __device__ __forceinline__ Part warp_sum_part(Part v) {
     return Part{warp_sum(v.a), warp_sum(v.b), warp_sum(v.c), warp_sum(v.d)};
 }
 
-// Block-wide sums of NV values per thread, in a fixed order (deterministic
-// for a fixed block size).  The result is valid in warp 0.  FP64 issue is
-// scarce on this GPU (1/64 of FP32), so the values go through shared memory
-// and only warp 0 adds: NV * (kWarps + 5) warp-wide FP64 adds in total
-// instead of NV * 5 per warp with shuffles alone.
-template <int NV>
-__device__ __forceinline__ void block_reduce(double (&v)[NV], double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NV; ++j) red[j * kThreads + threadIdx.x] = v[j];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            double s = 0.0;
-#pragma unroll
-            for (int q = 0; q < kWarps; ++q) s += red[j * kThreads + q * 32 + lane];
-            v[j] = warp_sum(s);
-        }
+// x is neither infinite nor NaN (integer test on the exponent field).
+__device__ __forceinline__ bool finite64(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// 1 / sqrt(s).  A warp-wide FP64 instruction costs 1/64 of the FP32 rate on
+// this GPU and the library's sqrt and division each take many, so for a
+// positive normal s this scales s by an even power of two into [1, 4)
+// (keeping it inside FP32's range), takes the FP32 estimate of 1/sqrt and
+// refines it with two steps of Newton's iteration for 1/sqrt,
+// y <- y + (y/2)(1 - m y^2), each of which squares the relative error
+// (about 2^-22 -> 2^-43 -> FP64 rounding); the power of two goes back in
+// through the exponent field.  Zero, subnormal, infinite and NaN inputs take
+// the library's route.
+__device__ __forceinline__ double rsqrt_fast(double s) {
+    const long long b = __double_as_longlong(s);
+    const int ef = (int)((b >> 52) & 0x7ff);
+    if (b <= 0 || ef == 0 || ef == 0x7ff) return 1.0 / sqrt(s);
+    const int k = (ef - 1023) >> 1;  // s = m 2^(2k), m in [1, 4)
+    const double m = __longlong_as_double(b - ((long long)(2 * k) << 52));
+    double y = (double)rsqrtf((float)m);
+    y = fma(0.5 * y, fma(-(m * y), y, 1.0), y);
+    y = fma(0.5 * y, fma(-(m * y), y, 1.0), y);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
+}
+
+// sqrt(ss) and 1 / sqrt(ss) (0 for ss = 0; a non-finite norm for a
+// non-finite ss) for a sum of squares ss.
+__device__ __forceinline__ void norm_and_inverse(double ss, double& nrm, double& inv) {
+    if (ss > 0.0) {
+        const double y = rsqrt_fast(ss);
+        nrm = ss * y;  // NaN for ss = inf (y = 0)
+        inv = y;
+    } else {
+        nrm = ss;  // 0, or NaN
+        inv = 0.0;
     }
+}
+
+// Block-wide sums of NV values per thread, in a fixed order (deterministic
+// for a fixed block size); the sums are returned in every thread.  A
+// warp-wide FP64 instruction costs the same on this GPU (1/64 of the FP32
+// rate) however many lanes it has, so the sum is a halving tree in shared
+// memory (NT/64 + NT/128 + ... + 1 warp-wide adds per value, spread over the
+// warps) ending in one warp per value for the last 32 partial sums.
+template <int NV, int NT = kThreads>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double* red) {
+    static_assert(NV <= NT / 32, "one warp per value in the last stage");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) red[j * NT + tid] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int w = NT / 2; w >= 32; w >>= 1) {
+        if (tid < w) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) red[j * NT + tid] += red[j * NT + tid + w];
+        }
+        __syncthreads();
+    }
+    if (warp < NV) {
+        const double s = warp_sum(red[warp * NT + lane]);
+        __syncwarp();
+        if (lane == 0) red[warp * NT] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = red[j * NT];
     __syncthreads();
 }
 
@@ -177,6 +242,7 @@ struct Scratch {
     double red[4 * kThreads];
 };
 
+// Block sums; valid in every thread.
 __device__ __forceinline__ Part block_sum_part(Part p, Scratch* sc) {
     double v[4] = {p.a, p.b, p.c, p.d};
     block_reduce<4>(v, sc->red);
@@ -209,7 +275,8 @@ __device__ __forceinline__ Part ld_part(const Part* p) {
 // false.  After the arrival barrier only warp 0 works (shuffles, no block
 // barriers): FP64 adds are scarce and every barrier and dependent add sits on
 // the pass's critical path.  Sums run in a fixed order, so results do not
-// depend on CTA scheduling.  No CTA ever waits on another: the last one to
+// depend on CTA scheduling (except for a row cut into several LONG tiles,
+// whose terms arrive with whichever of its tiles finishes last).  No CTA ever waits on another: the last one to
 // arrive does the work.
 __device__ __forceinline__ bool finish_tile(const Reduce& R, const Tile& tl, int32_t g0, int32_t g1,
                                             int tile, Part part, Part* total, Scratch* scratch) {
@@ -257,13 +324,20 @@ __device__ __forceinline__ bool finish_tile(const Reduce& R, const Tile& tl, int
 // D Pi_{K*} applied to the tile's rows (Appendix A).  src/dst are shared
 // arrays indexed by (row - r0); x-rows (row < n) pass through (D Pi = I on
 // R^n).  y-rows: R+ rows use their 0/1 flag, zero-cone rows 1 (the dual of
-// {0} is R), SOC blocks (whole inside the tile) use one warp each:
-//   D(ct, cu) = (1/(2r)) (r ct + u^T cu,  u ct + (t + r) cu - (t/r^2)(u^T cu) u).
-// Caller synchronises before and after.
-template <typename T>
+// {0} is R), and a second-order-cone block (whole inside the range) with
+// z_y = (t, u), r = ||u|| in the formula case maps (ct, cu) to
+//   (1/(2r)) (r ct + u^T cu,  (ct - (t/r^2) u^T cu) u + (t + r) cu).
+// Every warp-wide FP64 instruction costs the same on this GPU however many
+// lanes it has, so blocks of up to kSocThread entries take one thread each
+// (all lanes busy, two FP64 operations per entry) and only larger blocks
+// take a warp.  zy[row - zoff] holds the block's z_y.  Caller synchronises
+// before and after.
+constexpr int kSocThread = 32;
+
+template <typename T, int NW = kWarps>
 __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int r0, int r1, int n,
                                              const int8_t* flag, const SocBlock* blocks, int cb0,
-                                             int cb1, const T* zy) {
+                                             int cb1, const T* zy, int zoff = 0) {
     for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
         if (i < n) {
             dst[i - r0] = src[i - r0];
@@ -272,27 +346,52 @@ __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int
             if (f != RF_SOC) dst[i - r0] = (f == RF_ONE) ? src[i - r0] : 0.0;
         }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int bi = cb0 + warp; bi < cb1; bi += kWarps) {
+    // small blocks: one thread each
+    for (int bi = cb0 + (int)threadIdx.x; bi < cb1; bi += blockDim.x) {
         const SocBlock B = blocks[bi];
-        const int s0 = B.start - r0;
+        if (B.dim > kSocThread) continue;
+        const double* sb = src + (B.start - r0);
+        double* db = dst + (B.start - r0);
         if (B.kase == 0) {
-            for (int k = lane; k < B.dim; k += 32) dst[s0 + k] = 0.0;
+            for (int k = 0; k < B.dim; ++k) db[k] = 0.0;
         } else if (B.kase == 1) {
-            for (int k = lane; k < B.dim; k += 32) dst[s0 + k] = src[s0 + k];
+            for (int k = 0; k < B.dim; ++k) db[k] = sb[k];
         } else {
-            const double ct = src[s0];
-            double dot = 0.0;
-            for (int k = 1 + lane; k < B.dim; k += 32) dot += ld(zy + B.start + k) * src[s0 + k];
-            dot = warp_sum(dot);
-            const double inv2r = 0.5 / B.r;
-            const double tr = B.t + B.r;
-            const double tq = B.t / (B.r * B.r);
-            if (lane == 0) dst[s0] = (B.r * ct + dot) * inv2r;
-            for (int k = 1 + lane; k < B.dim; k += 32) {
-                const double u = ld(zy + B.start + k);
-                dst[s0 + k] = (u * ct + tr * src[s0 + k] - tq * dot * u) * inv2r;
+            const T* u = zy + (B.start - zoff);
+            double d0 = 0.0, d1 = 0.0;  // two chains: half the dependent latency
+            int k = 1;
+            for (; k + 1 < B.dim; k += 2) {
+                d0 = fma(ld(u + k), sb[k], d0);
+                d1 = fma(ld(u + k + 1), sb[k + 1], d1);
             }
+            if (k < B.dim) d0 = fma(ld(u + k), sb[k], d0);
+            const double dot = d0 + d1;
+            const double ct = sb[0];
+            db[0] = B.h * fma(B.r, ct, dot);
+            const double a = B.h * fma(-B.tq, dot, ct), b = B.h * (B.t + B.r);
+            for (int k = 1; k < B.dim; ++k) db[k] = fma(a, ld(u + k), b * sb[k]);
+        }
+    }
+    // large blocks: one warp each
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int bi = cb0 + warp; bi < cb1; bi += NW) {
+        const SocBlock B = blocks[bi];
+        if (B.dim <= kSocThread) continue;
+        const double* sb = src + (B.start - r0);
+        double* db = dst + (B.start - r0);
+        if (B.kase == 0) {
+            for (int k = lane; k < B.dim; k += 32) db[k] = 0.0;
+        } else if (B.kase == 1) {
+            for (int k = lane; k < B.dim; k += 32) db[k] = sb[k];
+        } else {
+            const T* u = zy + (B.start - zoff);
+            double dot = 0.0;
+            for (int k = 1 + lane; k < B.dim; k += 32) dot = fma(ld(u + k), sb[k], dot);
+            dot = warp_sum(dot);
+            const double ct = sb[0];
+            if (lane == 0) db[0] = B.h * fma(B.r, ct, dot);
+            const double a = B.h * fma(-B.tq, dot, ct), b = B.h * (B.t + B.r);
+            for (int k = 1 + lane; k < B.dim; k += 32) db[k] = fma(a, ld(u + k), b * sb[k]);
         }
     }
 }

@@ -120,17 +120,17 @@ __device__ __forceinline__ void load8(const int32_t* col, const float* val, int6
 // are srp[0..rows] in shared memory, into s0[] (zeroed by the caller, all
 // threads synchronised).  The merge-style segmented SpMV described at
 // tile_rowsums; gather(j) returns the vector entry of column j.  Ends with a
-// block barrier.
-template <typename VT, typename GF>
+// block barrier.  NW: warps of the CTA.
+template <int NW = kWarps, typename VT, typename GF>
 __device__ __forceinline__ void stream_rowsums(const int64_t* srp, const int rows, const int32_t* mcol,
                                                const VT* vals, GF gather, double* s0) {
     const int tid = threadIdx.x;
     const int64_t K0 = srp[0], K1 = srp[rows];
-    // Each warp owns the rows that start in its eighth of the tile's
+    // Each warp owns the rows that start in its share (1/NW) of the tile's
     // nonzeros, so no partial sum crosses a warp and the sweeps below need
     // only warp-level synchronisation.
     const int lane = tid & 31, warp = tid >> 5;
-    const int64_t q = (K1 - K0 + kWarps - 1) / kWarps;
+    const int64_t q = (K1 - K0 + NW - 1) / NW;
     auto lower = [&](int64_t key) {  // first row whose start is >= key
         int lo = 0, hi = rows;
         while (lo < hi) {
@@ -141,7 +141,7 @@ __device__ __forceinline__ void stream_rowsums(const int64_t* srp, const int row
         return lo;
     };
     const int w0 = (warp == 0) ? 0 : lower(K0 + warp * q);
-    const int w1 = (warp == kWarps - 1) ? rows : lower(K0 + (warp + 1) * q);
+    const int w1 = (warp == NW - 1) ? rows : lower(K0 + (warp + 1) * q);
     if (w1 > w0) {
         const int64_t WK0 = srp[w0], WK1 = srp[w1];
         for (int64_t c0 = WK0 & ~(int64_t)(kE - 1); c0 < WK1; c0 += 32 * kE) {
@@ -311,6 +311,69 @@ __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_
     __syncthreads();
     stream_rowsums(sm.srp, rows, mcol, vals, [&](int32_t c) { return ldv<L1>(gv + c); }, sm.s0);
     return rows;
+}
+
+// The LSQR scalar recurrences (Paige & Saunders 1982) after a u-update with
+// ||u_{k+1}|| = nrm (inv_nrm = 1/nrm, 0 when nrm = 0): the plane rotation
+// eliminating beta_{k+1}, the coefficients of the next v-update and
+// x-update, and the stopping tests.  S is LsqrState or volatile LsqrState.
+// One thread runs this and every FP64 instruction here costs a full
+// warp-wide issue, so the square root and the reciprocal of the rotation
+// share one rsqrt_fast.
+// nsq = nrm^2 (the sum of squares nrm came from), so the rotation's square
+// root does not wait for nrm's.
+template <typename S>
+__device__ __forceinline__ void lsqr_step_u(S* st, double nrm, double inv_nrm, double nsq) {
+    const double rhobar = st->rhobar;
+    double rho, inv;
+    norm_and_inverse(fma(rhobar, rhobar, nsq), rho, inv);
+    const double c = rhobar * inv, s = nrm * inv;
+    const double phibar = st->phibar;
+    const double phi = c * phibar;
+    st->phibar = s * phibar;
+    st->inv_rho = inv;
+    st->c = c;
+    st->s = s;
+    st->xcoef = phi * inv;
+    st->beta = nrm;
+    st->vc1 = inv_nrm;  // next v-update: 1/beta, beta/alpha
+    st->vc2 = nrm * st->uc1;
+    st->iters += 1;
+    if (!finite64(rho) || !finite64(phi) || !(rho > 0.0)) {
+        st->outcome = O_BREAKDOWN;
+        st->xcoef = 0.0;
+        st->status = S_FINAL;
+    } else if (st->phibar <= st->rtol * st->bnorm || nrm == 0.0) {
+        st->outcome = O_CONVERGED;
+        st->status = S_FINAL;
+    } else if (st->iters >= st->maxiter) {
+        st->outcome = O_MAXITER;
+        st->status = S_FINAL;
+    }
+}
+
+// The same after a v-update with ||v_{k+1}|| = nrm.  Returns true when the
+// system has just finished (v = 0: the current x solves the problem).
+template <typename S>
+__device__ __forceinline__ bool lsqr_step_v(S* st, double nrm, double inv_nrm) {
+    if (st->first) {
+        st->rhobar = nrm;
+        st->phibar = st->beta;
+        st->wcoef = 0.0;
+        st->first = 0;
+    } else {
+        st->rhobar = -st->c * nrm;
+        st->wcoef = (st->s * nrm) * st->inv_rho;
+    }
+    st->alpha = nrm;
+    st->uc1 = inv_nrm;  // next u-update: 1/alpha, alpha/beta
+    st->uc2 = nrm * st->vc1;
+    if (!(nrm > 0.0) || !finite64(nrm)) {
+        st->outcome = finite64(nrm) ? O_CONVERGED : O_BREAKDOWN;
+        st->status = S_DONE;
+        return true;
+    }
+    return false;
 }
 
 // One half-iteration of LSQR over all tiles of all systems.
@@ -503,57 +566,15 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
     const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * ldv<L1>(outv + rN);
     outv[rN] = nvN;
     if (PASS == PASS_GT) XI[rN] = 0.0;
-    const double nrm = sqrt(tot.a + nvN * nvN);
+    const double nsq = fma(nvN, nvN, tot.a);
+    double nrm, inv_nrm;
+    norm_and_inverse(nsq, nrm, inv_nrm);
     if (ROLE == ROLE_U) {
         W[rN] = tin * c1 - wcoef * ldv<L1>(W + rN);
-        // rotation eliminating beta_{k+1}
-        const double rhobar = st->rhobar;
-        const double rho = sqrt(rhobar * rhobar + nrm * nrm);
-        const double inv = 1.0 / rho;
-        const double c = rhobar * inv, s = nrm * inv;
-        const double phibar = st->phibar;
-        const double phi = c * phibar;
-        st->phibar = s * phibar;
-        st->inv_rho = inv;
-        st->c = c;
-        st->s = s;
-        st->xcoef = phi * inv;
-        st->beta = nrm;
-        st->vc1 = nrm > 0.0 ? 1.0 / nrm : 0.0;  // next v-update: 1/beta, beta/alpha
-        st->vc2 = nrm * st->uc1;
-        st->iters += 1;
-        if (!isfinite(rho) || !isfinite(phi) || rho == 0.0) {
-            st->outcome = O_BREAKDOWN;
-            st->xcoef = 0.0;
-            st->status = S_FINAL;
-        } else if (st->phibar <= st->rtol * st->bnorm || nrm == 0.0) {
-            st->outcome = O_CONVERGED;
-            st->status = S_FINAL;
-        } else if (st->iters >= st->maxiter) {
-            st->outcome = O_MAXITER;
-            st->status = S_FINAL;
-        }
+        lsqr_step_u(st, nrm, inv_nrm, nsq);
     } else {
         X[rN] = fma(xcoef, ldv<L1>(W + rN), ldv<L1>(X + rN));
-        if (st->first) {
-            st->rhobar = nrm;
-            st->phibar = st->beta;
-            st->wcoef = 0.0;
-            st->first = 0;
-        } else {
-            st->rhobar = -st->c * nrm;
-            st->wcoef = (st->s * nrm) * st->inv_rho;
-        }
-        st->alpha = nrm;
-        st->uc1 = nrm > 0.0 ? 1.0 / nrm : 0.0;  // next u-update: 1/alpha, alpha/beta
-        st->uc2 = nrm * st->vc1;
-        if (!(nrm > 0.0) || !isfinite(nrm)) {
-            // A^T r = 0: the current x solves the least-squares problem
-            if (!isfinite(nrm)) st->outcome = O_BREAKDOWN;
-            else st->outcome = O_CONVERGED;
-            st->status = S_DONE;
-            atomicSub(a.active, 1);
-        }
+        if (lsqr_step_v(st, nrm, inv_nrm)) atomicSub(a.active, 1);
     }
 }
 

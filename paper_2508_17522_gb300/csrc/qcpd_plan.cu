@@ -254,6 +254,8 @@ __global__ void k_socprep(SocBlock* blk, int64_t nb, const double* zy) {
         B.t = t;
         B.r = r;
         B.kase = (r <= -t) ? 0 : ((r <= t) ? 1 : 2);
+        B.h = B.kase == 2 ? 0.5 / r : 0.0;
+        B.tq = B.kase == 2 ? t / (r * r) : 0.0;
         blk[b] = B;
     }
 }

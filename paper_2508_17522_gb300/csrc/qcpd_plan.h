@@ -5,6 +5,7 @@
 
 #include <cstdio>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -72,6 +73,17 @@ struct GraphKey {
     }
 };
 
+// Thread-block-cluster layouts of every problem of a plan for one requested
+// cluster size (QCP_ENGINE_CLUSTER).
+struct ClusterLayout {
+    bool fits = false;              // every problem has a layout within the shared-memory limit
+    std::vector<ClusterProb> hp;    // per problem
+    DevBuf d_cprob;                 // device copy of hp
+    // SELL-32 copy of M by CTA: slices, row permutation, gather-buffer
+    // columns and the plain / column-scaled / row-scaled values per slot
+    DevBuf d_slices, d_perm, d_scol, d_sval, d_svalG, d_svalT;
+};
+
 }  // namespace qcpd
 
 struct qcp_plan {
@@ -98,7 +110,7 @@ struct qcp_plan {
     // schedule
     int tile_nnz = 4096;
     int long_row = 512;
-    int long_chunk = 4096;
+    int long_chunk = 1 << 20;
     int rmax = 1;
     std::vector<std::vector<qcpd::Tile>> ptiles;  // per problem, sys = problem
     std::vector<int64_t> h_mrowptr;               // host copy (schedule building)
@@ -116,6 +128,12 @@ struct qcp_plan {
     qcpd::DevBuf d_pctl;     // persistent mode: barrier count, generation, stop flag, error flag
     qcpd::DevBuf d_U, d_V, d_W, d_X, d_XI, d_RHS;
     int* h_active = nullptr;  // pinned
+
+    // cluster engine
+    int cluster_cap = 0;  // CTAs per system asked for (0: per call from the number of systems)
+    std::map<int, std::unique_ptr<qcpd::ClusterLayout>> clusters;  // by CTAs asked for
+    qcpd::DevBuf d_csys;  // system lists of the cluster launches
+    std::vector<int32_t> h_csys;
 
     std::map<qcpd::GraphKey, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;

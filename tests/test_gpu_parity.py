@@ -114,9 +114,16 @@ def test_config2_sixteen_directions(q, cfg2):
     for i in range(k):
         got = (gP[i * nP:(i + 1) * nP], gA[i * nA:(i + 1) * nA], gq[i * n:(i + 1) * n], gb[i * m:(i + 1) * m])
         assert rel_err(got, ref_v[i]) < TOL64, (i, rel_err(got, ref_v[i]), vi[i])
-    # a single-direction solve reproduces direction 0 of the multi solve bit for bit
-    j0, _ = gpu_jvp(q, plan, dirs[0], opts)
-    assert np.array_equal(j0[0], dx[:n]) and np.array_equal(j0[1], dy[:m])
+    # with the engine and cluster size fixed, a single-direction solve
+    # reproduces direction 0 of the multi solve bit for bit
+    plan.set_cluster(4)
+    for engine in ("passes", "cluster"):
+        o = q.options(rtol=1e-10, maxiter=100000, engine=engine)
+        mx, my, _, _ = q.qcp_derivative_jvp_multi(plan, 2, cat("dP")[:2 * nP], cat("dA")[:2 * nA], cat("dq")[:2 * n],
+                                                  cat("db")[:2 * m], o)
+        mx, my = to_np(mx, my)
+        j0, _ = gpu_jvp(q, plan, dirs[0], o)
+        assert np.array_equal(j0[0], mx[:n]) and np.array_equal(j0[1], my[:m]), engine
     plan.close()
 
 
@@ -130,9 +137,10 @@ def test_config2_schedules_agree(q, cfg2):
     for tile_nnz, long_row, long_chunk in [(4096, 512, 4096), (16384, 4096, 4096), (256, 8, 32), (1024, 16, 64)]:
         plan.set_schedule(tile_nnz, long_row, long_chunk)
         for precond in ("none", "equilibrate"):
-            jv, ji = gpu_jvp(q, plan, dirs[0], q.options(rtol=1e-10, precond=precond))
+            opts = q.options(rtol=1e-10, precond=precond, engine="passes")
+            jv, ji = gpu_jvp(q, plan, dirs[0], opts)
             assert rel_err(jv, ref_j[0]) < TOL64, (tile_nnz, long_row, precond, rel_err(jv, ref_j[0]))
-            vv, vi = gpu_vjp(q, plan, dirs[0], q.options(rtol=1e-10, precond=precond))
+            vv, vi = gpu_vjp(q, plan, dirs[0], opts)
             assert rel_err(vv, ref_v[0]) < TOL64, (tile_nnz, long_row, precond, rel_err(vv, ref_v[0]))
             outs.append(jv)
     plan.close()
@@ -147,20 +155,65 @@ def test_persistent_matches_launch_per_pass(q, cfg2, precond):
     plan = _plan(q, prob, max_rhs=k)
     cat = lambda name: np.concatenate([getattr(d, name) for d in dirs[:k]])
     res = {}
-    for persistent in (False, True):
-        opts = q.options(rtol=1e-10, precond=precond, persistent=persistent)
+    for engine in ("passes", "persistent", "cluster"):
+        opts = q.options(rtol=1e-10, precond=precond, engine=engine)
         dx, dy, ds, ji = q.qcp_derivative_jvp_multi(plan, k, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
         gP, gA, gq, gb, vi = q.qcp_derivative_vjp_multi(plan, k, cat("wx"), cat("wy"), cat("ws"), opts)
-        res[persistent] = (to_np(dx, dy, ds, gP, gA, gq, gb), ji, vi)
-        assert all(i["status"] == "QCP_OK" for i in ji + vi), (ji, vi)
-    a, b = res[False][0], res[True][0]
-    for x, y in zip(a, b):
+        res[engine] = (to_np(dx, dy, ds, gP, gA, gq, gb), ji, vi)
+        assert all(i["status"] == "QCP_OK" for i in ji + vi), (engine, ji, vi)
+    for x, y in zip(res["passes"][0], res["persistent"][0]):
         assert np.array_equal(x, y)
     n, m = prob.n, prob.m
-    dx, dy, ds = res[True][0][:3]
-    for i in range(k):
-        got = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
-        assert rel_err(got, ref_j[i]) < TOL64
+    nP, nA = prob.P.nnz, prob.A.nnz
+    for engine in ("persistent", "cluster"):
+        dx, dy, ds, gP, gA, gq, gb = res[engine][0]
+        for i in range(k):
+            got = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
+            assert rel_err(got, ref_j[i]) < TOL64, (engine, i)
+            got = (gP[i * nP:(i + 1) * nP], gA[i * nA:(i + 1) * nA], gq[i * n:(i + 1) * n], gb[i * m:(i + 1) * m])
+            assert rel_err(got, ref_v[i]) < TOL64, (engine, i)
+    plan.close()
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3, 7, 8, 16])
+def test_cluster_sizes_agree(q, ctas):
+    """The cluster engine with 1 to 16 CTAs per system (row splits at SOC
+    block boundaries, empty CTAs when a problem has few rows) matches the
+    oracle on problems with SOC blocks, a large block and m = 0."""
+    for prob in (g.small_qcp(61, 30, 3, 20, (3, 5, 9, 4)), g.small_qcp(25, 60, 3, 10, (40, 5), soc_mix=(0.5, 0.0)),
+                 g.unconstrained_qp(2, 9), g.config3(2, scale=0.004)):
+        d = g.make_directions(prob, 13)
+        fac = D.DenseFactor(prob)
+        ref_j = D.jvp_dense(prob, d, fac)[:3]
+        ref_v = D.vjp_dense(prob, d, fac)[:4]
+        plan = _plan(q, prob)
+        plan.set_cluster(ctas)
+        for precond in ("none", "equilibrate"):
+            opts = q.options(rtol=1e-11, precond=precond, engine="cluster")
+            jv, ji = gpu_jvp(q, plan, d, opts)
+            vv, vi = gpu_vjp(q, plan, d, opts)
+            assert rel_err(jv, ref_j) < TOL64, (ctas, precond, rel_err(jv, ref_j), ji)
+            assert rel_err(vv, ref_v) < TOL64, (ctas, precond, rel_err(vv, ref_v), vi)
+            assert plan.last_launches() < 20  # the whole Krylov loop is one launch
+        plan.close()
+
+
+def test_cluster_engine_limits(q):
+    """A system too large for 16 CTAs' shared memory: the cluster engine
+    refuses it, the automatic choice runs the pass engine instead."""
+    from paper_2508_17522_gb300._native import QCPError
+    prob = g.config3(3, scale=0.1)
+    d = g.make_directions(prob, 4)
+    plan = _plan(q, prob)
+    with pytest.raises(QCPError, match="ERR_ARG"):
+        gpu_jvp(q, plan, d, q.options(rtol=1e-8, engine="cluster"))
+    a, ai = gpu_jvp(q, plan, d, q.options(rtol=1e-8, engine="auto", precond="equilibrate"))
+    b, bi = gpu_jvp(q, plan, d, q.options(rtol=1e-8, engine="passes", precond="equilibrate"))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    for bad in (-1, 17):
+        with pytest.raises(QCPError, match="ERR_ARG"):
+            plan.set_cluster(bad)
     plan.close()
 
 
@@ -168,11 +221,15 @@ def test_determinism_and_graph(q):
     prob = g.small_qcp(30, 40, 5, 30, (3, 5, 9))
     d = g.make_directions(prob, 3)
     plan = _plan(q, prob)
-    a, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12))
-    b, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12))
-    c, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12, use_graph=False))
+    a, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12, engine="passes"))
+    b, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12, engine="passes"))
+    c, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12, engine="passes", use_graph=False))
     for x, y, z in zip(a, b, c):
         assert np.array_equal(x, y) and np.array_equal(x, z)
+    a, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12, engine="cluster"))
+    b, _ = gpu_jvp(q, plan, d, q.options(rtol=1e-12, engine="cluster"))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
     plan.close()
 
 
@@ -182,16 +239,27 @@ def test_batched_uneven_problems(q):
     dirs = [g.make_directions(p, 9) for p in probs]
     plan = q.qcp_batch_plan_create([q.problem_tensors(p, "cuda") for p in probs], torch.float64)
     cat = lambda name: np.concatenate([getattr(d, name) for d in dirs])
-    opts = q.options(rtol=1e-13)
+    opts = q.options(rtol=1e-13, engine="passes")
     dx, dy, ds, ji = q.qcp_derivative_jvp(plan, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
     gP, gA, gq, gb, vi = q.qcp_derivative_vjp(plan, cat("wx"), cat("wy"), cat("ws"), opts)
     dx, dy, ds, gP, gA, gq, gb = to_np(dx, dy, ds, gP, gA, gq, gb)
-    on = om = op = oa = 0
     # the persistent form gives the same answers on uneven problems
-    po = q.options(rtol=1e-13, persistent=True)
+    po = q.options(rtol=1e-13, engine="persistent")
     pdx, pdy, pds, pji = q.qcp_derivative_jvp(plan, cat("dP"), cat("dA"), cat("dq"), cat("db"), po)
     for x, y in zip(to_np(pdx, pdy, pds), (dx, dy, ds)):
         assert np.array_equal(x, y)
+    _batched_check(probs, dirs, (dx, dy, ds, gP, gA, gq, gb), ji, vi)
+    # the cluster engine: one cluster per problem, sizes chosen per problem
+    co = q.options(rtol=1e-13, engine="cluster")
+    cdx, cdy, cds, cji = q.qcp_derivative_jvp(plan, cat("dP"), cat("dA"), cat("dq"), cat("db"), co)
+    cgP, cgA, cgq, cgb, cvi = q.qcp_derivative_vjp(plan, cat("wx"), cat("wy"), cat("ws"), co)
+    _batched_check(probs, dirs, to_np(cdx, cdy, cds, cgP, cgA, cgq, cgb), cji, cvi)
+    plan.close()
+
+
+def _batched_check(probs, dirs, outs, ji, vi):
+    dx, dy, ds, gP, gA, gq, gb = outs
+    on = om = op = oa = 0
     for p, d, a, b in zip(probs, dirs, ji, vi):
         fac = D.DenseFactor(p)
         rj = D.jvp_dense(p, d, fac)[:3]
@@ -201,7 +269,6 @@ def test_batched_uneven_problems(q):
         assert rel_err(got_j, rj) < TOL64, (rel_err(got_j, rj), a)
         assert rel_err(got_v, rv) < TOL64, (rel_err(got_v, rv), b)
         on, om, op, oa = on + p.n, om + p.m, op + p.P.nnz, oa + p.A.nnz
-    plan.close()
 
 
 def test_zero_direction_and_maxiter(q):
