@@ -137,7 +137,13 @@ typedef enum {
                                    memory and only hardware cluster barriers separate passes.
                                    Needs every system to fit (about 8 N + 56 N / C bytes per CTA
                                    for C CTAs); QCP_ERR_ARG otherwise */
-    QCP_ENGINE_AUTO = 3         /* QCP_ENGINE_CLUSTER when every system fits, else PASSES */
+    QCP_ENGINE_AUTO = 3,        /* QCP_ENGINE_CLUSTER when every system fits, else PASSES */
+    QCP_ENGINE_CLUSTER_FP64 = 4 /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
+                                   otherwise computes its vector operations in double-float pairs of
+                                   binary32 numbers (about 48 significant bits, on the FP32 pipes,
+                                   which run 74 times faster than FP64 on this GPU), keeps the LSQR
+                                   scalars in FP64, and itself uses FP64 when a magnitude in the
+                                   data lies outside 2^-90..2^90 */
 } qcp_engine;
 
 typedef struct {

@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "QCP_OK", 1: "QCP_ERR_ARG", 2: "QCP_ERR_CUDA", 3: "QCP_ERR_AL
                 7: "QCP_WARN_NEAR_KINK"}
 QCP_F64, QCP_F32 = 0, 1
 QCP_PRECOND_NONE, QCP_PRECOND_EQUILIBRATE = 0, 1
-QCP_ENGINE_PASSES, QCP_ENGINE_PERSISTENT, QCP_ENGINE_CLUSTER, QCP_ENGINE_AUTO = 0, 1, 2, 3
+QCP_ENGINE_PASSES, QCP_ENGINE_PERSISTENT, QCP_ENGINE_CLUSTER, QCP_ENGINE_AUTO, QCP_ENGINE_CLUSTER_FP64 = 0, 1, 2, 3, 4
 
 
 class qcp_csr(ctypes.Structure):

@@ -97,14 +97,15 @@ _PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE
 
 
 _ENGINE = {"passes": N.QCP_ENGINE_PASSES, "persistent": N.QCP_ENGINE_PERSISTENT,
-           "cluster": N.QCP_ENGINE_CLUSTER, "auto": N.QCP_ENGINE_AUTO}
+           "cluster": N.QCP_ENGINE_CLUSTER, "auto": N.QCP_ENGINE_AUTO, "cluster_fp64": N.QCP_ENGINE_CLUSTER_FP64}
 
 
 def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_residual=True, precond="none",
             kink_tol=0.0, engine="auto"):
     """qcp_options; precond is "none" (the plain method) or "equilibrate";
     engine is "passes" (one launch per pass), "persistent" (one cooperative
-    launch), "cluster" (one thread-block cluster per system) or "auto"."""
+    launch), "cluster" (one thread-block cluster per system, double-float
+    vector arithmetic), "cluster_fp64" (the same in FP64) or "auto"."""
     o = N.qcp_options()
     N.lib().qcp_default_options(ctypes.byref(o))
     o.rtol, o.maxiter, o.check_every = float(rtol), int(maxiter), int(check_every)

@@ -282,17 +282,17 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         set_error("precond must be QCP_PRECOND_NONE or QCP_PRECOND_EQUILIBRATE");
         return QCP_ERR_ARG;
     }
-    if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_AUTO) {
-        set_error("engine must be one of QCP_ENGINE_PASSES, _PERSISTENT, _CLUSTER, _AUTO");
+    if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_CLUSTER_FP64) {
+        set_error("engine must be one of QCP_ENGINE_PASSES, _PERSISTENT, _CLUSTER, _AUTO, _CLUSTER_FP64");
         return QCP_ERR_ARG;
     }
     int engine = opts.engine;
-    if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO) {
+    if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER_FP64) {
         bool fits = false;
         QCP_TRY(cluster_ready(p, nsys, &fits));
         if (fits) {
             engine = QCP_ENGINE_CLUSTER;
-        } else if (engine == QCP_ENGINE_CLUSTER) {
+        } else if (engine != QCP_ENGINE_AUTO) {
             set_error("cluster engine: a problem's vectors do not fit in the shared memory of 16 CTAs");
             return QCP_ERR_ARG;
         } else {

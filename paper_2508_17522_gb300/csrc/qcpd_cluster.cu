@@ -152,6 +152,14 @@ static int cluster_smem_limit(size_t* out) {
     max_static_smem(k_cluster<0, true, float>, st);
     max_static_smem(k_cluster<1, false, float>, st);
     max_static_smem(k_cluster<1, true, float>, st);
+    max_static_smem(k_cluster_df<0, false, double>, st);
+    max_static_smem(k_cluster_df<0, true, double>, st);
+    max_static_smem(k_cluster_df<1, false, double>, st);
+    max_static_smem(k_cluster_df<1, true, double>, st);
+    max_static_smem(k_cluster_df<0, false, float>, st);
+    max_static_smem(k_cluster_df<0, true, float>, st);
+    max_static_smem(k_cluster_df<1, false, float>, st);
+    max_static_smem(k_cluster_df<1, true, float>, st);
     *out = (size_t)optin > st ? (size_t)optin - st : 0;
     return QCP_OK;
 }
@@ -224,6 +232,75 @@ static int fill_sell(qcp_plan* p, ClusterLayout* lay, const std::vector<SellSlic
     return QCP_OK;
 }
 
+// df64 copies: out[i] = (hi, lo) of in[i]; *bad set when a nonzero entry is
+// outside [2^-90, 2^90] or not finite (the df64 kernel's safe range).
+constexpr double kDfMin = 0x1p-90, kDfMax = 0x1p90;
+
+__device__ __forceinline__ bool df_unsafe(double x) {
+    const double a = fabs(x);
+    return !(a == 0.0 || (a >= kDfMin && a <= kDfMax));
+}
+
+template <typename T>
+__global__ void k_to_df(const T* in, int64_t n, df* out, int* bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = (double)in[i];
+        if (df_unsafe(x)) atomicExch(bad, 1);
+        out[i] = df_from(x);
+    }
+}
+
+__global__ void k_soc_df(const SocBlock* blk, int64_t nb, SocDf* out, int* bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+        const SocBlock B = blk[i];
+        SocDf s;
+        const double htr = B.h * (B.t + B.r);
+        if (B.kase == 2 && (df_unsafe(B.r) || df_unsafe(B.h) || df_unsafe(B.tq) || df_unsafe(htr))) atomicExch(bad, 1);
+        s.r = df_from(B.r);
+        s.h = df_from(B.h);
+        s.tq = df_from(B.tq);
+        s.htr = df_from(htr);
+        out[i] = s;
+    }
+}
+
+template <typename T>
+static int to_df(qcp_plan* p, const DevBuf& in, int64_t n, DevBuf& out, int* bad) {
+    QCP_TRY(out.alloc(sizeof(df) * (size_t)std::max<int64_t>(n, 1)));
+    if (n > 0) {
+        const int grid = (int)std::min<int64_t>(4096, (n + 255) / 256);
+        k_to_df<T><<<grid, 256, 0, p->stream>>>(in.as<T>(), n, out.as<df>(), bad);
+    }
+    return QCP_OK;
+}
+
+template <typename T>
+static int build_df(qcp_plan* p, ClusterLayout* lay, int64_t slots) {
+    DevBuf bad;
+    QCP_TRY(bad.alloc(sizeof(int)));
+    QCP_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), p->stream));
+    int* b = bad.as<int>();
+    QCP_TRY(to_df<T>(p, lay->d_sval, slots, lay->d_dsval, b));
+    QCP_TRY(to_df<T>(p, lay->d_svalG, slots, lay->d_dsvalG, b));
+    QCP_TRY(to_df<T>(p, lay->d_svalT, slots, lay->d_dsvalT, b));
+    QCP_TRY(to_df<double>(p, p->d_coefA, p->N_tot, lay->d_dcA, b));
+    QCP_TRY(to_df<double>(p, p->d_coefB, p->N_tot, lay->d_dcB, b));
+    QCP_TRY(to_df<double>(p, p->d_rw, p->N_tot, lay->d_drw, b));
+    QCP_TRY(to_df<double>(p, p->d_cd, p->N_tot, lay->d_dcd, b));
+    QCP_TRY(to_df<double>(p, p->d_zy, p->N_tot, lay->d_dzy, b));
+    QCP_TRY(lay->d_dsoc.alloc(sizeof(SocDf) * (size_t)std::max<int64_t>(p->nsoc_tot, 1)));
+    if (p->nsoc_tot > 0) {
+        const int grid = (int)std::min<int64_t>(4096, (p->nsoc_tot + 255) / 256);
+        k_soc_df<<<grid, 256, 0, p->stream>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot, lay->d_dsoc.as<SocDf>(), b);
+    }
+    QCP_CUDA(cudaGetLastError());
+    int hbad = 1;
+    QCP_CUDA(cudaMemcpyAsync(&hbad, b, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    QCP_CUDA(cudaStreamSynchronize(p->stream));
+    lay->df_ok = hbad == 0;
+    return QCP_OK;
+}
+
 static int build_sell(qcp_plan* p, ClusterLayout* lay) {
     std::vector<SellSlice> hs;
     std::vector<int32_t> hperm, hsp, hsr;
@@ -275,8 +352,12 @@ static int build_sell(qcp_plan* p, ClusterLayout* lay) {
                              p->stream));
     QCP_CUDA(cudaMemcpyAsync(lay->d_perm.p, hperm.data(), sizeof(int32_t) * hperm.size(), cudaMemcpyHostToDevice,
                              p->stream));
-    if (p->dtype == QCP_F64) return fill_sell<double>(p, lay, hs, hsp, hsr, slots);
-    return fill_sell<float>(p, lay, hs, hsp, hsr, slots);
+    if (p->dtype == QCP_F64) {
+        QCP_TRY(fill_sell<double>(p, lay, hs, hsp, hsr, slots));
+        return build_df<double>(p, lay, slots);
+    }
+    QCP_TRY(fill_sell<float>(p, lay, hs, hsp, hsr, slots));
+    return build_df<float>(p, lay, slots);
 }
 
 static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
@@ -324,6 +405,25 @@ static auto cluster_kernel(bool scaled) -> void (*)(PlanView<T>, ClusterArgs) {
     return scaled ? k_cluster<MODE, true, T> : k_cluster<MODE, false, T>;
 }
 
+template <int MODE, typename T>
+static auto cluster_kernel_df(bool scaled) -> void (*)(PlanView<T>, ClusterArgs, ClusterDfArgs) {
+    return scaled ? k_cluster_df<MODE, true, T> : k_cluster_df<MODE, false, T>;
+}
+
+// Dynamic shared memory, non-portable size and occupancy of one cluster launch.
+template <typename K>
+static int prepare_launch(K fn, int C, size_t bytes, cudaLaunchConfig_t& cfg) {
+    QCP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (C > 8) QCP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    int active = 0;
+    QCP_CUDA(cudaOccupancyMaxActiveClusters(&active, fn, &cfg));
+    if (active < 1) {
+        set_error("cluster engine: a cluster of %d CTAs with %zu bytes of shared memory each cannot run", C, bytes);
+        return QCP_ERR_ARG;
+    }
+    return QCP_OK;
+}
+
 template <typename T>
 int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const qcp_options& opts) {
     ClusterLayout* lay = nullptr;
@@ -359,9 +459,6 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
             L = std::max(L, cp.L);
         }
         const size_t bytes = cluster_smem_bytes(FN, L);
-        auto fn = mode == 0 ? cluster_kernel<0, T>(v.scaled != 0) : cluster_kernel<1, T>(v.scaled != 0);
-        QCP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        if (C > 8) QCP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         const int nclus = gstart[g + 1] - gstart[g];
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -375,13 +472,6 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
         cfg.stream = st;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        int active = 0;
-        QCP_CUDA(cudaOccupancyMaxActiveClusters(&active, fn, &cfg));
-        if (active < 1) {
-            set_error("cluster engine: a cluster of %d CTAs with %zu bytes of shared memory each cannot run", C,
-                      bytes);
-            return QCP_ERR_ARG;
-        }
         ClusterArgs ca;
         ca.cprob = lay->d_cprob.as<ClusterProb>();
         ca.slices = lay->d_slices.as<SellSlice>();
@@ -396,7 +486,25 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
         ca.L = L;
         ca.pad = 0;
         ca.max_passes = 2 * (opts.maxiter + 2);
-        QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, v, ca));
+        if (lay->df_ok && opts.engine != QCP_ENGINE_CLUSTER_FP64) {
+            ClusterDfArgs da;
+            da.sval = lay->d_dsval.as<df>();
+            da.svalG = lay->d_dsvalG.as<df>();
+            da.svalT = lay->d_dsvalT.as<df>();
+            da.cA = lay->d_dcA.as<df>();
+            da.cB = lay->d_dcB.as<df>();
+            da.rw = lay->d_drw.as<df>();
+            da.cd = lay->d_dcd.as<df>();
+            da.zy = lay->d_dzy.as<df>();
+            da.soc = lay->d_dsoc.as<SocDf>();
+            auto fn = mode == 0 ? cluster_kernel_df<0, T>(v.scaled != 0) : cluster_kernel_df<1, T>(v.scaled != 0);
+            QCP_TRY(prepare_launch(fn, C, bytes, cfg));
+            QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, v, ca, da));
+        } else {
+            auto fn = mode == 0 ? cluster_kernel<0, T>(v.scaled != 0) : cluster_kernel<1, T>(v.scaled != 0);
+            QCP_TRY(prepare_launch(fn, C, bytes, cfg));
+            QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, v, ca));
+        }
         p->last_launches += 1;
     }
     QCP_CUDA(cudaEventRecord(p->ev1, st));

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "qcpd_cluster.cuh"
+#include "qcpd_cluster_df.cuh"
 #include "qcpd_plan.h"
 
 namespace qcpd {

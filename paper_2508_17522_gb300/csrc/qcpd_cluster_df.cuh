@@ -1,0 +1,571 @@
+// Double-float form of the cluster engine's kernel (see qcpd_cluster.cuh for
+// the pass structure and qcpd_df64.cuh for the arithmetic).
+//
+// Every per-pass operation on vectors (row sums, epilogue, D Pi, block
+// sums) runs in df64 on the FP32 pipes; the LSQR scalar recurrences (one
+// lane per pass) stay in FP64.  The Krylov vectors live as df64 pairs: u, v,
+// xi in shared memory, w and x in the plan's FP64 arrays reinterpreted as
+// pairs for the kernel's lifetime (each CTA touches only its own rows).
+// Matrix values, per-row data and second-order-cone constants come as df64
+// copies made at plan time.
+//
+// Magnitudes: the right-hand side of each system is scaled by a power of two
+// to norm in [1/2, 1) for the kernel's lifetime (exact; LSQR's iterates and
+// scalars are homogeneous in it), so the vectors stay near unit scale; the
+// plan falls back to the FP64 kernel when the data leave about 2^-90..2^90.
+#pragma once
+
+#include "qcpd_cluster.cuh"
+#include "qcpd_df64.cuh"
+
+namespace qcpd {
+
+// df64 constants of one second-order-cone block in the formula case:
+// r = ||u||, h = 1/(2r), tq = t/r^2, htr = h (t + r).
+struct SocDf {
+    df r, h, tq, htr;
+};
+
+struct ClusterDfArgs {
+    const df* sval;   // SELL-32 values of M, M diag(c), M diag(w) per slot
+    const df* svalG;
+    const df* svalT;
+    const df* cA;     // N-indexed (plan-wide offsets) per-row data: coefA, coefB, rw, cd, z_y
+    const df* cB;
+    const df* rw;
+    const df* cd;
+    const df* zy;
+    const SocDf* soc;  // per SOC block (plan-wide indices)
+};
+
+// This pass's scalars: FP64 for the finisher, df64 for the vector work.
+struct PassScal {
+    double c1, c2, tin, tout, tt, wcoef, xcoef;
+    df dc1, dnc2, dnw, dxc, dtt;  // c1, -c2, -wcoef, xcoef, tt
+};
+
+struct CCtxDf {
+    const ClusterProb* cp;
+    LsqrState* st;
+    PassScal* ps;
+    double* tau;
+    df* scr;
+    df *F, *U, *V, *XI, *s0, *s1, *s2, *ZY, *red;
+    const SellSlice* slices;
+    const int32_t* perm;
+    const int32_t* scol;
+    const df* valG;
+    const df* valT;
+    const df *cA, *cB, *rw, *cd;  // problem-relative
+    const double *rwd, *cdd;     // FP64 per-row scalings (tau entries)
+    const int8_t* flag;
+    const SocBlock* blocks;
+    const SocDf* soc;
+    df* W;  // the plan's w and x rows of this system, as df64 pairs
+    df* X;
+    int* active;
+    double kappa;
+    int n, N, R0, L, C, rank, cb0, cb1, sl0, sl1;
+};
+
+// D Pi_{K*} in df64 on rows [r0, r1) (same cases as apply_D_tile); zy[] is
+// indexed by row - r0.
+template <int NW>
+__device__ __forceinline__ void apply_D_df(const df* src, df* dst, int r0, int r1, int n, const int8_t* flag,
+                                           const SocBlock* blocks, const SocDf* sdf, int cb0, int cb1,
+                                           const df* zy) {
+    for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
+        if (i < n) {
+            dst[i - r0] = src[i - r0];
+        } else {
+            const int8_t f = flag[i];
+            if (f != RF_SOC) dst[i - r0] = (f == RF_ONE) ? src[i - r0] : df_zero();
+        }
+    }
+    for (int bi = cb0 + (int)threadIdx.x; bi < cb1; bi += blockDim.x) {
+        const SocBlock B = blocks[bi];
+        if (B.dim > kSocThread) continue;
+        const df* sb = src + (B.start - r0);
+        df* db = dst + (B.start - r0);
+        if (B.kase == 0) {
+            for (int k = 0; k < B.dim; ++k) db[k] = df_zero();
+        } else if (B.kase == 1) {
+            for (int k = 0; k < B.dim; ++k) db[k] = sb[k];
+        } else {
+            const SocDf S = sdf[bi];
+            const df* u = zy + (B.start - r0);
+            DfAcc d = dfacc_zero();
+            for (int k = 1; k < B.dim; ++k) dfacc_fma(d, u[k], sb[k]);
+            const df dot = dfacc_result(d);
+            const df ct = sb[0];
+            db[0] = df_mul(S.h, df_fma(S.r, ct, dot));
+            const df a = df_mul(S.h, df_fma(df_neg(S.tq), dot, ct));
+            for (int k = 1; k < B.dim; ++k) db[k] = df_fma(a, u[k], df_mul(S.htr, sb[k]));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int bi = cb0 + warp; bi < cb1; bi += NW) {
+        const SocBlock B = blocks[bi];
+        if (B.dim <= kSocThread) continue;
+        const df* sb = src + (B.start - r0);
+        df* db = dst + (B.start - r0);
+        if (B.kase == 0) {
+            for (int k = lane; k < B.dim; k += 32) db[k] = df_zero();
+        } else if (B.kase == 1) {
+            for (int k = lane; k < B.dim; k += 32) db[k] = sb[k];
+        } else {
+            const SocDf S = sdf[bi];
+            const df* u = zy + (B.start - r0);
+            DfAcc d = dfacc_zero();
+            for (int k = 1 + lane; k < B.dim; k += 32) dfacc_fma(d, u[k], sb[k]);
+            const df dot = warp_sum_df(dfacc_result(d));
+            const df ct = sb[0];
+            if (lane == 0) db[0] = df_mul(S.h, df_fma(S.r, ct, dot));
+            const df a = df_mul(S.h, df_fma(df_neg(S.tq), dot, ct));
+            for (int k = 1 + lane; k < B.dim; k += 32) db[k] = df_fma(a, u[k], df_mul(S.htr, sb[k]));
+        }
+    }
+}
+
+// Block sums of three df64 values (fixed order), returned in every thread.
+__device__ __forceinline__ void block_reduce_df3(df (&v)[3], df* red) {
+    constexpr int NT = kCThreads;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 3; ++j) red[j * NT + tid] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int w = NT / 2; w >= 32; w >>= 1) {
+        if (tid < w) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) red[j * NT + tid] = df_add(red[j * NT + tid], red[j * NT + tid + w]);
+        }
+        __syncthreads();
+    }
+    if (warp < 3) {
+        const df s = warp_sum_df(red[warp * NT + lane]);
+        __syncwarp();
+        if (lane == 0) red[warp * NT] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[j] = red[j * NT];
+    __syncthreads();
+}
+
+// Row sums by warps 1.. (the SELL-32 walk of sell_rowsums, one TwoProduct
+// and one TwoSum per entry).
+__device__ __forceinline__ void sell_rowsums_df(const CCtxDf& c, const df* sval, const df* F, df* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nw = kCWarps - 1;
+    for (int s = c.sl0 + warp - 1; s < c.sl1; s += nw) {
+        const SellSlice d = c.slices[s];
+        const int32_t* cp = c.scol + d.base + lane;
+        const df* vp = sval + d.base + lane;
+        DfAcc acc = dfacc_zero();
+        int k = 0;
+        for (; k + 4 <= d.width; k += 4) {
+            int32_t j[4];
+            df v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                j[u] = __ldg(cp + 32 * (k + u));
+                v[u] = __ldg(vp + 32 * (k + u));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dfacc_fma(acc, v[u], F[j[u]]);
+        }
+        for (; k < d.width; ++k) dfacc_fma(acc, __ldg(vp + 32 * k), F[__ldg(cp + 32 * k)]);
+        df r = dfacc_result(acc);
+        if (d.row >= 0) {
+            r = warp_sum_df(r);
+            if (lane == 0) out[d.row] = r;
+        } else {
+            const int row = c.perm[d.pidx + lane];
+            if (row >= 0) out[row] = r;
+        }
+    }
+}
+
+// Lane 0 of warp 0: this pass's scalars from the state and tau entries.
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void prep_scalars_df(const CCtxDf& c) {
+    const LsqrState& st = *c.st;
+    PassScal p;
+    p.c1 = (ROLE == ROLE_U) ? st.uc1 : st.vc1;
+    p.c2 = (ROLE == ROLE_U) ? st.uc2 : st.vc2;
+    p.tin = c.tau[ROLE == ROLE_U ? TAU_V : TAU_U];
+    p.tout = c.tau[ROLE == ROLE_U ? TAU_U : TAU_V];
+    p.tt = SC ? (PASS == PASS_G ? c.cdd[c.N - 1] : c.rwd[c.N - 1]) * p.tin : p.tin;
+    p.wcoef = st.wcoef;
+    p.xcoef = st.xcoef;
+    p.dc1 = df_from(p.c1);
+    p.dnc2 = df_from(-p.c2);
+    p.dnw = df_from(-p.wcoef);
+    p.dxc = df_from(p.xcoef);
+    p.dtt = df_from(p.tt);
+    *c.ps = p;
+}
+
+// The end of the previous pass (kind PASS, ROLE) by warp 0, as in
+// cluster_finish, with the sums converted to FP64 once.
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void cluster_finish_df(const CCtxDf& c, const int par) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = threadIdx.x & 31;
+    df ta = df_zero(), tb = df_zero(), tc = df_zero();
+    if (lane < c.C) {
+        const df* rr = cl.map_shared_rank(c.red + 4 * par, lane);
+        ta = rr[0];
+        tb = rr[1];
+        tc = rr[2];
+    }
+    for (int o = 1; o < c.C; o <<= 1) {  // the same butterfly in every CTA
+        df x;
+        x.x = __shfl_xor_sync(0xffffffffu, ta.x, o);
+        x.y = __shfl_xor_sync(0xffffffffu, ta.y, o);
+        ta = df_add(ta, x);
+        x.x = __shfl_xor_sync(0xffffffffu, tb.x, o);
+        x.y = __shfl_xor_sync(0xffffffffu, tb.y, o);
+        tb = df_add(tb, x);
+        x.x = __shfl_xor_sync(0xffffffffu, tc.x, o);
+        x.y = __shfl_xor_sync(0xffffffffu, tc.y, o);
+        tc = df_add(tc, x);
+    }
+    if (lane != 0) return;
+    const PassScal pd = *c.ps;
+    LsqrState& st = *c.st;
+    const int rN = c.N - 1;
+    const double sa = df_to(ta), sb = df_to(tb), sc = df_to(tc);
+    double oN;
+    if (PASS == PASS_G) {
+        oN = -sb - sc + c.kappa * pd.tt;
+        if (SC) oN *= c.rwd[rN];
+    } else {
+        oN = sb - sc + c.kappa * pd.tt;
+        if (SC) oN *= c.cdd[rN];
+    }
+    const double nvN = (PASS == PASS_GT) ? 0.0 : pd.c1 * oN - pd.c2 * pd.tout;
+    c.tau[ROLE == ROLE_U ? TAU_U : TAU_V] = nvN;
+    if (PASS == PASS_GT) c.tau[TAU_XI] = 0.0;
+    const double nsq = fma(nvN, nvN, sa);
+    double nrm, inv_nrm;
+    norm_and_inverse(nsq, nrm, inv_nrm);
+    if (ROLE == ROLE_U) {
+        c.tau[TAU_W] = pd.tin * pd.c1 - pd.wcoef * c.tau[TAU_W];
+        lsqr_step_u(&st, nrm, inv_nrm, nsq);
+    } else {
+        c.tau[TAU_X] = fma(pd.xcoef, c.tau[TAU_W], c.tau[TAU_X]);
+        if (lsqr_step_v(&st, nrm, inv_nrm) && c.rank == 0) atomicSub(c.active, 1);
+    }
+}
+
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, const bool pending) {
+    constexpr int PPASS = (PASS == PASS_G) ? PASS_GT : PASS_G;
+    constexpr int PROLE = (ROLE == ROLE_U) ? ROLE_V : ROLE_U;
+    cg::cluster_group cl = cg::this_cluster();
+    const int tid = threadIdx.x;
+    df* s0 = c.s0;
+    if (tid < 32) {
+        if (pending) cluster_finish_df<PPASS, PROLE, SC>(c, par ^ 1);
+        if (tid == 0) prep_scalars_df<PASS, ROLE, SC>(c);
+    } else {
+        sell_rowsums_df(c, PASS == PASS_G ? c.valG : c.valT, c.F, s0);
+    }
+    __syncthreads();
+
+    LsqrState& st = *c.st;
+    const int status = st.status;
+    if (status == S_DONE) return true;
+    const PassScal ps = *c.ps;
+    if (ROLE == ROLE_V && status == S_FINAL) {
+        for (int i = tid; i < c.L; i += kCThreads) {
+            const int r = c.R0 + i;
+            c.X[r] = df_fma(ps.dxc, c.W[r], c.X[r]);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            c.tau[TAU_X] = fma(ps.xcoef, c.tau[TAU_W], c.tau[TAU_X]);
+            st.status = S_DONE;
+            if (c.rank == 0) atomicSub(c.active, 1);
+        }
+        __syncthreads();
+        return true;
+    }
+    const df c1 = ps.dc1, nc2 = ps.dnc2, nw = ps.dnw, xc = ps.dxc, tt = ps.dtt;
+    df* in_s = (ROLE == ROLE_U) ? c.V : c.U;
+    df* out_s = (ROLE == ROLE_U) ? c.U : c.V;
+    const int L = c.L, R0 = c.R0, n = c.n;
+    df* s1 = c.s1;
+    df* s2 = c.s2;
+    df* XIs = c.XI;
+
+    DfAcc ss = dfacc_zero(), dtop = dfacc_zero(), dbot = dfacc_zero();
+    if (PASS == PASS_G) {
+        for (int i = tid; i < L; i += kCThreads) {
+            const int r = R0 + i;
+            const df iv = in_s[i];
+            df o;
+            if (r < n) {
+                o = df_fma(c.cA[r], tt, s0[i]);
+                dfacc_fma(dtop, c.cB[r], SC ? df_mul(c.cd[r], iv) : iv);
+            } else {
+                const df xi = XIs[i];
+                const df dxi = SC ? df_mul(c.cd[r], df_sub(xi, iv)) : df_sub(xi, iv);
+                o = df_add(df_fma(df_neg(c.cA[r]), tt, s0[i]), dxi);
+                dfacc_fma(dbot, c.cB[r], SC ? df_mul(c.cd[r], xi) : xi);
+            }
+            if (SC) o = df_mul(o, c.rw[r]);
+            const df nv = df_fma(c1, o, df_mul(nc2, out_s[i]));
+            out_s[i] = nv;
+            dfacc_fma(ss, nv, nv);
+            if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c1, df_mul(nw, c.W[r]));
+            else c.X[r] = df_fma(xc, c.W[r], c.X[r]);
+        }
+    } else {
+        for (int i = tid; i < L; i += kCThreads) {
+            const int r = R0 + i;
+            const df iv = SC ? df_mul(c.rw[r], in_s[i]) : in_s[i];
+            const df h = df_fma(df_neg(c.cB[r]), tt, s0[i]);
+            if (r < n) {
+                s1[i] = h;
+                dfacc_fma(dtop, c.cA[r], iv);
+            } else {
+                s1[i] = df_add(h, iv);
+                dfacc_fma(dbot, c.cA[r], iv);
+            }
+        }
+        __syncthreads();
+        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY);
+        __syncthreads();
+        for (int i = tid; i < L; i += kCThreads) {
+            const int r = R0 + i;
+            const df iv = in_s[i];
+            df o = (r < n) ? s2[i] : df_sub(s2[i], SC ? df_mul(c.rw[r], iv) : iv);
+            if (SC) o = df_mul(o, c.cd[r]);
+            const df nv = df_fma(c1, o, df_mul(nc2, out_s[i]));
+            out_s[i] = nv;
+            s1[i] = nv;
+            dfacc_fma(ss, nv, nv);
+            if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c1, df_mul(nw, c.W[r]));
+            else c.X[r] = df_fma(xc, c.W[r], c.X[r]);
+        }
+        __syncthreads();
+        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY);
+        __syncthreads();
+        for (int i = tid; i < L; i += kCThreads) XIs[i] = s2[i];
+    }
+    df v3[3] = {dfacc_result(ss), dfacc_result(dtop), dfacc_result(dbot)};
+    block_reduce_df3(v3, c.scr);
+    if (tid == 0) {
+        c.red[4 * par + 0] = v3[0];
+        c.red[4 * par + 1] = v3[1];
+        c.red[4 * par + 2] = v3[2];
+    }
+    cl.sync();
+
+    {
+        const df* bvec = (PASS == PASS_GT) ? XIs : out_s;
+        float4* dst = reinterpret_cast<float4*>(c.F);
+        const int npairs = c.cp->FN >> 1;
+        constexpr int kU = 4;
+        for (int k0 = tid; k0 < npairs; k0 += kU * kCThreads) {
+            float4 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int k = k0 + u * kCThreads;
+                if (k < npairs) {
+                    int lo = 0, hi = c.C;  // the last CTA r with poff[r] <= 2k
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (c.cp->poff[mid] <= 2 * k) lo = mid;
+                        else hi = mid;
+                    }
+                    const float4* src = reinterpret_cast<const float4*>(cl.map_shared_rank(bvec, lo));
+                    v[u] = src[k - (c.cp->poff[lo] >> 1)];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int k = k0 + u * kCThreads;
+                if (k < npairs) dst[k] = v[u];
+            }
+        }
+    }
+    __syncthreads();
+    return false;
+}
+
+template <int MODE, bool SC, typename T>
+__global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, ClusterArgs ca, ClusterDfArgs da) {
+    extern __shared__ __align__(16) double csm[];
+    __shared__ df scr[3 * kCThreads];
+    __shared__ LsqrState st;
+    __shared__ PassScal ps;
+    __shared__ double tau[5];
+    __shared__ ClusterProb cp;
+    __shared__ double s_scale;
+    __shared__ int s_uscaled;
+    constexpr int PU = MODE == 0 ? PASS_G : PASS_GT;
+    constexpr int PV = MODE == 0 ? PASS_GT : PASS_G;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = ca.C;
+    const int rank = (int)cl.block_rank();
+    const int si = ca.sys_list[blockIdx.x / C];
+    const Sys sy = a.sys[si];
+    const Prob pr = a.probs[sy.prob];
+    const int tid = threadIdx.x;
+    const int N = pr.n + pr.m + 1, rN = N - 1;
+    double* gU = a.U + sy.voff;
+    double* gV = a.V + sy.voff;
+    double* gXI = a.XI + sy.voff;
+    double* gW = a.W + sy.voff;
+    double* gX = a.X + sy.voff;
+    if (tid == 0) {
+        cp = ca.cprob[sy.prob];
+        st = a.state[si];
+        tau[TAU_U] = gU[rN];
+        tau[TAU_V] = gV[rN];
+        tau[TAU_W] = gW[rN];
+        tau[TAU_X] = gX[rN];
+        tau[TAU_XI] = gXI[rN];
+        // scale the right-hand side to norm in [1/2, 1) by a power of two:
+        // x, phibar, xcoef and bnorm are proportional to it, and so are u,
+        // beta and 1/uc2 before the first u-update
+        double s = 1.0;
+        if (st.bnorm > 0.0 && finite64(st.bnorm)) {
+            int e = 0;
+            frexp(st.bnorm, &e);
+            s = ldexp(1.0, -e);
+        }
+        s_scale = s;
+        s_uscaled = st.iters == 0;
+        st.phibar *= s;
+        st.xcoef *= s;
+        st.bnorm *= s;
+        tau[TAU_X] *= s;
+        if (s_uscaled) {
+            st.beta *= s;
+            st.uc2 /= s;
+            tau[TAU_U] *= s;
+        }
+    }
+    __syncthreads();
+    const double sc = s_scale;
+    const double su = s_uscaled ? sc : 1.0;
+    CCtxDf c;
+    {
+        const CSmem m = cluster_smem(csm, ca.FN, ca.L);
+        c.F = reinterpret_cast<df*>(m.F);
+        c.U = reinterpret_cast<df*>(m.U);
+        c.V = reinterpret_cast<df*>(m.V);
+        c.XI = reinterpret_cast<df*>(m.XI);
+        c.s0 = reinterpret_cast<df*>(m.s0);
+        c.s1 = reinterpret_cast<df*>(m.s1);
+        c.s2 = reinterpret_cast<df*>(m.s2);
+        c.ZY = reinterpret_cast<df*>(m.ZY);
+        c.red = reinterpret_cast<df*>(m.red);
+    }
+    c.cp = &cp;
+    c.st = &st;
+    c.ps = &ps;
+    c.tau = tau;
+    c.scr = scr;
+    c.slices = ca.slices;
+    c.perm = ca.perm;
+    c.scol = ca.scol;
+    c.valG = a.scaled ? da.svalG : da.sval;
+    c.valT = a.scaled ? da.svalT : da.sval;
+    c.cA = da.cA + pr.doff;
+    c.cB = da.cB + pr.doff;
+    c.rw = da.rw + pr.doff;
+    c.cd = da.cd + pr.doff;
+    c.rwd = a.rw + pr.doff;
+    c.cdd = a.cd + pr.doff;
+    c.flag = a.flag + pr.doff;
+    c.blocks = a.blocks + pr.soff;
+    c.soc = da.soc + pr.soff;
+    c.W = reinterpret_cast<df*>(gW);
+    c.X = reinterpret_cast<df*>(gX);
+    c.active = a.active;
+    c.kappa = pr.kappa;
+    c.n = pr.n;
+    c.N = N;
+    c.R0 = cp.split[rank];
+    c.L = cp.split[rank + 1] - c.R0;
+    c.C = C;
+    c.rank = rank;
+    c.cb0 = cp.cb[rank];
+    c.cb1 = cp.cb[rank + 1];
+    c.sl0 = cp.sl[rank];
+    c.sl1 = cp.sl[rank + 1];
+
+    const bool live = st.status != S_DONE;
+    if (live) {
+        const df* zyd = da.zy + pr.doff;
+        for (int i = tid; i < c.L; i += kCThreads) {
+            const int r = c.R0 + i;
+            c.U[i] = df_from(gU[r] * su);
+            c.V[i] = df_from(gV[r]);
+            c.XI[i] = df_from(gXI[r]);
+            c.ZY[i] = zyd[r];
+            // w and x become df64 pairs in place (same 8 bytes per entry)
+            const double w = gW[r], x = gX[r] * sc;
+            c.W[r] = df_from(w);
+            c.X[r] = df_from(x);
+        }
+        // the first u-update gathers xi (JVP) or v (VJP); slot FN stays 0 for padding
+        const double* g0 = (MODE == 0) ? gXI : gV;
+        for (int r = 0; r < C; ++r) {
+            const int r0 = cp.split[r], len = cp.split[r + 1] - r0;
+            df* dst = c.F + cp.poff[r];
+            for (int i = tid; i < len; i += kCThreads) dst[i] = df_from(g0[r0 + i]);
+        }
+        if (tid == 0) c.F[cp.FN] = df_zero();
+    }
+    __syncthreads();
+    cl.sync();  // every CTA of the cluster runs before any remote access
+    if (live) {
+        int par = 0;
+        bool pending = false;
+        for (int64_t pass = 0; pass < ca.max_passes; pass += 2) {
+            if (cluster_pass_df<PU, ROLE_U, SC>(c, par, pending)) break;
+            pending = true;
+            par ^= 1;
+            if (cluster_pass_df<PV, ROLE_V, SC>(c, par, true)) break;
+            par ^= 1;
+        }
+        // undo the scaling; back to FP64
+        const bool u_still = s_uscaled && st.iters == 0;
+        const double iu = u_still ? 1.0 / sc : 1.0, ix = 1.0 / sc;
+        for (int i = tid; i < c.L; i += kCThreads) {
+            const int r = c.R0 + i;
+            gU[r] = df_to(c.U[i]) * iu;
+            gV[r] = df_to(c.V[i]);
+            gXI[r] = df_to(c.XI[i]);
+            const double w = df_to(c.W[r]), x = df_to(c.X[r]) * ix;
+            gW[r] = w;
+            gX[r] = x;
+        }
+        if (tid == 0 && rank == 0) {
+            st.phibar *= ix;
+            st.xcoef *= ix;
+            st.bnorm *= ix;
+            if (u_still) {
+                st.beta *= iu;
+                st.uc2 /= iu;
+            }
+            gU[rN] = tau[TAU_U] * iu;
+            gV[rN] = tau[TAU_V];
+            gW[rN] = tau[TAU_W];
+            gX[rN] = tau[TAU_X] * ix;
+            gXI[rN] = tau[TAU_XI];
+            a.state[si] = st;
+        }
+    }
+    cl.sync();  // no CTA leaves while a peer may still read its shared memory
+}
+
+}  // namespace qcpd

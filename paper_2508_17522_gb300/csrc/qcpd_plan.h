@@ -82,6 +82,9 @@ struct ClusterLayout {
     // SELL-32 copy of M by CTA: slices, row permutation, gather-buffer
     // columns and the plain / column-scaled / row-scaled values per slot
     DevBuf d_slices, d_perm, d_scol, d_sval, d_svalG, d_svalT;
+    // double-float copies for the df64 kernel (df_ok: every magnitude in range)
+    bool df_ok = false;
+    DevBuf d_dsval, d_dsvalG, d_dsvalT, d_dcA, d_dcB, d_drw, d_dcd, d_dzy, d_dsoc;
 };
 
 }  // namespace qcpd

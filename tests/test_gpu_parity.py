@@ -155,7 +155,7 @@ def test_persistent_matches_launch_per_pass(q, cfg2, precond):
     plan = _plan(q, prob, max_rhs=k)
     cat = lambda name: np.concatenate([getattr(d, name) for d in dirs[:k]])
     res = {}
-    for engine in ("passes", "persistent", "cluster"):
+    for engine in ("passes", "persistent", "cluster", "cluster_fp64"):
         opts = q.options(rtol=1e-10, precond=precond, engine=engine)
         dx, dy, ds, ji = q.qcp_derivative_jvp_multi(plan, k, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
         gP, gA, gq, gb, vi = q.qcp_derivative_vjp_multi(plan, k, cat("wx"), cat("wy"), cat("ws"), opts)
@@ -165,7 +165,7 @@ def test_persistent_matches_launch_per_pass(q, cfg2, precond):
         assert np.array_equal(x, y)
     n, m = prob.n, prob.m
     nP, nA = prob.P.nnz, prob.A.nnz
-    for engine in ("persistent", "cluster"):
+    for engine in ("persistent", "cluster", "cluster_fp64"):
         dx, dy, ds, gP, gA, gq, gb = res[engine][0]
         for i in range(k):
             got = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
@@ -189,12 +189,13 @@ def test_cluster_sizes_agree(q, ctas):
         plan = _plan(q, prob)
         plan.set_cluster(ctas)
         for precond in ("none", "equilibrate"):
-            opts = q.options(rtol=1e-11, precond=precond, engine="cluster")
-            jv, ji = gpu_jvp(q, plan, d, opts)
-            vv, vi = gpu_vjp(q, plan, d, opts)
-            assert rel_err(jv, ref_j) < TOL64, (ctas, precond, rel_err(jv, ref_j), ji)
-            assert rel_err(vv, ref_v) < TOL64, (ctas, precond, rel_err(vv, ref_v), vi)
-            assert plan.last_launches() < 20  # the whole Krylov loop is one launch
+            for engine in ("cluster", "cluster_fp64"):
+                opts = q.options(rtol=1e-11, precond=precond, engine=engine)
+                jv, ji = gpu_jvp(q, plan, d, opts)
+                vv, vi = gpu_vjp(q, plan, d, opts)
+                assert rel_err(jv, ref_j) < TOL64, (ctas, precond, engine, rel_err(jv, ref_j), ji)
+                assert rel_err(vv, ref_v) < TOL64, (ctas, precond, engine, rel_err(vv, ref_v), vi)
+                assert plan.last_launches() < 20  # the whole Krylov loop is one launch
         plan.close()
 
 
