@@ -120,6 +120,17 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
         cp.split[k] = Nx;
         cp.cb[k] = nsb;
     }
+    for (int r = 0; r < C; ++r) {  // SOC blocks too large for one thread each
+        int nl = 0, bi = 0;
+        for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
+            const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
+            if (t == QCP_CONE_SOC) {
+                if (bi >= cp.cb[r] && bi < cp.cb[r + 1] && d > kSocThread) ++nl;
+                ++bi;
+            }
+        }
+        cp.nlarge[r] = nl;
+    }
     int L = 0;
     cp.poff[0] = 0;
     for (int r = 0; r < kMaxCluster; ++r) {
@@ -488,6 +499,10 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
         ca.max_passes = 2 * (opts.maxiter + 2);
         if (lay->df_ok && opts.engine != QCP_ENGINE_CLUSTER_FP64) {
             ClusterDfArgs da;
+            da.bhalf = even_up(FN);
+            const size_t need = sizeof(df) * 2 * (size_t)da.bhalf * (size_t)nclus;
+            if (p->d_bcast.bytes < need) QCP_TRY(p->d_bcast.alloc(need));
+            da.bcast = p->d_bcast.as<df>();
             da.sval = lay->d_dsval.as<df>();
             da.svalG = lay->d_dsvalG.as<df>();
             da.svalT = lay->d_dsvalT.as<df>();

@@ -306,7 +306,8 @@ __device__ __forceinline__ bool cluster_pass(const CCtx<T>& c, const int par, co
             }
         }
         __syncthreads();
-        apply_D_tile<double, kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.cb0, c.cb1, c.sm.ZY, R0);
+        apply_D_tile<double, kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.cb0, c.cb1, c.sm.ZY, R0,
+                                      c.cp->nlarge[c.rank] > 0);
         __syncthreads();
         for (int i = tid; i < L; i += kCThreads) {
             const int r = R0 + i;
@@ -321,7 +322,8 @@ __device__ __forceinline__ bool cluster_pass(const CCtx<T>& c, const int par, co
             else c.X[r] = fma(xcoef, c.W[r], c.X[r]);
         }
         __syncthreads();
-        apply_D_tile<double, kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.cb0, c.cb1, c.sm.ZY, R0);
+        apply_D_tile<double, kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.cb0, c.cb1, c.sm.ZY, R0,
+                                      c.cp->nlarge[c.rank] > 0);
         __syncthreads();
         for (int i = tid; i < L; i += kCThreads) XIs[i] = s2[i];
     }

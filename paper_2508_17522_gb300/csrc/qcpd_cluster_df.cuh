@@ -3,9 +3,19 @@
 //
 // Every per-pass operation on vectors (row sums, epilogue, D Pi, block
 // sums) runs in df64 on the FP32 pipes; the LSQR scalar recurrences (one
-// lane per pass) stay in FP64.  The Krylov vectors live as df64 pairs: u, v,
-// xi in shared memory, w and x in the plan's FP64 arrays reinterpreted as
-// pairs for the kernel's lifetime (each CTA touches only its own rows).
+// lane per pass) stay in FP64.
+//
+// The vector a pass produces for the next one travels through L2, not
+// shared memory: each CTA stores its slice in the system's broadcast buffer
+// (gather-buffer layout, two buffers alternating by pass parity) and, after
+// the cluster barrier, every CTA reads the whole buffer with coalesced
+// loads.  The SM-to-SM network moves only about 10 bytes per cycle per SM,
+// several times less than an SM reads from L2.  Warps 1.. do that copy and
+// the row sums while warp 0 finishes the previous pass.
+//
+// The Krylov vectors live as df64 pairs: u, v, xi in shared memory, w and x
+// in the plan's FP64 arrays reinterpreted as pairs for the kernel's lifetime
+// (each CTA touches only its own rows).
 // Matrix values, per-row data and second-order-cone constants come as df64
 // copies made at plan time.
 //
@@ -27,6 +37,8 @@ struct SocDf {
 };
 
 struct ClusterDfArgs {
+    df* bcast;        // per cluster of the launch (at cluster * 2 bhalf): two broadcast buffers
+    int64_t bhalf;    // df entries per buffer (gather-buffer layout, even)
     const df* sval;   // SELL-32 values of M, M diag(c), M diag(w) per slot
     const df* svalG;
     const df* svalT;
@@ -63,6 +75,9 @@ struct CCtxDf {
     const SocDf* soc;
     df* W;  // the plan's w and x rows of this system, as df64 pairs
     df* X;
+    df* B;  // the system's broadcast buffers (bhalf entries each)
+    int64_t bhalf;
+    bool any_large;
     int* active;
     double kappa;
     int n, N, R0, L, C, rank, cb0, cb1, sl0, sl1;
@@ -73,7 +88,7 @@ struct CCtxDf {
 template <int NW>
 __device__ __forceinline__ void apply_D_df(const df* src, df* dst, int r0, int r1, int n, const int8_t* flag,
                                            const SocBlock* blocks, const SocDf* sdf, int cb0, int cb1,
-                                           const df* zy) {
+                                           const df* zy, bool any_large) {
     for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
         if (i < n) {
             dst[i - r0] = src[i - r0];
@@ -103,6 +118,7 @@ __device__ __forceinline__ void apply_D_df(const df* src, df* dst, int r0, int r
             for (int k = 1; k < B.dim; ++k) db[k] = df_fma(a, u[k], df_mul(S.htr, sb[k]));
         }
     }
+    if (!any_large) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int bi = cb0 + warp; bi < cb1; bi += NW) {
         const SocBlock B = blocks[bi];
@@ -272,6 +288,27 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
         if (pending) cluster_finish_df<PPASS, PROLE, SC>(c, par ^ 1);
         if (tid == 0) prep_scalars_df<PASS, ROLE, SC>(c);
     } else {
+        if (pending) {
+            // the previous pass's vector, from its broadcast buffer (L2)
+            const float4* src = reinterpret_cast<const float4*>(c.B + (par ^ 1) * c.bhalf);
+            float4* dst = reinterpret_cast<float4*>(c.F);
+            const int npairs = c.cp->FN >> 1;
+            constexpr int kU = 4, nth = kCThreads - 32;
+            for (int k0 = tid - 32; k0 < npairs; k0 += kU * nth) {
+                float4 v[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int k = k0 + u * nth;
+                    if (k < npairs) v[u] = __ldcg(src + k);
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int k = k0 + u * nth;
+                    if (k < npairs) dst[k] = v[u];
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(kCThreads - 32) : "memory");
+        }
         sell_rowsums_df(c, PASS == PASS_G ? c.valG : c.valT, c.F, s0);
     }
     __syncthreads();
@@ -301,6 +338,7 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
     df* s1 = c.s1;
     df* s2 = c.s2;
     df* XIs = c.XI;
+    df* bout = c.B + par * c.bhalf + c.cp->poff[c.rank];  // this CTA's slice of this pass's broadcast
 
     DfAcc ss = dfacc_zero(), dtop = dfacc_zero(), dbot = dfacc_zero();
     if (PASS == PASS_G) {
@@ -320,6 +358,7 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             if (SC) o = df_mul(o, c.rw[r]);
             const df nv = df_fma(c1, o, df_mul(nc2, out_s[i]));
             out_s[i] = nv;
+            bout[i] = nv;
             dfacc_fma(ss, nv, nv);
             if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c1, df_mul(nw, c.W[r]));
             else c.X[r] = df_fma(xc, c.W[r], c.X[r]);
@@ -338,7 +377,7 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             }
         }
         __syncthreads();
-        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY);
+        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY, c.any_large);
         __syncthreads();
         for (int i = tid; i < L; i += kCThreads) {
             const int r = R0 + i;
@@ -353,9 +392,12 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             else c.X[r] = df_fma(xc, c.W[r], c.X[r]);
         }
         __syncthreads();
-        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY);
+        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY, c.any_large);
         __syncthreads();
-        for (int i = tid; i < L; i += kCThreads) XIs[i] = s2[i];
+        for (int i = tid; i < L; i += kCThreads) {
+            XIs[i] = s2[i];
+            bout[i] = s2[i];
+        }
     }
     df v3[3] = {dfacc_result(ss), dfacc_result(dtop), dfacc_result(dbot)};
     block_reduce_df3(v3, c.scr);
@@ -365,36 +407,6 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
         c.red[4 * par + 2] = v3[2];
     }
     cl.sync();
-
-    {
-        const df* bvec = (PASS == PASS_GT) ? XIs : out_s;
-        float4* dst = reinterpret_cast<float4*>(c.F);
-        const int npairs = c.cp->FN >> 1;
-        constexpr int kU = 4;
-        for (int k0 = tid; k0 < npairs; k0 += kU * kCThreads) {
-            float4 v[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int k = k0 + u * kCThreads;
-                if (k < npairs) {
-                    int lo = 0, hi = c.C;  // the last CTA r with poff[r] <= 2k
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (c.cp->poff[mid] <= 2 * k) lo = mid;
-                        else hi = mid;
-                    }
-                    const float4* src = reinterpret_cast<const float4*>(cl.map_shared_rank(bvec, lo));
-                    v[u] = src[k - (c.cp->poff[lo] >> 1)];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int k = k0 + u * kCThreads;
-                if (k < npairs) dst[k] = v[u];
-            }
-        }
-    }
-    __syncthreads();
     return false;
 }
 
@@ -489,6 +501,9 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
     c.soc = da.soc + pr.soff;
     c.W = reinterpret_cast<df*>(gW);
     c.X = reinterpret_cast<df*>(gX);
+    c.B = da.bcast + (int64_t)(blockIdx.x / C) * 2 * da.bhalf;
+    c.bhalf = da.bhalf;
+    c.any_large = cp.nlarge[rank] > 0;
     c.active = a.active;
     c.kappa = pr.kappa;
     c.n = pr.n;

@@ -128,6 +128,7 @@ struct ClusterProb {
     int32_t poff[kMaxCluster + 1];
     int32_t cb[kMaxCluster + 1];      // CTA r's SOC blocks [cb[r], cb[r+1]) (problem-relative)
     int32_t sl[kMaxCluster + 1];      // CTA r's row-sum slices [sl[r], sl[r+1]) (global indices)
+    int32_t nlarge[kMaxCluster];      // CTA r's SOC blocks with more than kSocThread entries
 };
 
 // Four partial sums carried through the reductions.
@@ -337,7 +338,7 @@ constexpr int kSocThread = 32;
 template <typename T, int NW = kWarps>
 __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int r0, int r1, int n,
                                              const int8_t* flag, const SocBlock* blocks, int cb0,
-                                             int cb1, const T* zy, int zoff = 0) {
+                                             int cb1, const T* zy, int zoff = 0, bool any_large = true) {
     for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
         if (i < n) {
             dst[i - r0] = src[i - r0];
@@ -373,6 +374,7 @@ __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int
         }
     }
     // large blocks: one warp each
+    if (!any_large) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int bi = cb0 + warp; bi < cb1; bi += NW) {
         const SocBlock B = blocks[bi];

@@ -136,6 +136,7 @@ struct qcp_plan {
     int cluster_cap = 0;  // CTAs per system asked for (0: per call from the number of systems)
     std::map<int, std::unique_ptr<qcpd::ClusterLayout>> clusters;  // by CTAs asked for
     qcpd::DevBuf d_csys;  // system lists of the cluster launches
+    qcpd::DevBuf d_bcast; // broadcast buffers of the double-float cluster kernel
     std::vector<int32_t> h_csys;
 
     std::map<qcpd::GraphKey, cudaGraphExec_t> graphs;
