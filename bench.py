@@ -67,23 +67,34 @@ def algorithmic_bytes_per_pass(prob):
     return b_iter / 2.0
 
 
-def kernel_source_hash():
+# the dominant kernel of each engine and the sources it is built from
+KERNELS = {
+    "passes": ("k_pass", ("qcpd_kernels.cuh", "qcpd_common.cuh")),
+    "persistent": ("k_persist", ("qcpd_kernels.cuh", "qcpd_common.cuh")),
+    "cluster": ("k_cluster_df", ("qcpd_cluster_df.cuh", "qcpd_cluster.cuh", "qcpd_df64.cuh", "qcpd_kernels.cuh",
+                                 "qcpd_common.cuh")),
+    "cluster_fp64": ("k_cluster", ("qcpd_cluster.cuh", "qcpd_kernels.cuh", "qcpd_common.cuh")),
+}
+
+
+def kernel_source_hash(engine):
     h = hashlib.sha256()
-    for f in ("qcpd_kernels.cuh", "qcpd_common.cuh"):
+    for f in KERNELS[engine][1]:
         with open(os.path.join(ROOT, "paper_2508_17522_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name, bytes_per_pass):
-    """dram read+write bytes per pass launch from a committed ncu summary
-    (profiles/*.json), if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"k_pass_{workload_name}_dram.json")
+def recorded_traffic(engine, workload_name):
+    """dram read+write bytes per pass of the engine's dominant kernel from a
+    committed ncu summary (profiles/*.json), if it was taken on the current
+    kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{KERNELS[engine][0]}_{workload_name}_dram.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_source_sha") != kernel_source_hash():
+    if rec.get("kernel_source_sha") != kernel_source_hash(engine):
         return None
     return rec.get("dram_bytes_per_pass")
 
@@ -171,6 +182,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
     ap.add_argument("--workload", default="config2", choices=["config2", "config3"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
+    ap.add_argument("--maxiter", type=int, default=400000,
+                    help="Krylov iteration cap (lower it only for profiling runs: solves then stop early)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -223,7 +237,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     plan = q.qcp_plan_create(q.problem_tensors(prob, dev), torch.float64, max_rhs=k, stream=stream)
-    opts = q.options(rtol=rtol, maxiter=400000, precond=args.precond)
+    opts = q.options(rtol=rtol, maxiter=args.maxiter, precond=args.precond, engine=args.engine)
     cat = lambda nm: np.concatenate([getattr(d, nm) for d in dirs])
     host = {nm: torch.as_tensor(cat(nm)).pin_memory() for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
     with torch.cuda.stream(stream):
@@ -321,24 +335,30 @@ def main():
     peak = peaks.get("hbm_gbs")
     peak_note = "measured" if peak else "fallback"
     peak = peak or 6800.0
+    engine = plan.last_engine()
+    kname = KERNELS[engine][0]
     bpp = algorithmic_bytes_per_pass(prob) * k
     avg_pass_s = (pass_ms[0] / 1e3) / max(passes[0], 1)
     achieved = bpp / avg_pass_s / 1e9
-    traffic = recorded_traffic(args.workload, bpp)
+    traffic = recorded_traffic(engine, args.workload)
 
     if rank == 0:
         line = {
             "metric": metric, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "solver": "LSQR",
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64" if engine == "cluster" else "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "solver": "LSQR", "engine": engine,
+                       "arithmetic": ("vectors in double-float (binary32 pairs), LSQR scalars f64, data f64"
+                                      if engine == "cluster" else "f64"),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every timed step "
                        f"({L2_FLUSH_BYTES >> 20} MiB write)", "status": statuses,
                        "max_true_rel_residual": max_res},
-            "roofline": {"bound": "hbm", "kernel": "k_pass (one product with F or F^T, all systems)",
-                         "achieved": achieved, "peak": peak, "peak_source": peak_note, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "bytes_per_launch": bpp, "avg_launch_us": avg_pass_s * 1e6},
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_note, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "per": "pass (one product with F or F^T for all systems; a cluster-engine launch "
+                                "runs every pass of a solve, so per launch the ratio is the same)",
+                         "bytes_per_pass": bpp, "avg_pass_us": avg_pass_s * 1e6, "passes": passes[0]},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": dev_launches,

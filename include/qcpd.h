@@ -269,6 +269,11 @@ int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, in
    them.  Returns QCP_ERR_ARG for other values. */
 int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas);
 
+/* The qcp_engine the most recent JVP/VJP call of the plan ran: PASSES,
+   PERSISTENT, CLUSTER (double-float vector arithmetic) or CLUSTER_FP64; -1
+   for a NULL plan. */
+int qcp_plan_last_engine(const qcp_plan* plan);
+
 /* Number of kernel launches made by the most recent JVP/VJP call of the plan
    (graph replays counted per kernel node). */
 int64_t qcp_plan_last_launches(const qcp_plan* plan);

@@ -88,6 +88,8 @@ def lib():
         f.argtypes = [c_void_p, P(qcp_options), c_int32] + [c_void_p] * 7 + [P(qcp_info)]
     L.qcp_plan_set_schedule.restype = ctypes.c_int
     L.qcp_plan_set_schedule.argtypes = [c_void_p, c_int32, c_int32, c_int32]
+    L.qcp_plan_last_engine.restype = ctypes.c_int
+    L.qcp_plan_last_engine.argtypes = [c_void_p]
     L.qcp_plan_set_cluster.restype = ctypes.c_int
     L.qcp_plan_set_cluster.argtypes = [c_void_p, c_int32]
     L.qcp_plan_last_launches.restype = c_int64

@@ -176,6 +176,11 @@ class Plan:
         _check(N.lib().qcp_plan_last_timing(self._h, ctypes.byref(ms), ctypes.byref(n)), "qcp_plan_last_timing")
         return ms.value, n.value
 
+    def last_engine(self) -> str:
+        """Engine of the last call: passes, persistent, cluster or cluster_fp64."""
+        e = N.lib().qcp_plan_last_engine(self._h)
+        return {v: k for k, v in _ENGINE.items()}.get(e, str(e))
+
     def set_cluster(self, max_ctas: int = 0):
         """CTAs per system of the cluster engine (0: chosen per call)."""
         _check(N.lib().qcp_plan_set_cluster(self._h, int(max_ctas)), "qcp_plan_set_cluster")

@@ -306,6 +306,7 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
     const size_t smem = tile_smem_bytes(p->rmax);
     QCP_TRY(set_smem_attrs<T>(smem));
     p->last_launches = 0;
+    p->last_engine = engine;
     p->pass_ms = 0.0;
     p->pass_launches = 0;
     QCP_CUDA(cudaMemsetAsync(p->d_active.p, 0, sizeof(int), st));
@@ -755,6 +756,8 @@ int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas) {
 }
 
 int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }
+
+int qcp_plan_last_engine(const qcp_plan* plan) { return plan ? plan->last_engine : -1; }
 
 int qcp_derivative_jvp_noalloc(qcp_plan* plan, const qcp_options* opts, const void* dP, const void* dA,
                                const void* dq, const void* db, void* dx, void* dy, void* ds, qcp_info* info) {

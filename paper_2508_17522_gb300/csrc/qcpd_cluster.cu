@@ -497,7 +497,9 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
         ca.L = L;
         ca.pad = 0;
         ca.max_passes = 2 * (opts.maxiter + 2);
-        if (lay->df_ok && opts.engine != QCP_ENGINE_CLUSTER_FP64) {
+        const bool use_df = lay->df_ok && opts.engine != QCP_ENGINE_CLUSTER_FP64;
+        if (!use_df) p->last_engine = QCP_ENGINE_CLUSTER_FP64;
+        if (use_df) {
             ClusterDfArgs da;
             da.bhalf = even_up(FN);
             const size_t need = sizeof(df) * 2 * (size_t)da.bhalf * (size_t)nclus;

@@ -141,6 +141,7 @@ struct qcp_plan {
 
     std::map<qcpd::GraphKey, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;
+    int last_engine = 0;  // qcp_engine the last call ran (CLUSTER_FP64 when the cluster kernel stayed in FP64)
     // device time of the iteration chunks of the last call (CUDA events on
     // the plan's stream) and the number of pass launches they contain
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
