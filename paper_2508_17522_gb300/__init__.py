@@ -8,4 +8,5 @@ from .api import (  # noqa: F401
     qcp_derivative_jvp_multi, qcp_derivative_jvp_noalloc, qcp_derivative_vjp, qcp_derivative_vjp_multi,
     qcp_plan_create,
 )
+from .autograd import QCPSolution, qcp_layer  # noqa: F401
 from .buildlib import build  # noqa: F401
