@@ -118,9 +118,13 @@ typedef struct {
 
 typedef enum {
     QCP_PRECOND_NONE = 0,     /* LSQR on F itself: the plain method of Sec. 3.1 */
-    QCP_PRECOND_EQUILIBRATE = 1 /* LSQR on W F C: W = 1/(row norms of F), C = 1/(column norms of W F),
+    QCP_PRECOND_EQUILIBRATE = 1, /* LSQR on W F C: W = 1/(row norms of F), C = 1/(column norms of W F),
                                    C constant on each SOC block; D Pi's off-diagonal SOC terms are
                                    left out of the norms (any positive diagonal is a valid choice) */
+    QCP_PRECOND_DIAG = 2        /* LSQR on F C with C = diag(opts->precond_d), a caller-given positive
+                                   right preconditioner (for instance the learned one), averaged
+                                   over each SOC block (C must commute with D Pi); pass or
+                                   persistent engine */
 } qcp_precond;
 
 /* How the Krylov iterations are run on the GPU (all give the same iterates up
@@ -137,7 +141,8 @@ typedef enum {
                                    memory and only hardware cluster barriers separate passes.
                                    Needs every system to fit (about 8 N + 56 N / C bytes per CTA
                                    for C CTAs); QCP_ERR_ARG otherwise */
-    QCP_ENGINE_AUTO = 3,        /* QCP_ENGINE_CLUSTER when every system fits, else PASSES */
+    QCP_ENGINE_AUTO = 3,        /* QCP_ENGINE_CLUSTER when every system fits (and precond is not
+                                   QCP_PRECOND_DIAG), else PASSES */
     QCP_ENGINE_CLUSTER_FP64 = 4 /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,
@@ -159,6 +164,13 @@ typedef struct {
     int32_t precond;          /* qcp_precond */
     int32_t engine;           /* qcp_engine */
     double kink_tol;          /* QCP_WARN_NEAR_KINK threshold on info.kink_margin */
+    const double* warm_start; /* device, N = n + m + 1 entries per system (system-major), or NULL for
+                                 the zero start: the initial iterate dz (JVP) or r (VJP) in the
+                                 embedding's coordinates; its tau entry is ignored (gauge dz_N = 0).
+                                 LSQR then solves for the correction, and rtol stays relative to the
+                                 right-hand side itself */
+    const double* precond_d;  /* device, N entries per problem (all directions of a problem share
+                                 them): the positive column scaling C of QCP_PRECOND_DIAG */
 } qcp_options;
 
 typedef struct {
@@ -176,7 +188,7 @@ const char* qcp_last_error(void);
 
 /* Fill *opts with defaults: LSQR, rtol 1e-10, maxiter 100000, check_every 32,
    use_graph 1, compute_residual 1, precond QCP_PRECOND_NONE,
-   engine QCP_ENGINE_AUTO, kink_tol 0. */
+   engine QCP_ENGINE_AUTO, kink_tol 0, warm_start NULL, precond_d NULL. */
 void qcp_default_options(qcp_options* opts);
 
 /* Library version as an integer (major * 10000 + minor * 100 + patch). */
@@ -311,6 +323,71 @@ int qcp_derivative_jvp_noalloc(qcp_plan* plan, const qcp_options* opts, const vo
    (products with F or F^T over all systems) they contain; their ratio is
    the average duration of one pass.  Errors: QCP_ERR_ARG (null plan). */
 int qcp_plan_last_timing(const qcp_plan* plan, double* pass_ms, int64_t* passes);
+
+/* The embedding-space solution of the plan's most recent call: dz (JVP) or
+   r (VJP; F^T r = -g_phi), N = n + m + 1 doubles per system of that call
+   (system-major), device pointer.  The training targets of the learned form
+   come from here.  QCP_ERR_ARG before the first call. */
+int qcp_plan_last_solution(qcp_plan* plan, double* out);
+
+/* The plan's equilibration: row scaling w and column scaling c (N per
+   problem, device, concatenated over the plan's problems). */
+int qcp_plan_scalings(const qcp_plan* plan, double* w, double* c);
+
+/* ---------------------------------------------------------------------------
+ * Learned form: a network on per-row features predicts a warm start and a
+ * diagonal right preconditioner for the Krylov solve (the paper has no
+ * learned part; this follows the problem statement of the build).
+ * ------------------------------------------------------------------------- */
+#define QCP_MLP_IN 16
+#define QCP_MLP_HIDDEN 256
+#define QCP_MLP_OUT 2
+
+/* Per-row features of every embedding row of the plan's problems (N per
+   problem, concatenated), QCP_MLP_IN floats each, row-major, device:
+   0 one; 1-5 one-hot row kind (x, zero cone, R+, SOC, tau); 6 x_i, y_i or 1;
+   7 z_i = y_i - s_i; 8 q_i or b_i; 9 g_i = (2Px + q)_i, s_i or kappa; 10 the
+   diagonal of D Pi; 11 log(||row of M||) / 4; 12 log(nnz(row of M) + 1) / 4;
+   13 SOC block size / 32; 14 1 on an SOC block's entries after its first;
+   15 feature 6 times feature 10 (0 where a feature does not apply). */
+int qcp_plan_features(qcp_plan* plan, float* out);
+
+typedef struct qcp_mlp qcp_mlp;
+
+/* Number of parameters, packed W1 [256 x 16], b1 [256], W2 [256 x 256],
+   b2 [256], W3 [2 x 256], b3 [2] (FP32; W[j][i] maps input i to output j). */
+int32_t qcp_mlp_param_count(void);
+
+/* A 16-256-256-2 ReLU network for batches of up to max_rows rows on the given
+   stream: BF16 weights and activations, FP32 accumulation (tensor cores),
+   FP32 master weights and Adam state.  Parameters start at 0: set them with
+   qcp_mlp_set_params. */
+int qcp_mlp_create(int32_t max_rows, void* stream, qcp_mlp** out);
+int qcp_mlp_destroy(qcp_mlp* mlp);
+int qcp_mlp_set_params(qcp_mlp* mlp, const float* host_params);  /* also resets Adam */
+/* Per-feature input normalisation x' = (x - mean) * inv_std (host arrays of
+   QCP_MLP_IN; default 0 and 1), applied before x is rounded to BF16. */
+int qcp_mlp_set_input_norm(qcp_mlp* mlp, const float* mean, const float* inv_std);
+int qcp_mlp_get_params(const qcp_mlp* mlp, float* host_params);
+
+/* y = W3 relu(W2 relu(W1 x' + b1) + b2) + b3 for rows x rows (device x:
+   rows x 16, y: rows x 2; x' the normalised x), with x', the hidden
+   activations and the weights rounded to BF16 (nearest even) where they
+   enter a product. */
+int qcp_mlp_forward(qcp_mlp* mlp, const float* x, int32_t rows, float* y);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the
+   weighted squared error sum w (y - target)^2 / max(sum w, 1) (device
+   rows x 2 arrays).  *loss_host gets the loss before the step; grad_host,
+   if not NULL, the gradient in the packed layout (host). */
+int qcp_mlp_train_step(qcp_mlp* mlp, const float* x, const float* target, const float* weight, int32_t rows,
+                       float lr, double* loss_host, float* grad_host);
+
+/* With v = y + offset (offset: rows x 2, or NULL for 0): warm_start[i] =
+   scale * v[i][0] and precond_d[i] = exp(clamp(v[i][1], -8, 8)) (either
+   output may be NULL); device arrays. */
+int qcp_mlp_decode(const float* y, const float* offset, int64_t rows, double scale, double* warm_start,
+                   double* precond_d, void* stream);
 
 #ifdef __cplusplus
 }

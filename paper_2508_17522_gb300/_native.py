@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "QCP_OK", 1: "QCP_ERR_ARG", 2: "QCP_ERR_CUDA", 3: "QCP_ERR_AL
                 4: "QCP_NOT_CONVERGED", 5: "QCP_BREAKDOWN", 6: "QCP_ERR_TIMEOUT",
                 7: "QCP_WARN_NEAR_KINK"}
 QCP_F64, QCP_F32 = 0, 1
-QCP_PRECOND_NONE, QCP_PRECOND_EQUILIBRATE = 0, 1
+QCP_PRECOND_NONE, QCP_PRECOND_EQUILIBRATE, QCP_PRECOND_DIAG = 0, 1, 2
 QCP_ENGINE_PASSES, QCP_ENGINE_PERSISTENT, QCP_ENGINE_CLUSTER, QCP_ENGINE_AUTO, QCP_ENGINE_CLUSTER_FP64 = 0, 1, 2, 3, 4
 
 
@@ -41,7 +41,8 @@ class qcp_solution(ctypes.Structure):
 class qcp_options(ctypes.Structure):
     _fields_ = [("solver", c_int32), ("rtol", c_double), ("maxiter", c_int64), ("check_every", c_int32),
                 ("use_graph", c_int32), ("compute_residual", c_int32), ("precond", c_int32),
-                ("engine", c_int32), ("kink_tol", c_double)]
+                ("engine", c_int32), ("kink_tol", c_double),
+                ("warm_start", c_void_p), ("precond_d", c_void_p)]
 
 
 class qcp_info(ctypes.Structure):
@@ -88,6 +89,23 @@ def lib():
         f.argtypes = [c_void_p, P(qcp_options), c_int32] + [c_void_p] * 7 + [P(qcp_info)]
     L.qcp_plan_set_schedule.restype = ctypes.c_int
     L.qcp_plan_set_schedule.argtypes = [c_void_p, c_int32, c_int32, c_int32]
+    for name, args in (("qcp_plan_last_solution", [c_void_p, c_void_p]),
+                       ("qcp_plan_scalings", [c_void_p, c_void_p, c_void_p]),
+                       ("qcp_plan_features", [c_void_p, c_void_p]),
+                       ("qcp_mlp_create", [c_int32, c_void_p, P(c_void_p)]),
+                       ("qcp_mlp_destroy", [c_void_p]),
+                       ("qcp_mlp_set_params", [c_void_p, c_void_p]),
+                       ("qcp_mlp_get_params", [c_void_p, c_void_p]),
+                       ("qcp_mlp_set_input_norm", [c_void_p, c_void_p, c_void_p]),
+                       ("qcp_mlp_forward", [c_void_p, c_void_p, c_int32, c_void_p]),
+                       ("qcp_mlp_train_step", [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, ctypes.c_float,
+                                               P(c_double), c_void_p]),
+                       ("qcp_mlp_decode", [c_void_p, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p])):
+        f = getattr(L, name)
+        f.restype = ctypes.c_int
+        f.argtypes = args
+    L.qcp_mlp_param_count.restype = c_int32
+    L.qcp_mlp_param_count.argtypes = []
     L.qcp_plan_last_engine.restype = ctypes.c_int
     L.qcp_plan_last_engine.argtypes = [c_void_p]
     L.qcp_plan_set_cluster.restype = ctypes.c_int

@@ -93,7 +93,7 @@ def _c_problem(pt: ProblemTensors):
     return prob, sol
 
 
-_PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE}
+_PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE, "diag": N.QCP_PRECOND_DIAG}
 
 
 _ENGINE = {"passes": N.QCP_ENGINE_PASSES, "persistent": N.QCP_ENGINE_PERSISTENT,
@@ -101,17 +101,29 @@ _ENGINE = {"passes": N.QCP_ENGINE_PASSES, "persistent": N.QCP_ENGINE_PERSISTENT,
 
 
 def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_residual=True, precond="none",
-            kink_tol=0.0, engine="auto"):
-    """qcp_options; precond is "none" (the plain method) or "equilibrate";
+            kink_tol=0.0, engine="auto", warm_start=None, precond_d=None):
+    """qcp_options; precond is "none" (the plain method), "equilibrate" or
+    "diag" (precond_d: a float64 device tensor, N per problem); warm_start:
+    a float64 device tensor of N per system (dz for the JVP, r for the VJP).
     engine is "passes" (one launch per pass), "persistent" (one cooperative
     launch), "cluster" (one thread-block cluster per system, double-float
-    vector arithmetic), "cluster_fp64" (the same in FP64) or "auto"."""
+    vector arithmetic), "cluster_fp64" (the same in FP64) or "auto".  The
+    returned object keeps the tensors alive."""
     o = N.qcp_options()
     N.lib().qcp_default_options(ctypes.byref(o))
     o.rtol, o.maxiter, o.check_every = float(rtol), int(maxiter), int(check_every)
     o.use_graph, o.compute_residual, o.kink_tol = int(bool(use_graph)), int(bool(compute_residual)), float(kink_tol)
     o.precond = _PRECOND[precond] if isinstance(precond, str) else int(precond)
     o.engine = _ENGINE[engine] if isinstance(engine, str) else int(engine)
+    keep = []
+    for name, t in (("warm_start", warm_start), ("precond_d", precond_d)):
+        if t is not None:
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+                raise ValueError(f"{name} must be a float64 CUDA tensor")
+            t = t.contiguous()
+            keep.append(t)
+            setattr(o, name, t.data_ptr())
+    o._keep = keep
     return o
 
 

@@ -21,8 +21,10 @@ namespace qcpd {
 const char* last_error();
 int create_plan(qcp_plan* p, const qcp_problem* probs, const qcp_solution* sols);
 
+// precond: QCP_PRECOND_NONE, _EQUILIBRATE or _DIAG (caller's C, W = I)
 template <typename T>
-static PlanView<T> view(qcp_plan* p, bool scaled) {
+static PlanView<T> view(qcp_plan* p, int precond) {
+    const bool scaled = precond != QCP_PRECOND_NONE;
     PlanView<T> v;
     v.tiles = p->d_tiles.as<Tile>();
     v.sys = p->d_sys.as<Sys>();
@@ -41,6 +43,12 @@ static PlanView<T> view(qcp_plan* p, bool scaled) {
     v.rw = p->d_rw.as<double>();
     v.cd = p->d_cd.as<double>();
     v.scaled = scaled ? 1 : 0;
+    if (precond == QCP_PRECOND_DIAG) {  // W = I, the caller's column scaling (block-averaged)
+        v.rw = p->d_onesD.as<double>();
+        v.cd = p->d_cdD.as<double>();
+        v.mvalG = p->d_mvalD.as<T>();
+        v.mvalT = p->d_mval.as<T>();
+    }
     v.mvmap = p->d_mvmap.as<int32_t>();
     v.coefA = p->d_coefA.as<double>();
     v.coefB = p->d_coefB.as<double>();
@@ -73,6 +81,8 @@ static int set_smem_attrs_sc(size_t smem) {
     QCP_CUDA(allow_smem(k_pass<PASS_GT, ROLE_U, SC, T>, smem));
     QCP_CUDA(allow_smem(k_pass<PASS_GT, ROLE_V, SC, T>, smem));
     QCP_CUDA(allow_smem(k_pass<PASS_GT, ROLE_RES, SC, T>, smem));
+    QCP_CUDA(allow_smem(k_pass<PASS_G, ROLE_WARM, SC, T>, smem));
+    QCP_CUDA(allow_smem(k_pass<PASS_GT, ROLE_WARM, SC, T>, smem));
     return QCP_OK;
 }
 
@@ -82,6 +92,7 @@ static int set_smem_attrs(size_t smem) {
     QCP_TRY((set_smem_attrs_sc<T, true>(smem)));
     QCP_CUDA(allow_smem(k_vjp_rhs<T>, smem));
     QCP_CUDA(allow_smem(k_jvp_out<T>, smem));
+    QCP_CUDA(allow_smem(k_dpi<T>, smem));
     return QCP_OK;
 }
 
@@ -114,7 +125,7 @@ static int run_chunk(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int 
         p->last_launches += 2 * chunk;
         return QCP_OK;
     }
-    GraphKey key{mode, nsys, chunk, v.scaled};
+    GraphKey key{mode, nsys, chunk, p->view_precond};
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -263,6 +274,61 @@ static void launch_output(qcp_plan* p, int mode, int nsys, const PlanView<T>& v,
     p->last_launches += 1 + (residual ? 1 : 0);
 }
 
+// QCP_PRECOND_DIAG: the caller's column scaling C, averaged over each
+// second-order-cone block (the G-pass multiplies M diag(C) with D Pi x, which
+// equals M D Pi C x only when C is constant on every block), unit W, and
+// M diag(C).
+template <typename T>
+__global__ void k_scale_cols(const T* mval, const int32_t* mcol, int64_t k0, int64_t k1, const double* d, T* out) {
+    const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < k1) out[k] = (T)((double)mval[k] * d[mcol[k]]);
+}
+
+__global__ void k_block_mean(const SocBlock* blocks, int64_t nb, double* d) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const SocBlock B = blocks[b];
+    double s = 0.0;
+    for (int k = 0; k < B.dim; ++k) s += d[B.start + k];
+    s /= B.dim;
+    for (int k = 0; k < B.dim; ++k) d[B.start + k] = s;
+}
+
+__global__ void k_set_ones(double* x, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 1.0;
+}
+
+
+template <typename T>
+static int prepare_diag(qcp_plan* p, const double* d) {
+    cudaStream_t st = p->stream;
+    if (!p->d_cdD.p) {
+        QCP_TRY(p->d_cdD.alloc(sizeof(double) * (size_t)p->N_tot));
+        QCP_TRY(p->d_onesD.alloc(sizeof(double) * (size_t)p->N_tot));
+        QCP_TRY(p->d_mvalD.alloc(sizeof(T) * (size_t)(p->mnnz + 16)));
+        QCP_CUDA(cudaMemsetAsync(p->d_mvalD.p, 0, sizeof(T) * (size_t)(p->mnnz + 16), st));
+        k_set_ones<<<(unsigned)((p->N_tot + 255) / 256), 256, 0, st>>>(p->d_onesD.as<double>(), p->N_tot);
+    }
+    QCP_CUDA(cudaMemcpyAsync(p->d_cdD.p, d, sizeof(double) * (size_t)p->N_tot, cudaMemcpyDeviceToDevice, st));
+    for (int pi = 0; pi < p->nprob; ++pi) {
+        const Prob& pr = p->hprob[pi];
+        if (pr.nsoc > 0)
+            k_block_mean<<<(unsigned)((pr.nsoc + 255) / 256), 256, 0, st>>>(p->d_blocks.as<SocBlock>() + pr.soff,
+                                                                             pr.nsoc, p->d_cdD.as<double>() + pr.doff);
+    }
+    for (int pi = 0; pi < p->nprob; ++pi) {
+        const Prob& pr = p->hprob[pi];
+        const int64_t k0 = p->h_mrowptr[pr.mrow], k1 = p->h_mrowptr[pr.mrow + pr.n + pr.m + 1];
+        if (k1 > k0)
+            k_scale_cols<T><<<(unsigned)((k1 - k0 + 255) / 256), 256, 0, st>>>(
+                p->d_mval.as<T>(), p->d_mcol.as<int32_t>(), k0, k1, p->d_cdD.as<double>() + pr.doff,
+                p->d_mvalD.as<T>());
+    }
+    QCP_CUDA(cudaGetLastError());
+    return QCP_OK;
+}
+
 // mode 0: JVP, 1: VJP.  nsys systems (the first nsys of the plan).
 template <typename T>
 static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, const RhsArgs<T>& rin,
@@ -278,8 +344,18 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         set_error("only solver 0 (LSQR) is built");
         return QCP_ERR_ARG;
     }
-    if (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE) {
-        set_error("precond must be QCP_PRECOND_NONE or QCP_PRECOND_EQUILIBRATE");
+    if (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE &&
+        opts.precond != QCP_PRECOND_DIAG) {
+        set_error("precond must be QCP_PRECOND_NONE, _EQUILIBRATE or _DIAG");
+        return QCP_ERR_ARG;
+    }
+    if (opts.precond == QCP_PRECOND_DIAG && !opts.precond_d) {
+        set_error("QCP_PRECOND_DIAG needs opts->precond_d");
+        return QCP_ERR_ARG;
+    }
+    if (opts.precond == QCP_PRECOND_DIAG &&
+        (opts.engine == QCP_ENGINE_CLUSTER || opts.engine == QCP_ENGINE_CLUSTER_FP64)) {
+        set_error("QCP_PRECOND_DIAG runs on the pass or persistent engine");
         return QCP_ERR_ARG;
     }
     if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_CLUSTER_FP64) {
@@ -287,6 +363,7 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         return QCP_ERR_ARG;
     }
     int engine = opts.engine;
+    if (engine == QCP_ENGINE_AUTO && opts.precond == QCP_PRECOND_DIAG) engine = QCP_ENGINE_PASSES;
     if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER_FP64) {
         bool fits = false;
         QCP_TRY(cluster_ready(p, nsys, &fits));
@@ -300,13 +377,16 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         }
     }
     cudaStream_t st = p->stream;
-    const bool scaled = opts.precond == QCP_PRECOND_EQUILIBRATE;
-    const PlanView<T> v = view<T>(p, scaled);
+    if (opts.precond == QCP_PRECOND_DIAG) QCP_TRY(prepare_diag<T>(p, opts.precond_d));
+    p->view_precond = opts.precond;
+    const PlanView<T> v = view<T>(p, opts.precond);
     const int ntiles = p->batched ? p->ntiles : nsys * p->tiles_per_sys;
     const size_t smem = tile_smem_bytes(p->rmax);
     QCP_TRY(set_smem_attrs<T>(smem));
     p->last_launches = 0;
     p->last_engine = engine;
+    p->last_mode = mode;
+    p->last_nsys = nsys;
     p->pass_ms = 0.0;
     p->pass_launches = 0;
     QCP_CUDA(cudaMemsetAsync(p->d_active.p, 0, sizeof(int), st));
@@ -315,6 +395,23 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
     ra.maxiter = opts.maxiter;
     if (mode == 0) k_jvp_rhs<T><<<ntiles, kThreads, 0, st>>>(v, ra);
     else k_vjp_rhs<T><<<ntiles, kThreads, smem, st>>>(v, ra);
+    if (opts.warm_start) {
+        // x0 from the caller's iterate; the right-hand side becomes b - Op x0
+        int maxN = 1;
+        for (int s = 0; s < nsys; ++s) {
+            const Prob& pr = p->hprob[p->hsys[s].prob];
+            maxN = std::max(maxN, pr.n + pr.m + 1);
+        }
+        k_warm_init<T><<<dim3((unsigned)std::min(1024, (maxN + 255) / 256), (unsigned)nsys), 256, 0, st>>>(
+            v, opts.warm_start, mode);
+        if (mode == 0) {
+            k_dpi<T><<<ntiles, kThreads, smem, st>>>(v);
+            launch_pass<PASS_G, ROLE_WARM, T>(v, ntiles, smem, st);
+        } else {
+            launch_pass<PASS_GT, ROLE_WARM, T>(v, ntiles, smem, st);
+        }
+        p->last_launches += mode == 0 ? 3 : 2;
+    }
     launch_v_pass<T>(mode, v, ntiles, smem, st);
     QCP_CUDA(cudaGetLastError());
     p->last_launches += 2;
@@ -553,7 +650,7 @@ static size_t noalloc_layout(qcp_plan* p, unsigned char* base, PlanView<T>* v, b
     unsigned char* vec[6];
     for (int i = 0; i < 6; ++i) vec[i] = take(N * sizeof(double));
     if (v) {
-        *v = view<T>(p, scaled);
+        *v = view<T>(p, scaled ? QCP_PRECOND_EQUILIBRATE : QCP_PRECOND_NONE);
         v->state = reinterpret_cast<LsqrState*>(state);
         v->R = Reduce{reinterpret_cast<Part*>(tpart), reinterpret_cast<Part*>(gpart),
                       reinterpret_cast<int32_t*>(gcnt), reinterpret_cast<int32_t*>(scnt), p->d_groups.as<Group>()};
@@ -577,8 +674,9 @@ static int jvp_noalloc(qcp_plan* p, const qcp_options* opts_in, const void* dP, 
     if (opts_in) opts = *opts_in;
     else qcp_default_options(&opts);
     if (!(opts.rtol >= 0.0) || opts.maxiter < 1 || opts.check_every < 1 || opts.solver != 0 ||
-        (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE)) {
-        set_error("bad options: rtol >= 0, maxiter >= 1, check_every >= 1, solver 0, known precond required");
+        (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE) || opts.warm_start) {
+        set_error("bad options: rtol >= 0, maxiter >= 1, check_every >= 1, solver 0, precond NONE or EQUILIBRATE "
+                  "and no warm start required");
         return QCP_ERR_ARG;
     }
     const size_t need = noalloc_layout<T>(p, nullptr, nullptr, false);
@@ -668,6 +766,8 @@ void qcp_default_options(qcp_options* o) {
     o->compute_residual = 1;
     o->precond = QCP_PRECOND_NONE;
     o->engine = QCP_ENGINE_AUTO;
+    o->warm_start = nullptr;
+    o->precond_d = nullptr;
     o->kink_tol = 0.0;
 }
 
@@ -758,6 +858,26 @@ int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas) {
 int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }
 
 int qcp_plan_last_engine(const qcp_plan* plan) { return plan ? plan->last_engine : -1; }
+
+int qcp_plan_last_solution(qcp_plan* plan, double* out) {
+    if (!plan || !out || plan->last_mode < 0) {
+        set_error("qcp_plan_last_solution: null argument or no solve yet");
+        return QCP_ERR_ARG;
+    }
+    int maxN = 1;
+    for (int s = 0; s < plan->last_nsys; ++s) {
+        const Prob& pr = plan->hprob[plan->hsys[s].prob];
+        maxN = std::max(maxN, pr.n + pr.m + 1);
+    }
+    const dim3 grid((unsigned)std::min(1024, (maxN + 255) / 256), (unsigned)plan->last_nsys);
+    if (plan->dtype == QCP_F64)
+        k_export<double><<<grid, 256, 0, plan->stream>>>(view<double>(plan, plan->view_precond), plan->last_mode, out);
+    else
+        k_export<float><<<grid, 256, 0, plan->stream>>>(view<float>(plan, plan->view_precond), plan->last_mode, out);
+    QCP_CUDA(cudaGetLastError());
+    QCP_CUDA(cudaStreamSynchronize(plan->stream));
+    return QCP_OK;
+}
 
 int qcp_derivative_jvp_noalloc(qcp_plan* plan, const qcp_options* opts, const void* dP, const void* dA,
                                const void* dq, const void* db, void* dx, void* dy, void* ds, qcp_info* info) {

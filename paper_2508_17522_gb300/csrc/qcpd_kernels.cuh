@@ -20,7 +20,7 @@
 namespace qcpd {
 
 enum PassKind { PASS_G = 0, PASS_GT = 1 };
-enum RoleKind { ROLE_U = 0, ROLE_V = 1, ROLE_RES = 2 };
+enum RoleKind { ROLE_U = 0, ROLE_V = 1, ROLE_RES = 2, ROLE_WARM = 3 };
 
 template <typename T>
 struct PlanView {
@@ -407,7 +407,7 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
     double* s2 = sm.s2;
 
     const double* in = (ROLE == ROLE_U) ? a.V + sy.voff : (ROLE == ROLE_V ? a.U + sy.voff : a.X + sy.voff);
-    double* outv = (ROLE == ROLE_U) ? a.U + sy.voff : (ROLE == ROLE_V ? a.V + sy.voff : nullptr);
+    double* outv = (ROLE == ROLE_U || ROLE == ROLE_WARM) ? a.U + sy.voff : (ROLE == ROLE_V ? a.V + sy.voff : nullptr);
     const double* cA = a.coefA + pr.doff;
     const double* cB = a.coefB + pr.doff;
     const double* rw = a.rw + pr.doff;
@@ -469,6 +469,10 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
                     double e = o - ldv<L1>(a.RHS + sy.voff + r);
                     if (SC) e /= rw[r];
                     ss = fma(e, e, ss);
+                } else if (ROLE == ROLE_WARM) {
+                    const double u = ldv<L1>(a.RHS + sy.voff + r) - o;
+                    outv[r] = u;
+                    ss = fma(u, u, ss);
                 } else {
                     const double nv = fma(c1, o, -c2 * ldv<L1>(outv + r));
                     outv[r] = nv;
@@ -505,6 +509,11 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
                     double e = o - ldv<L1>(a.RHS + sy.voff + r);
                     if (SC) e /= cd[r];
                     ss = fma(e, e, ss);
+                } else if (ROLE == ROLE_WARM) {
+                    const double u = ldv<L1>(a.RHS + sy.voff + r) - o;
+                    outv[r] = u;
+                    s1[i] = u;
+                    ss = fma(u, u, ss);
                 } else {
                     const double nv = fma(c1, o, -c2 * ldv<L1>(outv + r));
                     outv[r] = nv;
@@ -553,6 +562,30 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
     // it also keeps the system well posed when rounding of the data has
     // moved z off the root.  G^T-passes therefore leave the tau entry of
     // their output at 0 and leave it out of norms and residuals.
+    if (ROLE == ROLE_WARM) {
+        // warm start: u = b - Op x0 is the new right-hand side of the
+        // correction; ||b|| (bnorm) stays the reference of the stopping test
+        double ss = tot.a;
+        if (PASS == PASS_G) {
+            const double uN = ldv<L1>(a.RHS + sy.voff + rN) - oN;
+            outv[rN] = uN;
+            ss = fma(uN, uN, ss);
+        } else {
+            outv[rN] = 0.0;
+            XI[rN] = 0.0;
+        }
+        double nrm, inv;
+        norm_and_inverse(ss, nrm, inv);
+        st->beta = nrm;
+        st->vc1 = inv;
+        st->vc2 = 0.0;
+        if (!(nrm > 0.0) || !finite64(nrm)) {
+            st->outcome = finite64(nrm) ? O_CONVERGED : O_BREAKDOWN;
+            st->status = S_DONE;
+            atomicSub(a.active, 1);
+        }
+        return;
+    }
     if (ROLE == ROLE_RES) {
         double ss = tot.a;
         if (PASS == PASS_G) {
@@ -651,6 +684,75 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PlanView<T> a, PersistC
             __syncthreads();
         }
         if (!grid_sync(c, a.active)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warm start: the LSQR iterate of a caller-given initial dz (JVP:
+// x0 = C^-1 dz0, tau entry 0 by the gauge dz_N = 0) or r (VJP:
+// x0 = W^-1 S r0, every entry), one system per blockIdx.y.  z0 uses the
+// systems' N-vector layout.
+template <typename T>
+__global__ void k_warm_init(PlanView<T> a, const double* z0, int mode) {
+    const Sys sy = a.sys[blockIdx.y];
+    const Prob pr = a.probs[sy.prob];
+    const int n = pr.n, N = pr.n + pr.m + 1;
+    const double* cd = a.cd + pr.doff;
+    const double* rw = a.rw + pr.doff;
+    double* X = a.X + sy.voff;
+    const double* z = z0 + sy.voff;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+        double x = 0.0;
+        if (mode == 0) {
+            if (r < N - 1) x = a.scaled ? z[r] / cd[r] : z[r];
+        } else {
+            const double rp = (r >= n && r < N - 1) ? -z[r] : z[r];
+            x = a.scaled ? rp / rw[r] : rp;
+        }
+        X[r] = x;
+    }
+}
+
+// XI = D Pi(X) on the tile's rows (what a G-pass gathers), for the warm
+// start's first product.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dpi(PlanView<T> a) {
+    extern __shared__ double smem[];
+    const Tile tl = a.tiles[blockIdx.x];
+    if (tl.kind == TILE_LONG && tl.cb0 != 0) return;  // one chunk per long row
+    const Sys sy = a.sys[tl.sys];
+    const Prob pr = a.probs[sy.prob];
+    const int rows = tl.r1 - tl.r0;
+    const TileSmem sm = tile_smem(smem, a.rmax);
+    const double* X = a.X + sy.voff;
+    for (int i = threadIdx.x; i < rows; i += kThreads) sm.s1[i] = X[tl.r0 + i];
+    __syncthreads();
+    const int cb0 = tl.kind == TILE_STREAM ? tl.cb0 : 0, cb1 = tl.kind == TILE_STREAM ? tl.cb1 : 0;
+    apply_D_tile<double>(sm.s1, sm.s2, tl.r0, tl.r0 + rows, pr.n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1,
+                         a.zy + pr.doff);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += kThreads) a.XI[sy.voff + tl.r0 + i] = sm.s2[i];
+}
+
+// ---------------------------------------------------------------------------
+// Solution export
+// The embedding-space solution of the last solve: dz = C x (JVP) or
+// r = S W x (VJP), N per system.
+template <typename T>
+__global__ void k_export(PlanView<T> a, int mode, double* out) {
+    const Sys sy = a.sys[blockIdx.y];
+    const Prob pr = a.probs[sy.prob];
+    const int n = pr.n, N = pr.n + pr.m + 1;
+    const double* X = a.X + sy.voff;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+        double v;
+        if (mode == 0) {
+            v = a.scaled ? a.cd[pr.doff + r] * X[r] : X[r];
+        } else {
+            v = a.scaled ? a.rw[pr.doff + r] * X[r] : X[r];
+            if (r >= n && r < N - 1) v = -v;
+        }
+        out[sy.voff + r] = v;
     }
 }
 

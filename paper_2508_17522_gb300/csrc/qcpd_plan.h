@@ -64,7 +64,7 @@ struct GraphKey {
     int mode;    // 0 JVP, 1 VJP
     int nsys;
     int chunk;
-    int scaled;  // diagonal scaling on (different kernels)
+    int scaled;  // qcp_precond of the view (different kernels and value arrays)
     bool operator<(const GraphKey& o) const {
         if (mode != o.mode) return mode < o.mode;
         if (nsys != o.nsys) return nsys < o.nsys;
@@ -108,6 +108,7 @@ struct qcp_plan {
     qcpd::DevBuf d_prob, d_mrowptr, d_mcol, d_mvmap, d_mval;
     qcpd::DevBuf d_coefA, d_coefB, d_pz, d_zy, d_flag, d_blocks;
     qcpd::DevBuf d_rw, d_cd, d_mvalG, d_mvalT;   // equilibration: row/column scalings, scaled values
+    qcpd::DevBuf d_cdD, d_onesD, d_mvalD;        // QCP_PRECOND_DIAG: the caller's C, unit W, M diag(C)
     qcpd::DevBuf d_pip, d_pix, d_aip, d_aix;
 
     // schedule
@@ -141,7 +142,10 @@ struct qcp_plan {
 
     std::map<qcpd::GraphKey, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;
-    int last_engine = 0;  // qcp_engine the last call ran (CLUSTER_FP64 when the cluster kernel stayed in FP64)
+    int last_engine = 0;
+    int view_precond = 0;  // qcp_precond of the current call's view (graph cache key)
+    int last_mode = -1;    // 0 JVP, 1 VJP: the last call
+    int last_nsys = 0;  // qcp_engine the last call ran (CLUSTER_FP64 when the cluster kernel stayed in FP64)
     // device time of the iteration chunks of the last call (CUDA events on
     // the plan's stream) and the number of pass launches they contain
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -49,7 +49,7 @@ def test_struct_layout():
     assert ctypes.sizeof(N.qcp_csr) == 48
     assert ctypes.sizeof(N.qcp_cone) == 24
     assert ctypes.sizeof(N.qcp_problem) == 16 + 3 * 48 + 24 + 24
-    assert ctypes.sizeof(N.qcp_options) == 56
+    assert ctypes.sizeof(N.qcp_options) == 72
     assert ctypes.sizeof(N.qcp_info) == 40
 
 

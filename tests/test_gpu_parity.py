@@ -339,3 +339,48 @@ def test_config3_full_size_properties(q):
     assert KL.relative_residual(prob, d, *jv) < 1e-7
     assert adjoint_gap(prob, d, jv, vv) < 1e-7
     plan.close()
+
+
+def test_warm_start_and_diag_preconditioner(q):
+    """A warm start anywhere gives the same outputs; the exact dz (JVP) or r
+    (VJP) as warm start needs at most one iteration; a caller-given diagonal
+    right preconditioner (QCP_PRECOND_DIAG) gives the same outputs."""
+    from oracle import embedding as E
+    prob = g.small_qcp(81, 20, 2, 10, (3, 5, 4))
+    d = g.make_directions(prob, 7)
+    fac = D.DenseFactor(prob)
+    ref_j = D.jvp_dense(prob, d, fac)[:3]
+    ref_v = D.vjp_dense(prob, d, fac)[:4]
+    z = fac.z
+    dz, _ = fac.solve(-D.d_theta_N(prob, z, d.dP, d.dA, d.dq, d.db))
+    r, _ = fac.solve(-(E.Dphi(prob, z).T @ np.concatenate([d.wx, d.wy, d.ws])), trans=1)
+    plan = _plan(q, prob)
+    N = prob.n + prob.m + 1
+    rng = np.random.default_rng(3)
+    cuda = lambda a: torch.tensor(np.asarray(a, np.float64), device="cuda")
+    for engine in ("passes", "cluster", "persistent"):
+        for precond in ("none", "equilibrate"):
+            ws = cuda(rng.standard_normal(N))
+            opts = q.options(rtol=1e-11, warm_start=ws, engine=engine, precond=precond)
+            jv, ji = gpu_jvp(q, plan, d, opts)
+            assert rel_err(jv, ref_j) < TOL64, (engine, precond, rel_err(jv, ref_j), ji)
+            vv, vi = gpu_vjp(q, plan, d, opts)
+            assert rel_err(vv, ref_v) < TOL64, (engine, precond, rel_err(vv, ref_v), vi)
+            jv, ji = gpu_jvp(q, plan, d, q.options(rtol=1e-9, warm_start=cuda(dz), engine=engine, precond=precond))
+            assert ji[0]["iters"] <= 1 and rel_err(jv, ref_j) < TOL64, (engine, precond, ji)
+            vv, vi = gpu_vjp(q, plan, d, q.options(rtol=1e-9, warm_start=cuda(r), engine=engine, precond=precond))
+            assert vi[0]["iters"] <= 1 and rel_err(vv, ref_v) < TOL64, (engine, precond, vi)
+    for dd in (np.ones(N), np.exp(rng.uniform(-1.0, 1.0, N))):
+        for engine in ("passes", "persistent", "auto"):
+            opts = q.options(rtol=1e-11, precond="diag", precond_d=cuda(dd), engine=engine)
+            jv, ji = gpu_jvp(q, plan, d, opts)
+            assert rel_err(jv, ref_j) < TOL64, (engine, rel_err(jv, ref_j), ji)
+            vv, vi = gpu_vjp(q, plan, d, opts)
+            assert rel_err(vv, ref_v) < TOL64, (engine, rel_err(vv, ref_v), vi)
+            assert plan.last_engine() in ("passes", "persistent")
+    from paper_2508_17522_gb300._native import QCPError
+    with pytest.raises(QCPError, match="ERR_ARG"):
+        gpu_jvp(q, plan, d, q.options(precond="diag", precond_d=cuda(np.ones(N)), engine="cluster"))
+    with pytest.raises(QCPError, match="ERR_ARG"):
+        gpu_jvp(q, plan, d, q.options(precond="diag"))
+    plan.close()
