@@ -4,11 +4,13 @@
 Workload (default): the single second-order-cone QCP with n=2000, m=5500
 (cone {0}^500 x R+^2000 x SOC(10)^300), 16 forward and 16 adjoint directions,
 relative residual tolerance 1e-10, FP64, synthetic seeded data with an
-optimum built by construction.  One step = the 16 JVPs plus the 16 VJPs,
-each group solved together in one multi-direction call.
+optimum built by construction.  One step = the 16 JVPs plus the 16 VJPs in
+one qcp_derivative_jvp_vjp_multi call (the cluster engine runs the two
+groups side by side; --call separate makes one multi-direction call per
+group).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--precond equilibrate|none] [--workload config2|config3]
+                    [--precond equilibrate|none] [--workload config2|config3|example]
 
 Prints one JSON line (rank 0).  `value` counts JVP+VJP solves per second
 over all ranks with inputs resident in device memory; `e2e` measures the
@@ -54,6 +56,12 @@ def workload(name, rank):
         dirs = g.make_directions_batch(prob, 5 + 1000 * rank, 1)
         return prob, dirs, 1e-6, ("large sparse QCP n=100000 m=220000 {0}^20000 x R+^150000 x lognormal SOC "
                                   "blocks on 50000 rows, 1 JVP + 1 VJP direction")
+    if name == "example":
+        prob = g.paper_example(seed=rank)
+        dirs = g.make_directions_batch(prob, 5 + 1000 * rank, 16)
+        return prob, dirs, 1e-10, ("the paper's example shape (Sec. 4): x in R^1000, r in R^2000, "
+                                   "[C D; E 0; f^T 0] with C 2000x1000 dense, {0}^2000 x R+^1000 x {0}, "
+                                   "P diagonal on r; 16 JVP + 16 VJP directions")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -86,9 +94,9 @@ def kernel_source_hash(engine):
 
 
 def recorded_traffic(engine, workload_name):
-    """dram read+write bytes per pass of the engine's dominant kernel from a
-    committed ncu summary (profiles/*.json), if it was taken on the current
-    kernel source."""
+    """dram read+write bytes per system pass (one product with F or F^T of
+    one system) of the engine's dominant kernel from a committed ncu summary
+    (profiles/*.json), if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", f"{KERNELS[engine][0]}_{workload_name}_dram.json")
     try:
         rec = json.load(open(path))
@@ -96,7 +104,7 @@ def recorded_traffic(engine, workload_name):
         return None
     if rec.get("kernel_source_sha") != kernel_source_hash(engine):
         return None
-    return rec.get("dram_bytes_per_pass")
+    return rec.get("dram_bytes_per_system_pass")
 
 
 # --------------------------------------------------------------------------- clocks
@@ -181,10 +189,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
-    ap.add_argument("--workload", default="config2", choices=["config2", "config3"])
+    ap.add_argument("--workload", default="config2", choices=["config2", "config3", "example"])
     ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
     ap.add_argument("--maxiter", type=int, default=400000,
                     help="Krylov iteration cap (lower it only for profiling runs: solves then stop early)")
+    ap.add_argument("--call", default="pair", choices=["pair", "separate"],
+                    help="pair: the JVPs and VJPs in one qcp_derivative_jvp_vjp_multi call (side by side on the "
+                         "cluster engine); separate: one _multi call per kind")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -197,8 +208,8 @@ def main():
         if rank != 0:
             return
         prob, dirs, rtol, desc = workload(args.workload, 0)
-        if args.workload != "config2":
-            raise SystemExit("the oracle reference arm covers the config2 workload (dense LU)")
+        if args.workload not in ("config2", "example"):
+            raise SystemExit("the oracle reference arm covers the dense-LU workloads (config2, example)")
         for _ in range(args.warmup):
             oracle_step(prob, dirs)
         t0 = time.perf_counter()
@@ -230,13 +241,13 @@ def main():
     prob, dirs, rtol, desc = workload(args.workload, rank)
     k = len(dirs)
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and args.workload == "config2":
+    if rank == 0 and not args.no_cpu_baseline and args.workload in ("config2", "example"):
         log("timing the CPU oracle sample ...")
         cpu = oracle_sample(prob, dirs)
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    plan = q.qcp_plan_create(q.problem_tensors(prob, dev), torch.float64, max_rhs=k, stream=stream)
+    plan = q.qcp_plan_create(q.problem_tensors(prob, dev), torch.float64, max_rhs=2 * k, stream=stream)
     opts = q.options(rtol=rtol, maxiter=args.maxiter, precond=args.precond, engine=args.engine)
     cat = lambda nm: np.concatenate([getattr(d, nm) for d in dirs])
     host = {nm: torch.as_tensor(cat(nm)).pin_memory() for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
@@ -248,28 +259,37 @@ def main():
     launches = [0]
     pass_ms = [0.0]
     passes = [0]
+    sys_passes = [0]  # sum over systems of the passes each ran (2 per LSQR iteration)
     infos = []
 
+    def account(info):
+        launches[0] += plan.last_launches()
+        ms, n_ = plan.last_timing()
+        pass_ms[0] += ms
+        passes[0] += n_
+        sys_passes[0] += sum(2 * i["iters"] for i in info)
+
     def step(inputs):
+        if args.call == "pair":
+            jout, vout, info = q.qcp_derivative_jvp_vjp_multi(
+                plan, k, inputs["dP"], inputs["dA"], inputs["dq"], inputs["db"], k, inputs["wx"], inputs["wy"],
+                inputs["ws"], opts)
+            account(info)
+            infos.append((info[:k], info[k:]))
+            return list(jout) + list(vout)
         jout = q.qcp_derivative_jvp_multi(plan, k, inputs["dP"], inputs["dA"], inputs["dq"], inputs["db"], opts)
-        launches[0] += plan.last_launches()
-        ms, n_ = plan.last_timing()
-        pass_ms[0] += ms
-        passes[0] += n_
+        account(jout[-1])
         vout = q.qcp_derivative_vjp_multi(plan, k, inputs["wx"], inputs["wy"], inputs["ws"], opts)
-        launches[0] += plan.last_launches()
-        ms, n_ = plan.last_timing()
-        pass_ms[0] += ms
-        passes[0] += n_
+        account(vout[-1])
         infos.append((jout[-1], vout[-1]))
-        return jout[:-1] + vout[:-1]
+        return list(jout[:-1]) + list(vout[:-1])
 
     for _ in range(args.warmup):
         step(devin)
     torch.cuda.synchronize(dev)
 
     # ---- device-resident timed region (L2 flushed before every step)
-    launches[0], pass_ms[0], passes[0] = 0, 0.0, 0
+    launches[0], pass_ms[0], passes[0], sys_passes[0] = 0, 0.0, 0, 0
     infos.clear()
     sampler = ClockSampler(local)
     if dist is not None:
@@ -292,6 +312,7 @@ def main():
     if dist is not None:
         dist.barrier()
     dev_launches = launches[0]
+    dev_pass_ms, dev_passes, dev_sys_passes = pass_ms[0], passes[0], sys_passes[0]
     statuses = sorted({i["status"] for pair in infos for grp in pair for i in grp})
     max_res = max(i["rel_residual"] for pair in infos for grp in pair for i in grp)
 
@@ -337,9 +358,11 @@ def main():
     peak = peak or 6800.0
     engine = plan.last_engine()
     kname = KERNELS[engine][0]
-    bpp = algorithmic_bytes_per_pass(prob) * k
-    avg_pass_s = (pass_ms[0] / 1e3) / max(passes[0], 1)
-    achieved = bpp / avg_pass_s / 1e9
+    # algorithmic bytes of every pass every system ran, over the device time
+    # of the iteration launches
+    bsys = algorithmic_bytes_per_pass(prob)
+    achieved = bsys * dev_sys_passes / (dev_pass_ms / 1e3) / 1e9
+    avg_pass_s = (dev_pass_ms / 1e3) / max(dev_passes, 1)
     traffic = recorded_traffic(engine, args.workload)
 
     if rank == 0:
@@ -351,14 +374,19 @@ def main():
             "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "solver": "LSQR", "engine": engine,
                        "arithmetic": ("vectors in double-float (binary32 pairs), LSQR scalars f64, data f64"
                                       if engine == "cluster" else "f64"),
+                       "call": ("qcp_derivative_jvp_vjp_multi (16 JVP + 16 VJP systems side by side)"
+                                if args.call == "pair" else "qcp_derivative_jvp_multi then qcp_derivative_vjp_multi"),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every timed step "
                        f"({L2_FLUSH_BYTES >> 20} MiB write)", "status": statuses,
                        "max_true_rel_residual": max_res},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                          "peak_source": peak_note, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "per": "pass (one product with F or F^T for all systems; a cluster-engine launch "
-                                "runs every pass of a solve, so per launch the ratio is the same)",
-                         "bytes_per_pass": bpp, "avg_pass_us": avg_pass_s * 1e6, "passes": passes[0]},
+                         "traffic_per": "system pass (dram read + write bytes, ncu)",
+                         "per": "algorithmic bytes of all passes of all systems (one pass = one product with F "
+                                "or F^T of one system) over the device time of the iteration launches; a "
+                                "cluster-engine launch runs every pass of its systems",
+                         "bytes_per_system_pass": bsys, "system_passes": dev_sys_passes,
+                         "avg_pass_us": avg_pass_s * 1e6, "passes": dev_passes},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": dev_launches,

@@ -121,10 +121,14 @@ typedef enum {
     QCP_PRECOND_EQUILIBRATE = 1, /* LSQR on W F C: W = 1/(row norms of F), C = 1/(column norms of W F),
                                    C constant on each SOC block; D Pi's off-diagonal SOC terms are
                                    left out of the norms (any positive diagonal is a valid choice) */
-    QCP_PRECOND_DIAG = 2        /* LSQR on F C with C = diag(opts->precond_d), a caller-given positive
+    QCP_PRECOND_DIAG = 2,       /* LSQR on F C with C = diag(opts->precond_d), a caller-given positive
                                    right preconditioner (for instance the learned one), averaged
                                    over each SOC block (C must commute with D Pi); pass or
                                    persistent engine */
+    QCP_PRECOND_JACOBI = 3      /* the classical column-norm (Jacobi) preconditioner: LSQR on F C with
+                                   C = 1/(column norms of F), D Pi by its diagonal in the norms, C
+                                   constant on each SOC block; computed on the plan's first such call;
+                                   pass or persistent engine (as QCP_PRECOND_DIAG) */
 } qcp_precond;
 
 /* How the Krylov iterations are run on the GPU (all give the same iterates up
@@ -152,7 +156,10 @@ typedef enum {
 } qcp_engine;
 
 typedef struct {
-    int32_t solver;           /* 0 = LSQR (the only solver built) */
+    int32_t solver;           /* 0 = LSQR (Paige & Saunders 1982), 1 = LSMR (Fong & Saunders 2011; the
+                                 pass and persistent engines: AUTO then runs the pass engine, CLUSTER
+                                 is an error).  Both minimise the same ||Op x - b|| and stop on the
+                                 same estimate of ||r|| <= rtol ||b|| */
     double rtol;              /* target for ||F dz + dN|| / ||dN|| (JVP) or ||F^T r + g|| / ||g|| (VJP) */
     int64_t maxiter;          /* iteration cap per system (counted over all restarts) */
     int32_t check_every;      /* iterations between host convergence checks; 0 = none */
@@ -259,6 +266,25 @@ int qcp_derivative_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k,
                              qcp_info* info);
 
 /*
+ * JVPs of kj directions and VJPs of kv directions of a single-problem plan
+ * in one call (kj, kv >= 1, kj + kv <= max_rhs): the two kinds of solve are
+ * independent (Sec. 3.1 and 3.2 at the same point), so the cluster engine
+ * runs them side by side, the JVP systems on the plan's stream and the VJP
+ * systems on a second stream of the plan forked from it and joined back
+ * before the call returns; the other engines run them one after the other.
+ * The JVP arrays (dP .. ds) hold kj directions and the VJP arrays (wx .. gb)
+ * kv directions, back to back as in the _multi calls; the results equal
+ * those of qcp_derivative_jvp_multi and qcp_derivative_vjp_multi (bit for
+ * bit on the same engine and cluster size).  info holds kj + kv structs, the
+ * JVPs first.  opts->warm_start must be NULL.  Errors: QCP_ERR_ARG (batch
+ * plan, bad counts, NULL arrays), the status codes of the single calls.
+ */
+int qcp_derivative_jvp_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t kj, const void* dP,
+                                 const void* dA, const void* dq, const void* db, void* dx, void* dy, void* ds,
+                                 int32_t kv, const void* wx, const void* wy, const void* ws, void* gP, void* gA,
+                                 void* gq, void* gb, qcp_info* info);
+
+/*
  * Tile schedule of a plan (QCP_ENGINE_PASSES and _PERSISTENT): tile_nnz is
  * the target number of nonzeros of M per tile (rows are grouped into tiles,
  * never splitting an SOC block); a row with more than long_row nonzeros
@@ -272,6 +298,34 @@ int qcp_derivative_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k,
  * long_chunk < 32), QCP_ERR_ALLOC.
  */
 int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, int32_t long_chunk);
+
+/*
+ * Autotuner.  Times every engine / schedule candidate on the plan itself
+ * (synthetic directions from a fixed hash, rtol 0, `iters` LSQR iterations,
+ * no true-residual pass) and keeps the fastest per pass as the plan's
+ * choice for QCP_ENGINE_AUTO:
+ *   - QCP_ENGINE_PASSES and _PERSISTENT with tile_nnz in {1024, 2048, 4096,
+ *     8192, 16384} (long_row = tile_nnz / 8, long_chunk 1 << 20),
+ *   - QCP_ENGINE_CLUSTER with 1, 2, 4, 8 and 16 CTAs per system, where every
+ *     problem fits.
+ * mode 0 tunes JVP solves, 1 VJP solves; nsys systems per call (ignored by
+ * batch plans, which always solve all problems).  entries (host, capacity
+ * cap, may be NULL) receives every candidate measured, *count their number
+ * and *best (may be NULL) the chosen one, which stays in force until the
+ * next qcp_plan_set_schedule, qcp_plan_set_cluster or autotune call (the
+ * plan's schedule is left at the winner's tile size).  Errors: QCP_ERR_ARG
+ * (bad mode, nsys, iters < 4), QCP_ERR_ALLOC, QCP_ERR_CUDA.
+ */
+typedef struct {
+    int32_t engine;        /* qcp_engine */
+    int32_t cluster_ctas;  /* CTAs per system (QCP_ENGINE_CLUSTER), else 0 */
+    int32_t tile_nnz;      /* tile schedule (PASSES / PERSISTENT), else 0 */
+    int32_t pad;
+    double us_per_pass;    /* device time of one pass (one product with F or F^T of all systems) */
+} qcp_tune_entry;
+
+int qcp_plan_autotune(qcp_plan* plan, const qcp_options* opts, int32_t mode, int32_t nsys, int32_t iters,
+                      qcp_tune_entry* entries, int32_t cap, int32_t* count, qcp_tune_entry* best);
 
 /* CTAs per system under QCP_ENGINE_CLUSTER: 1 to 16 (above 8 is a
    non-portable cluster size), or 0 (the default) to choose per call: the
@@ -326,7 +380,8 @@ int qcp_plan_last_timing(const qcp_plan* plan, double* pass_ms, int64_t* passes)
 
 /* The embedding-space solution of the plan's most recent call: dz (JVP) or
    r (VJP; F^T r = -g_phi), N = n + m + 1 doubles per system of that call
-   (system-major), device pointer.  The training targets of the learned form
+   (system-major; after qcp_derivative_jvp_vjp_multi the JVP systems come
+   first), device pointer.  The training targets of the learned form
    come from here.  QCP_ERR_ARG before the first call. */
 int qcp_plan_last_solution(qcp_plan* plan, double* out);
 

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "QCP_OK", 1: "QCP_ERR_ARG", 2: "QCP_ERR_CUDA", 3: "QCP_ERR_AL
                 4: "QCP_NOT_CONVERGED", 5: "QCP_BREAKDOWN", 6: "QCP_ERR_TIMEOUT",
                 7: "QCP_WARN_NEAR_KINK"}
 QCP_F64, QCP_F32 = 0, 1
-QCP_PRECOND_NONE, QCP_PRECOND_EQUILIBRATE, QCP_PRECOND_DIAG = 0, 1, 2
+QCP_PRECOND_NONE, QCP_PRECOND_EQUILIBRATE, QCP_PRECOND_DIAG, QCP_PRECOND_JACOBI = 0, 1, 2, 3
 QCP_ENGINE_PASSES, QCP_ENGINE_PERSISTENT, QCP_ENGINE_CLUSTER, QCP_ENGINE_AUTO, QCP_ENGINE_CLUSTER_FP64 = 0, 1, 2, 3, 4
 
 
@@ -48,6 +48,11 @@ class qcp_options(ctypes.Structure):
 class qcp_info(ctypes.Structure):
     _fields_ = [("status", c_int32), ("iters", c_int64), ("rel_residual", c_double),
                 ("rel_residual_est", c_double), ("kink_margin", c_double)]
+
+
+class qcp_tune_entry(ctypes.Structure):
+    _fields_ = [("engine", c_int32), ("cluster_ctas", c_int32), ("tile_nnz", c_int32), ("pad", c_int32),
+                ("us_per_pass", c_double)]
 
 
 _lib = None
@@ -87,6 +92,12 @@ def lib():
         f = getattr(L, name)
         f.restype = ctypes.c_int
         f.argtypes = [c_void_p, P(qcp_options), c_int32] + [c_void_p] * 7 + [P(qcp_info)]
+    L.qcp_derivative_jvp_vjp_multi.restype = ctypes.c_int
+    L.qcp_derivative_jvp_vjp_multi.argtypes = ([c_void_p, P(qcp_options), c_int32] + [c_void_p] * 7 + [c_int32]
+                                               + [c_void_p] * 7 + [P(qcp_info)])
+    L.qcp_plan_autotune.restype = ctypes.c_int
+    L.qcp_plan_autotune.argtypes = [c_void_p, P(qcp_options), c_int32, c_int32, c_int32, P(qcp_tune_entry), c_int32,
+                                    P(c_int32), P(qcp_tune_entry)]
     L.qcp_plan_set_schedule.restype = ctypes.c_int
     L.qcp_plan_set_schedule.argtypes = [c_void_p, c_int32, c_int32, c_int32]
     for name, args in (("qcp_plan_last_solution", [c_void_p, c_void_p]),

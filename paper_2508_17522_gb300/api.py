@@ -93,7 +93,8 @@ def _c_problem(pt: ProblemTensors):
     return prob, sol
 
 
-_PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE, "diag": N.QCP_PRECOND_DIAG}
+_PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE, "diag": N.QCP_PRECOND_DIAG,
+            "jacobi": N.QCP_PRECOND_JACOBI}
 
 
 _ENGINE = {"passes": N.QCP_ENGINE_PASSES, "persistent": N.QCP_ENGINE_PERSISTENT,
@@ -101,8 +102,10 @@ _ENGINE = {"passes": N.QCP_ENGINE_PASSES, "persistent": N.QCP_ENGINE_PERSISTENT,
 
 
 def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_residual=True, precond="none",
-            kink_tol=0.0, engine="auto", warm_start=None, precond_d=None):
-    """qcp_options; precond is "none" (the plain method), "equilibrate" or
+            kink_tol=0.0, engine="auto", warm_start=None, precond_d=None, solver="lsqr"):
+    """qcp_options; solver is "lsqr" or "lsmr" (LSMR runs on the pass and
+    persistent engines); precond is "none" (the plain method), "equilibrate",
+    "jacobi" (column norms of F) or
     "diag" (precond_d: a float64 device tensor, N per problem); warm_start:
     a float64 device tensor of N per system (dz for the JVP, r for the VJP).
     engine is "passes" (one launch per pass), "persistent" (one cooperative
@@ -115,6 +118,7 @@ def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_
     o.use_graph, o.compute_residual, o.kink_tol = int(bool(use_graph)), int(bool(compute_residual)), float(kink_tol)
     o.precond = _PRECOND[precond] if isinstance(precond, str) else int(precond)
     o.engine = _ENGINE[engine] if isinstance(engine, str) else int(engine)
+    o.solver = {"lsqr": 0, "lsmr": 1}[solver] if isinstance(solver, str) else int(solver)
     keep = []
     for name, t in (("warm_start", warm_start), ("precond_d", precond_d)):
         if t is not None:
@@ -192,6 +196,24 @@ class Plan:
         """Engine of the last call: passes, persistent, cluster or cluster_fp64."""
         e = N.lib().qcp_plan_last_engine(self._h)
         return {v: k for k, v in _ENGINE.items()}.get(e, str(e))
+
+    def autotune(self, mode="jvp", nsys=None, iters=64, opts=None):
+        """Time every engine / schedule candidate on this plan (qcp_plan_autotune)
+        and keep the fastest for engine="auto".  Returns (best, all), dicts
+        with engine, cluster_ctas, tile_nnz and us_per_pass."""
+        cap = 32
+        entries = (N.qcp_tune_entry * cap)()
+        count = ctypes.c_int32()
+        best = N.qcp_tune_entry()
+        o = opts if opts is not None else options()
+        nsys = self.nprob if self.batched else (nsys or 1)
+        _check(N.lib().qcp_plan_autotune(self._h, ctypes.byref(o), 0 if mode == "jvp" else 1, int(nsys), int(iters),
+                                         entries, cap, ctypes.byref(count), ctypes.byref(best)),
+               "qcp_plan_autotune")
+        names = {v: k for k, v in _ENGINE.items()}
+        d = lambda e: {"engine": names.get(e.engine, str(e.engine)), "cluster_ctas": e.cluster_ctas,
+                       "tile_nnz": e.tile_nnz, "us_per_pass": e.us_per_pass}
+        return d(best), [d(entries[i]) for i in range(min(count.value, cap))]
 
     def set_cluster(self, max_ctas: int = 0):
         """CTAs per system of the cluster engine (0: chosen per call)."""
@@ -288,3 +310,24 @@ def qcp_derivative_vjp_multi(plan: Plan, k, wx, wy, ws, opts=None):
                                           [k * plan.nnzP_total, k * plan.nnzA_total, k * plan.n_total,
                                            k * plan.m_total], opts, _ALLOW)
     return dP, dA, dq, db, info
+
+
+def qcp_derivative_jvp_vjp_multi(plan: Plan, kj, dP, dA, dq, db, kv, wx, wy, ws, opts=None):
+    """kj JVPs and kv VJPs of a single-problem plan in one call (the cluster
+    engine runs the two kinds side by side).  Returns ((dx, dy, ds),
+    (gP, gA, gq, gb), info) with info listing the JVPs first."""
+    if plan.batched:
+        raise ValueError("qcp_derivative_jvp_vjp_multi takes a single-problem plan")
+    jin = [plan._vec(dP, kj * plan.nnzP_total), plan._vec(dA, kj * plan.nnzA_total),
+           plan._vec(dq, kj * plan.n_total), plan._vec(db, kj * plan.m_total)]
+    vin = [plan._vec(wx, kv * plan.n_total), plan._vec(wy, kv * plan.m_total), plan._vec(ws, kv * plan.m_total)]
+    e = lambda n: torch.empty(n, device=plan.device, dtype=plan.dtype)
+    jout = [e(kj * plan.n_total), e(kj * plan.m_total), e(kj * plan.m_total)]
+    vout = [e(kv * plan.nnzP_total), e(kv * plan.nnzA_total), e(kv * plan.n_total), e(kv * plan.m_total)]
+    infos = (N.qcp_info * (kj + kv))()
+    o = opts if opts is not None else options()
+    code = N.lib().qcp_derivative_jvp_vjp_multi(plan.handle, ctypes.byref(o), int(kj), *[_vp(t) for t in jin],
+                                                *[_vp(t) for t in jout], int(kv), *[_vp(t) for t in vin],
+                                                *[_vp(t) for t in vout], infos)
+    _check(code, "qcp_derivative_jvp_vjp_multi", ok=_ALLOW)
+    return tuple(jout), tuple(vout), [_info_dict(i) for i in infos]

@@ -62,8 +62,11 @@ static PlanView<T> view(qcp_plan* p, int precond) {
     v.X = p->d_X.as<double>();
     v.XI = p->d_XI.as<double>();
     v.RHS = p->d_RHS.as<double>();
+    v.HB = p->d_HB.as<double>();
+    v.lsmr = 0;
     v.rmax = p->rmax;
     v.long_chunk = p->long_chunk;
+    v.tile0 = 0;
     return v;
 }
 
@@ -125,7 +128,7 @@ static int run_chunk(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int 
         p->last_launches += 2 * chunk;
         return QCP_OK;
     }
-    GraphKey key{mode, nsys, chunk, p->view_precond};
+    GraphKey key{mode, v.tile0, nsys, chunk, p->view_precond, v.lsmr};
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -188,7 +191,7 @@ static int iterate(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int nt
         done_iters += chunk;
         p->pass_launches += 2 * chunk;
         if (opts.check_every > 0) {
-            QCP_CUDA(cudaMemcpyAsync(p->h_active, p->d_active.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+            QCP_CUDA(cudaMemcpyAsync(p->h_active, v.active, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
             QCP_CUDA(cudaStreamSynchronize(p->stream));
         } else {
             QCP_CUDA(cudaEventSynchronize(p->ev1));
@@ -262,7 +265,7 @@ static void launch_output(qcp_plan* p, int mode, int nsys, const PlanView<T>& v,
         if (residual) launch_pass<PASS_G, ROLE_RES, T>(v, ntiles, smem, st);
     } else {
         int maxrows = 0;
-        for (int s = 0; s < nsys; ++s) {
+        for (int s = out.s0; s < out.s0 + nsys; ++s) {
             const Prob& pr = p->hprob[p->hsys[s].prob];
             maxrows = std::max(maxrows, pr.n + pr.m);
         }
@@ -329,10 +332,34 @@ static int prepare_diag(qcp_plan* p, const double* d) {
     return QCP_OK;
 }
 
-// mode 0: JVP, 1: VJP.  nsys systems (the first nsys of the plan).
+// A range of a plan's systems that a call solves in one mode: JVP (mode 0)
+// or VJP (mode 1) on systems [s0, s0 + ns), with the user arrays of that
+// range.
 template <typename T>
-static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, const RhsArgs<T>& rin,
-                 const OutArgs<T>& out, qcp_info* info) {
+struct Seg {
+    int mode;
+    int s0, ns;
+    RhsArgs<T> ra;
+    OutArgs<T> out;
+};
+
+// The view of a range: tile launches start at its first tile, and it has
+// its own count of iterating systems.
+template <typename T>
+static PlanView<T> seg_view(const qcp_plan* p, PlanView<T> v, const Seg<T>& g, int gi) {
+    v.tile0 = p->batched ? 0 : g.s0 * p->tiles_per_sys;
+    v.active = p->d_active.as<int>() + gi;
+    return v;
+}
+
+static int seg_tiles(const qcp_plan* p, int ns) { return p->batched ? p->ntiles : ns * p->tiles_per_sys; }
+
+// Solve the systems of nseg ranges (the plan's systems [0, nsys) in all).
+// Every range gets its right-hand side and first v-pass, then the engine
+// iterates: the cluster engine runs the ranges side by side, the others one
+// after another.  Outputs and the true-residual continuation are per range.
+template <typename T>
+static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* opts_in, qcp_info* info) {
     qcp_options opts;
     if (opts_in) opts = *opts_in;
     else qcp_default_options(&opts);
@@ -340,14 +367,31 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         set_error("bad options: rtol >= 0, maxiter >= 1, check_every >= 0 required");
         return QCP_ERR_ARG;
     }
-    if (opts.solver != 0) {
-        set_error("only solver 0 (LSQR) is built");
+    if (opts.solver != 0 && opts.solver != 1) {
+        set_error("solver must be 0 (LSQR) or 1 (LSMR)");
+        return QCP_ERR_ARG;
+    }
+    if (opts.solver == 1 && (opts.engine == QCP_ENGINE_CLUSTER || opts.engine == QCP_ENGINE_CLUSTER_FP64)) {
+        set_error("LSMR runs on the pass or persistent engine");
         return QCP_ERR_ARG;
     }
     if (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE &&
-        opts.precond != QCP_PRECOND_DIAG) {
-        set_error("precond must be QCP_PRECOND_NONE, _EQUILIBRATE or _DIAG");
+        opts.precond != QCP_PRECOND_DIAG && opts.precond != QCP_PRECOND_JACOBI) {
+        set_error("precond must be QCP_PRECOND_NONE, _EQUILIBRATE, _DIAG or _JACOBI");
         return QCP_ERR_ARG;
+    }
+    // Jacobi is the diagonal right preconditioner with the plan's column norms
+    if (opts.precond == QCP_PRECOND_JACOBI) {
+        if (!p->d_cdJ.p) {
+            QCP_TRY(p->d_cdJ.alloc(sizeof(double) * (size_t)p->N_tot));
+            const int rc = jacobi_cols(p, p->d_cdJ.as<double>());
+            if (rc != QCP_OK) {
+                p->d_cdJ.release();
+                return rc;
+            }
+        }
+        opts.precond = QCP_PRECOND_DIAG;
+        opts.precond_d = p->d_cdJ.as<double>();
     }
     if (opts.precond == QCP_PRECOND_DIAG && !opts.precond_d) {
         set_error("QCP_PRECOND_DIAG needs opts->precond_d");
@@ -355,15 +399,27 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
     }
     if (opts.precond == QCP_PRECOND_DIAG &&
         (opts.engine == QCP_ENGINE_CLUSTER || opts.engine == QCP_ENGINE_CLUSTER_FP64)) {
-        set_error("QCP_PRECOND_DIAG runs on the pass or persistent engine");
+        set_error("QCP_PRECOND_DIAG and _JACOBI run on the pass or persistent engine");
         return QCP_ERR_ARG;
     }
     if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_CLUSTER_FP64) {
         set_error("engine must be one of QCP_ENGINE_PASSES, _PERSISTENT, _CLUSTER, _AUTO, _CLUSTER_FP64");
         return QCP_ERR_ARG;
     }
+    if (nseg < 1 || nseg > kMaxSegments) {
+        set_error("internal: %d system ranges in one call", nseg);
+        return QCP_ERR_ARG;
+    }
+    if (nseg > 1 && opts.warm_start) {
+        set_error("a warm start takes a call of one kind (JVP or VJP)");
+        return QCP_ERR_ARG;
+    }
+    int nsys = 0;
+    for (int gi = 0; gi < nseg; ++gi) nsys = std::max(nsys, segs[gi].s0 + segs[gi].ns);
     int engine = opts.engine;
     if (engine == QCP_ENGINE_AUTO && opts.precond == QCP_PRECOND_DIAG) engine = QCP_ENGINE_PASSES;
+    if (engine == QCP_ENGINE_AUTO && p->tuned_engine >= 0) engine = p->tuned_engine;
+    if (opts.solver == 1 && (engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER)) engine = QCP_ENGINE_PASSES;
     if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER_FP64) {
         bool fits = false;
         QCP_TRY(cluster_ready(p, nsys, &fits));
@@ -379,53 +435,76 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
     cudaStream_t st = p->stream;
     if (opts.precond == QCP_PRECOND_DIAG) QCP_TRY(prepare_diag<T>(p, opts.precond_d));
     p->view_precond = opts.precond;
-    const PlanView<T> v = view<T>(p, opts.precond);
-    const int ntiles = p->batched ? p->ntiles : nsys * p->tiles_per_sys;
+    PlanView<T> v = view<T>(p, opts.precond);
+    v.lsmr = opts.solver == 1 ? 1 : 0;
     const size_t smem = tile_smem_bytes(p->rmax);
     QCP_TRY(set_smem_attrs<T>(smem));
     p->last_launches = 0;
     p->last_engine = engine;
-    p->last_mode = mode;
+    p->last_mode = nseg == 1 ? segs[0].mode : 2;
     p->last_nsys = nsys;
+    p->last_jvp_sys = segs[0].mode == 0 ? segs[0].s0 + segs[0].ns : 0;
     p->pass_ms = 0.0;
     p->pass_launches = 0;
-    QCP_CUDA(cudaMemsetAsync(p->d_active.p, 0, sizeof(int), st));
-    RhsArgs<T> ra = rin;
-    ra.rtol = opts.rtol;
-    ra.maxiter = opts.maxiter;
-    if (mode == 0) k_jvp_rhs<T><<<ntiles, kThreads, 0, st>>>(v, ra);
-    else k_vjp_rhs<T><<<ntiles, kThreads, smem, st>>>(v, ra);
-    if (opts.warm_start) {
-        // x0 from the caller's iterate; the right-hand side becomes b - Op x0
-        int maxN = 1;
-        for (int s = 0; s < nsys; ++s) {
-            const Prob& pr = p->hprob[p->hsys[s].prob];
-            maxN = std::max(maxN, pr.n + pr.m + 1);
+    QCP_CUDA(cudaMemsetAsync(p->d_active.p, 0, kMaxSegments * sizeof(int), st));
+    for (int gi = 0; gi < nseg; ++gi) {
+        const Seg<T>& g = segs[gi];
+        const PlanView<T> vs = seg_view(p, v, g, gi);
+        const int nt = seg_tiles(p, g.ns);
+        RhsArgs<T> ra = g.ra;
+        ra.rtol = opts.rtol;
+        ra.maxiter = opts.maxiter;
+        if (g.mode == 0) k_jvp_rhs<T><<<nt, kThreads, 0, st>>>(vs, ra);
+        else k_vjp_rhs<T><<<nt, kThreads, smem, st>>>(vs, ra);
+        if (opts.warm_start) {
+            // x0 from the caller's iterate; the right-hand side becomes b - Op x0
+            int maxN = 1;
+            for (int s = g.s0; s < g.s0 + g.ns; ++s) {
+                const Prob& pr = p->hprob[p->hsys[s].prob];
+                maxN = std::max(maxN, pr.n + pr.m + 1);
+            }
+            k_warm_init<T><<<dim3((unsigned)std::min(1024, (maxN + 255) / 256), (unsigned)g.ns), 256, 0, st>>>(
+                vs, opts.warm_start, g.mode, g.s0);
+            if (g.mode == 0) {
+                k_dpi<T><<<nt, kThreads, smem, st>>>(vs, vs.X);
+                launch_pass<PASS_G, ROLE_WARM, T>(vs, nt, smem, st);
+            } else {
+                launch_pass<PASS_GT, ROLE_WARM, T>(vs, nt, smem, st);
+            }
+            p->last_launches += g.mode == 0 ? 3 : 2;
         }
-        k_warm_init<T><<<dim3((unsigned)std::min(1024, (maxN + 255) / 256), (unsigned)nsys), 256, 0, st>>>(
-            v, opts.warm_start, mode);
-        if (mode == 0) {
-            k_dpi<T><<<ntiles, kThreads, smem, st>>>(v);
-            launch_pass<PASS_G, ROLE_WARM, T>(v, ntiles, smem, st);
-        } else {
-            launch_pass<PASS_GT, ROLE_WARM, T>(v, ntiles, smem, st);
-        }
-        p->last_launches += mode == 0 ? 3 : 2;
+        launch_v_pass<T>(g.mode, vs, nt, smem, st);
+        QCP_CUDA(cudaGetLastError());
+        p->last_launches += 2;
     }
-    launch_v_pass<T>(mode, v, ntiles, smem, st);
-    QCP_CUDA(cudaGetLastError());
-    p->last_launches += 2;
-    auto run_iterations = [&]() -> int {
-        if (engine == QCP_ENGINE_PERSISTENT) return iterate_persistent<T>(p, mode, v, ntiles, smem, opts);
-        if (engine == QCP_ENGINE_CLUSTER) return iterate_cluster<T>(p, mode, nsys, v, opts);
-        return iterate<T>(p, mode, nsys, v, ntiles, smem, opts);
+    // iterate the ranges whose flag is set
+    auto run_iterations = [&](const std::vector<int>& todo) -> int {
+        if (engine == QCP_ENGINE_CLUSTER) {
+            ClusterSeg cs[kMaxSegments];
+            int nc = 0;
+            for (int gi = 0; gi < nseg; ++gi)
+                if (todo[gi]) cs[nc++] = ClusterSeg{segs[gi].mode, segs[gi].s0, segs[gi].ns, gi};
+            return iterate_cluster<T>(p, cs, nc, nsys, v, opts);
+        }
+        for (int gi = 0; gi < nseg; ++gi) {
+            if (!todo[gi]) continue;
+            const Seg<T>& g = segs[gi];
+            const PlanView<T> vs = seg_view(p, v, g, gi);
+            const int nt = seg_tiles(p, g.ns);
+            if (engine == QCP_ENGINE_PERSISTENT) QCP_TRY(iterate_persistent<T>(p, g.mode, vs, nt, smem, opts));
+            else QCP_TRY(iterate<T>(p, g.mode, g.ns, vs, nt, smem, opts));
+        }
+        return QCP_OK;
     };
-    QCP_TRY(run_iterations());
+    QCP_TRY(run_iterations(std::vector<int>(nseg, 1)));
     std::vector<LsqrState> hs(nsys);
     std::vector<double> prev_res(nsys, INFINITY);
     const bool residual = opts.compute_residual != 0;
     for (int round = 0;; ++round) {
-        launch_output<T>(p, mode, nsys, v, ntiles, smem, out, residual);
+        for (int gi = 0; gi < nseg; ++gi) {
+            const Seg<T>& g = segs[gi];
+            launch_output<T>(p, g.mode, g.ns, seg_view(p, v, g, gi), seg_tiles(p, g.ns), smem, g.out, residual);
+        }
         QCP_CUDA(cudaGetLastError());
         QCP_CUDA(cudaMemcpyAsync(hs.data(), p->d_state.p, nsys * sizeof(LsqrState), cudaMemcpyDeviceToHost, st));
         QCP_CUDA(cudaStreamSynchronize(st));
@@ -433,27 +512,48 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
         // The Krylov estimate measures the scaled residual; where the true
         // one misses the target, continue the same recurrence with a tighter
         // internal tolerance.
-        int resumed = 0;
-        for (int s = 0; s < nsys; ++s) {
-            LsqrState& q = hs[s];
-            const bool improving = q.resid_true < 0.5 * prev_res[s];  // else rounding has stalled it
-            prev_res[s] = q.resid_true;
-            if (q.outcome != O_CONVERGED || !(q.resid_true > opts.rtol) || !(q.alpha > 0.0) ||
-                !isfinite(q.resid_true) || q.iters >= q.maxiter || q.bnorm_true <= 0.0 || !improving)
-                continue;
-            q.rtol *= std::max(0.01, 0.5 * opts.rtol / q.resid_true);
-            q.status = S_ACTIVE;
-            q.outcome = O_RUNNING;
-            q.xcoef = 0.0;
-            ++resumed;
+        int resumed[kMaxSegments] = {0, 0};
+        int total = 0;
+        for (int gi = 0; gi < nseg; ++gi) {
+            for (int s = segs[gi].s0; s < segs[gi].s0 + segs[gi].ns; ++s) {
+                LsqrState& q = hs[s];
+                const bool improving = q.resid_true < 0.5 * prev_res[s];  // else rounding has stalled it
+                prev_res[s] = q.resid_true;
+                if (q.outcome != O_CONVERGED || !(q.resid_true > opts.rtol) || !(q.alpha > 0.0) ||
+                    !isfinite(q.resid_true) || q.iters >= q.maxiter || q.bnorm_true <= 0.0 || !improving)
+                    continue;
+                q.rtol *= std::max(0.01, 0.5 * opts.rtol / q.resid_true);
+                q.status = S_ACTIVE;
+                q.outcome = O_RUNNING;
+                q.xcoef = 0.0;
+                ++resumed[gi];
+                ++total;
+            }
         }
-        if (!resumed) break;
+        if (!total) break;
         QCP_CUDA(cudaMemcpyAsync(p->d_state.p, hs.data(), nsys * sizeof(LsqrState), cudaMemcpyHostToDevice, st));
-        QCP_CUDA(cudaMemcpyAsync(p->d_active.p, &resumed, sizeof(int), cudaMemcpyHostToDevice, st));
+        QCP_CUDA(cudaMemcpyAsync(p->d_active.p, resumed, kMaxSegments * sizeof(int), cudaMemcpyHostToDevice, st));
         QCP_CUDA(cudaStreamSynchronize(st));
-        launch_v_pass<T>(mode, v, ntiles, smem, st);
-        p->last_launches += 1;
-        QCP_TRY(run_iterations());
+        std::vector<int> todo(nseg, 0);
+        for (int gi = 0; gi < nseg; ++gi) {
+            if (!resumed[gi]) continue;
+            todo[gi] = 1;
+            const Seg<T>& g = segs[gi];
+            const PlanView<T> vs = seg_view(p, v, g, gi);
+            if (v.lsmr) {
+                // LSMR's last update pass left u_{k+1}, v_{k+1}, h_{k+1} in
+                // place; a JVP's u-pass gathers D Pi(v), which the output
+                // pass overwrote
+                if (g.mode == 0) {
+                    k_dpi<T><<<seg_tiles(p, g.ns), kThreads, smem, st>>>(vs, vs.V);
+                    p->last_launches += 1;
+                }
+            } else {
+                launch_v_pass<T>(g.mode, vs, seg_tiles(p, g.ns), smem, st);
+                p->last_launches += 1;
+            }
+        }
+        QCP_TRY(run_iterations(todo));
     }
     if (engine != QCP_ENGINE_PASSES) {
         int64_t it = 0;
@@ -479,6 +579,64 @@ static int solve(qcp_plan* p, int mode, int nsys, const qcp_options* opts_in, co
 
 static bool ptr_ok(const void* p, int64_t count) { return count == 0 || p != nullptr; }
 
+template <typename T>
+static RhsArgs<T> jvp_in(const void* dP, const void* dA, const void* dq, const void* db) {
+    RhsArgs<T> r{(const T*)dP, (const T*)dA, (const T*)dq, (const T*)db, nullptr, nullptr, nullptr, 0, 0};
+    return r;
+}
+template <typename T>
+static RhsArgs<T> vjp_in(const void* wx, const void* wy, const void* ws) {
+    RhsArgs<T> r{nullptr, nullptr, nullptr, nullptr, (const T*)wx, (const T*)wy, (const T*)ws, 0, 0};
+    return r;
+}
+template <typename T>
+static OutArgs<T> jvp_out(void* dx, void* dy, void* ds) {
+    OutArgs<T> o{(T*)dx, (T*)dy, (T*)ds, nullptr};
+    return o;
+}
+template <typename T>
+static OutArgs<T> vjp_out(void* dP, void* dA, void* dq, void* db) {
+    OutArgs<T> o{(T*)dP, (T*)dA, (T*)dq, (T*)db};
+    return o;
+}
+
+// JVPs of kj directions and VJPs of kv directions of a single-problem plan
+// in one call: systems [0, kj) solve the JVPs, [kj, kj + kv) the VJPs.
+static int pair_entry(qcp_plan* plan, const qcp_options* opts, int kj, const void* dP, const void* dA,
+                      const void* dq, const void* db, void* dx, void* dy, void* ds, int kv, const void* wx,
+                      const void* wy, const void* ws, void* gP, void* gA, void* gq, void* gb, qcp_info* info) {
+    if (!plan || plan->batched) {
+        set_error("qcp_derivative_jvp_vjp_multi takes a single-problem plan");
+        return QCP_ERR_ARG;
+    }
+    if (kj < 1 || kv < 1 || kj + kv > plan->max_rhs) {
+        set_error("kj = %d JVP and kv = %d VJP directions: each >= 1, together <= %d", kj, kv, plan->max_rhs);
+        return QCP_ERR_ARG;
+    }
+    const Prob& pr = plan->hprob[0];
+    const int64_t a = kj, b = kv;
+    if (!ptr_ok(dP, pr.pnz * a) || !ptr_ok(dA, pr.anz * a) || !ptr_ok(dq, pr.n * a) || !ptr_ok(db, pr.m * a) ||
+        !ptr_ok(dx, pr.n * a) || !ptr_ok(dy, pr.m * a) || !ptr_ok(ds, pr.m * a) || !ptr_ok(wx, pr.n * b) ||
+        !ptr_ok(wy, pr.m * b) || !ptr_ok(ws, pr.m * b) || !ptr_ok(gP, pr.pnz * b) || !ptr_ok(gA, pr.anz * b) ||
+        !ptr_ok(gq, pr.n * b) || !ptr_ok(gb, pr.m * b)) {
+        set_error("null array argument");
+        return QCP_ERR_ARG;
+    }
+    auto run = [&](auto tag) {
+        using T = decltype(tag);
+        Seg<T> g[2] = {{0, 0, kj, jvp_in<T>(dP, dA, dq, db), jvp_out<T>(dx, dy, ds)},
+                       {1, kj, kv, vjp_in<T>(wx, wy, ws), vjp_out<T>(gP, gA, gq, gb)}};
+        // the VJP range indexes its arrays from its first system
+        g[1].ra.bx = g[1].out.bx = a * pr.n;
+        g[1].ra.by = g[1].out.by = a * pr.m;
+        g[1].ra.bp = g[1].out.bp = a * pr.pnz;
+        g[1].ra.ba = g[1].out.ba = a * pr.anz;
+        g[1].out.s0 = kj;
+        return solve<T>(plan, g, 2, opts, info);
+    };
+    return plan->dtype == QCP_F64 ? run(double{}) : run(float{});
+}
+
 static int jvp_entry(qcp_plan* plan, const qcp_options* opts, int k, const void* dP, const void* dA,
                      const void* dq, const void* db, void* dx, void* dy, void* ds, qcp_info* info) {
     if (!plan) {
@@ -499,14 +657,12 @@ static int jvp_entry(qcp_plan* plan, const qcp_options* opts, int k, const void*
     }
     if (plan->dtype == QCP_F64) {
         using T = double;
-        RhsArgs<T> r{(const T*)dP, (const T*)dA, (const T*)dq, (const T*)db, nullptr, nullptr, nullptr, 0, 0};
-        OutArgs<T> o{(T*)dx, (T*)dy, (T*)ds, nullptr};
-        return solve<T>(plan, 0, nsys, opts, r, o, info);
+        const Seg<T> g{0, 0, nsys, jvp_in<T>(dP, dA, dq, db), jvp_out<T>(dx, dy, ds)};
+        return solve<T>(plan, &g, 1, opts, info);
     }
     using T = float;
-    RhsArgs<T> r{(const T*)dP, (const T*)dA, (const T*)dq, (const T*)db, nullptr, nullptr, nullptr, 0, 0};
-    OutArgs<T> o{(T*)dx, (T*)dy, (T*)ds, nullptr};
-    return solve<T>(plan, 0, nsys, opts, r, o, info);
+    const Seg<T> g{0, 0, nsys, jvp_in<T>(dP, dA, dq, db), jvp_out<T>(dx, dy, ds)};
+    return solve<T>(plan, &g, 1, opts, info);
 }
 
 static int vjp_entry(qcp_plan* plan, const qcp_options* opts, int k, const void* wx, const void* wy,
@@ -529,14 +685,126 @@ static int vjp_entry(qcp_plan* plan, const qcp_options* opts, int k, const void*
     }
     if (plan->dtype == QCP_F64) {
         using T = double;
-        RhsArgs<T> r{nullptr, nullptr, nullptr, nullptr, (const T*)wx, (const T*)wy, (const T*)ws, 0, 0};
-        OutArgs<T> o{(T*)dP, (T*)dA, (T*)dq, (T*)db};
-        return solve<T>(plan, 1, nsys, opts, r, o, info);
+        const Seg<T> g{1, 0, nsys, vjp_in<T>(wx, wy, ws), vjp_out<T>(dP, dA, dq, db)};
+        return solve<T>(plan, &g, 1, opts, info);
     }
     using T = float;
-    RhsArgs<T> r{nullptr, nullptr, nullptr, nullptr, (const T*)wx, (const T*)wy, (const T*)ws, 0, 0};
-    OutArgs<T> o{(T*)dP, (T*)dA, (T*)dq, (T*)db};
-    return solve<T>(plan, 1, nsys, opts, r, o, info);
+    const Seg<T> g{1, 0, nsys, vjp_in<T>(wx, wy, ws), vjp_out<T>(dP, dA, dq, db)};
+    return solve<T>(plan, &g, 1, opts, info);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: every candidate engine / schedule runs the same synthetic solve
+// (fixed-hash directions, rtol 0, a fixed number of iterations) twice; the
+// second run's device time per pass is the candidate's score.
+
+// Uniform values in [-1, 1) from a SplitMix64 hash of (seed, index)
+// (Steele, Lea and Flood, 2014).
+template <typename T>
+__global__ void k_hash_fill(T* x, int64_t n, uint64_t seed) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+}
+
+template <typename T>
+static int autotune(qcp_plan* p, const qcp_options& base, int mode, int nsys, int iters,
+                    std::vector<qcp_tune_entry>& out, qcp_tune_entry* best_out) {
+    const int64_t k = p->batched ? 1 : nsys;
+    if (p->batched) nsys = p->nprob;
+    const int64_t sz[7] = {mode == 0 ? p->pnz_tot : p->n_tot, mode == 0 ? p->anz_tot : p->m_tot,
+                           mode == 0 ? p->n_tot : p->m_tot, mode == 0 ? p->m_tot : 0,
+                           mode == 0 ? p->n_tot : p->pnz_tot, mode == 0 ? p->m_tot : p->anz_tot,
+                           mode == 0 ? p->m_tot : p->n_tot};
+    const int64_t sz_o4 = mode == 0 ? 0 : p->m_tot;
+    DevBuf buf[8];
+    cudaStream_t st = p->stream;
+    for (int i = 0; i < 7; ++i) {
+        QCP_TRY(buf[i].alloc(sizeof(T) * (size_t)(sz[i] * k)));
+        if (i < 4 && sz[i] * k > 0)
+            k_hash_fill<T><<<(unsigned)((sz[i] * k + 255) / 256), 256, 0, st>>>(buf[i].as<T>(), sz[i] * k,
+                                                                                0x5eed0000ull + i);
+    }
+    QCP_TRY(buf[7].alloc(sizeof(T) * (size_t)(sz_o4 * k)));
+    QCP_CUDA(cudaGetLastError());
+    Seg<T> g{mode, 0, nsys, {}, {}};
+    if (mode == 0) {
+        g.ra = jvp_in<T>(buf[0].p, buf[1].p, buf[2].p, buf[3].p);
+        g.out = jvp_out<T>(buf[4].p, buf[5].p, buf[6].p);
+    } else {
+        g.ra = vjp_in<T>(buf[0].p, buf[1].p, buf[2].p);
+        g.out = vjp_out<T>(buf[4].p, buf[5].p, buf[6].p, buf[7].p);
+    }
+    qcp_options o = base;
+    o.rtol = 0.0;
+    o.maxiter = iters;
+    o.compute_residual = 0;
+    o.warm_start = nullptr;
+    const int tiles[5] = {1024, 2048, 4096, 8192, 16384};
+    const int ctas[5] = {1, 2, 4, 8, 16};
+    const int tile0 = p->tile_nnz, lrow0 = p->long_row, lchunk0 = p->long_chunk, cap0 = p->cluster_cap;
+    p->tuned_engine = -1;
+    auto measure = [&](int engine, qcp_tune_entry& e) -> int {
+        o.engine = engine;
+        for (int rep = 0; rep < 2; ++rep) {
+            const int rc = solve<T>(p, &g, 1, &o, nullptr);
+            if (rc != QCP_OK && rc != QCP_NOT_CONVERGED && rc != QCP_WARN_NEAR_KINK) return rc;
+        }
+        e.us_per_pass = 1e3 * p->pass_ms / (double)std::max<int64_t>(1, p->pass_launches);
+        return QCP_OK;
+    };
+    int best = -1;
+    for (int engine : {(int)QCP_ENGINE_PASSES, (int)QCP_ENGINE_PERSISTENT}) {
+        for (int t : tiles) {
+            p->tile_nnz = t;
+            p->long_row = std::max(1, t / 8);
+            p->long_chunk = 1 << 20;
+            QCP_TRY(build_schedule(p));
+            qcp_tune_entry e{engine, 0, t, 0, 0.0};
+            QCP_TRY(measure(engine, e));
+            out.push_back(e);
+            if (best < 0 || e.us_per_pass < out[best].us_per_pass) best = (int)out.size() - 1;
+        }
+    }
+    // the cluster engine runs on the default tile schedule (its right-hand
+    // side and output kernels use tiles)
+    p->tile_nnz = tile0;
+    p->long_row = lrow0;
+    p->long_chunk = lchunk0;
+    QCP_TRY(build_schedule(p));
+    if (o.precond != QCP_PRECOND_DIAG) {
+        for (int c : ctas) {
+            p->cluster_cap = c;
+            bool fits = false;
+            QCP_TRY(cluster_ready(p, nsys, &fits));
+            if (fits) {
+                qcp_tune_entry e{QCP_ENGINE_CLUSTER, c, 0, 0, 0.0};
+                QCP_TRY(measure(QCP_ENGINE_CLUSTER, e));
+                out.push_back(e);
+                if (e.us_per_pass < out[best].us_per_pass) best = (int)out.size() - 1;
+            }
+            // keep the device copies of the fastest cluster layout only
+            if (!(best >= 0 && out[best].engine == QCP_ENGINE_CLUSTER && out[best].cluster_ctas == c))
+                p->clusters.erase(c);
+        }
+    }
+    const qcp_tune_entry w = out[best];
+    if (w.engine == QCP_ENGINE_CLUSTER) {
+        p->cluster_cap = w.cluster_ctas;
+    } else {
+        p->cluster_cap = cap0;
+        p->tile_nnz = w.tile_nnz;
+        p->long_row = std::max(1, w.tile_nnz / 8);
+        p->long_chunk = 1 << 20;
+        QCP_TRY(build_schedule(p));
+    }
+    p->tuned_engine = w.engine;
+    if (best_out) *best_out = w;
+    return QCP_OK;
 }
 
 static int make_plan(int np, const qcp_problem* probs, const qcp_solution* sols, qcp_dtype dtype, int max_rhs,
@@ -663,6 +931,7 @@ static size_t noalloc_layout(qcp_plan* p, unsigned char* base, PlanView<T>* v, b
         v->X = reinterpret_cast<double*>(vec[3]);
         v->XI = reinterpret_cast<double*>(vec[4]);
         v->RHS = reinterpret_cast<double*>(vec[5]);
+        v->HB = nullptr;  // LSQR only
     }
     return off;
 }
@@ -835,11 +1104,41 @@ int qcp_derivative_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t k,
     return vjp_entry(plan, opts, k, wx, wy, ws, dP, dA, dq, db, info);
 }
 
+int qcp_derivative_jvp_vjp_multi(qcp_plan* plan, const qcp_options* opts, int32_t kj, const void* dP,
+                                 const void* dA, const void* dq, const void* db, void* dx, void* dy, void* ds,
+                                 int32_t kv, const void* wx, const void* wy, const void* ws, void* gP, void* gA,
+                                 void* gq, void* gb, qcp_info* info) {
+    return pair_entry(plan, opts, kj, dP, dA, dq, db, dx, dy, ds, kv, wx, wy, ws, gP, gA, gq, gb, info);
+}
+
+int qcp_plan_autotune(qcp_plan* plan, const qcp_options* opts, int32_t mode, int32_t nsys, int32_t iters,
+                      qcp_tune_entry* entries, int32_t cap, int32_t* count, qcp_tune_entry* best) {
+    if (!plan || (mode != 0 && mode != 1) || iters < 4 || cap < 0 || (cap > 0 && !entries) ||
+        (!plan->batched && (nsys < 1 || nsys > plan->max_rhs))) {
+        set_error("autotune: plan, mode 0 or 1, 1 <= nsys <= max_rhs, iters >= 4 and room for the entries required");
+        return QCP_ERR_ARG;
+    }
+    qcp_options o;
+    if (opts) o = *opts;
+    else qcp_default_options(&o);
+    if (o.precond == QCP_PRECOND_DIAG) {
+        set_error("autotune: tune with QCP_PRECOND_NONE or _EQUILIBRATE");
+        return QCP_ERR_ARG;
+    }
+    std::vector<qcp_tune_entry> all;
+    const int rc = plan->dtype == QCP_F64 ? autotune<double>(plan, o, mode, nsys, iters, all, best)
+                                          : autotune<float>(plan, o, mode, nsys, iters, all, best);
+    if (count) *count = (int32_t)all.size();
+    for (int i = 0; i < (int)all.size() && i < cap; ++i) entries[i] = all[i];
+    return rc;
+}
+
 int qcp_plan_set_schedule(qcp_plan* plan, int32_t tile_nnz, int32_t long_row, int32_t long_chunk) {
     if (!plan || tile_nnz < 64 || long_row < 1 || long_chunk < 32) {
         set_error("bad schedule: tile_nnz >= 64, long_row >= 1 and long_chunk >= 32 required");
         return QCP_ERR_ARG;
     }
+    plan->tuned_engine = -1;
     plan->tile_nnz = tile_nnz;
     plan->long_row = long_row;
     plan->long_chunk = long_chunk;
@@ -852,6 +1151,7 @@ int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas) {
         return QCP_ERR_ARG;
     }
     plan->cluster_cap = max_ctas;
+    plan->tuned_engine = -1;
     return QCP_OK;
 }
 
@@ -871,9 +1171,11 @@ int qcp_plan_last_solution(qcp_plan* plan, double* out) {
     }
     const dim3 grid((unsigned)std::min(1024, (maxN + 255) / 256), (unsigned)plan->last_nsys);
     if (plan->dtype == QCP_F64)
-        k_export<double><<<grid, 256, 0, plan->stream>>>(view<double>(plan, plan->view_precond), plan->last_mode, out);
+        k_export<double><<<grid, 256, 0, plan->stream>>>(view<double>(plan, plan->view_precond), plan->last_jvp_sys,
+                                                         out);
     else
-        k_export<float><<<grid, 256, 0, plan->stream>>>(view<float>(plan, plan->view_precond), plan->last_mode, out);
+        k_export<float><<<grid, 256, 0, plan->stream>>>(view<float>(plan, plan->view_precond), plan->last_jvp_sys,
+                                                        out);
     QCP_CUDA(cudaGetLastError());
     QCP_CUDA(cudaStreamSynchronize(plan->stream));
     return QCP_OK;

@@ -106,10 +106,15 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
     int k = 1, start = 0;
     for (size_t u = 0; u < ends.size() && k < C; ++u) {
         const int e = ends[u];
-        // a range also closes before its next unit would take it past lcap rows
+        // a range also closes before its next unit would take it past lcap
+        // rows, and never closes at its weight target while the rows after
+        // it would not fit in the remaining ranges (dense rows first, then
+        // many light ones: the weight alone would give the light ones a
+        // single range)
         const int next = (u + 1 < ends.size()) ? ends[u + 1] : e;
         const double acc = (double)(rp[e] - rp[0]) + kRowWeight * e;
-        while (k < C && (acc >= total * k / C || next - start > lcap)) {
+        while (k < C && ((acc >= total * k / C && (int64_t)(Nx - e) <= (int64_t)(C - k) * lcap) ||
+                         next - start > lcap)) {
             cp.split[k] = e;
             cp.cb[k] = socs[u];
             start = e;
@@ -436,51 +441,76 @@ static int prepare_launch(K fn, int C, size_t bytes, cudaLaunchConfig_t& cfg) {
 }
 
 template <typename T>
-int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const qcp_options& opts) {
+int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call, const PlanView<T>& v,
+                    const qcp_options& opts) {
     ClusterLayout* lay = nullptr;
-    QCP_TRY(get_layout(p, cap_for(p, nsys), &lay));
+    QCP_TRY(get_layout(p, cap_for(p, nsys_call), &lay));
     if (!lay->fits) {
         set_error("cluster engine: a problem's vectors do not fit in the shared memory of 16 CTAs");
         return QCP_ERR_ARG;
     }
     cudaStream_t st = p->stream;
-    // systems grouped by cluster size, one launch per size
+    // per range, its systems grouped by cluster size: one launch per group
+    struct Launch {
+        int seg, C, start, count, FN, L;
+        size_t boff;  // offset of the launch's broadcast buffers (df)
+    };
+    std::vector<Launch> launches;
     p->h_csys.clear();
-    std::vector<int> gsize, gstart;
-    for (int C = 1; C <= kMaxCluster; ++C) {
-        const int start = (int)p->h_csys.size();
-        for (int s = 0; s < nsys; ++s)
-            if (lay->hp[p->hsys[s].prob].C == C) p->h_csys.push_back(s);
-        if ((int)p->h_csys.size() > start) {
-            gsize.push_back(C);
-            gstart.push_back(start);
+    size_t bneed = 0;
+    for (int k = 0; k < nseg; ++k) {
+        for (int C = 1; C <= kMaxCluster; ++C) {
+            Launch L{k, C, (int)p->h_csys.size(), 0, 0, 0, 0};
+            for (int s = segs[k].s0; s < segs[k].s0 + segs[k].ns; ++s) {
+                const ClusterProb& cp = lay->hp[p->hsys[s].prob];
+                if (cp.C != C) continue;
+                p->h_csys.push_back(s);
+                L.FN = std::max(L.FN, cp.FN);
+                L.L = std::max(L.L, cp.L);
+            }
+            L.count = (int)p->h_csys.size() - L.start;
+            if (L.count == 0) continue;
+            L.boff = bneed;
+            bneed += sizeof(df) * 2 * (size_t)even_up(L.FN) * (size_t)L.count;
+            launches.push_back(L);
         }
     }
-    gstart.push_back((int)p->h_csys.size());
-    if (p->d_csys.bytes < sizeof(int32_t) * p->h_csys.size()) QCP_TRY(p->d_csys.alloc(sizeof(int32_t) * nsys));
+    const size_t ncs = std::max<size_t>(1, p->h_csys.size());
+    if (p->d_csys.bytes < sizeof(int32_t) * ncs) QCP_TRY(p->d_csys.alloc(sizeof(int32_t) * ncs));
+    const bool use_df = lay->df_ok && opts.engine != QCP_ENGINE_CLUSTER_FP64;
+    if (use_df && p->d_bcast.bytes < bneed) QCP_TRY(p->d_bcast.alloc(bneed));
     QCP_CUDA(cudaMemcpyAsync(p->d_csys.p, p->h_csys.data(), sizeof(int32_t) * p->h_csys.size(),
                              cudaMemcpyHostToDevice, st));
+    bool forked = false;
+    for (const Launch& L : launches)
+        if (L.seg > 0) forked = true;
+    if (forked && !p->aux_stream) {
+        QCP_CUDA(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+        QCP_CUDA(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+        QCP_CUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    }
     QCP_CUDA(cudaEventRecord(p->ev0, st));
-    for (size_t g = 0; g < gsize.size(); ++g) {
-        const int C = gsize[g];
-        int FN = 0, L = 0;
-        for (int i = gstart[g]; i < gstart[g + 1]; ++i) {
-            const ClusterProb& cp = lay->hp[p->hsys[p->h_csys[i]].prob];
-            FN = std::max(FN, cp.FN);
-            L = std::max(L, cp.L);
-        }
-        const size_t bytes = cluster_smem_bytes(FN, L);
-        const int nclus = gstart[g + 1] - gstart[g];
+    if (forked) {
+        QCP_CUDA(cudaEventRecord(p->ev_fork, st));
+        QCP_CUDA(cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0));
+    }
+    if (!use_df) p->last_engine = QCP_ENGINE_CLUSTER_FP64;
+    for (const Launch& L : launches) {
+        const int C = L.C;
+        const size_t bytes = cluster_smem_bytes(L.FN, L.L);
+        const int mode = segs[L.seg].mode;
+        PlanView<T> vs = v;
+        vs.active = p->d_active.as<int>() + segs[L.seg].seg;
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = (unsigned)C;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)(nclus * C));
+        cfg.gridDim = dim3((unsigned)(L.count * C));
         cfg.blockDim = dim3(kCThreads);
         cfg.dynamicSmemBytes = bytes;
-        cfg.stream = st;
+        cfg.stream = L.seg == 0 ? st : p->aux_stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         ClusterArgs ca;
@@ -491,20 +521,16 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
         ca.sval = lay->d_sval.p;
         ca.svalG = lay->d_svalG.p;
         ca.svalT = lay->d_svalT.p;
-        ca.sys_list = p->d_csys.as<int32_t>() + gstart[g];
+        ca.sys_list = p->d_csys.as<int32_t>() + L.start;
         ca.C = C;
-        ca.FN = FN;
-        ca.L = L;
+        ca.FN = L.FN;
+        ca.L = L.L;
         ca.pad = 0;
         ca.max_passes = 2 * (opts.maxiter + 2);
-        const bool use_df = lay->df_ok && opts.engine != QCP_ENGINE_CLUSTER_FP64;
-        if (!use_df) p->last_engine = QCP_ENGINE_CLUSTER_FP64;
         if (use_df) {
             ClusterDfArgs da;
-            da.bhalf = even_up(FN);
-            const size_t need = sizeof(df) * 2 * (size_t)da.bhalf * (size_t)nclus;
-            if (p->d_bcast.bytes < need) QCP_TRY(p->d_bcast.alloc(need));
-            da.bcast = p->d_bcast.as<df>();
+            da.bhalf = even_up(L.FN);
+            da.bcast = reinterpret_cast<df*>(static_cast<unsigned char*>(p->d_bcast.p) + L.boff);
             da.sval = lay->d_dsval.as<df>();
             da.svalG = lay->d_dsvalG.as<df>();
             da.svalT = lay->d_dsvalT.as<df>();
@@ -514,15 +540,19 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
             da.cd = lay->d_dcd.as<df>();
             da.zy = lay->d_dzy.as<df>();
             da.soc = lay->d_dsoc.as<SocDf>();
-            auto fn = mode == 0 ? cluster_kernel_df<0, T>(v.scaled != 0) : cluster_kernel_df<1, T>(v.scaled != 0);
+            auto fn = mode == 0 ? cluster_kernel_df<0, T>(vs.scaled != 0) : cluster_kernel_df<1, T>(vs.scaled != 0);
             QCP_TRY(prepare_launch(fn, C, bytes, cfg));
-            QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, v, ca, da));
+            QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, vs, ca, da));
         } else {
-            auto fn = mode == 0 ? cluster_kernel<0, T>(v.scaled != 0) : cluster_kernel<1, T>(v.scaled != 0);
+            auto fn = mode == 0 ? cluster_kernel<0, T>(vs.scaled != 0) : cluster_kernel<1, T>(vs.scaled != 0);
             QCP_TRY(prepare_launch(fn, C, bytes, cfg));
-            QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, v, ca));
+            QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, vs, ca));
         }
         p->last_launches += 1;
+    }
+    if (forked) {
+        QCP_CUDA(cudaEventRecord(p->ev_join, p->aux_stream));
+        QCP_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
     }
     QCP_CUDA(cudaEventRecord(p->ev1, st));
     QCP_CUDA(cudaEventSynchronize(p->ev1));
@@ -531,8 +561,9 @@ int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const
     p->pass_ms += ms;
     return QCP_OK;
 }
-
-template int iterate_cluster<double>(qcp_plan*, int, int, const PlanView<double>&, const qcp_options&);
-template int iterate_cluster<float>(qcp_plan*, int, int, const PlanView<float>&, const qcp_options&);
+template int iterate_cluster<double>(qcp_plan*, const ClusterSeg*, int, int, const PlanView<double>&,
+                                     const qcp_options&);
+template int iterate_cluster<float>(qcp_plan*, const ClusterSeg*, int, int, const PlanView<float>&,
+                                    const qcp_options&);
 
 }  // namespace qcpd

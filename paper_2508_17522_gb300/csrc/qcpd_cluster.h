@@ -11,10 +11,20 @@ namespace qcpd {
 // problems; *ok tells whether every problem fits the shared-memory limit.
 int cluster_ready(qcp_plan* p, int nsys, bool* ok);
 
-// Runs the remaining LSQR iterations of systems [0, nsys) with one cluster
-// per system, one launch per cluster size present; adds the device time to
-// p->pass_ms.
+// A range of systems [s0, s0 + ns) iterating one mode (0 JVP, 1 VJP);
+// seg is its index in the call (its active counter).
+struct ClusterSeg {
+    int mode, s0, ns, seg;
+};
+
+// Runs the remaining LSQR iterations of the given system ranges with one
+// cluster per system, one launch per (range, cluster size).  The first
+// range's launches go to the plan's stream, the others to a second stream
+// forked from it and joined back, so a JVP range and a VJP range run side by
+// side.  nsys_call (all systems of the call) sets the automatic cluster size.
+// Adds the device time to p->pass_ms.
 template <typename T>
-int iterate_cluster(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, const qcp_options& opts);
+int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call, const PlanView<T>& v,
+                    const qcp_options& opts);
 
 }  // namespace qcpd

@@ -111,7 +111,16 @@ struct LsqrState {
     double resid_true;      // unscaled ||F dz + dN|| / ||dN|| (or the adjoint's) when computed
     double rtol;
     int64_t iters, maxiter;
-    int32_t status, outcome, first, pad;
+    int32_t status, outcome, first, upd;  // upd (LSMR): the next u-pass applies the deferred updates
+    // LSMR (Fong & Saunders 2011) with damping 0: the two rotations' state
+    // (alphabar_k, zetabar_k, rho_{k-1}, rhobar_{k-1}, cbar_{k-1},
+    // sbar_{k-1}), the residual-norm estimate's state (betadd_k, betad_{k-1},
+    // rhod_{k-1}, tautilde_{k-2}, thetatilde_{k-1}, zeta_{k-1}) and the
+    // coefficient of hbar_k <- h_k - hcoef hbar_{k-1} (xcoef and wcoef are
+    // then zeta_k / (rho_k rhobar_k) and theta_{k+1} / rho_k)
+    double alphabar, zetabar, rho_old, rhobar_old, cbar, sbar;
+    double betadd, betad, rhod_old, tautilde_old, thetatilde, zeta_old;
+    double hcoef;
 };
 
 // Thread-block-cluster layout of one problem: CTA r of a system's cluster

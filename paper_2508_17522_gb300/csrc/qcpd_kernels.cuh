@@ -53,8 +53,11 @@ struct PlanView {
     double* X;               // LSQR iterate
     double* XI;              // D Pi applied to the vector the G-pass gathers
     double* RHS;             // right-hand side b of min ||Op x - b||
+    double* HB;              // LSMR hbar (W holds h)
+    int lsmr;                // 0: LSQR, 1: LSMR (pass and persistent engines)
     int rmax;                // most rows in any tile (shared-memory sizing)
     int long_chunk;          // nonzeros per LONG tile
+    int tile0;               // tile of blockIdx.x 0 in a tile launch (a range of the plan's systems)
 };
 
 // Dynamic shared memory of the tile kernels:
@@ -376,6 +379,130 @@ __device__ __forceinline__ bool lsqr_step_v(S* st, double nrm, double inv_nrm) {
     return false;
 }
 
+// LSMR (Fong & Saunders 2011, damping 0) on the same bidiagonalisation.
+// The u-pass only stores beta_{k+1}; once the v-pass has alpha_{k+1}, the
+// finisher runs both rotations of iteration k, the residual-norm estimate
+// and the stopping test, and leaves the coefficients of the deferred vector
+// updates for the next u-pass:
+//   hbar_k = h_k - hcoef hbar_{k-1},  x_k = x_{k-1} + xcoef hbar_k,
+//   h_{k+1} = v_{k+1} - wcoef h_k.
+template <typename S>
+__device__ __forceinline__ bool lsmr_step_u(S* st, double nrm, double inv_nrm) {
+    st->beta = nrm;
+    // beta = 0: the Krylov space is exhausted; the v-pass then yields
+    // alpha = 0 and the finisher stops after the last update
+    const bool live = nrm > 0.0 && finite64(nrm);
+    st->vc1 = live ? inv_nrm : 0.0;
+    st->vc2 = live ? nrm * st->uc1 : 0.0;
+    if (!finite64(nrm)) {  // x keeps the last finite update
+        st->outcome = O_BREAKDOWN;
+        st->status = S_DONE;
+        return true;
+    }
+    return false;
+}
+
+// Returns true when the system stops without a final update pass.
+template <typename S>
+__device__ __forceinline__ bool lsmr_step_v(S* st, double nrm, double inv_nrm) {
+    const bool live = nrm > 0.0 && finite64(nrm);
+    st->uc1 = live ? inv_nrm : 0.0;  // next u-update: 1/alpha, alpha/beta
+    st->uc2 = nrm * st->vc1;
+    st->alpha = nrm;
+    st->upd = 1;
+    if (st->first) {
+        const double beta1 = st->beta;
+        st->first = 0;
+        st->alphabar = nrm;
+        st->zetabar = nrm * beta1;
+        st->rho_old = 1.0;
+        st->rhobar_old = 1.0;
+        st->cbar = 1.0;
+        st->sbar = 0.0;
+        st->betadd = beta1;
+        st->betad = 0.0;
+        st->rhod_old = 1.0;
+        st->tautilde_old = 0.0;
+        st->thetatilde = 0.0;
+        st->zeta_old = 0.0;
+        st->hcoef = st->xcoef = st->wcoef = 0.0;  // first u-pass: h_1 = v_1
+        st->phibar = beta1;
+        if (!live) {  // A^T b = 0: x = 0 is the least-squares solution
+            st->outcome = finite64(nrm) ? O_CONVERGED : O_BREAKDOWN;
+            st->status = S_DONE;
+            return true;
+        }
+        return false;
+    }
+    const double beta = st->beta;  // beta_{k+1}
+    // first rotation: (alphabar_k, beta_{k+1}) -> rho_k
+    double rho, irho;
+    norm_and_inverse(fma(st->alphabar, st->alphabar, beta * beta), rho, irho);
+    const double c = st->alphabar * irho, s = beta * irho;
+    const double theta_new = s * nrm;  // theta_{k+1}
+    st->alphabar = c * nrm;
+    // second rotation: (cbar_{k-1} rho_k, theta_{k+1}) -> rhobar_k
+    const double thetabar = st->sbar * rho;
+    const double t = st->cbar * rho;
+    double rhobar, irhobar;
+    norm_and_inverse(fma(t, t, theta_new * theta_new), rhobar, irhobar);
+    const double cbar = t * irhobar, sbar = theta_new * irhobar;
+    const double zeta = cbar * st->zetabar;
+    st->zetabar = -sbar * st->zetabar;
+    // deferred vector updates of iteration k
+    st->hcoef = thetabar * rho / (st->rho_old * st->rhobar_old);
+    st->xcoef = zeta * (irho * irhobar);
+    st->wcoef = theta_new * irho;
+    // estimate of ||r_k|| (the residual of the least-squares problem)
+    const double betahat = c * st->betadd;
+    st->betadd = -s * st->betadd;
+    double rhotilde, irhotilde;
+    norm_and_inverse(fma(st->rhod_old, st->rhod_old, thetabar * thetabar), rhotilde, irhotilde);
+    const double ctilde = st->rhod_old * irhotilde, stilde = thetabar * irhotilde;
+    const double thetatilde_old = st->thetatilde;
+    st->thetatilde = stilde * rhobar;
+    const double rhod = ctilde * rhobar;
+    st->betad = -stilde * st->betad + ctilde * betahat;
+    st->tautilde_old = (st->zeta_old - thetatilde_old * st->tautilde_old) * irhotilde;
+    const double taud = (zeta - st->thetatilde * st->tautilde_old) / rhod;
+    const double dr = st->betad - taud;
+    const double normr = sqrt(fma(dr, dr, st->betadd * st->betadd));
+    st->rhod_old = rhod;
+    st->zeta_old = zeta;
+    st->rho_old = rho;
+    st->rhobar_old = rhobar;
+    st->cbar = cbar;
+    st->sbar = sbar;
+    st->phibar = normr;
+    st->iters += 1;
+    if (!finite64(st->xcoef) || !finite64(st->hcoef) || !finite64(st->wcoef) || !(rho > 0.0) ||
+        !(rhobar > 0.0)) {
+        st->outcome = O_BREAKDOWN;
+        st->status = S_DONE;
+        return true;
+    }
+    if (normr <= st->rtol * st->bnorm || !live) {
+        st->outcome = finite64(nrm) ? O_CONVERGED : O_BREAKDOWN;
+        st->status = S_FINAL;
+    } else if (st->iters >= st->maxiter) {
+        st->outcome = O_MAXITER;
+        st->status = S_FINAL;
+    }
+    return false;
+}
+
+// LSMR's deferred vector updates of row r (w holds h, hb holds hbar; iv is
+// the row of the unnormalised v_{k+1}, c1 = 1 / alpha_{k+1}):
+//   hbar <- h - hcoef hbar,  x <- x + xcoef hbar,  h <- v - wcoef h.
+__device__ __forceinline__ void lsmr_update(double* X, double* W, double* HB, int r, double iv, double c1,
+                                            double hcoef, double xcoef, double wcoef) {
+    const double h = W[r];
+    const double hb = fma(-hcoef, HB[r], h);
+    HB[r] = hb;
+    X[r] = fma(xcoef, hb, X[r]);
+    W[r] = fma(iv, c1, -wcoef * h);
+}
+
 // One half-iteration of LSQR over all tiles of all systems.
 //   PASS_G : out = W G C in     (gathers XI = D Pi in, values M diag(c))
 //   PASS_GT: out = C G^T W in   (gathers in, values M diag(w); D Pi on the output side)
@@ -397,7 +524,11 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
     volatile LsqrState* st = a.state + tl.sys;
     const int status = st->status;
     if (ROLE != ROLE_RES && status == S_DONE) return;
-    const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
+    const bool lsmr = a.lsmr != 0;
+    // the last deferred update of a stopped system: LSQR's x-update in the
+    // v-pass, LSMR's (hbar, x, h) updates in the u-pass
+    const bool only_x = (ROLE == ROLE_V && status == S_FINAL && !lsmr);
+    const bool only_upd = (ROLE == ROLE_U && status == S_FINAL && lsmr);
     const Prob pr = a.probs[sy.prob];
     const int n = pr.n;
     const int N = pr.n + pr.m + 1;
@@ -429,17 +560,21 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
         c2 = 0.0;
     }
     const double wcoef = st->wcoef, xcoef = st->xcoef;
+    const double hcoef = lsmr ? st->hcoef : 0.0;
+    const bool upd = lsmr && st->upd != 0;  // LSMR: this u-pass applies the deferred updates
+    double* HB = lsmr ? a.HB + sy.voff : nullptr;
     const double tin = ldv<L1>(in + N - 1);  // tau entry of the input vector
     // the t-column term: (scaled) tau entry of the input
     const double tt = SC ? (PASS == PASS_G ? cd[N - 1] : rw[N - 1]) * tin : tin;
 
     Part part = pzero();
     int rows = tl.r1 - tl.r0;
-    if (only_x) {
+    if (only_x || only_upd) {
         if (tl.kind == TILE_LONG && tl.cb0 != 0) rows = 0;  // one chunk updates the row
         for (int i = threadIdx.x; i < rows; i += kThreads) {
             const int r = tl.r0 + i;
-            X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
+            if (only_x) X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
+            else lsmr_update(X, W, HB, r, ldv<L1>(in + r), c1, hcoef, xcoef, wcoef);
         }
     } else {
         const int64_t* rp = a.mrowptr + pr.mrow;
@@ -477,8 +612,12 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
                     const double nv = fma(c1, o, -c2 * ldv<L1>(outv + r));
                     outv[r] = nv;
                     ss = fma(nv, nv, ss);
-                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * ldv<L1>(W + r));
-                    else X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
+                    if (ROLE == ROLE_U) {
+                        if (!lsmr) W[r] = fma(iv, c1, -wcoef * ldv<L1>(W + r));
+                        else if (upd) lsmr_update(X, W, HB, r, iv, c1, hcoef, xcoef, wcoef);
+                    } else if (!lsmr) {
+                        X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
+                    }
                 }
             }
         } else {
@@ -519,8 +658,12 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
                     outv[r] = nv;
                     s1[i] = nv;
                     ss = fma(nv, nv, ss);
-                    if (ROLE == ROLE_U) W[r] = fma(iv, c1, -wcoef * ldv<L1>(W + r));
-                    else X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
+                    if (ROLE == ROLE_U) {
+                        if (!lsmr) W[r] = fma(iv, c1, -wcoef * ldv<L1>(W + r));
+                        else if (upd) lsmr_update(X, W, HB, r, iv, c1, hcoef, xcoef, wcoef);
+                    } else if (!lsmr) {
+                        X[r] = fma(xcoef, ldv<L1>(W + r), ldv<L1>(X + r));
+                    }
                 }
             }
             if (ROLE != ROLE_RES) {
@@ -541,8 +684,10 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
     // ---- the system's finisher: tau entry and LSQR scalars ----
     __threadfence();
     const int rN = N - 1;
-    if (only_x) {
-        X[rN] = fma(xcoef, ldv<L1>(W + rN), ldv<L1>(X + rN));
+    if (only_x || only_upd) {
+        if (only_x) X[rN] = fma(xcoef, ldv<L1>(W + rN), ldv<L1>(X + rN));
+        else lsmr_update(X, W, HB, rN, tin, c1, hcoef, xcoef, wcoef);
+        st->upd = 0;  // applied: a continuation starts with a plain u-pass
         st->status = S_DONE;
         atomicSub(a.active, 1);
         return;
@@ -602,7 +747,14 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
     const double nsq = fma(nvN, nvN, tot.a);
     double nrm, inv_nrm;
     norm_and_inverse(nsq, nrm, inv_nrm);
-    if (ROLE == ROLE_U) {
+    if (lsmr) {
+        if (ROLE == ROLE_U) {
+            if (upd) lsmr_update(X, W, HB, rN, tin, c1, hcoef, xcoef, wcoef);
+            if (lsmr_step_u(st, nrm, inv_nrm)) atomicSub(a.active, 1);
+        } else {
+            if (lsmr_step_v(st, nrm, inv_nrm)) atomicSub(a.active, 1);
+        }
+    } else if (ROLE == ROLE_U) {
         W[rN] = tin * c1 - wcoef * ldv<L1>(W + rN);
         lsqr_step_u(st, nrm, inv_nrm, nsq);
     } else {
@@ -615,7 +767,7 @@ template <int PASS, int ROLE, bool SC, typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
     extern __shared__ double smem[];
     __shared__ Scratch scratch;
-    run_tile<PASS, ROLE, SC, true, T>(a, blockIdx.x, smem, scratch);
+    run_tile<PASS, ROLE, SC, true, T>(a, a.tile0 + blockIdx.x, smem, scratch);
 }
 
 // ---------------------------------------------------------------------------
@@ -675,12 +827,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PlanView<T> a, PersistC
     constexpr int PV = MODE == 0 ? PASS_GT : PASS_G;   // v-update pass
     for (int64_t it = 0; it < c.max_iters; ++it) {
         for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-            run_tile<PU, ROLE_U, SC, false, T>(a, ti, smem, scratch);
+            run_tile<PU, ROLE_U, SC, false, T>(a, a.tile0 + ti, smem, scratch);
             __syncthreads();
         }
         if (!grid_sync(c, a.active)) return;
         for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-            run_tile<PV, ROLE_V, SC, false, T>(a, ti, smem, scratch);
+            run_tile<PV, ROLE_V, SC, false, T>(a, a.tile0 + ti, smem, scratch);
             __syncthreads();
         }
         if (!grid_sync(c, a.active)) return;
@@ -693,8 +845,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PlanView<T> a, PersistC
 // x0 = W^-1 S r0, every entry), one system per blockIdx.y.  z0 uses the
 // systems' N-vector layout.
 template <typename T>
-__global__ void k_warm_init(PlanView<T> a, const double* z0, int mode) {
-    const Sys sy = a.sys[blockIdx.y];
+__global__ void k_warm_init(PlanView<T> a, const double* z0, int mode, int s0) {
+    const Sys sy = a.sys[s0 + blockIdx.y];
     const Prob pr = a.probs[sy.prob];
     const int n = pr.n, N = pr.n + pr.m + 1;
     const double* cd = a.cd + pr.doff;
@@ -713,18 +865,19 @@ __global__ void k_warm_init(PlanView<T> a, const double* z0, int mode) {
     }
 }
 
-// XI = D Pi(X) on the tile's rows (what a G-pass gathers), for the warm
-// start's first product.
+// XI = D Pi(src) on the tile's rows (what a G-pass gathers): src = X for
+// the warm start's first product, V when LSMR continues a JVP recurrence
+// (the output pass has left D Pi(X) in XI).  src has the N-vector layout.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dpi(PlanView<T> a) {
+__global__ void __launch_bounds__(kThreads) k_dpi(PlanView<T> a, const double* src) {
     extern __shared__ double smem[];
-    const Tile tl = a.tiles[blockIdx.x];
+    const Tile tl = a.tiles[a.tile0 + blockIdx.x];
     if (tl.kind == TILE_LONG && tl.cb0 != 0) return;  // one chunk per long row
     const Sys sy = a.sys[tl.sys];
     const Prob pr = a.probs[sy.prob];
     const int rows = tl.r1 - tl.r0;
     const TileSmem sm = tile_smem(smem, a.rmax);
-    const double* X = a.X + sy.voff;
+    const double* X = src + sy.voff;
     for (int i = threadIdx.x; i < rows; i += kThreads) sm.s1[i] = X[tl.r0 + i];
     __syncthreads();
     const int cb0 = tl.kind == TILE_STREAM ? tl.cb0 : 0, cb1 = tl.kind == TILE_STREAM ? tl.cb1 : 0;
@@ -737,10 +890,11 @@ __global__ void __launch_bounds__(kThreads) k_dpi(PlanView<T> a) {
 // ---------------------------------------------------------------------------
 // Solution export
 // The embedding-space solution of the last solve: dz = C x (JVP) or
-// r = S W x (VJP), N per system.
+// r = S W x (VJP), N per system; systems below jvp_sys solved a JVP.
 template <typename T>
-__global__ void k_export(PlanView<T> a, int mode, double* out) {
+__global__ void k_export(PlanView<T> a, int jvp_sys, double* out) {
     const Sys sy = a.sys[blockIdx.y];
+    const int mode = (int)blockIdx.y < jvp_sys ? 0 : 1;
     const Prob pr = a.probs[sy.prob];
     const int n = pr.n, N = pr.n + pr.m + 1;
     const double* X = a.X + sy.voff;
@@ -768,6 +922,9 @@ struct RhsArgs {
     const T* ws;
     double rtol;
     int64_t maxiter;
+    // user-array offsets of the call's first system (a call on a range of
+    // a plan's systems indexes its arrays from that system)
+    int64_t bx = 0, by = 0, bp = 0, ba = 0;
 };
 
 __device__ __forceinline__ void init_state(LsqrState* st, int* active, double bn, double bn_true, double rtol,
@@ -803,7 +960,7 @@ __device__ __forceinline__ void init_state(LsqrState* st, int* active, double bn
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jvp_rhs(PlanView<T> a, RhsArgs<T> in) {
     __shared__ Scratch scratch;
-    const int ti = blockIdx.x;
+    const int ti = a.tile0 + blockIdx.x;
     const Tile tl = a.tiles[ti];
     const Sys sy = a.sys[tl.sys];
     const Prob pr = a.probs[sy.prob];
@@ -811,8 +968,8 @@ __global__ void __launch_bounds__(kThreads) k_jvp_rhs(PlanView<T> a, RhsArgs<T> 
     const int N = pr.n + pr.m + 1;
     const int64_t* rp = a.mrowptr + pr.mrow;
     const double* pz = a.pz + pr.doff;
-    const T* dP = in.dP + sy.po;
-    const T* dA = in.dA + sy.ao;
+    const T* dP = in.dP + (sy.po - in.bp);
+    const T* dA = in.dA + (sy.ao - in.ba);
     const double* rw = a.rw + pr.doff;
     const bool sc = a.scaled != 0;
     const int64_t pnz = pr.pnz;
@@ -848,12 +1005,12 @@ __global__ void __launch_bounds__(kThreads) k_jvp_rhs(PlanView<T> a, RhsArgs<T> 
         if ((is_long ? threadIdx.x : lane) == 0) {
             double bval;
             if (r < n) {
-                const double dq = ld(in.dq + sy.xo + r), x = ld(pz + r);
+                const double dq = ld(in.dq + (sy.xo - in.bx) + r), x = ld(pz + r);
                 bval = -(hp + ha + dq);
                 dtop += x * hp + dq * x;
             } else {
                 const int j = r - n;
-                const double db = ld(in.db + sy.yo + j);
+                const double db = ld(in.db + (sy.yo - in.by) + j);
                 bval = -ha + db;
                 dbot += db * ld(pz + r);
             }
@@ -863,6 +1020,7 @@ __global__ void __launch_bounds__(kThreads) k_jvp_rhs(PlanView<T> a, RhsArgs<T> 
             RHS[r] = bval;
             X[r] = 0.0;
             W[r] = 0.0;
+            if (a.HB) a.HB[sy.voff + r] = 0.0;
             ss += bval * bval;
         }
     }
@@ -876,6 +1034,7 @@ __global__ void __launch_bounds__(kThreads) k_jvp_rhs(PlanView<T> a, RhsArgs<T> 
     RHS[N - 1] = bN;
     X[N - 1] = 0.0;
     W[N - 1] = 0.0;
+    if (a.HB) a.HB[sy.voff + N - 1] = 0.0;
     init_state(a.state + tl.sys, a.active, sqrt(tot.a + bN * bN), sqrt(tot.d + bNt * bNt), in.rtol, in.maxiter);
 }
 
@@ -887,7 +1046,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> in) {
     extern __shared__ double smem[];
     __shared__ Scratch scratch;
-    const int ti = blockIdx.x;
+    const int ti = a.tile0 + blockIdx.x;
     const Tile tl = a.tiles[ti];
     const Sys sy = a.sys[tl.sys];
     const Prob pr = a.probs[sy.prob];
@@ -913,12 +1072,12 @@ __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> 
     for (int i = threadIdx.x; i < rows; i += kThreads) {
         const int r = tl.r0 + i;
         if (r < n) {
-            const double w = ld(in.wx + sy.xo + r);
+            const double w = ld(in.wx + (sy.xo - in.bx) + r);
             s0[i] = w;
             dtop += ld(pz + r) * w;
         } else {
             const int j = r - n;
-            const double wy = ld(in.wy + sy.yo + j), ws = ld(in.ws + sy.yo + j);
+            const double wy = ld(in.wy + (sy.yo - in.by) + j), ws = ld(in.ws + (sy.yo - in.by) + j);
             s0[i] = wy + ws;
             const double y = ld(pz + r);
             dbot += y * wy + (y - ld(zy + r)) * ws;
@@ -931,7 +1090,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> 
     for (int i = threadIdx.x; i < rows; i += kThreads) {
         const int r = tl.r0 + i;
         double g = s1[i];
-        if (r >= n) g -= ld(in.ws + sy.yo + (r - n));
+        if (r >= n) g -= ld(in.ws + (sy.yo - in.by) + (r - n));
         double bval = -g;
         sst += bval * bval;
         if (sc) bval *= cd[r];
@@ -939,6 +1098,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> 
         RHS[r] = bval;
         X[r] = 0.0;
         W[r] = 0.0;
+        if (a.HB) a.HB[sy.voff + r] = 0.0;
         s0[i] = bval;
         ss += bval * bval;
     }
@@ -957,6 +1117,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> 
     XI[N - 1] = 0.0;
     X[N - 1] = 0.0;
     W[N - 1] = 0.0;
+    if (a.HB) a.HB[sy.voff + N - 1] = 0.0;
     init_state(a.state + tl.sys, a.active, sqrt(tot.a), sqrt(tot.d), in.rtol, in.maxiter);
 }
 
@@ -969,12 +1130,14 @@ struct OutArgs {
     T* o2;  // dy  | dA
     T* o3;  // ds  | dq
     T* o4;  //     | db
+    int64_t bx = 0, by = 0, bp = 0, ba = 0;  // user-array offsets of the first system (as RhsArgs)
+    int32_t s0 = 0;                          // first system (k_vjp_out: system s0 + blockIdx.y)
 };
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_jvp_out(PlanView<T> a, OutArgs<T> o) {
     extern __shared__ double smem[];
-    const Tile tl = a.tiles[blockIdx.x];
+    const Tile tl = a.tiles[a.tile0 + blockIdx.x];
     const Sys sy = a.sys[tl.sys];
     const Prob pr = a.probs[sy.prob];
     const int n = pr.n;
@@ -1006,14 +1169,14 @@ __global__ void __launch_bounds__(kThreads) k_jvp_out(PlanView<T> a, OutArgs<T> 
         XI[r] = s1[i];
         const double cr = sc ? cd[r] : 1.0;  // D commutes with C (C is constant on SOC blocks)
         if (r < n) {
-            o.o1[sy.xo + r] = (T)(s2[i] - dzN * ld(pz + r));
+            o.o1[sy.xo - o.bx + r] = (T)(s2[i] - dzN * ld(pz + r));
         } else {
             const int j = r - n;
             const double y = ld(pz + r);
             const double s = y - ld(zy + r);
             const double Ddz = cr * s1[i];
-            o.o2[sy.yo + j] = (T)(Ddz - dzN * y);
-            o.o3[sy.yo + j] = (T)(Ddz - s2[i] - dzN * s);
+            o.o2[sy.yo - o.by + j] = (T)(Ddz - dzN * y);
+            o.o3[sy.yo - o.by + j] = (T)(Ddz - s2[i] - dzN * s);
         }
     }
 }
@@ -1028,7 +1191,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_vjp_out(PlanView<T> a, OutArgs<T> o, const int64_t* pip,
                                                      const int32_t* pix, const int64_t* aip,
                                                      const int32_t* aix) {
-    const Sys sy = a.sys[blockIdx.y];
+    const Sys sy = a.sys[o.s0 + blockIdx.y];
     const Prob pr = a.probs[sy.prob];
     const int n = pr.n, m = pr.m;
     const int N = n + m + 1;
@@ -1051,18 +1214,18 @@ __global__ void __launch_bounds__(kThreads) k_vjp_out(PlanView<T> a, OutArgs<T> 
             for (int64_t k = pp[i] + lane; k < pp[i + 1]; k += 32) {
                 const int j = px[k];
                 const double xj = ld(pz + j), r1j = X[j] * (sc ? rw[j] : 1.0);
-                o.o1[sy.po + k] = (T)(0.5 * (r1i * xj + xi * r1j) - rN * xi * xj);
+                o.o1[sy.po - o.bp + k] = (T)(0.5 * (r1i * xj + xi * r1j) - rN * xi * xj);
             }
-            if (lane == 0) o.o3[sy.xo + i] = (T)(r1i - rN * xi);
+            if (lane == 0) o.o3[sy.xo - o.bx + i] = (T)(r1i - rN * xi);
         } else {
             const int i = row - n;
             const double yi = ld(pz + n + i), r2i = -X[n + i] * (sc ? rw[n + i] : 1.0);
             for (int64_t k = ap[i] + lane; k < ap[i + 1]; k += 32) {
                 const int j = ax[k];
                 const double r1j = X[j] * (sc ? rw[j] : 1.0);
-                o.o2[sy.ao + k] = (T)(yi * r1j - r2i * ld(pz + j));
+                o.o2[sy.ao - o.ba + k] = (T)(yi * r1j - r2i * ld(pz + j));
             }
-            if (lane == 0) o.o4[sy.yo + i] = (T)(r2i - rN * yi);
+            if (lane == 0) o.o4[sy.yo - o.by + i] = (T)(r2i - rN * yi);
         }
     }
 }

@@ -671,7 +671,7 @@ int build_schedule(qcp_plan* p) {
     QCP_TRY(p->d_gcnt.alloc(groups.size() * sizeof(int32_t)));
     QCP_TRY(p->d_scnt.alloc(nsys * sizeof(int32_t)));
     QCP_TRY(p->d_state.alloc(nsys * sizeof(LsqrState)));
-    QCP_TRY(p->d_active.alloc(sizeof(int)));
+    QCP_TRY(p->d_active.alloc(kMaxSegments * sizeof(int)));  // one counter per system range of a call
     const size_t vb = (size_t)voff * sizeof(double);  // Krylov vectors are float64
     QCP_TRY(p->d_U.alloc(vb));
     QCP_TRY(p->d_V.alloc(vb));
@@ -679,6 +679,7 @@ int build_schedule(qcp_plan* p) {
     QCP_TRY(p->d_X.alloc(vb));
     QCP_TRY(p->d_XI.alloc(vb));
     QCP_TRY(p->d_RHS.alloc(vb));
+    QCP_TRY(p->d_HB.alloc(vb));
     QCP_CUDA(cudaMemcpyAsync(p->d_tiles.p, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice, p->stream));
     QCP_CUDA(cudaMemcpyAsync(p->d_groups.p, groups.data(), groups.size() * sizeof(Group), cudaMemcpyHostToDevice, p->stream));
     QCP_CUDA(cudaMemcpyAsync(p->d_sys.p, p->hsys.data(), p->hsys.size() * sizeof(Sys), cudaMemcpyHostToDevice, p->stream));
@@ -691,6 +692,7 @@ int build_schedule(qcp_plan* p) {
     QCP_CUDA(cudaMemsetAsync(p->d_X.p, 0, vb, p->stream));
     QCP_CUDA(cudaMemsetAsync(p->d_XI.p, 0, vb, p->stream));
     QCP_CUDA(cudaMemsetAsync(p->d_RHS.p, 0, vb, p->stream));
+    QCP_CUDA(cudaMemsetAsync(p->d_HB.p, 0, vb, p->stream));
     QCP_CUDA(cudaStreamSynchronize(p->stream));
     return QCP_OK;
 }
@@ -765,6 +767,57 @@ static int run_equilibrate(qcp_plan* p) {
     QCP_CUDA(cudaGetLastError());
     QCP_CUDA(cudaStreamSynchronize(st));
     return QCP_OK;
+}
+
+// Column scaling of the Jacobi (column-norm) preconditioner: C = 1 / column
+// norms of F itself (W = I), D Pi by its diagonal, averaged over each SOC
+// block like the equilibration's C.
+__global__ void k_fill(double* x, int64_t n, double v) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+template <typename T>
+static int jacobi_cols_t(qcp_plan* p, double* out) {
+    Reduce R{p->d_ppart.as<Part>(), p->d_pgpart.as<Part>(), p->d_pgcnt.as<int32_t>(), p->d_pscnt.as<int32_t>(),
+             p->d_pgroups.as<Group>()};
+    int nt = 0;
+    for (auto& v : p->ptiles) nt += (int)v.size();
+    cudaStream_t st = p->stream;
+    DevBuf dd, csq, ones;
+    QCP_TRY(dd.alloc(p->N_tot * sizeof(double)));
+    QCP_TRY(csq.alloc(p->N_tot * sizeof(double)));
+    QCP_TRY(ones.alloc(p->N_tot * sizeof(double)));
+    k_fill<<<grid_for(p->N_tot, 256), 256, 0, st>>>(ones.as<double>(), p->N_tot, 1.0);
+    for (int i = 0; i < p->nprob; ++i) {
+        const Prob& pr = p->hprob[i];
+        k_dd_rows<T><<<grid_for((int64_t)pr.n + pr.m + 1, 256), 256, 0, st>>>(p->d_flag.as<int8_t>() + pr.doff, pr.n,
+                                                                             pr.m, dd.as<double>() + pr.doff);
+        if (pr.nsoc)
+            k_dd_soc<T><<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
+                p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_zy.as<double>() + pr.doff, dd.as<double>() + pr.doff);
+    }
+    if (nt)
+        k_prec_cols<T><<<nt, kThreads, 0, st>>>(p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R,
+                                                p->d_mrowptr.as<int64_t>(), p->d_mcol.as<int32_t>(),
+                                                p->d_mval.as<T>(), p->d_coefA.as<double>(), p->d_coefB.as<double>(),
+                                                dd.as<double>(), ones.as<double>(), csq.as<double>());
+    for (int i = 0; i < p->nprob; ++i) {
+        const Prob& pr = p->hprob[i];
+        k_cd_rows<<<grid_for((int64_t)pr.n + pr.m + 1, 256), 256, 0, st>>>(
+            csq.as<double>() + pr.doff, p->d_flag.as<int8_t>() + pr.doff, pr.n, pr.m, out + pr.doff);
+        if (pr.nsoc)
+            k_cd_soc<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(p->d_blocks.as<SocBlock>() + pr.soff,
+                                                                          pr.nsoc, csq.as<double>() + pr.doff,
+                                                                          out + pr.doff);
+    }
+    QCP_CUDA(cudaGetLastError());
+    QCP_CUDA(cudaStreamSynchronize(st));
+    return QCP_OK;
+}
+
+int jacobi_cols(qcp_plan* p, double* out) {
+    return p->dtype == QCP_F64 ? jacobi_cols_t<double>(p, out) : jacobi_cols_t<float>(p, out);
 }
 
 // ---------------------------------------------------------------- plan build
@@ -1091,5 +1144,8 @@ qcp_plan::~qcp_plan() {
     qcpd::drop_graphs(this);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (aux_stream) cudaStreamDestroy(aux_stream);
     if (h_active) cudaFreeHost(h_active);
 }

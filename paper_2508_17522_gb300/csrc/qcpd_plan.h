@@ -60,15 +60,21 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+constexpr int kMaxSegments = 2;  // system ranges of one call (JVP systems, VJP systems)
+
 struct GraphKey {
     int mode;    // 0 JVP, 1 VJP
+    int tile0;   // first tile of the system range
     int nsys;
     int chunk;
     int scaled;  // qcp_precond of the view (different kernels and value arrays)
+    int solver;  // 0 LSQR, 1 LSMR (a kernel parameter of the captured launches)
     bool operator<(const GraphKey& o) const {
         if (mode != o.mode) return mode < o.mode;
+        if (tile0 != o.tile0) return tile0 < o.tile0;
         if (nsys != o.nsys) return nsys < o.nsys;
         if (scaled != o.scaled) return scaled < o.scaled;
+        if (solver != o.solver) return solver < o.solver;
         return chunk < o.chunk;
     }
 };
@@ -109,6 +115,7 @@ struct qcp_plan {
     qcpd::DevBuf d_coefA, d_coefB, d_pz, d_zy, d_flag, d_blocks;
     qcpd::DevBuf d_rw, d_cd, d_mvalG, d_mvalT;   // equilibration: row/column scalings, scaled values
     qcpd::DevBuf d_cdD, d_onesD, d_mvalD;        // QCP_PRECOND_DIAG: the caller's C, unit W, M diag(C)
+    qcpd::DevBuf d_cdJ;                          // QCP_PRECOND_JACOBI: 1 / column norms of F (made on first use)
     qcpd::DevBuf d_pip, d_pix, d_aip, d_aix;
 
     // schedule
@@ -130,11 +137,12 @@ struct qcp_plan {
     qcpd::DevBuf d_sys, d_tiles, d_groups, d_state, d_tpart, d_gpart, d_gcnt, d_scnt, d_active;
     qcpd::DevBuf d_split_cnt, d_row_part;
     qcpd::DevBuf d_pctl;     // persistent mode: barrier count, generation, stop flag, error flag
-    qcpd::DevBuf d_U, d_V, d_W, d_X, d_XI, d_RHS;
+    qcpd::DevBuf d_U, d_V, d_W, d_X, d_XI, d_RHS, d_HB;  // Krylov vectors (HB: LSMR's hbar)
     int* h_active = nullptr;  // pinned
 
     // cluster engine
     int cluster_cap = 0;  // CTAs per system asked for (0: per call from the number of systems)
+    int tuned_engine = -1; // the autotuner's choice for QCP_ENGINE_AUTO (-1: none)
     std::map<int, std::unique_ptr<qcpd::ClusterLayout>> clusters;  // by CTAs asked for
     qcpd::DevBuf d_csys;  // system lists of the cluster launches
     qcpd::DevBuf d_bcast; // broadcast buffers of the double-float cluster kernel
@@ -142,13 +150,18 @@ struct qcp_plan {
 
     std::map<qcpd::GraphKey, cudaGraphExec_t> graphs;
     int64_t last_launches = 0;
-    int last_engine = 0;
+    int last_engine = 0;   // qcp_engine the last call ran (CLUSTER_FP64 when the cluster kernel stayed in FP64)
     int view_precond = 0;  // qcp_precond of the current call's view (graph cache key)
-    int last_mode = -1;    // 0 JVP, 1 VJP: the last call
-    int last_nsys = 0;  // qcp_engine the last call ran (CLUSTER_FP64 when the cluster kernel stayed in FP64)
+    int last_mode = -1;    // 0 JVP, 1 VJP, 2 both (JVP systems first): the last call
+    int last_nsys = 0;     // systems of the last call
+    int last_jvp_sys = 0;  // of which the first last_jvp_sys solved a JVP
     // device time of the iteration chunks of the last call (CUDA events on
     // the plan's stream) and the number of pass launches they contain
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // a second stream for the cluster launches of a call's second system
+    // range (JVP and VJP systems side by side), created on first use
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double pass_ms = 0.0;
     int64_t pass_launches = 0;
 
@@ -160,4 +173,6 @@ namespace qcpd {
 int build_schedule(qcp_plan* p);
 // Free captured graphs.
 void drop_graphs(qcp_plan* p);
+// The Jacobi preconditioner's column scaling (N_tot doubles, device).
+int jacobi_cols(qcp_plan* p, double* out);
 }  // namespace qcpd

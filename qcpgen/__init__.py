@@ -11,7 +11,7 @@ optimum (b = A x* + s*, q = -P x* - A^T y*).
 """
 from .problems import (  # noqa: F401
     ZERO, NONNEG, SOC, CSR, QCP, Directions,
-    config1, config2, config3, config4, config5_family, small_qcp,
+    config1, config2, config3, config4, config5_family, paper_example, small_qcp,
     unconstrained_qp, equality_qp, make_directions, make_directions_batch,
     round_to_fp32, cone_dims_ok,
 )

@@ -606,6 +606,56 @@ def config5_family(seed: int = 0, scale: float = 1.0) -> Family:
     raise RuntimeError("config5: no differentiable draw")
 
 
+def paper_example(seed: int = 0, m: int = 2000, n: int = 1000, frac_active: float = 0.3,
+                  max_attempts: int = 20) -> QCP:
+    """The shape of the paper's worked example (Sec. 4, "Example"): variables
+    (x, r) with x in R^n, r in R^m; constraints
+        [C D; E 0; f^T 0] (x, r) + s = b,  s in {0}^m x R+^n x {0},
+    C dense m x n, D and E diagonal, objective r^T P r + q^T (x, r) with P
+    diagonal (no quadratic term on x).  The values and the optimum are
+    drawn, not taken from a solve:
+      * C ~ N(0, 1/n), D = -diag(U(0.5, 2)), E = -diag(U(0.5, 2)),
+        f ~ U(0.5, 2), P = diag(U(0.5, 2)) on r (stored: m upper entries);
+      * frac_active of the x entries are 0 with their R+ row active
+        (y ~ U(0.5, 2), s = 0); the others have s = -E_ii x_i ~ U(0.5, 2)
+        and y = 0, so b = 0 on the R+ rows as in the example's constraint
+        x >= 0; r ~ N(0, 1); y ~ N(0, 1) on the zero rows;
+      * b and q follow from the optimality conditions.
+    The active rows (m + 1 zero rows and the active R+ rows) have full row
+    rank, and the reduced Hessian is positive definite when C has full
+    column rank, so the solution map is differentiable at the optimum.
+    """
+    nv = n + m
+    cones = [(ZERO, m), (NONNEG, n), (ZERO, 1)]
+    for attempt in range(max_attempts):
+        rng = _rng(1006, seed, attempt)
+        Cd = rng.standard_normal((m, n)) / np.sqrt(n)
+        dD = -rng.uniform(0.5, 2.0, m)
+        dE = -rng.uniform(0.5, 2.0, n)
+        f = rng.uniform(0.5, 2.0, n)
+        p = rng.uniform(0.5, 2.0, m)
+        top = sp.hstack([sp.csr_matrix(Cd), sp.diags(dD)])
+        mid = sp.hstack([sp.diags(dE), sp.csr_matrix((n, m))])
+        bot = sp.hstack([sp.csr_matrix(f[None, :]), sp.csr_matrix((1, m))])
+        A = _csr_from_scipy(sp.vstack([top, mid, bot]).tocsr())
+        Pm = sp.diags(np.concatenate([np.zeros(n), p])).tocsr()
+        Pm.eliminate_zeros()
+        P = _upper_csr_from_sym_sparse(Pm)
+        active = np.zeros(n, bool)
+        active[rng.permutation(n)[:int(round(frac_active * n))]] = True
+        y, s = _optimum(rng, cones, active, [])
+        x = np.zeros(nv)
+        x[:n] = np.where(active, 0.0, s[m:m + n] / -dE)
+        x[n:] = rng.standard_normal(m)
+        Cr = _constraint_rows(A, cones, y, s)
+        if not _full_row_rank(Cr, "structural"):
+            continue
+        return _assemble(nv, m + n + 1, P, A, cones, x, y, s,
+                         {"workload": "paper example", "seed": seed, "attempts": attempt + 1,
+                          "active_dirs": int(Cr.shape[0])})
+    raise RuntimeError("paper_example: no differentiable draw")
+
+
 def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_per_row: int = 4,
               p_rank: int | None = None, frac_active: float = 0.5, soc_mix=(0.4, 0.2),
               max_attempts: int = 200) -> QCP:

@@ -92,3 +92,15 @@ def test_fp32_rounding():
     r = g.round_to_fp32(p)
     assert np.all(r.A.data == r.A.data.astype(np.float32).astype(np.float64))
     assert np.max(np.abs(r.q - p.q)) <= 1e-6 * np.max(np.abs(p.q))
+
+
+def test_paper_example_shape():
+    p = g.paper_example(0, m=60, n=30)
+    _check(p)
+    assert (p.n, p.m) == (90, 91)
+    assert p.cones == [(g.ZERO, 60), (g.NONNEG, 30), (g.ZERO, 1)]
+    assert p.P.nnz == 60 and np.all(p.P.indices >= 30)         # r^T P r: diagonal on r only
+    assert p.A.nnz == 60 * 30 + 60 + 30 + 30                   # [C D; E 0; f^T 0]
+    assert np.all(p.x[:30] >= 0) and np.allclose(p.b[60:90], 0.0)   # x >= 0 as in the example
+    C = _constraint_rows(p.A, p.cones, p.y, p.s)
+    assert np.linalg.matrix_rank(C.toarray()) == C.shape[0] <= p.n

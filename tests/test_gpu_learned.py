@@ -81,8 +81,9 @@ def test_network_forward_gradient_adam_match_reference(q, L):
 def test_learned_solve_gains_over_plain(q, L):
     """Train on the method's own solves of 40 instances, then on 8 held-out
     instances compare adjoint solves of ||x*||^2 to rtol 1e-6: the plain
-    method (no preconditioner, zero start), the classical equilibration, and
-    the learned warm start + preconditioner.  The learned solves must match
+    method (no preconditioner, zero start; LSQR and LSMR), the classical
+    equilibration and column-norm (Jacobi) scalings, and the learned warm
+    start + preconditioner.  The learned solves must match
     the oracle and take at least 20% fewer iterations than the plain method
     (the iterations are the solve time: all three run the same kernels)."""
     fam = g.config5_family(2, scale=0.1)
@@ -91,12 +92,14 @@ def test_learned_solve_gains_over_plain(q, L):
     lp = L.LearnedPreconditioner(seed=3).fit(train, steps=800, lr=1e-3)
     assert np.mean(lp.losses[-50:]) < np.mean(lp.losses[:50])
     print("preconditioner exponent chosen on training instances:", lp.alpha, lp.alpha_cost)
-    its = {"plain": [], "equilibrate": [], "learned": []}
+    its = {"plain": [], "equilibrate": [], "jacobi": [], "plain_lsmr": [], "learned": []}
     for prob in held:
         plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
         wx, wy, ws = L.adjoint_direction(prob)
         for name, opts in (("plain", q.options(rtol=1e-6, engine="passes")),
-                           ("equilibrate", q.options(rtol=1e-6, precond="equilibrate", engine="passes"))):
+                           ("equilibrate", q.options(rtol=1e-6, precond="equilibrate", engine="passes")),
+                           ("jacobi", q.options(rtol=1e-6, precond="jacobi", engine="passes")),
+                           ("plain_lsmr", q.options(rtol=1e-6, engine="passes", solver="lsmr"))):
             *_, info = q.qcp_derivative_vjp(plan, wx, wy, ws, opts)
             its[name].append(info[0]["iters"])
         gP, gA, gq, gb, info = lp.vjp(plan, prob, rtol=1e-6)

@@ -127,6 +127,43 @@ def test_config2_sixteen_directions(q, cfg2):
     plan.close()
 
 
+@pytest.mark.parametrize("engine", ["passes", "persistent", "cluster", "cluster_fp64"])
+def test_jvp_and_vjp_in_one_call(q, cfg2, engine):
+    """qcp_derivative_jvp_vjp_multi (JVP systems first, VJP systems after
+    them; side by side on the cluster engine) gives the oracle's results and,
+    with the engine and cluster size fixed, exactly the separate calls'."""
+    prob, dirs, ref_j, ref_v = cfg2
+    kj, kv = 4, 3
+    plan = _plan(q, prob, max_rhs=kj + kv)
+    plan.set_cluster(4)
+    opts = q.options(rtol=1e-10, maxiter=100000, engine=engine)
+    cat = lambda name, ds: np.concatenate([getattr(d, name) for d in ds])
+    J, V = dirs[:kj], dirs[5:5 + kv]
+    (dx, dy, ds), (gP, gA, gq, gb), info = q.qcp_derivative_jvp_vjp_multi(
+        plan, kj, cat("dP", J), cat("dA", J), cat("dq", J), cat("db", J), kv, cat("wx", V), cat("wy", V),
+        cat("ws", V), opts)
+    assert len(info) == kj + kv and all(i["status"] == "QCP_OK" for i in info), info
+    dx, dy, ds, gP, gA, gq, gb = to_np(dx, dy, ds, gP, gA, gq, gb)
+    n, m, nP, nA = prob.n, prob.m, prob.P.nnz, prob.A.nnz
+    for i in range(kj):
+        got = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
+        assert rel_err(got, ref_j[i]) < TOL64, (i, rel_err(got, ref_j[i]))
+    for i in range(kv):
+        got = (gP[i * nP:(i + 1) * nP], gA[i * nA:(i + 1) * nA], gq[i * n:(i + 1) * n], gb[i * m:(i + 1) * m])
+        assert rel_err(got, ref_v[5 + i]) < TOL64, (i, rel_err(got, ref_v[5 + i]))
+    sx, sy, ss, sji = q.qcp_derivative_jvp_multi(plan, kj, cat("dP", J), cat("dA", J), cat("dq", J), cat("db", J),
+                                                 opts)
+    tP, tA, tq, tb, svi = q.qcp_derivative_vjp_multi(plan, kv, cat("wx", V), cat("wy", V), cat("ws", V), opts)
+    for a, b in zip((dx, dy, ds, gP, gA, gq, gb), to_np(sx, sy, ss, tP, tA, tq, tb)):
+        assert np.array_equal(a, b), engine
+    assert [i["iters"] for i in info] == [i["iters"] for i in sji + svi]
+    with pytest.raises(RuntimeError):
+        q.qcp_derivative_jvp_vjp_multi(plan, kj, cat("dP", J), cat("dA", J), cat("dq", J), cat("db", J), kv + 1,
+                                       cat("wx", dirs[:kv + 1]), cat("wy", dirs[:kv + 1]),
+                                       cat("ws", dirs[:kv + 1]), opts)
+    plan.close()
+
+
 def test_config2_schedules_agree(q, cfg2):
     """Different tile sizes (multi-chunk tiles, CTA-per-row tiles) agree."""
     prob, dirs, ref_j, ref_v = cfg2
@@ -258,6 +295,36 @@ def test_batched_uneven_problems(q):
     plan.close()
 
 
+def test_autotuner_picks_the_fastest_and_auto_uses_it(q):
+    """qcp_plan_autotune times every candidate on the plan, keeps the fastest
+    per pass for engine="auto", and the tuned solves still match the oracle."""
+    probs = [g.config1(0), g.small_qcp(41, 17, 2, 8, (3, 6)), g.config3(1, scale=0.003)]
+    dirs = [g.make_directions(p, 9) for p in probs]
+    plan = q.qcp_batch_plan_create([q.problem_tensors(p, "cuda") for p in probs], torch.float64)
+    cat = lambda name: np.concatenate([getattr(d, name) for d in dirs])
+    for mode in ("jvp", "vjp"):
+        best, entries = plan.autotune(mode, iters=16, opts=q.options(precond="equilibrate"))
+        kinds = {(e["engine"], e["cluster_ctas"], e["tile_nnz"]) for e in entries}
+        assert len(kinds) == len(entries) >= 10, entries
+        assert all(e["us_per_pass"] > 0 for e in entries), entries
+        assert best["us_per_pass"] == min(e["us_per_pass"] for e in entries), (best, entries)
+        opts = q.options(rtol=1e-13, precond="equilibrate", engine="auto")
+        dx, dy, ds, ji = q.qcp_derivative_jvp(plan, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
+        used = plan.last_engine()
+        assert used == best["engine"] or (best["engine"] == "cluster" and used == "cluster_fp64"), (used, best)
+        gP, gA, gq, gb, vi = q.qcp_derivative_vjp(plan, cat("wx"), cat("wy"), cat("ws"), opts)
+        _batched_check(probs, dirs, to_np(dx, dy, ds, gP, gA, gq, gb), ji, vi)
+    # a single-problem plan with several directions
+    prob = g.config1(0)
+    plan2 = _plan(q, prob, max_rhs=4)
+    best, entries = plan2.autotune("vjp", nsys=4, iters=16)
+    assert best["us_per_pass"] == min(e["us_per_pass"] for e in entries)
+    with pytest.raises(RuntimeError):
+        plan2.autotune("vjp", nsys=5)
+    plan2.close()
+    plan.close()
+
+
 def _batched_check(probs, dirs, outs, ji, vi):
     dx, dy, ds, gP, gA, gq, gb = outs
     on = om = op = oa = 0
@@ -383,4 +450,104 @@ def test_warm_start_and_diag_preconditioner(q):
         gpu_jvp(q, plan, d, q.options(precond="diag", precond_d=cuda(np.ones(N)), engine="cluster"))
     with pytest.raises(QCPError, match="ERR_ARG"):
         gpu_jvp(q, plan, d, q.options(precond="diag"))
+    plan.close()
+
+
+@pytest.mark.parametrize("precond", ["none", "equilibrate"])
+@pytest.mark.parametrize("name,mk", SMALL[:6] + SMALL[8:], ids=[s[0] for s in SMALL[:6] + SMALL[8:]])
+def test_lsmr_matches_oracle(q, name, mk, precond):
+    """LSMR (solver 1) on the pass engine reaches the oracle's JVP and VJP;
+    the persistent engine gives the same bits."""
+    prob = mk()
+    d = g.make_directions(prob, 7)
+    fac = D.DenseFactor(prob)
+    rj = D.jvp_dense(prob, d, fac)[:3]
+    rv = D.vjp_dense(prob, d, fac)[:4]
+    plan = _plan(q, prob)
+    opts = q.options(rtol=1e-11, precond=precond, solver="lsmr", engine="passes")
+    jv, ji = gpu_jvp(q, plan, d, opts)
+    vv, vi = gpu_vjp(q, plan, d, opts)
+    assert rel_err(jv, rj) < TOL64, (rel_err(jv, rj), ji)
+    assert rel_err(vv, rv) < TOL64, (rel_err(vv, rv), vi)
+    for inf in (ji[0], vi[0]):
+        assert inf["status"] in ("QCP_OK", "QCP_NOT_CONVERGED"), inf
+        assert inf["rel_residual"] <= (1e-11 if inf["status"] == "QCP_OK" else 1e-8), inf
+    assert plan.last_engine() == "passes"
+    po = q.options(rtol=1e-11, precond=precond, solver="lsmr", engine="persistent")
+    pj, _ = gpu_jvp(q, plan, d, po)
+    pv, _ = gpu_vjp(q, plan, d, po)
+    for a, b in zip(pj + pv, jv + vv):
+        assert np.array_equal(a, b)
+    plan.close()
+
+
+def test_lsmr_config2_and_engine_rules(q, cfg2):
+    """Configuration 2 with LSMR: four directions each way at rtol 1e-10;
+    auto runs LSMR on the pass engine and the cluster engines refuse it."""
+    prob, dirs, ref_j, ref_v = cfg2
+    k = 4
+    plan = _plan(q, prob, max_rhs=k)
+    opts = q.options(rtol=1e-10, precond="equilibrate", solver="lsmr")
+    cat = lambda name: np.concatenate([getattr(d, name) for d in dirs[:k]])
+    dx, dy, ds, ji = q.qcp_derivative_jvp_multi(plan, k, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
+    assert plan.last_engine() == "passes"
+    dx, dy, ds = to_np(dx, dy, ds)
+    n, m = prob.n, prob.m
+    for i in range(k):
+        got = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
+        assert rel_err(got, ref_j[i]) < TOL64, (i, rel_err(got, ref_j[i]), ji[i])
+    gP, gA, gq, gb, vi = q.qcp_derivative_vjp_multi(plan, k, cat("wx"), cat("wy"), cat("ws"), opts)
+    gP, gA, gq, gb = to_np(gP, gA, gq, gb)
+    nP, nA = prob.P.nnz, prob.A.nnz
+    for i in range(k):
+        got = (gP[i * nP:(i + 1) * nP], gA[i * nA:(i + 1) * nA], gq[i * n:(i + 1) * n], gb[i * m:(i + 1) * m])
+        assert rel_err(got, ref_v[i]) < TOL64, (i, rel_err(got, ref_v[i]), vi[i])
+    for engine in ("cluster", "cluster_fp64"):
+        with pytest.raises(RuntimeError):
+            q.qcp_derivative_jvp_multi(plan, 1, cat("dP")[:nP], cat("dA")[:nA], cat("dq")[:n], cat("db")[:m],
+                                       q.options(solver="lsmr", engine=engine))
+    plan.close()
+
+
+@pytest.mark.parametrize("engine", ["auto", "passes"])
+def test_paper_example_full_size(q, engine):
+    """The paper's example shape at its size (Sec. 4: m = 2000, n = 1000; 3000
+    variables, 3001 rows, C dense): 2 JVPs and 2 VJPs in one call against the
+    dense oracle, rtol 1e-10."""
+    prob = g.paper_example(0)
+    dirs = g.make_directions_batch(prob, 13, 2)
+    fac = D.DenseFactor(prob)
+    plan = _plan(q, prob, max_rhs=4)
+    cat = lambda name: np.concatenate([getattr(d, name) for d in dirs])
+    (dx, dy, ds), (gP, gA, gq, gb), info = q.qcp_derivative_jvp_vjp_multi(
+        plan, 2, cat("dP"), cat("dA"), cat("dq"), cat("db"), 2, cat("wx"), cat("wy"), cat("ws"),
+        q.options(rtol=1e-10, precond="equilibrate", engine=engine))
+    assert all(i["status"] == "QCP_OK" for i in info), info
+    dx, dy, ds, gP, gA, gq, gb = to_np(dx, dy, ds, gP, gA, gq, gb)
+    n, m, nP, nA = prob.n, prob.m, prob.P.nnz, prob.A.nnz
+    for i, d in enumerate(dirs):
+        rj = D.jvp_dense(prob, d, fac)[:3]
+        rv = D.vjp_dense(prob, d, fac)[:4]
+        got_j = (dx[i * n:(i + 1) * n], dy[i * m:(i + 1) * m], ds[i * m:(i + 1) * m])
+        got_v = (gP[i * nP:(i + 1) * nP], gA[i * nA:(i + 1) * nA], gq[i * n:(i + 1) * n], gb[i * m:(i + 1) * m])
+        assert rel_err(got_j, rj) < TOL64, (i, rel_err(got_j, rj))
+        assert rel_err(got_v, rv) < TOL64, (i, rel_err(got_v, rv))
+    plan.close()
+
+
+@pytest.mark.parametrize("solver", ["lsqr", "lsmr"])
+@pytest.mark.parametrize("name,mk", [SMALL[2], SMALL[5], SMALL[8]], ids=[SMALL[2][0], SMALL[5][0], SMALL[8][0]])
+def test_jacobi_preconditioner(q, name, mk, solver):
+    """The column-norm (Jacobi) preconditioner reaches the oracle's results
+    with either solver."""
+    prob = mk()
+    d = g.make_directions(prob, 17)
+    fac = D.DenseFactor(prob)
+    plan = _plan(q, prob)
+    opts = q.options(rtol=1e-11, precond="jacobi", solver=solver)
+    jv, ji = gpu_jvp(q, plan, d, opts)
+    vv, vi = gpu_vjp(q, plan, d, opts)
+    assert rel_err(jv, D.jvp_dense(prob, d, fac)[:3]) < TOL64, ji
+    assert rel_err(vv, D.vjp_dense(prob, d, fac)[:4]) < TOL64, vi
+    assert plan.last_engine() == "passes"
     plan.close()

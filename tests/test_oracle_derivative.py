@@ -24,7 +24,9 @@ from conftest import rel_err
 
 
 QPS = [lambda: g.config1(0), lambda: g.config1(1),
-       lambda: g.small_qcp(11, 12, 3, 10, ()), lambda: g.small_qcp(12, 20, 0, 30, (), nnz_per_row=5)]
+       lambda: g.small_qcp(11, 12, 3, 10, ()), lambda: g.small_qcp(12, 20, 0, 30, (), nnz_per_row=5),
+       # the paper's example shape (Sec. 4): P singular on x, a zero block after the R+ block
+       lambda: g.paper_example(0, m=40, n=20)]
 SOCS = [lambda: g.small_qcp(21, 10, 2, 5, (3, 4, 5)),
         lambda: g.small_qcp(22, 16, 0, 6, (3, 3, 6, 8), soc_mix=(0.5, 0.25)),
         lambda: g.small_qcp(23, 12, 1, 0, (2, 5, 7), soc_mix=(0.34, 0.33))]
