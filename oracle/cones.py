@@ -3,16 +3,96 @@
 The cone K is a product of blocks (type, dim) listed in row order.  The
 derivative method projects z_y = y - s onto the DUAL cone K*; the dual of the
 zero cone {0} is the whole line R (projection = identity, derivative = I),
-the nonnegative orthant and the second-order cone are self-dual.
+the nonnegative orthant, the second-order cone and the positive
+semidefinite cone are self-dual.
 
 Kinks (Appendix A leaves the derivative undefined there) are broken as
 follows: R+ uses the indicator 1{z > 0}; the SOC cases are tested in the
 order the projection lists them, with non-strict inequalities:
-||u|| <= -t gives 0, else ||u|| <= t gives the identity, else the formula.
+||u|| <= -t gives 0, else ||u|| <= t gives the identity, else the formula;
+the PSD cone treats an eigenvalue as positive only when it is > 0.
+
+A PSD block of order k holds a symmetric k x k matrix X as its scaled
+upper triangle, column by column (dim = k (k + 1) / 2):
+    svec(X) = (X_11, sqrt2 X_12, X_22, sqrt2 X_13, sqrt2 X_23, X_33, ...),
+so that <svec(X), svec(Y)> = trace(X Y).
 """
 import numpy as np
 
-ZERO, NONNEG, SOC = 0, 1, 2
+ZERO, NONNEG, SOC, PSD = 0, 1, 2, 3
+
+
+def psd_order(d):
+    """k with k (k + 1) / 2 = d."""
+    k = int(round((np.sqrt(8 * d + 1) - 1) / 2))
+    if k * (k + 1) // 2 != d:
+        raise ValueError(f"{d} is not a triangular number")
+    return k
+
+
+def smat(v):
+    """The symmetric matrix of a PSD block's entries (inverse of svec)."""
+    k = psd_order(v.shape[0])
+    X = np.empty((k, k))
+    i = 0
+    for j in range(k):           # column j of the upper triangle
+        for a in range(j + 1):   # row a <= j
+            X[a, j] = X[j, a] = v[i] if a == j else v[i] / np.sqrt(2.0)
+            i += 1
+    return X
+
+
+def svec(X):
+    k = X.shape[0]
+    out = np.empty(k * (k + 1) // 2)
+    i = 0
+    for j in range(k):
+        for a in range(j + 1):
+            out[i] = X[a, j] if a == j else np.sqrt(2.0) * X[a, j]
+            i += 1
+    return out
+
+
+def proj_psd(z):
+    """Projection onto the PSD cone (Appendix A): keep the nonnegative part
+    of the eigendecomposition, sum_i max(lambda_i, 0) v_i v_i^T."""
+    lam, V = np.linalg.eigh(smat(z))
+    return svec((V * np.maximum(lam, 0.0)) @ V.T)
+
+
+def psd_B(lam):
+    """The symmetric weights of D Pi_psd: the divided differences of
+    max(., 0) over the eigenvalues (Appendix A; 1 where both are positive,
+    0 where both are not, lambda_i / (lambda_i - lambda_j) for lambda_i > 0
+    >= lambda_j)."""
+    k = lam.shape[0]
+    B = np.empty((k, k))
+    for i in range(k):
+        for j in range(k):
+            pi, pj = lam[i] > 0.0, lam[j] > 0.0
+            if pi and pj:
+                B[i, j] = 1.0
+            elif not pi and not pj:
+                B[i, j] = 0.0
+            elif pi:
+                B[i, j] = lam[i] / (lam[i] - lam[j])
+            else:
+                B[i, j] = lam[j] / (lam[j] - lam[i])
+    return B
+
+
+def dproj_psd(z):
+    """Jacobian of proj_psd at z in svec coordinates (Appendix A):
+    D[dZ] = V (B o (V^T dZ V)) V^T, column by column."""
+    lam, V = np.linalg.eigh(smat(z))
+    B = psd_B(lam)
+    d = z.shape[0]
+    J = np.empty((d, d))
+    for c in range(d):
+        e = np.zeros(d)
+        e[c] = 1.0
+        J[:, c] = svec(V @ (B * (V.T @ smat(e) @ V)) @ V.T)
+    return J
 
 
 def proj_soc(z):
@@ -58,6 +138,8 @@ def proj_dual_block(ctype, z):
         return np.maximum(z, 0.0)
     if ctype == SOC:
         return proj_soc(z)
+    if ctype == PSD:
+        return proj_psd(z)
     raise ValueError(ctype)
 
 
@@ -69,6 +151,8 @@ def dproj_dual_block(ctype, z):
         return np.diag((z > 0.0).astype(np.float64))
     if ctype == SOC:
         return dproj_soc(z)
+    if ctype == PSD:
+        return dproj_psd(z)
     raise ValueError(ctype)
 
 
@@ -76,7 +160,7 @@ def proj_primal_block(ctype, z):
     """Projection onto the block of K itself (used by the Moreau pin)."""
     if ctype == ZERO:
         return np.zeros_like(z)
-    return proj_dual_block(ctype, z)      # R+ and SOC are self-dual
+    return proj_dual_block(ctype, z)      # R+, SOC and PSD are self-dual
 
 
 def _blocks(cones):
@@ -129,4 +213,6 @@ def kink_margin(cones, z):
         elif t == SOC:
             r = np.linalg.norm(zb[1:])
             best = min(best, abs(r - abs(zb[0])) if (r > 0 or zb[0] != 0) else 0.0)
+        elif t == PSD:
+            best = min(best, float(np.min(np.abs(np.linalg.eigvalsh(smat(zb))))))
     return best

@@ -103,6 +103,11 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
     std::memset(&cp, 0, sizeof(cp));
     cp.C = C;
     const double total = (double)(rp[Nx] - rp[0]) + kRowWeight * Nx;
+    // a range closed by the row cap holds at least lcap - umax + 1 rows
+    // (umax: the largest unit, an SOC block or one row)
+    int umax = 1;
+    for (size_t u = 0, prev = 0; u < ends.size(); prev = ends[u], ++u) umax = std::max(umax, ends[u] - (int)prev);
+    const int64_t room = std::max(1, lcap - umax + 1);
     int k = 1, start = 0;
     for (size_t u = 0; u < ends.size() && k < C; ++u) {
         const int e = ends[u];
@@ -113,7 +118,7 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
         // single range)
         const int next = (u + 1 < ends.size()) ? ends[u + 1] : e;
         const double acc = (double)(rp[e] - rp[0]) + kRowWeight * e;
-        while (k < C && ((acc >= total * k / C && (int64_t)(Nx - e) <= (int64_t)(C - k) * lcap) ||
+        while (k < C && ((acc >= total * k / C && (int64_t)(Nx - e) <= (int64_t)(C - k) * room) ||
                          next - start > lcap)) {
             cp.split[k] = e;
             cp.cb[k] = socs[u];

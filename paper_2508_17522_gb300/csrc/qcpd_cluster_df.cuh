@@ -175,24 +175,43 @@ __device__ __forceinline__ void block_reduce_df3(df (&v)[3], df* red) {
 __device__ __forceinline__ void sell_rowsums_df(const CCtxDf& c, const df* sval, const df* F, df* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nw = kCWarps - 1;
-    for (int s = c.sl0 + warp - 1; s < c.sl1; s += nw) {
-        const SellSlice d = c.slices[s];
+    // Each step below waits one L2 round trip, so the loop keeps as many
+    // loads in flight as it can: the next slice's header is fetched while
+    // this slice runs, and the entries go eight at a time.
+    int s = c.sl0 + warp - 1;
+    SellSlice d{};
+    if (s < c.sl1) d = c.slices[s];
+    for (; s < c.sl1; s += nw) {
+        SellSlice dn{};
+        if (s + nw < c.sl1) dn = c.slices[s + nw];
         const int32_t* cp = c.scol + d.base + lane;
         const df* vp = sval + d.base + lane;
         DfAcc acc = dfacc_zero();
         int k = 0;
-        for (; k + 4 <= d.width; k += 4) {
-            int32_t j[4];
-            df v[4];
+        for (; k + 8 <= d.width; k += 8) {
+            int32_t j[8];
+            df v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 j[u] = __ldg(cp + 32 * (k + u));
                 v[u] = __ldg(vp + 32 * (k + u));
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) dfacc_fma(acc, v[u], F[j[u]]);
+            for (int u = 0; u < 8; ++u) dfacc_fma(acc, v[u], F[j[u]]);
         }
-        for (; k < d.width; ++k) dfacc_fma(acc, __ldg(vp + 32 * k), F[__ldg(cp + 32 * k)]);
+        if (k < d.width) {  // the last 1..7 entries in one round trip (a zero product leaves acc as it is)
+            int32_t j[8];
+            df v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool in = k + u < d.width;
+                j[u] = in ? __ldg(cp + 32 * (k + u)) : 0;
+                v[u] = in ? __ldg(vp + 32 * (k + u)) : df_zero();
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (k + u < d.width) dfacc_fma(acc, v[u], F[j[u]]);
+        }
         df r = dfacc_result(acc);
         if (d.row >= 0) {
             r = warp_sum_df(r);
@@ -201,6 +220,7 @@ __device__ __forceinline__ void sell_rowsums_df(const CCtxDf& c, const df* sval,
             const int row = c.perm[d.pidx + lane];
             if (row >= 0) out[row] = r;
         }
+        d = dn;
     }
 }
 
@@ -342,27 +362,43 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
 
     DfAcc ss = dfacc_zero(), dtop = dfacc_zero(), dbot = dfacc_zero();
     if (PASS == PASS_G) {
-        for (int i = tid; i < L; i += kCThreads) {
+        // row i's per-row constants and w / x (from L2), then its update
+        struct RowIn {
+            df a, b, cd, rw, w, x;
+        };
+        auto load = [&](int i) {
+            const int r = R0 + i;
+            RowIn v;
+            v.a = c.cA[r];
+            v.b = c.cB[r];
+            v.cd = SC ? c.cd[r] : df_zero();
+            v.rw = SC ? c.rw[r] : df_zero();
+            v.w = c.W[r];
+            v.x = ROLE == ROLE_V ? c.X[r] : df_zero();
+            return v;
+        };
+        auto row = [&](int i, const RowIn& v) {
             const int r = R0 + i;
             const df iv = in_s[i];
             df o;
             if (r < n) {
-                o = df_fma(c.cA[r], tt, s0[i]);
-                dfacc_fma(dtop, c.cB[r], SC ? df_mul(c.cd[r], iv) : iv);
+                o = df_fma(v.a, tt, s0[i]);
+                dfacc_fma(dtop, v.b, SC ? df_mul(v.cd, iv) : iv);
             } else {
                 const df xi = XIs[i];
-                const df dxi = SC ? df_mul(c.cd[r], df_sub(xi, iv)) : df_sub(xi, iv);
-                o = df_add(df_fma(df_neg(c.cA[r]), tt, s0[i]), dxi);
-                dfacc_fma(dbot, c.cB[r], SC ? df_mul(c.cd[r], xi) : xi);
+                const df dxi = SC ? df_mul(v.cd, df_sub(xi, iv)) : df_sub(xi, iv);
+                o = df_add(df_fma(df_neg(v.a), tt, s0[i]), dxi);
+                dfacc_fma(dbot, v.b, SC ? df_mul(v.cd, xi) : xi);
             }
-            if (SC) o = df_mul(o, c.rw[r]);
+            if (SC) o = df_mul(o, v.rw);
             const df nv = df_fma(c1, o, df_mul(nc2, out_s[i]));
             out_s[i] = nv;
             bout[i] = nv;
             dfacc_fma(ss, nv, nv);
-            if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c1, df_mul(nw, c.W[r]));
-            else c.X[r] = df_fma(xc, c.W[r], c.X[r]);
-        }
+            if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c1, df_mul(nw, v.w));
+            else c.X[r] = df_fma(xc, v.w, v.x);
+        };
+        for (int i = tid; i < L; i += kCThreads) row(i, load(i));
     } else {
         for (int i = tid; i < L; i += kCThreads) {
             const int r = R0 + i;

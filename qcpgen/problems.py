@@ -9,8 +9,10 @@ single-valued and differentiable there (the regularity the implicit function
 theorem of Sec. 2.4 needs).
 
 Cone blocks are listed in row order as (type, dim) with type ZERO (the cone
-{0}), NONNEG (the nonnegative orthant) or SOC (the second-order cone, stored
-(t, u) with t first, Appendix A).
+{0}), NONNEG (the nonnegative orthant), SOC (the second-order cone, stored
+(t, u) with t first, Appendix A) or PSD (the positive semidefinite cone of
+order k, dim = k (k + 1) / 2, a symmetric matrix stored as its upper
+triangle column by column with the off-diagonal entries times sqrt 2).
 
 The five named workloads follow the problem descriptions of the benchmark
 configurations; the readings of under-specified points are:
@@ -34,7 +36,7 @@ import numpy as np
 import scipy.sparse as sp
 from scipy.sparse.csgraph import structural_rank
 
-ZERO, NONNEG, SOC = 0, 1, 2
+ZERO, NONNEG, SOC, PSD = 0, 1, 2, 3
 
 
 # --------------------------------------------------------------------------
@@ -208,6 +210,38 @@ def _unit(rng, k):
     return v / nv
 
 
+def _psd_order(d):
+    k = int(round((np.sqrt(8 * d + 1) - 1) / 2))
+    assert k * (k + 1) // 2 == d, d
+    return k
+
+
+def _sym_to_entries(X):
+    """A symmetric matrix as a PSD block's entries (upper triangle column by
+    column, off-diagonal entries times sqrt 2)."""
+    k = X.shape[0]
+    a, j = np.triu_indices(k)
+    order = np.lexsort((a, j))                    # column-major over the upper triangle
+    a, j = a[order], j[order]
+    return np.where(a == j, 1.0, np.sqrt(2.0)) * X[a, j]
+
+
+def _entries_to_sym(v):
+    k = _psd_order(v.shape[0])
+    a, j = np.triu_indices(k)
+    order = np.lexsort((a, j))
+    a, j = a[order], j[order]
+    X = np.zeros((k, k))
+    X[a, j] = np.where(a == j, 1.0, 1.0 / np.sqrt(2.0)) * v
+    X[j, a] = X[a, j]
+    return X
+
+
+def _orthogonal(rng, k):
+    Q, R = np.linalg.qr(rng.standard_normal((k, k)))
+    return Q * np.sign(np.diag(R))
+
+
 def cone_dims_ok(cone_type, cone_dim, m) -> bool:
     return int(np.sum(cone_dim)) == m and np.all(np.asarray(cone_dim) >= 1)
 
@@ -215,11 +249,14 @@ def cone_dims_ok(cone_type, cone_dim, m) -> bool:
 # --------------------------------------------------------------------------
 # optimum construction
 # --------------------------------------------------------------------------
-def _optimum(rng, cones, nonneg_active, soc_kind):
+def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=()):
     """Draw (y, s) block by block.
 
     nonneg_active: bool per row of the R+ blocks (concatenated in order).
     soc_kind: one of 'ray', 'yint', 'sint' per SOC block (in order).
+    psd_rank: per PSD block (in order), the rank r of s; s = Q diag(sigma) Q^T
+        on the first r columns of a random orthogonal Q and y on the other
+        k - r columns (eigenvalues ~ U(0.5, 2)), so y s = 0 and y + s > 0.
     """
     m = int(sum(d for _, d in cones))
     y = np.zeros(m)
@@ -227,6 +264,7 @@ def _optimum(rng, cones, nonneg_active, soc_kind):
     r = 0
     ia = 0
     isoc = 0
+    ipsd = 0
     for t, d in cones:
         if t == ZERO:
             y[r:r + d] = rng.standard_normal(d)
@@ -255,6 +293,14 @@ def _optimum(rng, cones, nonneg_active, soc_kind):
                 tgt = y if kind == "yint" else s
                 tgt[r] = tt
                 tgt[r + 1:r + d] = u
+        elif t == PSD:
+            k = _psd_order(d)
+            rk = psd_rank[ipsd]
+            ipsd += 1
+            Q = _orthogonal(rng, k)
+            ev = rng.uniform(0.5, 2.0, k)
+            s[r:r + d] = _sym_to_entries((Q[:, :rk] * ev[:rk]) @ Q[:, :rk].T)
+            y[r:r + d] = _sym_to_entries((Q[:, rk:] * ev[rk:]) @ Q[:, rk:].T)
         else:
             raise ValueError(f"unknown cone type {t}")
         r += d
@@ -273,6 +319,21 @@ def _constraint_rows(A: CSR, cones, y, s) -> sp.csr_matrix:
             idx = r + np.nonzero(s[r:r + d] == 0.0)[0]
             if idx.size:
                 pieces.append(As[idx])
+        elif t == PSD:
+            # s = Q_S diag Q_S^T binds the directions svec(N M N^T), N an
+            # orthonormal basis of s's null space and M any symmetric matrix
+            k = _psd_order(d)
+            lam, V = np.linalg.eigh(_entries_to_sym(s[r:r + d]))
+            N = V[:, lam <= 1e-9 * max(1.0, float(np.abs(lam).max(initial=0.0)))]
+            kn = N.shape[1]
+            if kn:
+                rows = []
+                for j in range(kn):
+                    for a in range(j + 1):
+                        M = np.zeros((kn, kn))
+                        M[a, j] = M[j, a] = 1.0
+                        rows.append(_sym_to_entries(N @ M @ N.T))
+                pieces.append(sp.csr_matrix(np.array(rows)) @ As[r:r + d])
         else:
             yb, sb = y[r:r + d], s[r:r + d]
             if np.all(sb == 0.0) and np.any(yb != 0.0):      # s = 0: all rows bind
@@ -658,10 +719,12 @@ def paper_example(seed: int = 0, m: int = 2000, n: int = 1000, frac_active: floa
 
 def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_per_row: int = 4,
               p_rank: int | None = None, frac_active: float = 0.5, soc_mix=(0.4, 0.2),
-              max_attempts: int = 200) -> QCP:
+              max_attempts: int = 200, psd_orders=(), psd_ranks=None) -> QCP:
     """A small QCP with any mix of blocks, for tests.
 
-    The zero block comes first, then the R+ block, then the SOC blocks.
+    The zero block comes first, then the R+ block, then the SOC blocks, then
+    the PSD blocks (orders psd_orders; psd_ranks gives the rank of s in each,
+    by default a draw from 0..k).
     soc_mix = (fraction on rays, fraction with s = 0); the rest have y = 0.
     """
     cones = []
@@ -670,7 +733,8 @@ def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_pe
     if m_nonneg:
         cones.append((NONNEG, m_nonneg))
     cones += [(SOC, int(d)) for d in soc_dims]
-    m = m_zero + m_nonneg + int(sum(soc_dims))
+    cones += [(PSD, int(k) * (int(k) + 1) // 2) for k in psd_orders]
+    m = m_zero + m_nonneg + int(sum(soc_dims)) + sum(int(k) * (int(k) + 1) // 2 for k in psd_orders)
     for attempt in range(max_attempts):
         rng = _rng(2000, seed, n, m, attempt)
         A = _sparse_rows(rng, m, n, min(nnz_per_row, n))
@@ -680,8 +744,9 @@ def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_pe
         active = np.zeros(m_nonneg, bool)
         active[rng.permutation(m_nonneg)[:int(round(frac_active * m_nonneg))]] = True
         kinds = _soc_kinds(rng, len(soc_dims), soc_mix[0], soc_mix[1], list(soc_dims))
+        ranks = list(psd_ranks) if psd_ranks is not None else [int(rng.integers(0, k + 1)) for k in psd_orders]
         x = rng.standard_normal(n)
-        y, s = _optimum(rng, cones, active, kinds)
+        y, s = _optimum(rng, cones, active, kinds, ranks)
         C = _constraint_rows(A, cones, y, s)
         if not _full_row_rank(C, "dense"):
             continue

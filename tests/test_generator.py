@@ -33,6 +33,12 @@ def _check(p):
         elif t == g.NONNEG:
             assert np.all(yb >= 0) and np.all(sb >= 0)
             assert np.all((yb > 0) ^ (sb > 0)), "strict complementarity"
+        elif t == g.PSD:
+            from oracle.cones import smat   # the oracle's own convention, as an independent check
+            ly, ls = np.linalg.eigvalsh(smat(yb)), np.linalg.eigvalsh(smat(sb))
+            assert ly.min() > -1e-12 and ls.min() > -1e-12
+            tol = 1e-9
+            assert int((ly > tol).sum()) + int((ls > tol).sum()) == ly.size, "strict complementarity"
         else:
             assert np.linalg.norm(yb[1:]) <= yb[0] + 1e-12
             assert np.linalg.norm(sb[1:]) <= sb[0] + 1e-12
@@ -104,3 +110,20 @@ def test_paper_example_shape():
     assert np.all(p.x[:30] >= 0) and np.allclose(p.b[60:90], 0.0)   # x >= 0 as in the example
     C = _constraint_rows(p.A, p.cones, p.y, p.s)
     assert np.linalg.matrix_rank(C.toarray()) == C.shape[0] <= p.n
+
+
+def test_psd_blocks():
+    from oracle.cones import smat
+    for ranks in [(1, 0), (0, 2), (3, 1), (2, 2)]:
+        p = g.small_qcp(31, 14, 1, 4, (3,), psd_orders=(3, 2), psd_ranks=ranks)
+        _check(p)
+        assert p.cones[-2:] == [(g.PSD, 6), (g.PSD, 3)]
+        C = _constraint_rows(p.A, p.cones, p.y, p.s)
+        # every active direction: 1 zero row, the active R+ rows, the SOC block's,
+        # and (k - r)(k - r + 1)/2 per PSD block
+        assert np.linalg.matrix_rank(C.toarray()) == C.shape[0]
+        # y s = 0 as matrices, not only in trace
+        r = p.m - 9
+        for d in (6, 3):
+            assert np.allclose(smat(p.y[r:r + d]) @ smat(p.s[r:r + d]), 0.0, atol=1e-12)
+            r += d

@@ -91,3 +91,87 @@ def test_product_cone_moreau_blockwise():
         Ds = C.dproj_dual_sparse(cones, z).toarray()
         np.testing.assert_array_equal(D, Ds)
         np.testing.assert_allclose(D @ z, C.proj_dual(cones, z), atol=1e-12)
+
+
+# ----------------------------------------------------------------- PSD cone
+def _rand_sym_entries(rng, k, scale=1.0):
+    X = rng.standard_normal((k, k)) * scale
+    return C.svec((X + X.T) / 2)
+
+
+def test_psd_svec_is_an_isometry():
+    rng = np.random.default_rng(7)
+    for k in (1, 2, 3, 5):
+        a, b = _rand_sym_entries(rng, k), _rand_sym_entries(rng, k)
+        assert abs(a @ b - np.trace(C.smat(a) @ C.smat(b))) <= 1e-12 * (1 + abs(a @ b))
+        np.testing.assert_allclose(C.svec(C.smat(a)), a, atol=1e-15)
+    # the layout: (X11, sqrt2 X12, X22, sqrt2 X13, sqrt2 X23, X33)
+    X = np.array([[1.0, 2.0, 4.0], [2.0, 3.0, 5.0], [4.0, 5.0, 6.0]])
+    r2 = np.sqrt(2.0)
+    np.testing.assert_allclose(C.svec(X), [1.0, 2 * r2, 3.0, 4 * r2, 5 * r2, 6.0])
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6])
+def test_psd_moreau_and_optimality(k):
+    rng = np.random.default_rng(300 + k)
+    for _ in range(100):
+        z = _rand_sym_entries(rng, k, rng.uniform(0.1, 5))
+        p = C.proj_psd(z)
+        pol = z - p
+        assert np.linalg.eigvalsh(C.smat(p)).min() >= -1e-12
+        assert np.linalg.eigvalsh(C.smat(-pol)).min() >= -1e-12
+        assert abs(p @ pol) <= 1e-12 * max(1.0, z @ z)
+        np.testing.assert_allclose(p - C.proj_psd(-z), z, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_psd_projection_is_nearest_point(k):
+    """Brute force over sampled PSD matrices: none is closer than Pi(z)."""
+    rng = np.random.default_rng(400 + k)
+    for _ in range(20):
+        z = _rand_sym_entries(rng, k)
+        dist = np.linalg.norm(z - C.proj_psd(z))
+        G = rng.standard_normal((4000, k, k))
+        cand = np.einsum("nij,nkj->nik", G, G) * rng.uniform(0, 2, (4000, 1, 1))
+        dists = [np.linalg.norm(z - C.svec(M)) for M in cand]
+        assert min(dists) >= dist - 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_psd_derivative_fd_symmetry_homogeneity(k):
+    rng = np.random.default_rng(500 + k)
+    for _ in range(20):
+        z = _rand_sym_entries(rng, k)
+        lam = np.linalg.eigvalsh(C.smat(z))
+        if np.min(np.abs(lam)) < 1e-3:
+            continue
+        J = C.dproj_psd(z)
+        h = 1e-6
+        for _ in range(3):
+            v = rng.standard_normal(z.shape[0])
+            fd = (C.proj_psd(z + h * v) - C.proj_psd(z - h * v)) / (2 * h)
+            np.testing.assert_allclose(J @ v, fd, atol=2e-7 * (1 + np.abs(fd).max()))
+        np.testing.assert_allclose(J, J.T, atol=1e-13)
+        np.testing.assert_allclose(J @ z, C.proj_psd(z), atol=1e-12 * (1 + np.abs(z).max()))
+
+
+def test_psd_derivative_special_cases():
+    """Diagonal Z: D maps the (a, b) entry to B_ab times itself, with B the
+    divided differences of max(., 0); a PSD Z gives the identity, a negative
+    definite Z gives 0."""
+    lam = np.array([2.0, -1.0, 0.5])
+    z = C.svec(np.diag(lam))
+    J = C.dproj_psd(z)
+    i = 0
+    for j in range(3):
+        for a in range(j + 1):
+            li, lj = lam[a], lam[j]
+            pa, pj = max(li, 0), max(lj, 0)
+            want = 1.0 if li == lj and li > 0 else (pa - pj) / (li - lj) if li != lj else 0.0
+            assert abs(J[i, i] - want) < 1e-13, (a, j, J[i, i], want)
+            assert np.allclose(np.delete(J[i], i), 0.0, atol=1e-13)
+            i += 1
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((4, 4))
+    np.testing.assert_allclose(C.dproj_psd(C.svec(G @ G.T + 0.1 * np.eye(4))), np.eye(10), atol=1e-12)
+    np.testing.assert_allclose(C.dproj_psd(C.svec(-(G @ G.T + 0.1 * np.eye(4)))), np.zeros((10, 10)), atol=1e-12)

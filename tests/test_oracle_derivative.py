@@ -29,7 +29,11 @@ QPS = [lambda: g.config1(0), lambda: g.config1(1),
        lambda: g.paper_example(0, m=40, n=20)]
 SOCS = [lambda: g.small_qcp(21, 10, 2, 5, (3, 4, 5)),
         lambda: g.small_qcp(22, 16, 0, 6, (3, 3, 6, 8), soc_mix=(0.5, 0.25)),
-        lambda: g.small_qcp(23, 12, 1, 0, (2, 5, 7), soc_mix=(0.34, 0.33))]
+        lambda: g.small_qcp(23, 12, 1, 0, (2, 5, 7), soc_mix=(0.34, 0.33)),
+        # PSD blocks (Appendix A): orders 3 and 2 with s of rank 1 and 0, and
+        # orders 4 and 3 with ranks 2 and 3
+        lambda: g.small_qcp(24, 14, 1, 4, (3,), psd_orders=(3, 2), psd_ranks=(1, 0)),
+        lambda: g.small_qcp(25, 18, 0, 3, (), psd_orders=(4, 3), psd_ranks=(2, 3))]
 
 
 @pytest.mark.parametrize("mk", QPS)
@@ -155,7 +159,7 @@ def test_planted_transposed_operand_is_caught(monkeypatch):
     assert rel_err(D.jvp_dense(p, d)[:3], ref) > 1e-3
 
 
-@pytest.mark.parametrize("mk", QPS[:2] + SOCS)
+@pytest.mark.parametrize("mk", QPS[:2] + SOCS[:3])   # the linearised KKT system covers R+ and SOC blocks
 def test_linearized_kkt_pins_dense_jvp(mk):
     """The dense JVP satisfies the differentiated optimality conditions, and
     a perturbed answer does not (so the check has teeth)."""
