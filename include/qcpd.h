@@ -44,8 +44,14 @@
  *             A's value array; it may be NULL, in which case the plan derives
  *             it from A.
  *  Cones      K is a product of blocks listed in row order: QCP_CONE_ZERO
- *             (the cone {0}), QCP_CONE_NONNEG (R+^d) and QCP_CONE_SOC
- *             (second-order cone, stored (t, u) with t first, Appendix A).
+ *             (the cone {0}), QCP_CONE_NONNEG (R+^d), QCP_CONE_SOC
+ *             (second-order cone, stored (t, u) with t first, Appendix A)
+ *             and QCP_CONE_PSD (positive semidefinite k x k matrices,
+ *             Appendix A: dim = k (k + 1) / 2 entries, the upper triangle
+ *             column by column with the off-diagonal entries times sqrt 2,
+ *             (X11, sqrt2 X12, X22, sqrt2 X13, sqrt2 X23, X33, ...), so the
+ *             layout preserves inner products; k <= 64).  Plans with PSD
+ *             blocks run on the pass and persistent engines.
  *  Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
  *             All work of a plan is enqueued on the stream given at creation.
  *             JVP/VJP calls return when the outputs are written: they
@@ -81,7 +87,7 @@ typedef enum {
 
 typedef enum { QCP_F64 = 0, QCP_F32 = 1 } qcp_dtype;
 
-typedef enum { QCP_CONE_ZERO = 0, QCP_CONE_NONNEG = 1, QCP_CONE_SOC = 2 } qcp_cone_type;
+typedef enum { QCP_CONE_ZERO = 0, QCP_CONE_NONNEG = 1, QCP_CONE_SOC = 2, QCP_CONE_PSD = 3 } qcp_cone_type;
 
 /* CSR matrix; all pointers are device pointers. */
 typedef struct {
@@ -391,8 +397,8 @@ int qcp_plan_scalings(const qcp_plan* plan, double* w, double* c);
 
 /* ---------------------------------------------------------------------------
  * Learned form: a network on per-row features predicts a warm start and a
- * diagonal right preconditioner for the Krylov solve (the paper has no
- * learned part; this follows the problem statement of the build).
+ * diagonal right preconditioner for the Krylov solve (an addition: the
+ * paper has no learned part).
  * ------------------------------------------------------------------------- */
 #define QCP_MLP_IN 16
 #define QCP_MLP_HIDDEN 256
@@ -404,7 +410,9 @@ int qcp_plan_scalings(const qcp_plan* plan, double* w, double* c);
    7 z_i = y_i - s_i; 8 q_i or b_i; 9 g_i = (2Px + q)_i, s_i or kappa; 10 the
    diagonal of D Pi; 11 log(||row of M||) / 4; 12 log(nnz(row of M) + 1) / 4;
    13 SOC block size / 32; 14 1 on an SOC block's entries after its first;
-   15 feature 6 times feature 10 (0 where a feature does not apply). */
+   15 feature 6 times feature 10 (0 where a feature does not apply).
+   QCP_ERR_ARG for plans with PSD blocks (the features cover the zero, R+
+   and SOC blocks). */
 int qcp_plan_features(qcp_plan* plan, float* out);
 
 typedef struct qcp_mlp qcp_mlp;

@@ -64,6 +64,8 @@ static PlanView<T> view(qcp_plan* p, int precond) {
     v.RHS = p->d_RHS.as<double>();
     v.HB = p->d_HB.as<double>();
     v.lsmr = 0;
+    v.psd = p->kpsd ? p->d_psd.as<double>() : nullptr;
+    v.kpsd = p->kpsd;
     v.rmax = p->rmax;
     v.long_chunk = p->long_chunk;
     v.tile0 = 0;
@@ -437,7 +439,7 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
     p->view_precond = opts.precond;
     PlanView<T> v = view<T>(p, opts.precond);
     v.lsmr = opts.solver == 1 ? 1 : 0;
-    const size_t smem = tile_smem_bytes(p->rmax);
+    const size_t smem = tile_smem_bytes(p->rmax, p->kpsd);
     QCP_TRY(set_smem_attrs<T>(smem));
     p->last_launches = 0;
     p->last_engine = engine;
@@ -961,7 +963,7 @@ static int jvp_noalloc(qcp_plan* p, const qcp_options* opts_in, const void* dP, 
     noalloc_layout<T>(p, static_cast<unsigned char*>(base), &v, scaled);
     cudaStream_t st = p->stream;
     const int ntiles = p->tiles_per_sys;
-    const size_t smem = tile_smem_bytes(p->rmax);
+    const size_t smem = tile_smem_bytes(p->rmax, p->kpsd);
     QCP_TRY(set_smem_attrs<T>(smem));
     // the array keeps the previous call's contents: counters, partial sums,
     // the LSQR scalars and the Krylov vectors all start at zero

@@ -88,7 +88,7 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
     }
     for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
         const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-        if (t == QCP_CONE_SOC) {
+        if (t == QCP_CONE_SOC || t == QCP_CONE_PSD) {
             row += d;
             ++nsb;
             ends.push_back(row);
@@ -130,11 +130,13 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
         cp.split[k] = Nx;
         cp.cb[k] = nsb;
     }
+    cp.nb = 0;
+    for (int r = 0; r < C; ++r) cp.nb = std::max(cp.nb, cp.cb[r + 1] - cp.cb[r]);
     for (int r = 0; r < C; ++r) {  // SOC blocks too large for one thread each
         int nl = 0, bi = 0;
         for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
             const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-            if (t == QCP_CONE_SOC) {
+            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD) {
                 if (bi >= cp.cb[r] && bi < cp.cb[r + 1] && d > kSocThread) ++nl;
                 ++bi;
             }
@@ -391,7 +393,7 @@ static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
     QCP_TRY(cluster_smem_limit(&limit));
     std::unique_ptr<ClusterLayout> lay(new ClusterLayout());
     lay->hp.resize(p->nprob);
-    lay->fits = true;
+    lay->fits = p->kpsd == 0;  // the cluster kernels apply D Pi to R+, zero and SOC blocks only
     for (int pi = 0; pi < p->nprob; ++pi) {
         bool ok = false;
         const Prob& pr = p->hprob[pi];
@@ -399,10 +401,14 @@ static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
             // most rows per CTA next to a gather buffer of n + m + C entries
             int lcap = 0;
             const int FN = pr.n + pr.m + C;
-            while (cluster_smem_bytes(FN, lcap + 2) <= limit) lcap += 2;
+            while (cluster_smem_bytes(FN, lcap + 2) + cluster_df_extra_bytes(lcap + 2, 0) <= limit) lcap += 2;
             if (lcap < 1) continue;
-            ok = cluster_split(p, pi, C, lcap, lay->hp[pi]) &&
-                 cluster_smem_bytes(lay->hp[pi].FN, lay->hp[pi].L) <= limit;
+            // the SOC-block tables grow with the blocks a CTA gets: cap the
+            // rows lower until the whole layout fits
+            for (int t = 0; t < 5 && !ok && lcap >= 2; ++t, lcap = lcap * 17 / 20)
+                ok = cluster_split(p, pi, C, lcap, lay->hp[pi]) &&
+                     cluster_smem_bytes(lay->hp[pi].FN, lay->hp[pi].L) +
+                             cluster_df_extra_bytes(lay->hp[pi].L, lay->hp[pi].nb) <= limit;
         }
         if (!ok) lay->fits = false;
     }
@@ -457,21 +463,28 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
     cudaStream_t st = p->stream;
     // per range, its systems grouped by cluster size: one launch per group
     struct Launch {
-        int seg, C, start, count, FN, L;
-        size_t boff;  // offset of the launch's broadcast buffers (df)
+        int seg, C, start, count, FN, L, NB;
+        size_t bytes64, bytesdf;  // dynamic shared memory: the largest problem layout of the launch
+        size_t boff;              // offset of the launch's broadcast buffers (df)
     };
     std::vector<Launch> launches;
     p->h_csys.clear();
     size_t bneed = 0;
     for (int k = 0; k < nseg; ++k) {
         for (int C = 1; C <= kMaxCluster; ++C) {
-            Launch L{k, C, (int)p->h_csys.size(), 0, 0, 0, 0};
+            Launch L{k, C, (int)p->h_csys.size(), 0, 0, 0, 0, 0, 0, 0};
             for (int s = segs[k].s0; s < segs[k].s0 + segs[k].ns; ++s) {
                 const ClusterProb& cp = lay->hp[p->hsys[s].prob];
                 if (cp.C != C) continue;
                 p->h_csys.push_back(s);
                 L.FN = std::max(L.FN, cp.FN);
                 L.L = std::max(L.L, cp.L);
+                L.NB = std::max(L.NB, cp.nb);
+                // each CTA lays out shared memory for its own problem, so
+                // the launch needs the largest single layout
+                const size_t b64 = cluster_smem_bytes(cp.FN, cp.L);
+                L.bytes64 = std::max(L.bytes64, b64);
+                L.bytesdf = std::max(L.bytesdf, b64 + cluster_df_extra_bytes(cp.L, cp.nb));
             }
             L.count = (int)p->h_csys.size() - L.start;
             if (L.count == 0) continue;
@@ -502,7 +515,7 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
     if (!use_df) p->last_engine = QCP_ENGINE_CLUSTER_FP64;
     for (const Launch& L : launches) {
         const int C = L.C;
-        const size_t bytes = cluster_smem_bytes(L.FN, L.L);
+        const size_t bytes = use_df ? L.bytesdf : L.bytes64;
         const int mode = segs[L.seg].mode;
         PlanView<T> vs = v;
         vs.active = p->d_active.as<int>() + segs[L.seg].seg;
@@ -530,7 +543,7 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
         ca.C = C;
         ca.FN = L.FN;
         ca.L = L.L;
-        ca.pad = 0;
+        ca.NB = L.NB;
         ca.max_passes = 2 * (opts.maxiter + 2);
         if (use_df) {
             ClusterDfArgs da;

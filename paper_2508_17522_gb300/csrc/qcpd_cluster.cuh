@@ -52,6 +52,9 @@ constexpr int kSellLong = 256;  // rows longer than this get a warp each
 // base + 32 k + l, for k < width (zero-valued padding past a row's end).
 // row >= 0: a single long row stored lane-strided (entry j at base + j);
 // row < 0: 32 rows, lane l's local row at perm[pidx + l] (-1: none).
+// A slice of the SELL-32 copy of M: 32 lanes x width slots from base (slot
+// base + 32 k + lane).  row >= 0: one long row, lane-strided; row < 0: the
+// 32 rows perm[pidx ..], one per lane.
 struct SellSlice {
     int64_t base;
     int32_t width;
@@ -70,9 +73,9 @@ struct ClusterArgs {
     const void* svalT;
     const int32_t* sys_list;   // the launch's systems, one cluster each
     int C;                     // CTAs per cluster
-    int FN;                    // gather-buffer length of the shared-memory layout
-    int L;                     // per-row buffer length of the layout
-    int pad;
+    int FN;                    // largest gather buffer of the launch's problems
+    int L;                     // most rows of one CTA over the launch's problems
+    int NB;                    // most SOC blocks of one CTA over the launch's problems
     int64_t max_passes;        // termination bound (the scalars stop it earlier)
 };
 
@@ -84,6 +87,14 @@ __host__ __device__ inline int even_up(int x) { return (x + 1) & ~1; }
 __host__ __device__ inline size_t cluster_smem_bytes(int FN, int L) {
     const size_t l2 = (size_t)even_up(L);
     return sizeof(double) * ((size_t)even_up(FN + 1) + 7 * l2 + 8);
+}
+
+// The double-float kernel's tables after the layout above: per row its
+// SOC block (or a row kind), per SOC block its rows and kind, its derivative
+// constants and the block's dot product of the current D Pi application.
+__host__ __device__ inline size_t cluster_df_extra_bytes(int L, int NB) {
+    const size_t rows = 4 * (size_t)even_up(L);
+    return ((rows + 15) & ~(size_t)15) + (size_t)NB * (16 + 32 + 8);
 }
 
 struct CSmem {
@@ -405,7 +416,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster(PlanView<T> a, Cluster
     }
     __syncthreads();
     CCtx<T> c;
-    c.sm = cluster_smem(csm, ca.FN, ca.L);
+    c.sm = cluster_smem(csm, cp.FN, cp.L);  // the problem's own layout (a cluster holds one problem)
     c.cp = &cp;
     c.st = &st;
     c.pd = &pd;

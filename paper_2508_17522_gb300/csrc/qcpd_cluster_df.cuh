@@ -81,64 +81,68 @@ struct CCtxDf {
     int* active;
     double kappa;
     int n, N, R0, L, C, rank, cb0, cb1, sl0, sl1;
+    // this CTA's SOC-block tables (shared memory): per local row its block
+    // (RB_ONE / RB_ZERO off blocks), per block (local start, dim, kase) and
+    // its derivative constants, and the dot products of one D Pi application
+    int* rowblk;
+    int4* bs;
+    SocDf* bsdf;
+    df* dotv;
 };
 
-// D Pi_{K*} in df64 on rows [r0, r1) (same cases as apply_D_tile); zy[] is
-// indexed by row - r0.
-template <int NW>
-__device__ __forceinline__ void apply_D_df(const df* src, df* dst, int r0, int r1, int n, const int8_t* flag,
-                                           const SocBlock* blocks, const SocDf* sdf, int cb0, int cb1,
-                                           const df* zy, bool any_large) {
-    for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
-        if (i < n) {
-            dst[i - r0] = src[i - r0];
-        } else {
-            const int8_t f = flag[i];
-            if (f != RF_SOC) dst[i - r0] = (f == RF_ONE) ? src[i - r0] : df_zero();
-        }
+constexpr int RB_ONE = -1;   // D Pi = 1 on the row (x-rows, zero-cone rows, R+ rows with z > 0)
+constexpr int RB_ZERO = -2;  // D Pi = 0 on the row
+
+// D Pi_{K*} in df64 on this CTA's rows, with the same arithmetic as the
+// block-by-block form: first every SOC block's u^T c (one thread per block,
+// one warp per block of more than kSocThread entries), then every row in
+// parallel.  src and dst are indexed by local row; the CTA synchronises once.
+__device__ __forceinline__ void apply_D_rows_df(const CCtxDf& c, const df* src, df* dst) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nb = c.cb1 - c.cb0;
+    const df* zy = c.ZY;
+    for (int j = tid; j < nb; j += nt) {
+        const int4 B = c.bs[j];
+        if (B.z != 2 || B.y > kSocThread) continue;
+        DfAcc d = dfacc_zero();
+        for (int k = 1; k < B.y; ++k) dfacc_fma(d, zy[B.x + k], src[B.x + k]);
+        c.dotv[j] = dfacc_result(d);
     }
-    for (int bi = cb0 + (int)threadIdx.x; bi < cb1; bi += blockDim.x) {
-        const SocBlock B = blocks[bi];
-        if (B.dim > kSocThread) continue;
-        const df* sb = src + (B.start - r0);
-        df* db = dst + (B.start - r0);
-        if (B.kase == 0) {
-            for (int k = 0; k < B.dim; ++k) db[k] = df_zero();
-        } else if (B.kase == 1) {
-            for (int k = 0; k < B.dim; ++k) db[k] = sb[k];
-        } else {
-            const SocDf S = sdf[bi];
-            const df* u = zy + (B.start - r0);
+    if (c.any_large) {
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int j = warp; j < nb; j += nt >> 5) {
+            const int4 B = c.bs[j];
+            if (B.z != 2 || B.y <= kSocThread) continue;
             DfAcc d = dfacc_zero();
-            for (int k = 1; k < B.dim; ++k) dfacc_fma(d, u[k], sb[k]);
-            const df dot = dfacc_result(d);
-            const df ct = sb[0];
-            db[0] = df_mul(S.h, df_fma(S.r, ct, dot));
-            const df a = df_mul(S.h, df_fma(df_neg(S.tq), dot, ct));
-            for (int k = 1; k < B.dim; ++k) db[k] = df_fma(a, u[k], df_mul(S.htr, sb[k]));
-        }
-    }
-    if (!any_large) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int bi = cb0 + warp; bi < cb1; bi += NW) {
-        const SocBlock B = blocks[bi];
-        if (B.dim <= kSocThread) continue;
-        const df* sb = src + (B.start - r0);
-        df* db = dst + (B.start - r0);
-        if (B.kase == 0) {
-            for (int k = lane; k < B.dim; k += 32) db[k] = df_zero();
-        } else if (B.kase == 1) {
-            for (int k = lane; k < B.dim; k += 32) db[k] = sb[k];
-        } else {
-            const SocDf S = sdf[bi];
-            const df* u = zy + (B.start - r0);
-            DfAcc d = dfacc_zero();
-            for (int k = 1 + lane; k < B.dim; k += 32) dfacc_fma(d, u[k], sb[k]);
+            for (int k = 1 + lane; k < B.y; k += 32) dfacc_fma(d, zy[B.x + k], src[B.x + k]);
             const df dot = warp_sum_df(dfacc_result(d));
-            const df ct = sb[0];
-            if (lane == 0) db[0] = df_mul(S.h, df_fma(S.r, ct, dot));
-            const df a = df_mul(S.h, df_fma(df_neg(S.tq), dot, ct));
-            for (int k = 1 + lane; k < B.dim; k += 32) db[k] = df_fma(a, u[k], df_mul(S.htr, sb[k]));
+            if (lane == 0) c.dotv[j] = dot;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < c.L; i += nt) {
+        const int rb = c.rowblk[i];
+        if (rb == RB_ONE) {
+            dst[i] = src[i];
+        } else if (rb == RB_ZERO) {
+            dst[i] = df_zero();
+        } else {
+            const int4 B = c.bs[rb];
+            if (B.z == 0) {
+                dst[i] = df_zero();
+            } else if (B.z == 1) {
+                dst[i] = src[i];
+            } else {
+                const SocDf S = c.bsdf[rb];
+                const df dot = c.dotv[rb];
+                const df ct = src[B.x];
+                if (i == B.x) {
+                    dst[i] = df_mul(S.h, df_fma(S.r, ct, dot));
+                } else {
+                    const df a = df_mul(S.h, df_fma(df_neg(S.tq), dot, ct));
+                    dst[i] = df_fma(a, zy[i], df_mul(S.htr, src[i]));
+                }
+            }
         }
     }
 }
@@ -413,7 +417,7 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             }
         }
         __syncthreads();
-        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY, c.any_large);
+        apply_D_rows_df(c, s1, s2);
         __syncthreads();
         for (int i = tid; i < L; i += kCThreads) {
             const int r = R0 + i;
@@ -428,7 +432,7 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             else c.X[r] = df_fma(xc, c.W[r], c.X[r]);
         }
         __syncthreads();
-        apply_D_df<kCWarps>(s1, s2, R0, R0 + L, n, c.flag, c.blocks, c.soc, c.cb0, c.cb1, c.ZY, c.any_large);
+        apply_D_rows_df(c, s1, s2);
         __syncthreads();
         for (int i = tid; i < L; i += kCThreads) {
             XIs[i] = s2[i];
@@ -505,7 +509,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
     const double su = s_uscaled ? sc : 1.0;
     CCtxDf c;
     {
-        const CSmem m = cluster_smem(csm, ca.FN, ca.L);
+        const CSmem m = cluster_smem(csm, cp.FN, cp.L);  // the problem's own layout
         c.F = reinterpret_cast<df*>(m.F);
         c.U = reinterpret_cast<df*>(m.U);
         c.V = reinterpret_cast<df*>(m.V);
@@ -552,6 +556,14 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
     c.cb1 = cp.cb[rank + 1];
     c.sl0 = cp.sl[rank];
     c.sl1 = cp.sl[rank + 1];
+    {
+        unsigned char* t = reinterpret_cast<unsigned char*>(csm) + cluster_smem_bytes(cp.FN, cp.L);
+        const size_t rows = ((4 * (size_t)even_up(cp.L)) + 15) & ~(size_t)15;
+        c.rowblk = reinterpret_cast<int*>(t);
+        c.bs = reinterpret_cast<int4*>(t + rows);
+        c.bsdf = reinterpret_cast<SocDf*>(t + rows + 16 * (size_t)cp.nb);
+        c.dotv = reinterpret_cast<df*>(t + rows + 48 * (size_t)cp.nb);
+    }
 
     const bool live = st.status != S_DONE;
     if (live) {
@@ -566,6 +578,18 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
             const double w = gW[r], x = gX[r] * sc;
             c.W[r] = df_from(w);
             c.X[r] = df_from(x);
+            const int8_t f = c.flag[r];
+            c.rowblk[i] = (r < c.n || f == RF_ONE) ? RB_ONE : (f == RF_SOC ? 0 : RB_ZERO);
+        }
+        for (int j = tid; j < c.cb1 - c.cb0; j += kCThreads) {
+            const SocBlock B = c.blocks[c.cb0 + j];
+            c.bs[j] = make_int4(B.start - c.R0, B.dim, B.kase, 0);
+            c.bsdf[j] = c.soc[c.cb0 + j];
+        }
+        __syncthreads();
+        for (int j = tid; j < c.cb1 - c.cb0; j += kCThreads) {  // the rows of each block (inside this CTA's rows)
+            const int4 B = c.bs[j];
+            for (int k = 0; k < B.y; ++k) c.rowblk[B.x + k] = j;
         }
         // the first u-update gathers xi (JVP) or v (VJP); slot FN stays 0 for padding
         const double* g0 = (MODE == 0) ? gXI : gV;

@@ -87,14 +87,21 @@ struct Sys {
     int64_t po, ao;  // offsets into P-value / A-value user arrays
 };
 
+// A block of rows that D Pi couples: a second-order cone (kase 0..2) or a
+// positive semidefinite cone (kase 3).
 struct SocBlock {
-    int32_t start;   // local embedding row of the block's t entry (n + first y row)
+    int32_t start;   // local embedding row of the block's first entry (n + first y row)
     int32_t dim;
-    int32_t kase;    // 0: ||u|| <= -t (D = 0), 1: ||u|| <= t (D = I), 2: formula
-    int32_t pad;
-    double t, r;     // t and ||u|| of z_y on the block
-    double h, tq;    // 1 / (2 r) and t / r^2 (kase 2), so no kernel divides
+    int32_t kase;    // SOC: 0 ||u|| <= -t (D = 0), 1 ||u|| <= t (D = I), 2 formula; 3: PSD block
+    int32_t order;   // PSD: the matrix order k (dim = k (k + 1) / 2); SOC: 0
+    double t, r;     // SOC: t and ||u|| of z_y on the block
+    double h, tq;    // SOC: 1 / (2 r) and t / r^2 (kase 2), so no kernel divides
+    int64_t psd;     // PSD: offset of its k x k eigenvectors V and weights B in the plan's PSD array
+    int64_t pad;
 };
+
+constexpr int kPsdMaxOrder = 64;  // largest PSD block order (its scratch is 2 k^2 doubles of shared memory)
+constexpr int kBlockPsd = 3;      // SocBlock::kase of a PSD block
 
 // LSQR scalars of one system (Paige & Saunders' recurrences).
 struct LsqrState {
@@ -132,7 +139,7 @@ struct ClusterProb {
     int32_t C;                        // CTAs per system
     int32_t FN;                       // gather-buffer length (poff[C])
     int32_t L;                        // most rows of one CTA
-    int32_t pad;
+    int32_t nb;                       // most SOC blocks of one CTA
     int32_t split[kMaxCluster + 1];
     int32_t poff[kMaxCluster + 1];
     int32_t cb[kMaxCluster + 1];      // CTA r's SOC blocks [cb[r], cb[r+1]) (problem-relative)
@@ -344,10 +351,74 @@ __device__ __forceinline__ bool finish_tile(const Reduce& R, const Tile& tl, int
 // before and after.
 constexpr int kSocThread = 32;
 
+// Row a <= column j of a PSD block's entry i (the upper triangle column by
+// column: i = j (j + 1) / 2 + a).
+__device__ __forceinline__ void psd_pos(int i, int& a, int& j) {
+    j = (int)((sqrt(8.0 * i + 1.0) - 1.0) * 0.5);
+    while ((j + 1) * (j + 2) / 2 <= i) ++j;
+    while (j * (j + 1) / 2 > i) --j;
+    a = i - j * (j + 1) / 2;
+}
+
+// D Pi_psd on every PSD block of [cb0, cb1) (Appendix A):
+//   dZ -> V (B o (V^T dZ V)) V^T
+// with Z's eigenvectors V (column q = eigenvector q) and the weights B made
+// at plan time.  All threads of the CTA call it (it synchronises); the
+// scratch holds 2 k^2 doubles.
+static __device__ __noinline__ void apply_D_psd(const double* src, double* dst, int r0, const SocBlock* blocks, int cb0,
+                                         int cb1, const double* psd, double* Y) {
+    constexpr double kR2 = 1.4142135623730951, kIR2 = 0.7071067811865476;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int bi = cb0; bi < cb1; ++bi) {
+        const SocBlock B = blocks[bi];
+        if (B.kase != kBlockPsd) continue;
+        const int k = B.order, kk = k * k, d = B.dim;
+        const double* V = psd + B.psd;
+        const double* W = V + kk;
+        const double* sb = src + (B.start - r0);
+        double* db = dst + (B.start - r0);
+        double* T = Y + kk;
+        for (int e = tid; e < kk; e += nt) {  // Y = dZ V
+            const int a = e / k, q = e - a * k;
+            double acc = 0.0;
+            for (int c = 0; c < k; ++c) {
+                const int lo = a < c ? a : c, hi = a < c ? c : a;
+                const double z = sb[hi * (hi + 1) / 2 + lo] * (a == c ? 1.0 : kIR2);
+                acc = fma(z, V[c * k + q], acc);
+            }
+            Y[e] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < kk; e += nt) {  // T = B o (V^T Y)
+            const int p = e / k, q = e - p * k;
+            double acc = 0.0;
+            for (int a = 0; a < k; ++a) acc = fma(V[a * k + p], Y[a * k + q], acc);
+            T[e] = W[e] * acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < kk; e += nt) {  // Y = V T
+            const int a = e / k, q = e - a * k;
+            double acc = 0.0;
+            for (int p = 0; p < k; ++p) acc = fma(V[a * k + p], T[p * k + q], acc);
+            Y[e] = acc;
+        }
+        __syncthreads();
+        for (int i = tid; i < d; i += nt) {   // the upper triangle of Y V^T
+            int a, j;
+            psd_pos(i, a, j);
+            double acc = 0.0;
+            for (int q = 0; q < k; ++q) acc = fma(Y[a * k + q], V[j * k + q], acc);
+            db[i] = a == j ? acc : kR2 * acc;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, int NW = kWarps>
 __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int r0, int r1, int n,
                                              const int8_t* flag, const SocBlock* blocks, int cb0,
-                                             int cb1, const T* zy, int zoff = 0, bool any_large = true) {
+                                             int cb1, const T* zy, int zoff = 0, bool any_large = true,
+                                             const double* psd = nullptr, double* pscr = nullptr) {
     for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
         if (i < n) {
             dst[i - r0] = src[i - r0];
@@ -359,7 +430,7 @@ __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int
     // small blocks: one thread each
     for (int bi = cb0 + (int)threadIdx.x; bi < cb1; bi += blockDim.x) {
         const SocBlock B = blocks[bi];
-        if (B.dim > kSocThread) continue;
+        if (B.dim > kSocThread || B.kase == kBlockPsd) continue;
         const double* sb = src + (B.start - r0);
         double* db = dst + (B.start - r0);
         if (B.kase == 0) {
@@ -382,12 +453,14 @@ __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int
             for (int k = 1; k < B.dim; ++k) db[k] = fma(a, ld(u + k), b * sb[k]);
         }
     }
+    // PSD blocks: the whole CTA, one block after the other
+    if (psd) apply_D_psd(src, dst, r0, blocks, cb0, cb1, psd, pscr);
     // large blocks: one warp each
     if (!any_large) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int bi = cb0 + warp; bi < cb1; bi += NW) {
         const SocBlock B = blocks[bi];
-        if (B.dim <= kSocThread) continue;
+        if (B.dim <= kSocThread || B.kase == kBlockPsd) continue;
         const double* sb = src + (B.start - r0);
         double* db = dst + (B.start - r0);
         if (B.kase == 0) {

@@ -55,6 +55,8 @@ struct PlanView {
     double* RHS;             // right-hand side b of min ||Op x - b||
     double* HB;              // LSMR hbar (W holds h)
     int lsmr;                // 0: LSQR, 1: LSMR (pass and persistent engines)
+    const double* psd;       // PSD blocks' eigenvectors and weights (nullptr: the plan has none)
+    int kpsd;                // largest PSD block order (0: none)
     int rmax;                // most rows in any tile (shared-memory sizing)
     int long_chunk;          // nonzeros per LONG tile
     int tile0;               // tile of blockIdx.x 0 in a tile launch (a range of the plan's systems)
@@ -63,13 +65,16 @@ struct PlanView {
 // Dynamic shared memory of the tile kernels:
 //   s0, s1, s2 rmax doubles each: per-row buffers (row sums, epilogue)
 //   srp        rmax + 1 int64: the tile's row pointers
+//   psd        2 kpsd^2 doubles: scratch of the PSD blocks' D Pi (kpsd = 0: none)
 struct TileSmem {
     double *s0, *s1, *s2;
     int64_t* srp;
+    double* psd;
 };
 
-__host__ __device__ inline size_t tile_smem_bytes(int rmax) {
-    return sizeof(double) * (size_t)(3 * rmax) + sizeof(int64_t) * (size_t)(rmax + 1);
+__host__ __device__ inline size_t tile_smem_bytes(int rmax, int kpsd = 0) {
+    return sizeof(double) * (size_t)(3 * rmax) + sizeof(int64_t) * (size_t)(rmax + 1) +
+           sizeof(double) * 2 * (size_t)kpsd * (size_t)kpsd;
 }
 
 __device__ __forceinline__ TileSmem tile_smem(double* base, int rmax) {
@@ -78,6 +83,7 @@ __device__ __forceinline__ TileSmem tile_smem(double* base, int rmax) {
     t.s1 = t.s0 + rmax;
     t.s2 = t.s1 + rmax;
     t.srp = reinterpret_cast<int64_t*>(t.s2 + rmax);
+    t.psd = reinterpret_cast<double*>(t.srp + rmax + 1);
     return t;
 }
 
@@ -637,7 +643,7 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
             __syncthreads();
             const int cb0 = tl.kind == TILE_STREAM ? tl.cb0 : 0, cb1 = tl.kind == TILE_STREAM ? tl.cb1 : 0;
             apply_D_tile<double>(s1, s2, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1,
-                            a.zy + pr.doff);
+                                 a.zy + pr.doff, 0, true, a.psd, sm.psd);
             __syncthreads();
             for (int i = threadIdx.x; i < rows; i += kThreads) {
                 const int r = tl.r0 + i;
@@ -669,7 +675,7 @@ __device__ __forceinline__ void run_tile(const PlanView<T>& a, const int ti, dou
             if (ROLE != ROLE_RES) {
                 __syncthreads();
                 apply_D_tile<double>(s1, s2, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1,
-                                a.zy + pr.doff);
+                                     a.zy + pr.doff, 0, true, a.psd, sm.psd);
                 __syncthreads();
                 for (int i = threadIdx.x; i < rows; i += kThreads) XI[tl.r0 + i] = s2[i];
             }
@@ -882,7 +888,7 @@ __global__ void __launch_bounds__(kThreads) k_dpi(PlanView<T> a, const double* s
     __syncthreads();
     const int cb0 = tl.kind == TILE_STREAM ? tl.cb0 : 0, cb1 = tl.kind == TILE_STREAM ? tl.cb1 : 0;
     apply_D_tile<double>(sm.s1, sm.s2, tl.r0, tl.r0 + rows, pr.n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1,
-                         a.zy + pr.doff);
+                         a.zy + pr.doff, 0, true, a.psd, sm.psd);
     __syncthreads();
     for (int i = threadIdx.x; i < rows; i += kThreads) a.XI[sy.voff + tl.r0 + i] = sm.s2[i];
 }
@@ -1084,7 +1090,8 @@ __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> 
         }
     }
     __syncthreads();
-    apply_D_tile<double>(s0, s1, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy);
+    apply_D_tile<double>(s0, s1, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy, 0,
+                         true, a.psd, sm.psd);
     __syncthreads();
     double ss = 0.0, sst = 0.0;
     for (int i = threadIdx.x; i < rows; i += kThreads) {
@@ -1103,7 +1110,8 @@ __global__ void __launch_bounds__(kThreads) k_vjp_rhs(PlanView<T> a, RhsArgs<T> 
         ss += bval * bval;
     }
     __syncthreads();
-    apply_D_tile<double>(s0, s2, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy);
+    apply_D_tile<double>(s0, s2, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy, 0,
+                         true, a.psd, sm.psd);
     __syncthreads();
     for (int i = threadIdx.x; i < rows; i += kThreads) XI[tl.r0 + i] = s2[i];
     const Part part = block_sum_part(Part{ss, dtop, dbot, sst}, &scratch);
@@ -1162,7 +1170,8 @@ __global__ void __launch_bounds__(kThreads) k_jvp_out(PlanView<T> a, OutArgs<T> 
         s2[i] = sc ? X[r] * cd[r] : X[r];  // dz = C x
     }
     __syncthreads();
-    apply_D_tile<double>(s0, s1, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy);
+    apply_D_tile<double>(s0, s1, tl.r0, tl.r0 + rows, n, a.flag + pr.doff, a.blocks + pr.soff, cb0, cb1, zy, 0,
+                         true, a.psd, sm.psd);
     __syncthreads();
     for (int i = threadIdx.x; i < rows; i += kThreads) {
         const int r = tl.r0 + i;

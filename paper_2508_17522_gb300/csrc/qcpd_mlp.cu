@@ -573,6 +573,10 @@ int qcp_plan_features(qcp_plan* p, float* out) {
         set_error("qcp_plan_features: null argument");
         return QCP_ERR_ARG;
     }
+    if (p->kpsd) {
+        set_error("qcp_plan_features: the features cover zero, R+ and SOC blocks; this plan has PSD blocks");
+        return QCP_ERR_ARG;
+    }
     cudaStream_t st = p->stream;
     const int64_t Nt = p->N_tot;
     // host tables: row kind, M row, problem, SOC size and position

@@ -242,6 +242,7 @@ __global__ void k_socprep(SocBlock* blk, int64_t nb, const double* zy) {
     const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     SocBlock B = blk[b];
+    if (B.kase == kBlockPsd) return;
     double ss = 0.0;
     for (int k = 1 + lane; k < B.dim; k += 32) {
         const double u = (double)zy[B.start + k];
@@ -270,7 +271,81 @@ __global__ void k_kink(const double* zy, const int8_t* ctype, int32_t n, int32_t
                        unsigned long long* slot) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < m && ctype[i] == QCP_CONE_NONNEG) atomic_min_nonneg(slot, fabs((double)zy[n + i]));
-    if (i < nb) atomic_min_nonneg(slot, fabs(blk[i].r - fabs(blk[i].t)));
+    if (i < nb && blk[i].kase != kBlockPsd) atomic_min_nonneg(slot, fabs(blk[i].r - fabs(blk[i].t)));
+}
+
+// Per PSD block (one thread each): the eigendecomposition Z = V diag(lam) V^T
+// of its z_y entries by the cyclic Jacobi method (rotations that zero one
+// off-diagonal entry at a time, sweeps until the off-diagonal mass is below
+// 1e-30 of the total or 60 sweeps), then the weights of D Pi (Appendix A):
+// B_pq = 1 when lam_p, lam_q > 0, 0 when neither is, lam_p / (lam_p - lam_q)
+// when only lam_p is.  V (column q = eigenvector q) and B go to the block's
+// slot of the PSD array; the B half serves as the matrix during the sweeps.
+// The kink margin is the smallest |lam|.
+__global__ void k_psdprep(SocBlock* blk, int64_t nb, const double* zy, double* psd, unsigned long long* kink) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb || blk[b].kase != kBlockPsd) return;
+    const SocBlock Bk = blk[b];
+    const int k = Bk.order;
+    double* V = psd + Bk.psd;
+    double* A = V + k * k;
+    const double* z = zy + Bk.start;
+    for (int j = 0; j < k; ++j)
+        for (int a = 0; a <= j; ++a) {
+            const double v = z[j * (j + 1) / 2 + a] * (a == j ? 1.0 : 0.7071067811865476);
+            A[a * k + j] = A[j * k + a] = v;
+        }
+    for (int i = 0; i < k * k; ++i) V[i] = 0.0;
+    for (int i = 0; i < k; ++i) V[i * k + i] = 1.0;
+    double total = 0.0;
+    for (int i = 0; i < k * k; ++i) total += A[i] * A[i];
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) off += 2.0 * A[p * k + q] * A[p * k + q];
+        if (!(off > 1e-30 * total)) break;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                const double apq = A[p * k + q];
+                if (apq == 0.0) continue;
+                // the rotation (c, s) with tan(2 theta) = 2 a_pq / (a_qq - a_pp)
+                const double th = (A[q * k + q] - A[p * k + p]) / (2.0 * apq);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int r = 0; r < k; ++r) {  // columns p, q
+                    const double arp = A[r * k + p], arq = A[r * k + q];
+                    A[r * k + p] = c * arp - sn * arq;
+                    A[r * k + q] = sn * arp + c * arq;
+                }
+                for (int r = 0; r < k; ++r) {  // rows p, q
+                    const double apr = A[p * k + r], aqr = A[q * k + r];
+                    A[p * k + r] = c * apr - sn * aqr;
+                    A[q * k + r] = sn * apr + c * aqr;
+                }
+                for (int r = 0; r < k; ++r) {
+                    const double vrp = V[r * k + p], vrq = V[r * k + q];
+                    V[r * k + p] = c * vrp - sn * vrq;
+                    V[r * k + q] = sn * vrp + c * vrq;
+                }
+            }
+    }
+    double lam[kPsdMaxOrder];
+    double margin = INFINITY;
+    for (int i = 0; i < k; ++i) {
+        lam[i] = A[i * k + i];
+        margin = fmin(margin, fabs(lam[i]));
+    }
+    for (int p = 0; p < k; ++p)
+        for (int q = 0; q < k; ++q) {
+            const bool pp = lam[p] > 0.0, pq = lam[q] > 0.0;
+            double w;
+            if (pp && pq) w = 1.0;
+            else if (!pp && !pq) w = 0.0;
+            else if (pp) w = lam[p] / (lam[p] - lam[q]);
+            else w = lam[q] / (lam[q] - lam[p]);
+            A[p * k + q] = w;
+        }
+    atomic_min_nonneg(kink, margin);
 }
 
 // g = 2 P x + q and kappa = x^T P x (Sec. 2.4: the last row of D_u Q at
@@ -329,6 +404,7 @@ __global__ void k_dd_soc(const SocBlock* blk, int64_t nb, const double* zy, doub
     const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     const SocBlock B = blk[b];
+    if (B.kase == kBlockPsd) return;
     for (int k = lane; k < B.dim; k += 32) {
         double v;
         if (B.kase == 0) v = 0.0;
@@ -339,6 +415,33 @@ __global__ void k_dd_soc(const SocBlock* blk, int64_t nb, const double* zy, doub
             v = ((B.t + B.r) - (B.t / (B.r * B.r)) * u * u) / (2.0 * B.r);
         }
         dd[B.start + k] = v;
+    }
+}
+
+// Diagonal of D Pi_psd per entry i of a PSD block: with E the symmetric
+// matrix of unit entry i and T = V^T E V, D_ii = sum_pq B_pq T_pq^2.  One
+// warp per block.
+__global__ void k_dd_psd(const SocBlock* blk, int64_t nb, const double* psd, double* dd) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (b >= nb) return;
+    const SocBlock B = blk[b];
+    if (B.kase != kBlockPsd) return;
+    const int k = B.order;
+    const double* V = psd + B.psd;
+    const double* W = V + k * k;
+    for (int i = lane; i < B.dim; i += 32) {
+        int a, j;
+        psd_pos(i, a, j);
+        const double sc = a == j ? 1.0 : 0.7071067811865476;
+        double acc = 0.0;
+        for (int p = 0; p < k; ++p)
+            for (int q = 0; q < k; ++q) {
+                const double t = a == j ? V[a * k + p] * V[a * k + q]
+                                        : sc * (V[a * k + p] * V[j * k + q] + V[j * k + p] * V[a * k + q]);
+                acc += W[p * k + q] * t * t;
+            }
+        dd[B.start + i] = acc;
     }
 }
 
@@ -522,7 +625,7 @@ static void cut_tiles(const qcp_plan* p, int pi, std::vector<Tile>& out, int& rm
     int sb = 0;
     for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
         const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-        if (t != QCP_CONE_SOC) {
+        if (t != QCP_CONE_SOC && t != QCP_CONE_PSD) {  // SOC and PSD blocks stay in one tile
             for (int r = row; r < row + d; ++r) single_row(r);
         } else {
             const int64_t nz = rp[row + d] - rp[row];
@@ -737,6 +840,9 @@ static int run_equilibrate(qcp_plan* p) {
         if (pr.nsoc)
             k_dd_soc<T><<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_zy.as<double>() + pr.doff, dd.as<double>() + pr.doff);
+        if (pr.nsoc && p->kpsd)
+            k_dd_psd<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
+                p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_psd.as<double>(), dd.as<double>() + pr.doff);
     }
     QCP_CUDA(cudaGetLastError());
     if (nt) {
@@ -796,6 +902,9 @@ static int jacobi_cols_t(qcp_plan* p, double* out) {
         if (pr.nsoc)
             k_dd_soc<T><<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_zy.as<double>() + pr.doff, dd.as<double>() + pr.doff);
+        if (pr.nsoc && p->kpsd)
+            k_dd_psd<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
+                p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_psd.as<double>(), dd.as<double>() + pr.doff);
     }
     if (nt)
         k_prec_cols<T><<<nt, kThreads, 0, st>>>(p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R,
@@ -831,7 +940,7 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
     p->cone_type.resize(np);
     p->cone_dim.resize(np);
     int64_t mrow = 0, soff = 0, prow = 0, arow = 0, poff = 0, aoff = 0;
-    int64_t max_pnz = 0, max_anz = 0, max_n = 0;
+    int64_t max_pnz = 0, max_anz = 0, max_n = 0, psd_off = 0;
     std::vector<int8_t> hctype;
     std::vector<SocBlock> hblocks;
     for (int i = 0; i < np; ++i) {
@@ -867,14 +976,30 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
         pr.m = (int)q.m;
         for (int b = 0; b < q.K.nblocks; ++b) {
             const int t = q.K.type[b], d = q.K.dim[b];
-            if ((t != QCP_CONE_ZERO && t != QCP_CONE_NONNEG && t != QCP_CONE_SOC) || d < 1) {
+            if ((t != QCP_CONE_ZERO && t != QCP_CONE_NONNEG && t != QCP_CONE_SOC && t != QCP_CONE_PSD) || d < 1) {
                 set_error("problem %d: cone block %d has type %d dim %d", i, b, t, d);
                 return QCP_ERR_ARG;
             }
-            if (t == QCP_CONE_SOC) {
+            int order = 0;
+            if (t == QCP_CONE_PSD) {
+                while ((order + 1) * (order + 2) / 2 <= d) ++order;
+                if (order * (order + 1) / 2 != d || order > kPsdMaxOrder) {
+                    set_error("problem %d: PSD block %d has %d entries: need k (k + 1) / 2 with k <= %d", i, b, d,
+                              kPsdMaxOrder);
+                    return QCP_ERR_ARG;
+                }
+            }
+            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD) {
                 SocBlock sb{};
                 sb.start = (int)(q.n + msum);
                 sb.dim = d;
+                if (t == QCP_CONE_PSD) {
+                    sb.kase = kBlockPsd;
+                    sb.order = order;
+                    sb.psd = psd_off;
+                    psd_off += 2 * (int64_t)order * order;
+                    p->kpsd = std::max(p->kpsd, order);
+                }
                 hblocks.push_back(sb);
                 ++nsoc;
             }
@@ -924,6 +1049,7 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
     QCP_TRY(p->d_zy.alloc(p->N_tot * sizeof(double)));
     QCP_TRY(p->d_flag.alloc(p->N_tot));
     QCP_TRY(p->d_blocks.alloc(std::max<int64_t>(1, soff) * sizeof(SocBlock)));
+    QCP_TRY(p->d_psd.alloc(std::max<int64_t>(1, psd_off) * sizeof(double)));
     QCP_TRY(p->d_pip.alloc(prow * sizeof(int64_t)));
     QCP_TRY(p->d_pix.alloc(std::max<int64_t>(1, poff) * sizeof(int32_t)));
     QCP_TRY(p->d_aip.alloc(arow * sizeof(int64_t)));
@@ -1098,6 +1224,10 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
         if (pr.nsoc)
             k_socprep<T><<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_zy.as<double>() + pr.doff);
+        if (pr.nsoc && p->kpsd)
+            k_psdprep<<<grid_for(pr.nsoc, 64), 64, 0, st>>>(p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc,
+                                                           p->d_zy.as<double>() + pr.doff, p->d_psd.as<double>(),
+                                                           d_kink.as<unsigned long long>() + i);
     }
     QCP_CUDA(cudaGetLastError());
     ctoff = 0;
