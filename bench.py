@@ -46,6 +46,10 @@ def log(*a):
 # --------------------------------------------------------------------------- workloads
 def workload(name, rank):
     import qcpgen as g
+    if name == "config1":
+        prob = g.config1(seed=rank)
+        dirs = g.make_directions_batch(prob, 5 + 1000 * rank, 2)
+        return prob, dirs, 1e-10, "tiny QP n=50 m=80 {0}^20 x R+^60, 2 JVP + 2 VJP directions"
     if name == "config2":
         prob = g.config2(seed=rank)
         dirs = g.make_directions_batch(prob, 5 + 1000 * rank, 16)
@@ -183,6 +187,23 @@ def oracle_sample(prob, dirs, budget_s=30.0):
                        f"{dt:.1f} s; numpy/scipy FP64 with the BLAS threads of all {os.cpu_count()} cores")}
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks (the job
+    takes as long as its slowest rank); identity without a process group."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(solves_per_rank_step, world, steps, max_ms):
+    """Solves per second of the whole job: every rank's solves over the
+    slowest rank's time (replicas: each rank solves its own directions)."""
+    return solves_per_rank_step * world * steps / (max_ms / 1e3)
+
+
 # --------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -191,7 +212,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
-    ap.add_argument("--workload", default="config2", choices=["config2", "config3", "example"])
+    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "example"])
     ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
     ap.add_argument("--maxiter", type=int, default=400000,
                     help="Krylov iteration cap (lower it only for profiling runs: solves then stop early)")
@@ -210,7 +231,7 @@ def main():
         if rank != 0:
             return
         prob, dirs, rtol, desc = workload(args.workload, 0)
-        if args.workload not in ("config2", "example"):
+        if args.workload not in ("config1", "config2", "example"):
             raise SystemExit("the oracle reference arm covers the dense-LU workloads (config2, example)")
         for _ in range(args.warmup):
             oracle_step(prob, dirs)
@@ -342,13 +363,9 @@ def main():
         e2e_ms += e0.elapsed_time(e1)
 
     # ---- max over ranks
-    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(t[0]), float(t[1])
-    solves_per_step = 2 * k * world
-    value = solves_per_step * args.steps / (total_ms / 1e3)
-    e2e = solves_per_step * args.steps / (e2e_ms / 1e3)
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dist, dev)
+    value = whole_job_rate(2 * k, world, args.steps, total_ms)
+    e2e = whole_job_rate(2 * k, world, args.steps, e2e_ms)
 
     peaks = {}
     try:
