@@ -11,7 +11,8 @@ namespace qcpd {
 // Weight of one row against one stored entry when balancing CTAs: the
 // epilogue spends about eight FP64 operations per row, the row sums one per
 // stored entry.
-constexpr double kRowWeight = 8.0;
+constexpr double kRowWeight = 8.0;      // per row, next to its stored entries
+constexpr double kSocRowWeight = 10.0;  // more per row of an SOC block (its D Pi rows cost more in the epilogue)
 
 // Slot -> (gather-buffer column, values) of the SELL-32 copy: column j of M
 // lives at poff[r] + j - split[r] of the gather buffer, r the CTA owning row
@@ -78,31 +79,36 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
     const int n = pr.n, Nx = pr.n + pr.m;
     const int64_t* rp = p->h_mrowptr.data() + pr.mrow;
     // cut candidates: the end of every row outside SOC blocks and of every SOC block
-    std::vector<int> ends, socs;
+    std::vector<int> ends, socs, brows;  // brows: rows of coupled blocks up to each end
     ends.reserve(Nx);
     socs.reserve(Nx);
-    int row = 0, nsb = 0;
+    brows.reserve(Nx);
+    int row = 0, nsb = 0, nbr = 0;
     for (; row < n; ++row) {
         ends.push_back(row + 1);
         socs.push_back(0);
+        brows.push_back(0);
     }
     for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
         const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
         if (t == QCP_CONE_SOC || t == QCP_CONE_PSD) {
             row += d;
+            nbr += d;
             ++nsb;
             ends.push_back(row);
             socs.push_back(nsb);
+            brows.push_back(nbr);
         } else {
             for (int k = 0; k < d; ++k) {
                 ends.push_back(++row);
                 socs.push_back(nsb);
+                brows.push_back(nbr);
             }
         }
     }
     std::memset(&cp, 0, sizeof(cp));
     cp.C = C;
-    const double total = (double)(rp[Nx] - rp[0]) + kRowWeight * Nx;
+    const double total = (double)(rp[Nx] - rp[0]) + kRowWeight * Nx + kSocRowWeight * nbr;
     // a range closed by the row cap holds at least lcap - umax + 1 rows
     // (umax: the largest unit, an SOC block or one row)
     int umax = 1;
@@ -117,7 +123,7 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
         // many light ones: the weight alone would give the light ones a
         // single range)
         const int next = (u + 1 < ends.size()) ? ends[u + 1] : e;
-        const double acc = (double)(rp[e] - rp[0]) + kRowWeight * e;
+        const double acc = (double)(rp[e] - rp[0]) + kRowWeight * e + kSocRowWeight * brows[u];
         while (k < C && ((acc >= total * k / C && (int64_t)(Nx - e) <= (int64_t)(C - k) * room) ||
                          next - start > lcap)) {
             cp.split[k] = e;
