@@ -187,6 +187,74 @@ def oracle_sample(prob, dirs, budget_s=30.0):
                        f"{dt:.1f} s; numpy/scipy FP64 with the BLAS threads of all {os.cpu_count()} cores")}
 
 
+# --------------------------------------------------------------------------- learned form
+def learned_bench(args, rank, local):
+    """The learned preconditioner's family (the parametric family with a fixed
+    pattern, shrunk to n = 500, m = 801): train on the method's own solves of
+    40 instances (untimed), then time, on 8 held-out instances, the adjoint
+    solve of ||x*||^2 to rtol 1e-6 (a) plain (zero start, no scaling) and
+    (b) learned (network features + forward + decode, warm start and
+    diagonal preconditioner), both on the pass engine.  value = learned
+    solves/s; the plain rate and the mean iterations ride along."""
+    import torch
+    import qcpgen as g
+    import paper_2508_17522_gb300 as q
+    from paper_2508_17522_gb300 import learned as L
+    from paper_2508_17522_gb300.buildlib import build
+    build()
+    dev = torch.device("cuda", local)
+    fam = g.config5_family(2 + 1000 * rank, scale=0.1)
+    train = [fam.instance(j) for j in range(40)]
+    held = [fam.instance(1000 + j) for j in range(8)]
+    lp = L.LearnedPreconditioner(seed=3, device=dev).fit(train, steps=800, lr=1e-3)
+    plans = [q.qcp_plan_create(q.problem_tensors(pr, dev), torch.float64) for pr in held]
+    dirs = [L.adjoint_direction(pr) for pr in held]
+    plain = q.options(rtol=1e-6, engine="passes")
+
+    def run(kind):
+        its, stat = [], set()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record()
+        for pl, pr, (wx, wy, ws) in zip(plans, held, dirs):
+            if kind == "plain":
+                *_, info = q.qcp_derivative_vjp(pl, wx, wy, ws, plain)
+            else:
+                *_, info = lp.vjp(pl, pr, rtol=1e-6)
+            its.append(info[0]["iters"])
+            stat.add(info[0]["status"])
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1), its, stat
+
+    for _ in range(max(args.warmup, 1)):
+        run("plain")
+        run("learned")
+    tp = tl = 0.0
+    ip, il, st = [], [], set()
+    for _ in range(args.steps):
+        t, i, s_ = run("plain")
+        tp, ip, st = tp + t, ip + i, st | s_
+        t, i, s_ = run("learned")
+        tl, il, st = tl + t, il + i, st | s_
+    n = len(held) * args.steps
+    val, vplain = n / (tl / 1e3), n / (tp / 1e3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "VJP solves/sec at 1e-6 rel residual, learned vs plain", "value": val, "unit": "solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tl / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "learned-preconditioner family shrunk to n=500 m=801 (1 zero row, R+ blocks, "
+                                   "one SOC of 20% of the rows, dense P); 40 training and 8 held-out instances; "
+                                   "VJP of ||x*||^2 at rtol 1e-6; pass engine",
+                       "plain_solves_per_s": vplain, "speedup_vs_plain": val / vplain,
+                       "mean_iters_learned": float(np.mean(il)), "mean_iters_plain": float(np.mean(ip)),
+                       "alpha": lp.alpha, "status": sorted(st)},
+            "gpu_launches": None, "e2e": None, "roofline": None, "cpu_baseline": None}), flush=True)
+    for pl in plans:
+        pl.close()
+
+
 # --------------------------------------------------------------------------- ranks
 def max_over_ranks(values, dist, device):
     """Element-wise maximum of per-rank timings over all ranks (the job
@@ -212,7 +280,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
-    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "example"])
+    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "example", "learned"])
     ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
     ap.add_argument("--maxiter", type=int, default=400000,
                     help="Krylov iteration cap (lower it only for profiling runs: solves then stop early)")
@@ -253,6 +321,8 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    if args.workload == "learned":
+        return learned_bench(args, rank, local)
     dist = None
     if world > 1:
         import torch.distributed as dist
