@@ -68,3 +68,11 @@ def test_soc_projection_problem_golden():
     np.testing.assert_allclose(dx, j["dx"], atol=1e-12)
     np.testing.assert_allclose(dy, j["dy"], atol=1e-12)
     np.testing.assert_allclose(ds, j["ds"], atol=1e-12)
+
+
+def test_psd_projection_golden():
+    g = GOLD["psd_projection"]
+    np.testing.assert_allclose(C.proj_psd(np.array(g["z"])), g["proj"], atol=1e-14)
+    np.testing.assert_allclose(C.dproj_psd(np.array(g["z"])) @ np.array(g["dproj_dir"]), g["dproj_times_dir"],
+                               atol=1e-14)
+    np.testing.assert_allclose(C.dproj_psd(np.array(g["z_diag"])), g["dproj_diag"], atol=1e-14)
