@@ -19,7 +19,7 @@ so that <svec(X), svec(Y)> = trace(X Y).
 """
 import numpy as np
 
-ZERO, NONNEG, SOC, PSD = 0, 1, 2, 3
+ZERO, NONNEG, SOC, PSD, EXP = 0, 1, 2, 3, 4
 
 
 def psd_order(d):
@@ -95,6 +95,118 @@ def dproj_psd(z):
     return J
 
 
+# ------------------------------------------------------------ exponential cone
+# K_exp = cl{(x, y, z): y > 0, y exp(x / y) <= z} (Appendix A).  Its
+# boundary away from the face {(x, 0, z): x <= 0, z >= 0} is the family of
+# rays t a(r), a(r) = (r, 1, exp(r)), t > 0.
+
+def in_exp(p, tol=0.0):
+    x, y, z = p
+    if abs(y) <= tol and x <= tol and z >= -tol:   # the face {(x, 0, z): x <= 0, z >= 0}
+        return True
+    if y > 0:
+        return y * np.exp(x / y) <= z + tol
+    return False
+
+
+def in_exp_dual(q, tol=0.0):
+    """K_exp* = cl{(u, v, w): u < 0, -u exp(v / u) <= e w} (Appendix A)."""
+    u, v, w = q
+    if abs(u) <= tol and v >= -tol and w >= -tol:  # the face {(0, v, w): v, w >= 0}
+        return True
+    if u < 0:
+        return -u * np.exp(v / u) <= np.e * w + tol
+    return False
+
+
+def proj_exp(p):
+    """Euclidean projection onto K_exp (Appendix A): p itself inside K, 0
+    inside the polar cone -K*, (x, 0, max(z, 0)) when x < 0 and y < 0, else
+    the nearest point of the boundary.  The last case is computed as its
+    definition: over the rays a(r), the nearest point of each ray is
+    max(<a, p>, 0) / |a|^2 a, and the best ray maximises <a, p>^2 / |a|^2 with
+    <a, p> > 0 (a grid over r, then scipy's bounded scalar minimiser); the
+    face {(x, 0, z): x <= 0, z >= 0} is a candidate too.  The best ray is
+    refined to full precision as the root of the stationarity condition
+    <a', p> |a|^2 - <a, p> <a', a> = 0 (a' = (1, 0, exp(r))) inside the grid
+    cell of the minimum."""
+    from scipy.optimize import brentq, minimize_scalar
+    p = np.asarray(p, np.float64)
+    x, y, z = p
+    if in_exp(p):
+        return p.copy()
+    if in_exp_dual(-p):
+        return np.zeros(3)
+    if x < 0 and y < 0:
+        return np.array([x, 0.0, max(z, 0.0)])
+    a = lambda r: np.array([r, 1.0, np.exp(r)])
+
+    def dist2(r):
+        ar = a(r)
+        t = max(ar @ p, 0.0) / (ar @ ar)
+        return float(np.sum((t * ar - p) ** 2))
+
+    def stat(r):
+        ar, da = a(r), np.array([1.0, 0.0, np.exp(r)])
+        return (da @ p) * (ar @ ar) - (ar @ p) * (da @ ar)
+
+    # rays toward the face need very negative r (r = x / y when y > 0 is
+    # the ray straight above p); exp(r) stays representable down to -700
+    grid = np.concatenate([np.linspace(-700.0, -40.0, 6601)[:-1], np.linspace(-40.0, 40.0, 8001)])
+    if y > 0 and -700.0 < x / y < 40.0:
+        grid = np.sort(np.append(grid, x / y))
+    A = np.stack([grid, np.ones_like(grid), np.exp(grid)], 1)
+    tg = np.maximum(A @ p, 0.0) / np.sum(A * A, 1)
+    vals = np.sum((tg[:, None] * A - p) ** 2, 1)
+    i = int(np.argmin(vals))
+    lo, hi = grid[max(i - 1, 0)], grid[min(i + 1, grid.size - 1)]
+    if stat(lo) * stat(hi) < 0:
+        rstar = brentq(stat, lo, hi, xtol=1e-16, rtol=4 * np.finfo(float).eps, maxiter=500)
+    else:
+        rstar = minimize_scalar(dist2, bounds=(lo, hi), method="bounded",
+                                options={"xatol": 1e-14, "maxiter": 500}).x
+    ar = a(rstar)
+    best = max(ar @ p, 0.0) / (ar @ ar) * ar
+    face = np.array([min(x, 0.0), 0.0, max(z, 0.0)])
+    return face if np.sum((face - p) ** 2) < np.sum((best - p) ** 2) else best
+
+
+def dproj_exp(p):
+    """Jacobian of proj_exp at p (Appendix A): I inside K, 0 inside the polar
+    cone, diag(1, 0, 1{z > 0}) when x < 0 and y < 0, else the leading 3 x 3
+    block of J^-1 with J the Jacobian of the projection's optimality
+    conditions at the projected point (x*, y*, z*) and multiplier
+    mu* = z* - z."""
+    p = np.asarray(p, np.float64)
+    x, y, z = p
+    if in_exp(p):
+        return np.eye(3)
+    if in_exp_dual(-p):
+        return np.zeros((3, 3))
+    if x < 0 and y < 0:
+        return np.diag([1.0, 0.0, 1.0 if z > 0 else 0.0])
+    xs, ys, zs = proj_exp(p)
+    mu = zs - z
+    e = np.exp(xs / ys)
+    J = np.array([
+        [1.0 + mu * e / ys, -mu * xs * e / ys ** 2, 0.0, e],
+        [-mu * xs * e / ys ** 2, 1.0 + mu * xs ** 2 * e / ys ** 3, 0.0, (1.0 - xs / ys) * e],
+        [0.0, 0.0, 1.0, -1.0],
+        [e, (1.0 - xs / ys) * e, -1.0, 0.0]])
+    return np.linalg.inv(J)[:3, :3]
+
+
+def proj_exp_dual(q):
+    """Projection onto K_exp* by the Moreau decomposition (Appendix A):
+    Pi_{K*}(q) = q + Pi_K(-q)."""
+    q = np.asarray(q, np.float64)
+    return q + proj_exp(-q)
+
+
+def dproj_exp_dual(q):
+    return np.eye(3) - dproj_exp(-np.asarray(q, np.float64))
+
+
 def proj_soc(z):
     """Euclidean projection onto {(t, u): ||u||_2 <= t} (Appendix A, SOC)."""
     t, u = z[0], z[1:]
@@ -140,6 +252,8 @@ def proj_dual_block(ctype, z):
         return proj_soc(z)
     if ctype == PSD:
         return proj_psd(z)
+    if ctype == EXP:
+        return proj_exp_dual(z)           # the exponential cone is not self-dual
     raise ValueError(ctype)
 
 
@@ -153,6 +267,8 @@ def dproj_dual_block(ctype, z):
         return dproj_soc(z)
     if ctype == PSD:
         return dproj_psd(z)
+    if ctype == EXP:
+        return dproj_exp_dual(z)
     raise ValueError(ctype)
 
 
@@ -160,6 +276,8 @@ def proj_primal_block(ctype, z):
     """Projection onto the block of K itself (used by the Moreau pin)."""
     if ctype == ZERO:
         return np.zeros_like(z)
+    if ctype == EXP:
+        return proj_exp(z)
     return proj_dual_block(ctype, z)      # R+, SOC and PSD are self-dual
 
 

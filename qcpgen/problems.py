@@ -12,7 +12,8 @@ Cone blocks are listed in row order as (type, dim) with type ZERO (the cone
 {0}), NONNEG (the nonnegative orthant), SOC (the second-order cone, stored
 (t, u) with t first, Appendix A) or PSD (the positive semidefinite cone of
 order k, dim = k (k + 1) / 2, a symmetric matrix stored as its upper
-triangle column by column with the off-diagonal entries times sqrt 2).
+triangle column by column with the off-diagonal entries times sqrt 2) or
+EXP (the exponential cone, dim 3, Appendix A).
 
 The five named workloads follow the problem descriptions of the benchmark
 configurations; the readings of under-specified points are:
@@ -36,7 +37,7 @@ import numpy as np
 import scipy.sparse as sp
 from scipy.sparse.csgraph import structural_rank
 
-ZERO, NONNEG, SOC, PSD = 0, 1, 2, 3
+ZERO, NONNEG, SOC, PSD, EXP = 0, 1, 2, 3, 4
 
 
 # --------------------------------------------------------------------------
@@ -249,7 +250,7 @@ def cone_dims_ok(cone_type, cone_dim, m) -> bool:
 # --------------------------------------------------------------------------
 # optimum construction
 # --------------------------------------------------------------------------
-def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=()):
+def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=(), exp_kind=()):
     """Draw (y, s) block by block.
 
     nonneg_active: bool per row of the R+ blocks (concatenated in order).
@@ -257,6 +258,10 @@ def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=()):
     psd_rank: per PSD block (in order), the rank r of s; s = Q diag(sigma) Q^T
         on the first r columns of a random orthogonal Q and y on the other
         k - r columns (eigenvalues ~ U(0.5, 2)), so y s = 0 and y + s > 0.
+    exp_kind: per exponential-cone block, 'ray' (s = b (r, 1, e^r) on the
+        boundary of K_exp and y = a (-e^r, (r - 1) e^r, 1) on the boundary of
+        K_exp*, orthogonal to it), 'sint' (s inside K_exp, y = 0) or 'yint'
+        (y inside K_exp*, s = 0); r ~ U(-1, 1), a, b ~ U(0.5, 2).
     """
     m = int(sum(d for _, d in cones))
     y = np.zeros(m)
@@ -265,6 +270,7 @@ def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=()):
     ia = 0
     isoc = 0
     ipsd = 0
+    iexp = 0
     for t, d in cones:
         if t == ZERO:
             y[r:r + d] = rng.standard_normal(d)
@@ -301,6 +307,20 @@ def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=()):
             ev = rng.uniform(0.5, 2.0, k)
             s[r:r + d] = _sym_to_entries((Q[:, :rk] * ev[:rk]) @ Q[:, :rk].T)
             y[r:r + d] = _sym_to_entries((Q[:, rk:] * ev[rk:]) @ Q[:, rk:].T)
+        elif t == EXP:
+            kind = exp_kind[iexp]
+            iexp += 1
+            rr = rng.uniform(-1.0, 1.0)
+            al, be = rng.uniform(0.5, 2.0, 2)
+            er = np.exp(rr)
+            if kind == "ray":
+                s[r:r + 3] = be * np.array([rr, 1.0, er])
+                y[r:r + 3] = al * np.array([-er, (rr - 1.0) * er, 1.0])
+            elif kind == "sint":
+                s[r:r + 3] = be * np.array([rr, 1.0, er * rng.uniform(1.5, 3.0)])
+            else:
+                v = rng.standard_normal()
+                y[r:r + 3] = np.array([-al, v, al * np.exp(-v / al) / np.e * rng.uniform(1.5, 3.0)])
         else:
             raise ValueError(f"unknown cone type {t}")
         r += d
@@ -719,12 +739,13 @@ def paper_example(seed: int = 0, m: int = 2000, n: int = 1000, frac_active: floa
 
 def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_per_row: int = 4,
               p_rank: int | None = None, frac_active: float = 0.5, soc_mix=(0.4, 0.2),
-              max_attempts: int = 200, psd_orders=(), psd_ranks=None) -> QCP:
+              max_attempts: int = 200, psd_orders=(), psd_ranks=None, exp_kinds=()) -> QCP:
     """A small QCP with any mix of blocks, for tests.
 
     The zero block comes first, then the R+ block, then the SOC blocks, then
     the PSD blocks (orders psd_orders; psd_ranks gives the rank of s in each,
-    by default a draw from 0..k).
+    by default a draw from 0..k), then one exponential-cone block per entry
+    of exp_kinds ('ray', 'sint' or 'yint').
     soc_mix = (fraction on rays, fraction with s = 0); the rest have y = 0.
     """
     cones = []
@@ -734,7 +755,9 @@ def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_pe
         cones.append((NONNEG, m_nonneg))
     cones += [(SOC, int(d)) for d in soc_dims]
     cones += [(PSD, int(k) * (int(k) + 1) // 2) for k in psd_orders]
-    m = m_zero + m_nonneg + int(sum(soc_dims)) + sum(int(k) * (int(k) + 1) // 2 for k in psd_orders)
+    cones += [(EXP, 3) for _ in exp_kinds]
+    m = (m_zero + m_nonneg + int(sum(soc_dims)) + sum(int(k) * (int(k) + 1) // 2 for k in psd_orders)
+         + 3 * len(exp_kinds))
     for attempt in range(max_attempts):
         rng = _rng(2000, seed, n, m, attempt)
         A = _sparse_rows(rng, m, n, min(nnz_per_row, n))
@@ -746,7 +769,7 @@ def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_pe
         kinds = _soc_kinds(rng, len(soc_dims), soc_mix[0], soc_mix[1], list(soc_dims))
         ranks = list(psd_ranks) if psd_ranks is not None else [int(rng.integers(0, k + 1)) for k in psd_orders]
         x = rng.standard_normal(n)
-        y, s = _optimum(rng, cones, active, kinds, ranks)
+        y, s = _optimum(rng, cones, active, kinds, ranks, list(exp_kinds))
         C = _constraint_rows(A, cones, y, s)
         if not _full_row_rank(C, "dense"):
             continue

@@ -33,6 +33,10 @@ def _check(p):
         elif t == g.NONNEG:
             assert np.all(yb >= 0) and np.all(sb >= 0)
             assert np.all((yb > 0) ^ (sb > 0)), "strict complementarity"
+        elif t == g.EXP:
+            from oracle.cones import in_exp, in_exp_dual
+            assert in_exp(sb, 1e-12) and in_exp_dual(yb, 1e-12)
+            assert np.any(yb != 0) or np.any(sb != 0)
         elif t == g.PSD:
             from oracle.cones import smat   # the oracle's own convention, as an independent check
             ly, ls = np.linalg.eigvalsh(smat(yb)), np.linalg.eigvalsh(smat(sb))
@@ -127,3 +131,12 @@ def test_psd_blocks():
         for d in (6, 3):
             assert np.allclose(smat(p.y[r:r + d]) @ smat(p.s[r:r + d]), 0.0, atol=1e-12)
             r += d
+
+
+def test_exp_blocks():
+    p = g.small_qcp(31, 12, 1, 3, (3,), exp_kinds=("ray", "ray", "sint", "yint"))
+    _check(p)
+    assert p.cones[-4:] == [(g.EXP, 3)] * 4
+    C = _constraint_rows(p.A, p.cones, p.y, p.s)
+    # 1 zero row, the active R+ rows, the SOC block's, 1 per boundary pair, 3 for y inside K_exp*
+    assert np.linalg.matrix_rank(C.toarray()) == C.shape[0] <= p.n

@@ -175,3 +175,72 @@ def test_psd_derivative_special_cases():
     G = rng.standard_normal((4, 4))
     np.testing.assert_allclose(C.dproj_psd(C.svec(G @ G.T + 0.1 * np.eye(4))), np.eye(10), atol=1e-12)
     np.testing.assert_allclose(C.dproj_psd(C.svec(-(G @ G.T + 0.1 * np.eye(4)))), np.zeros((10, 10)), atol=1e-12)
+
+
+# ------------------------------------------------------- exponential cone
+def test_exp_projection_characterised():
+    """Pi(p) in K_exp, Pi(p) - p in K_exp* (p - Pi(p) in the polar cone) and
+    the two orthogonal: the conditions that define the projection onto a
+    closed convex cone; and the same for the dual cone's projection."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        p = rng.standard_normal(3) * rng.uniform(0.1, 4)
+        P = C.proj_exp(p)
+        s = max(1.0, np.linalg.norm(p))
+        assert C.in_exp(P, 1e-9 * s), (p, P)
+        assert C.in_exp_dual(P - p, 1e-9 * s), (p, P)
+        assert abs(P @ (P - p)) <= 1e-10 * s * s
+        Q = C.proj_exp_dual(p)
+        assert C.in_exp_dual(Q, 1e-9 * s) and C.in_exp(Q - p, 1e-9 * s)
+        assert abs(Q @ (Q - p)) <= 1e-10 * s * s
+
+
+def test_exp_projection_is_nearest_point():
+    """Brute force over sampled points of K_exp (its rays and its face)."""
+    rng = np.random.default_rng(12)
+    r = rng.uniform(-6, 6, 20000)
+    t = rng.exponential(2.0, 20000)
+    pts = np.stack([t * r, t, t * np.exp(r)], 1)
+    face = np.stack([-rng.exponential(2.0, 5000), np.zeros(5000), rng.exponential(2.0, 5000)], 1)
+    cand = np.concatenate([pts, face])
+    for _ in range(30):
+        p = rng.standard_normal(3) * 2
+        d = np.linalg.norm(C.proj_exp(p) - p)
+        assert np.min(np.linalg.norm(cand - p, axis=1)) >= d - 1e-9
+
+
+def test_exp_derivative_fd_symmetry_homogeneity():
+    rng = np.random.default_rng(13)
+    seen = 0
+    for _ in range(200):
+        p = rng.standard_normal(3) * 2
+        if C.in_exp(p, 1e-3) or C.in_exp_dual(-p, 1e-3) or (p[0] < 0 and p[1] < 0):
+            continue
+        seen += 1
+        J = C.dproj_exp(p)
+        h = 1e-6
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            fd = (C.proj_exp(p + e) - C.proj_exp(p - e)) / (2 * h)
+            np.testing.assert_allclose(J[:, k], fd, atol=1e-6 * (1 + np.abs(fd).max()))
+        np.testing.assert_allclose(J, J.T, atol=1e-9)
+        np.testing.assert_allclose(J @ p, C.proj_exp(p), atol=1e-9 * (1 + np.abs(p).max()))
+        Jd = C.dproj_exp_dual(p)
+        fd = np.stack([(C.proj_exp_dual(p + h * e) - C.proj_exp_dual(p - h * e)) / (2 * h) for e in np.eye(3)], 1)
+        np.testing.assert_allclose(Jd, fd, atol=1e-6 * (1 + np.abs(fd).max()))
+    assert seen > 50
+
+
+def test_exp_special_cases():
+    """Inside K: identity; inside the polar cone: 0; x, y < 0: (x, 0, z+)."""
+    p_in = np.array([0.0, 1.0, 2.0])            # 1 * exp(0) = 1 <= 2
+    np.testing.assert_allclose(C.proj_exp(p_in), p_in)
+    np.testing.assert_allclose(C.dproj_exp(p_in), np.eye(3))
+    p_pol = -np.array([-1.0, 0.0, 1.0])          # -(u, v, w) with u < 0, -u exp(v/u) = 1 <= e
+    np.testing.assert_allclose(C.proj_exp(p_pol), np.zeros(3))
+    np.testing.assert_allclose(C.dproj_exp(p_pol), np.zeros((3, 3)))
+    p_neg = np.array([-2.0, -1.0, 3.0])
+    assert not C.in_exp(p_neg) and not C.in_exp_dual(-p_neg)
+    np.testing.assert_allclose(C.proj_exp(p_neg), [-2.0, 0.0, 3.0])
+    np.testing.assert_allclose(C.dproj_exp(p_neg), np.diag([1.0, 0.0, 1.0]))

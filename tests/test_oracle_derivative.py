@@ -33,7 +33,9 @@ SOCS = [lambda: g.small_qcp(21, 10, 2, 5, (3, 4, 5)),
         # PSD blocks (Appendix A): orders 3 and 2 with s of rank 1 and 0, and
         # orders 4 and 3 with ranks 2 and 3
         lambda: g.small_qcp(24, 14, 1, 4, (3,), psd_orders=(3, 2), psd_ranks=(1, 0)),
-        lambda: g.small_qcp(25, 18, 0, 3, (), psd_orders=(4, 3), psd_ranks=(2, 3))]
+        lambda: g.small_qcp(25, 18, 0, 3, (), psd_orders=(4, 3), psd_ranks=(2, 3)),
+        # exponential-cone blocks (Appendix A): boundary pairs and both interiors
+        lambda: g.small_qcp(31, 12, 1, 3, (3,), exp_kinds=("ray", "ray", "sint", "yint"))]
 
 
 @pytest.mark.parametrize("mk", QPS)
