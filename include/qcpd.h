@@ -50,8 +50,11 @@
  *             Appendix A: dim = k (k + 1) / 2 entries, the upper triangle
  *             column by column with the off-diagonal entries times sqrt 2,
  *             (X11, sqrt2 X12, X22, sqrt2 X13, sqrt2 X23, X33, ...), so the
- *             layout preserves inner products; k <= 64).  Plans with PSD
- *             blocks run on the pass and persistent engines.
+ *             layout preserves inner products; k <= 64) and QCP_CONE_EXP
+ *             (the exponential cone cl{(x, y, z): y > 0, y e^(x/y) <= z},
+ *             dim 3, Appendix A; the method projects onto its dual).  Plans
+ *             with PSD or exponential blocks run on the pass and persistent
+ *             engines.
  *  Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
  *             All work of a plan is enqueued on the stream given at creation.
  *             JVP/VJP calls return when the outputs are written: they
@@ -87,7 +90,13 @@ typedef enum {
 
 typedef enum { QCP_F64 = 0, QCP_F32 = 1 } qcp_dtype;
 
-typedef enum { QCP_CONE_ZERO = 0, QCP_CONE_NONNEG = 1, QCP_CONE_SOC = 2, QCP_CONE_PSD = 3 } qcp_cone_type;
+typedef enum {
+    QCP_CONE_ZERO = 0,
+    QCP_CONE_NONNEG = 1,
+    QCP_CONE_SOC = 2,
+    QCP_CONE_PSD = 3,
+    QCP_CONE_EXP = 4
+} qcp_cone_type;
 
 /* CSR matrix; all pointers are device pointers. */
 typedef struct {

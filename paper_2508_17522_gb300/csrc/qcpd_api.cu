@@ -64,7 +64,7 @@ static PlanView<T> view(qcp_plan* p, int precond) {
     v.RHS = p->d_RHS.as<double>();
     v.HB = p->d_HB.as<double>();
     v.lsmr = 0;
-    v.psd = p->kpsd ? p->d_psd.as<double>() : nullptr;
+    v.psd = (p->kpsd || p->ndense) ? p->d_psd.as<double>() : nullptr;
     v.kpsd = p->kpsd;
     v.rmax = p->rmax;
     v.long_chunk = p->long_chunk;

@@ -91,7 +91,7 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
     }
     for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
         const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-        if (t == QCP_CONE_SOC || t == QCP_CONE_PSD) {
+        if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP) {
             row += d;
             nbr += d;
             ++nsb;
@@ -142,7 +142,7 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
         int nl = 0, bi = 0;
         for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
             const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD) {
+            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP) {
                 if (bi >= cp.cb[r] && bi < cp.cb[r + 1] && d > kSocThread) ++nl;
                 ++bi;
             }
@@ -399,7 +399,7 @@ static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
     QCP_TRY(cluster_smem_limit(&limit));
     std::unique_ptr<ClusterLayout> lay(new ClusterLayout());
     lay->hp.resize(p->nprob);
-    lay->fits = p->kpsd == 0;  // the cluster kernels apply D Pi to R+, zero and SOC blocks only
+    lay->fits = p->kpsd == 0 && p->ndense == 0;  // the cluster kernels apply D Pi to R+, zero and SOC blocks only
     for (int pi = 0; pi < p->nprob; ++pi) {
         bool ok = false;
         const Prob& pr = p->hprob[pi];

@@ -92,16 +92,18 @@ struct Sys {
 struct SocBlock {
     int32_t start;   // local embedding row of the block's first entry (n + first y row)
     int32_t dim;
-    int32_t kase;    // SOC: 0 ||u|| <= -t (D = 0), 1 ||u|| <= t (D = I), 2 formula; 3: PSD block
+    int32_t kase;    // SOC: 0 ||u|| <= -t (D = 0), 1 ||u|| <= t (D = I), 2 formula; 3: PSD; 4: dense D
     int32_t order;   // PSD: the matrix order k (dim = k (k + 1) / 2); SOC: 0
     double t, r;     // SOC: t and ||u|| of z_y on the block
     double h, tq;    // SOC: 1 / (2 r) and t / r^2 (kase 2), so no kernel divides
-    int64_t psd;     // PSD: offset of its k x k eigenvectors V and weights B in the plan's PSD array
+    int64_t psd;     // PSD: offset of its k x k eigenvectors V and weights B in the plan's block array;
+                     // dense: offset of its dim x dim D Pi (row-major)
     int64_t pad;
 };
 
 constexpr int kPsdMaxOrder = 64;  // largest PSD block order (its scratch is 2 k^2 doubles of shared memory)
 constexpr int kBlockPsd = 3;      // SocBlock::kase of a PSD block
+constexpr int kBlockDense = 4;    // SocBlock::kase of a block whose D Pi is a stored dense matrix (exponential cone)
 
 // LSQR scalars of one system (Paige & Saunders' recurrences).
 struct LsqrState {
@@ -433,7 +435,14 @@ __device__ __forceinline__ void apply_D_tile(const double* src, double* dst, int
         if (B.dim > kSocThread || B.kase == kBlockPsd) continue;
         const double* sb = src + (B.start - r0);
         double* db = dst + (B.start - r0);
-        if (B.kase == 0) {
+        if (B.kase == kBlockDense) {
+            const double* Dm = psd + B.psd;
+            for (int i = 0; i < B.dim; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < B.dim; ++j) acc = fma(Dm[i * B.dim + j], sb[j], acc);
+                db[i] = acc;
+            }
+        } else if (B.kase == 0) {
             for (int k = 0; k < B.dim; ++k) db[k] = 0.0;
         } else if (B.kase == 1) {
             for (int k = 0; k < B.dim; ++k) db[k] = sb[k];

@@ -573,8 +573,8 @@ int qcp_plan_features(qcp_plan* p, float* out) {
         set_error("qcp_plan_features: null argument");
         return QCP_ERR_ARG;
     }
-    if (p->kpsd) {
-        set_error("qcp_plan_features: the features cover zero, R+ and SOC blocks; this plan has PSD blocks");
+    if (p->kpsd || p->ndense) {
+        set_error("qcp_plan_features: the features cover zero, R+ and SOC blocks; this plan has PSD or exp blocks");
         return QCP_ERR_ARG;
     }
     cudaStream_t st = p->stream;

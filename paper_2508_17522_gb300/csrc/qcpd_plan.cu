@@ -242,7 +242,7 @@ __global__ void k_socprep(SocBlock* blk, int64_t nb, const double* zy) {
     const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     SocBlock B = blk[b];
-    if (B.kase == kBlockPsd) return;
+    if (B.kase == kBlockPsd || B.kase == kBlockDense) return;
     double ss = 0.0;
     for (int k = 1 + lane; k < B.dim; k += 32) {
         const double u = (double)zy[B.start + k];
@@ -271,7 +271,8 @@ __global__ void k_kink(const double* zy, const int8_t* ctype, int32_t n, int32_t
                        unsigned long long* slot) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < m && ctype[i] == QCP_CONE_NONNEG) atomic_min_nonneg(slot, fabs((double)zy[n + i]));
-    if (i < nb && blk[i].kase != kBlockPsd) atomic_min_nonneg(slot, fabs(blk[i].r - fabs(blk[i].t)));
+    if (i < nb && blk[i].kase != kBlockPsd && blk[i].kase != kBlockDense)
+        atomic_min_nonneg(slot, fabs(blk[i].r - fabs(blk[i].t)));
 }
 
 // Per PSD block (one thread each): the eigendecomposition Z = V diag(lam) V^T
@@ -348,6 +349,136 @@ __global__ void k_psdprep(SocBlock* blk, int64_t nb, const double* zy, double* p
     atomic_min_nonneg(kink, margin);
 }
 
+// ---- exponential cone K_exp = cl{(x, y, z): y > 0, y e^(x/y) <= z} (Appendix A)
+__device__ bool exp_in(double x, double y, double z) {
+    if (y == 0.0 && x <= 0.0 && z >= 0.0) return true;
+    return y > 0.0 && y * exp(x / y) <= z;
+}
+
+__device__ bool exp_dual_in(double u, double v, double w) {
+    if (u == 0.0 && v >= 0.0 && w >= 0.0) return true;
+    return u < 0.0 && -u * exp(v / u) <= 2.718281828459045 * w;
+}
+
+// Squared distance from p to the nearest point of the ray t (r, 1, e^r),
+// t >= 0, and the stationarity function of r whose root is the best ray.
+__device__ double exp_ray_dist2(double r, const double* p) {
+    const double er = exp(r);
+    const double aa = r * r + 1.0 + er * er, ap = r * p[0] + p[1] + er * p[2];
+    const double t = ap > 0.0 ? ap / aa : 0.0;
+    const double d0 = t * r - p[0], d1 = t - p[1], d2 = t * er - p[2];
+    return d0 * d0 + d1 * d1 + d2 * d2;
+}
+
+__device__ double exp_ray_stat(double r, const double* p) {
+    const double er = exp(r);
+    const double aa = r * r + 1.0 + er * er, ap = r * p[0] + p[1] + er * p[2];
+    return (p[0] + er * p[2]) * aa - ap * (r + er * er);
+}
+
+// D Pi of the projection onto K_exp at p (3 x 3, row-major), from the cases
+// of Appendix A: I inside K, 0 inside the polar cone, diag(1, 0, 1{z > 0})
+// for x < 0 and y < 0 (and when the nearest point lies on the face
+// {(x, 0, z): x <= 0, z >= 0}); otherwise the nearest boundary point is
+// found over the rays t (r, 1, e^r): a scan of r in [-700, 40] (and r = x/y)
+// for the smallest distance, then bisection on the stationarity condition
+// in the scan cell (120 halvings), and D Pi is the leading 3 x 3 block of
+// J^-1 with J the Jacobian of the optimality conditions (multiplier
+// mu = z* - z), inverted by Gauss-Jordan elimination with partial pivoting.
+__device__ void exp_dproj(const double* p, double* Dm) {
+    for (int i = 0; i < 9; ++i) Dm[i] = 0.0;
+    const double x = p[0], y = p[1], z = p[2];
+    if (exp_in(x, y, z)) {
+        Dm[0] = Dm[4] = Dm[8] = 1.0;
+        return;
+    }
+    if (exp_dual_in(-x, -y, -z)) return;
+    if (x < 0.0 && y < 0.0) {
+        Dm[0] = 1.0;
+        Dm[8] = z > 0.0 ? 1.0 : 0.0;
+        return;
+    }
+    double best = INFINITY, rb = 0.0, step = 0.0;
+    for (int i = 0; i <= 6600; ++i) {  // [-700, -40] in steps of 0.1
+        const double r = -700.0 + 0.1 * i;
+        const double d2 = exp_ray_dist2(r, p);
+        if (d2 < best) { best = d2; rb = r; step = 0.1; }
+    }
+    for (int i = 0; i <= 8000; ++i) {  // [-40, 40] in steps of 0.01
+        const double r = -40.0 + 0.01 * i;
+        const double d2 = exp_ray_dist2(r, p);
+        if (d2 < best) { best = d2; rb = r; step = 0.01; }
+    }
+    if (y > 0.0 && x / y > -700.0 && x / y < 40.0 && exp_ray_dist2(x / y, p) < best) {
+        rb = x / y;
+        best = exp_ray_dist2(rb, p);
+        step = 0.01;
+    }
+    double lo = rb - step, hi = rb + step;
+    double flo = exp_ray_stat(lo, p), fhi = exp_ray_stat(hi, p);
+    double rs = rb;
+    if (flo * fhi < 0.0) {
+        for (int it = 0; it < 120; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            const double fm = exp_ray_stat(mid, p);
+            if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+        }
+        rs = 0.5 * (lo + hi);
+    }
+    const double er = exp(rs);
+    const double aa = rs * rs + 1.0 + er * er, ap = rs * x + y + er * z;
+    const double t = ap > 0.0 ? ap / aa : 0.0;
+    const double xs = t * rs, ys = t, zs = t * er;
+    const double fx = x < 0.0 ? x : 0.0, fz = z > 0.0 ? z : 0.0;  // the face candidate
+    const double dray = (xs - x) * (xs - x) + (ys - y) * (ys - y) + (zs - z) * (zs - z);
+    const double dface = (fx - x) * (fx - x) + y * y + (fz - z) * (fz - z);
+    if (!(ys > 0.0) || dface < dray) {
+        Dm[0] = x < 0.0 ? 1.0 : 0.0;
+        Dm[8] = z > 0.0 ? 1.0 : 0.0;
+        return;
+    }
+    const double mu = zs - z, e = exp(xs / ys), q = xs / ys;
+    double J[4][8] = {
+        {1.0 + mu * e / ys, -mu * q * e / ys, 0.0, e, 1, 0, 0, 0},
+        {-mu * q * e / ys, 1.0 + mu * q * q * e / ys, 0.0, (1.0 - q) * e, 0, 1, 0, 0},
+        {0.0, 0.0, 1.0, -1.0, 0, 0, 1, 0},
+        {e, (1.0 - q) * e, -1.0, 0.0, 0, 0, 0, 1}};
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(J[r][c]) > fabs(J[piv][c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < 8; ++k) {
+                const double tmp = J[c][k];
+                J[c][k] = J[piv][k];
+                J[piv][k] = tmp;
+            }
+        const double inv = 1.0 / J[c][c];
+        for (int k = 0; k < 8; ++k) J[c][k] *= inv;
+        for (int r = 0; r < 4; ++r) {
+            if (r == c) continue;
+            const double f = J[r][c];
+            for (int k = 0; k < 8; ++k) J[r][k] -= f * J[c][k];
+        }
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Dm[i * 3 + j] = J[i][4 + j];
+}
+
+// Per exponential-cone block (one thread each): D Pi onto the dual cone at
+// z_y, by the Moreau decomposition D Pi_{K*}(z) = I - D Pi_K(-z).
+__global__ void k_expprep(const SocBlock* blk, int64_t nb, const double* zy, double* dense) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb || blk[b].kase != kBlockDense) return;
+    const SocBlock B = blk[b];
+    const double p[3] = {-zy[B.start], -zy[B.start + 1], -zy[B.start + 2]};
+    double Dk[9];
+    exp_dproj(p, Dk);
+    double* D = dense + B.psd;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) D[i * 3 + j] = (i == j ? 1.0 : 0.0) - Dk[i * 3 + j];
+}
+
 // g = 2 P x + q and kappa = x^T P x (Sec. 2.4: the last row of D_u Q at
 // tau = 1 is (-(2 P x + q)^T, -b^T, x^T P x)).  P x comes from the columns
 // < n of M's x-rows.  One warp per row; kappa through the tile reduction.
@@ -404,7 +535,7 @@ __global__ void k_dd_soc(const SocBlock* blk, int64_t nb, const double* zy, doub
     const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     const SocBlock B = blk[b];
-    if (B.kase == kBlockPsd) return;
+    if (B.kase == kBlockPsd || B.kase == kBlockDense) return;
     for (int k = lane; k < B.dim; k += 32) {
         double v;
         if (B.kase == 0) v = 0.0;
@@ -426,6 +557,10 @@ __global__ void k_dd_psd(const SocBlock* blk, int64_t nb, const double* psd, dou
     const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (b >= nb) return;
     const SocBlock B = blk[b];
+    if (B.kase == kBlockDense) {  // the stored matrix's diagonal
+        for (int i = lane; i < B.dim; i += 32) dd[B.start + i] = psd[B.psd + i * B.dim + i];
+        return;
+    }
     if (B.kase != kBlockPsd) return;
     const int k = B.order;
     const double* V = psd + B.psd;
@@ -625,7 +760,7 @@ static void cut_tiles(const qcp_plan* p, int pi, std::vector<Tile>& out, int& rm
     int sb = 0;
     for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
         const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-        if (t != QCP_CONE_SOC && t != QCP_CONE_PSD) {  // SOC and PSD blocks stay in one tile
+        if (t != QCP_CONE_SOC && t != QCP_CONE_PSD && t != QCP_CONE_EXP) {  // coupled blocks stay in one tile
             for (int r = row; r < row + d; ++r) single_row(r);
         } else {
             const int64_t nz = rp[row + d] - rp[row];
@@ -840,7 +975,7 @@ static int run_equilibrate(qcp_plan* p) {
         if (pr.nsoc)
             k_dd_soc<T><<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_zy.as<double>() + pr.doff, dd.as<double>() + pr.doff);
-        if (pr.nsoc && p->kpsd)
+        if (pr.nsoc && (p->kpsd || p->ndense))
             k_dd_psd<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_psd.as<double>(), dd.as<double>() + pr.doff);
     }
@@ -902,7 +1037,7 @@ static int jacobi_cols_t(qcp_plan* p, double* out) {
         if (pr.nsoc)
             k_dd_soc<T><<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_zy.as<double>() + pr.doff, dd.as<double>() + pr.doff);
-        if (pr.nsoc && p->kpsd)
+        if (pr.nsoc && (p->kpsd || p->ndense))
             k_dd_psd<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_psd.as<double>(), dd.as<double>() + pr.doff);
     }
@@ -976,7 +1111,9 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
         pr.m = (int)q.m;
         for (int b = 0; b < q.K.nblocks; ++b) {
             const int t = q.K.type[b], d = q.K.dim[b];
-            if ((t != QCP_CONE_ZERO && t != QCP_CONE_NONNEG && t != QCP_CONE_SOC && t != QCP_CONE_PSD) || d < 1) {
+            if ((t != QCP_CONE_ZERO && t != QCP_CONE_NONNEG && t != QCP_CONE_SOC && t != QCP_CONE_PSD &&
+                 t != QCP_CONE_EXP) ||
+                d < 1 || (t == QCP_CONE_EXP && d != 3)) {
                 set_error("problem %d: cone block %d has type %d dim %d", i, b, t, d);
                 return QCP_ERR_ARG;
             }
@@ -989,10 +1126,17 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
                     return QCP_ERR_ARG;
                 }
             }
-            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD) {
+            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP) {
                 SocBlock sb{};
                 sb.start = (int)(q.n + msum);
                 sb.dim = d;
+                if (t == QCP_CONE_EXP) {
+                    sb.kase = kBlockDense;
+                    sb.order = 3;
+                    sb.psd = psd_off;
+                    psd_off += 9;
+                    ++p->ndense;
+                }
                 if (t == QCP_CONE_PSD) {
                     sb.kase = kBlockPsd;
                     sb.order = order;
@@ -1228,6 +1372,9 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
             k_psdprep<<<grid_for(pr.nsoc, 64), 64, 0, st>>>(p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc,
                                                            p->d_zy.as<double>() + pr.doff, p->d_psd.as<double>(),
                                                            d_kink.as<unsigned long long>() + i);
+        if (pr.nsoc && p->ndense)
+            k_expprep<<<grid_for(pr.nsoc, 64), 64, 0, st>>>(p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc,
+                                                           p->d_zy.as<double>() + pr.doff, p->d_psd.as<double>());
     }
     QCP_CUDA(cudaGetLastError());
     ctoff = 0;

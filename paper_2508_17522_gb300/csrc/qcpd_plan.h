@@ -113,8 +113,9 @@ struct qcp_plan {
     // problem data (device)
     qcpd::DevBuf d_prob, d_mrowptr, d_mcol, d_mvmap, d_mval;
     qcpd::DevBuf d_coefA, d_coefB, d_pz, d_zy, d_flag, d_blocks;
-    qcpd::DevBuf d_psd;   // PSD blocks: eigenvectors V and D Pi weights B, 2 k^2 doubles each
+    qcpd::DevBuf d_psd;   // PSD blocks: eigenvectors V and D Pi weights B, 2 k^2 doubles each; exp blocks: D Pi
     int kpsd = 0;         // largest PSD block order (0: no PSD block)
+    int ndense = 0;       // exponential-cone blocks (D Pi stored as a dense 3 x 3 in d_psd)
     qcpd::DevBuf d_rw, d_cd, d_mvalG, d_mvalT;   // equilibration: row/column scalings, scaled values
     qcpd::DevBuf d_cdD, d_onesD, d_mvalD;        // QCP_PRECOND_DIAG: the caller's C, unit W, M diag(C)
     qcpd::DevBuf d_cdJ;                          // QCP_PRECOND_JACOBI: 1 / column norms of F (made on first use)
