@@ -19,7 +19,7 @@ so that <svec(X), svec(Y)> = trace(X Y).
 """
 import numpy as np
 
-ZERO, NONNEG, SOC, PSD, EXP = 0, 1, 2, 3, 4
+ZERO, NONNEG, SOC, PSD, EXP, POW = 0, 1, 2, 3, 4, 5
 
 
 def psd_order(d):
@@ -207,6 +207,104 @@ def dproj_exp_dual(q):
     return np.eye(3) - dproj_exp(-np.asarray(q, np.float64))
 
 
+# ------------------------------------------------------------------ power cone
+# K_pow,a = {(x, y, z): x, y >= 0, x^a y^(1-a) >= |z|}, 0 < a < 1 (Appendix A).
+
+def in_pow(p, a, tol=0.0):
+    x, y, z = p
+    if x < -tol or y < -tol:
+        return False
+    return max(x, 0.0) ** a * max(y, 0.0) ** (1 - a) >= abs(z) - tol
+
+
+def in_pow_dual(q, a, tol=0.0):
+    u, v, w = q
+    if u < -tol or v < -tol:
+        return False
+    return (max(u, 0.0) / a) ** a * (max(v, 0.0) / (1 - a)) ** (1 - a) >= abs(w) - tol
+
+
+def _pow_f(x, y, z, a, r):
+    fx = 0.5 * (x + np.sqrt(x * x + 4 * a * r * (abs(z) - r)))
+    fy = 0.5 * (y + np.sqrt(y * y + 4 * (1 - a) * r * (abs(z) - r)))
+    return fx, fy
+
+
+def _pow_r(x, y, z, a):
+    """The root r in (0, |z|) of r = f_x(r)^a f_y(r)^(1-a) (Appendix A).
+    r = 0 solves the equation too whenever x <= 0 or y <= 0, so the bracket
+    starts at the largest of |z| 10^-k (k = 1, 2, ...) where the residual is
+    positive (it is negative at |z|)."""
+    from scipy.optimize import brentq
+    g = lambda r: (lambda f: f[0] ** a * f[1] ** (1 - a))(_pow_f(x, y, z, a, r)) - r
+    az = abs(z)
+    lo = None
+    for k in range(1, 300):
+        if g(az * 10.0 ** -k) > 0:
+            lo = az * 10.0 ** -k
+            break
+    if lo is None:
+        return 0.0
+    return brentq(g, lo, az, xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=1000)
+
+
+def proj_pow(p, a):
+    """Projection onto K_pow,a (Appendix A): p inside K, 0 inside the polar
+    cone, (x+, y+, 0) for z = 0, else (f_x(r), f_y(r), sign(z) r)."""
+    p = np.asarray(p, np.float64)
+    x, y, z = p
+    if in_pow(p, a):
+        return p.copy()
+    if in_pow_dual(-p, a):
+        return np.zeros(3)
+    if z == 0.0:
+        return np.array([max(x, 0.0), max(y, 0.0), 0.0])
+    r = _pow_r(x, y, z, a)
+    fx, fy = _pow_f(x, y, z, a, r)
+    return np.array([fx, fy, np.sign(z) * r])
+
+
+def dproj_pow(p, a):
+    """Jacobian of proj_pow (Appendix A, from Hien 2015 Theorem 3.1)."""
+    p = np.asarray(p, np.float64)
+    x, y, z = p
+    if in_pow(p, a):
+        return np.eye(3)
+    if in_pow_dual(-p, a):
+        return np.zeros((3, 3))
+    if z == 0.0:
+        if x > 0 and y < 0:
+            d = 1.0 if a > 0.5 else (0.0 if a < 0.5 else x / (2 * abs(y) + x))
+        elif y > 0 and x < 0:
+            d = 1.0 if a < 0.5 else (0.0 if a > 0.5 else y / (2 * abs(x) + y))
+        else:
+            d = 0.0
+        return np.diag([1.0 if x > 0 else 0.0, 1.0 if y > 0 else 0.0, d])
+    r = _pow_r(x, y, z, a)
+    fx, fy = _pow_f(x, y, z, a, r)
+    az, sz = abs(z), np.sign(z)
+    gx, gy = 2 * fx - x, 2 * fy - y
+    T = -(a * x / gx + (1 - a) * y / gy)
+    L = 2 * (az - r) / (az + (az - 2 * r) * (a * x / gx + (1 - a) * y / gy))
+    J = np.empty((3, 3))
+    J[0, 0] = 0.5 + x / (2 * gx) + a * a * (az - 2 * r) * r * L / gx ** 2
+    J[0, 1] = J[1, 0] = (a - a * a) * (az - 2 * r) * r * L / (gx * gy)
+    J[0, 2] = J[2, 0] = sz * a * r * L / gx
+    J[1, 1] = 0.5 + y / (2 * gy) + (1 - a) ** 2 * (az - 2 * r) * r * L / gy ** 2
+    J[1, 2] = J[2, 1] = sz * (1 - a) * r * L / gy
+    J[2, 2] = r / az + r / az * T * L
+    return J
+
+
+def proj_pow_dual(q, a):
+    q = np.asarray(q, np.float64)
+    return q + proj_pow(-q, a)
+
+
+def dproj_pow_dual(q, a):
+    return np.eye(3) - dproj_pow(-np.asarray(q, np.float64), a)
+
+
 def proj_soc(z):
     """Euclidean projection onto {(t, u): ||u||_2 <= t} (Appendix A, SOC)."""
     t, u = z[0], z[1:]
@@ -243,7 +341,8 @@ def dproj_soc(z):
     return J
 
 
-def proj_dual_block(ctype, z):
+def proj_dual_block(ctype, z, a=None):
+    """Projection onto the dual of one block (a: the power cone's exponent)."""
     if ctype == ZERO:
         return z.copy()                   # dual of {0} is R
     if ctype == NONNEG:
@@ -253,11 +352,13 @@ def proj_dual_block(ctype, z):
     if ctype == PSD:
         return proj_psd(z)
     if ctype == EXP:
-        return proj_exp_dual(z)           # the exponential cone is not self-dual
+        return proj_exp_dual(z)           # the exponential and power cones are not self-dual
+    if ctype == POW:
+        return proj_pow_dual(z, a)
     raise ValueError(ctype)
 
 
-def dproj_dual_block(ctype, z):
+def dproj_dual_block(ctype, z, a=None):
     d = z.shape[0]
     if ctype == ZERO:
         return np.eye(d)
@@ -269,36 +370,53 @@ def dproj_dual_block(ctype, z):
         return dproj_psd(z)
     if ctype == EXP:
         return dproj_exp_dual(z)
+    if ctype == POW:
+        return dproj_pow_dual(z, a)
     raise ValueError(ctype)
 
 
-def proj_primal_block(ctype, z):
+def proj_primal_block(ctype, z, a=None):
     """Projection onto the block of K itself (used by the Moreau pin)."""
     if ctype == ZERO:
         return np.zeros_like(z)
     if ctype == EXP:
         return proj_exp(z)
+    if ctype == POW:
+        return proj_pow(z, a)
     return proj_dual_block(ctype, z)      # R+, SOC and PSD are self-dual
 
 
 def _blocks(cones):
+    """(type, first row, end row, parameter) per block; cones holds (type,
+    dim) or (type, dim, parameter) entries (the parameter: the power cone's
+    exponent)."""
     r = 0
-    for t, d in cones:
-        yield t, r, r + d
+    for c in cones:
+        t, d = c[0], c[1]
+        yield t, r, r + d, (c[2] if len(c) > 2 else None)
         r += d
+
+
+def cone_list(prob):
+    """(type, dim, parameter) per block of a problem (parameter 0 unless a
+    power cone)."""
+    par = getattr(prob, "cone_param", None)
+    if par is None:
+        par = np.zeros(len(prob.cone_type))
+    return [(int(t), int(d), float(a)) for t, d, a in zip(prob.cone_type, prob.cone_dim, par)]
 
 
 def proj_dual(cones, z):
     out = np.empty_like(z)
-    for t, a, b in _blocks(cones):
-        out[a:b] = proj_dual_block(t, z[a:b])
+    for t, a, b, par in _blocks(cones):
+        out[a:b] = proj_dual_block(t, z[a:b], par)
     return out
 
 
 def proj_primal(cones, z):
     out = np.empty_like(z)
-    for t, a, b in _blocks(cones):
-        out[a:b] = proj_primal_block(t, z[a:b])
+    for t, a, b, par in _blocks(cones):
+        out[a:b] = proj_primal_block(t, z[a:b], par)
     return out
 
 
@@ -306,15 +424,15 @@ def dproj_dual(cones, z):
     """Block-diagonal dense Jacobian of the projection onto K* at z."""
     m = z.shape[0]
     D = np.zeros((m, m))
-    for t, a, b in _blocks(cones):
-        D[a:b, a:b] = dproj_dual_block(t, z[a:b])
+    for t, a, b, par in _blocks(cones):
+        D[a:b, a:b] = dproj_dual_block(t, z[a:b], par)
     return D
 
 
 def dproj_dual_sparse(cones, z):
     """Same Jacobian as a scipy sparse block-diagonal matrix."""
     import scipy.sparse as sp
-    blocks = [sp.csr_matrix(dproj_dual_block(t, z[a:b])) for t, a, b in _blocks(cones)]
+    blocks = [sp.csr_matrix(dproj_dual_block(t, z[a:b], par)) for t, a, b, par in _blocks(cones)]
     if not blocks:
         return sp.csr_matrix((0, 0))
     return sp.block_diag(blocks, format="csr")
@@ -324,7 +442,7 @@ def kink_margin(cones, z):
     """Distance (in the quantities the case tests compare) to the nearest
     point where the projection is not differentiable."""
     best = np.inf
-    for t, a, b in _blocks(cones):
+    for t, a, b, _ in _blocks(cones):
         zb = z[a:b]
         if t == NONNEG and zb.size:
             best = min(best, float(np.min(np.abs(zb))))

@@ -119,7 +119,7 @@ class FOperator:
         zx, zy, zN = E.split(prob, self.z)
         pz = E.proj_K(prob, self.z)
         self.x, self.y, self.tau = E.split(prob, pz)
-        self.Dy = C.dproj_dual_sparse(prob.cones, zy)
+        self.Dy = C.dproj_dual_sparse(C.cone_list(prob), zy)
         self.dtau = 1.0 if zN > 0 else 0.0
         self.zN = zN
         self.Px = self.P @ self.x
@@ -198,8 +198,8 @@ def _phi_apply(prob, z, dz):
     """D phi(z) dz without forming D phi."""
     n, m = prob.n, prob.m
     zx, zy, zN = E.split(prob, z)
-    py = C.proj_dual(prob.cones, zy)
-    D = C.dproj_dual_sparse(prob.cones, zy)
+    py = C.proj_dual(C.cone_list(prob), zy)
+    D = C.dproj_dual_sparse(C.cone_list(prob), zy)
     dzx, dzy, dzN = dz[:n], dz[n:n + m], dz[-1]
     Ddy = D @ dzy
     return ((dzx - dzN * zx / zN) / zN, (Ddy - dzN * py / zN) / zN,
@@ -209,8 +209,8 @@ def _phi_apply(prob, z, dz):
 def _phi_apply_T(prob, z, wx, wy, ws):
     """D phi(z)^T (wx, wy, ws) without forming D phi."""
     zx, zy, zN = E.split(prob, z)
-    py = C.proj_dual(prob.cones, zy)
-    D = C.dproj_dual_sparse(prob.cones, zy)
+    py = C.proj_dual(C.cone_list(prob), zy)
+    D = C.dproj_dual_sparse(C.cone_list(prob), zy)
     gy = (D.T @ (wy + ws) - ws) / zN
     gN = -(zx @ wx + py @ wy + (py - zy) @ ws) / zN ** 2
     return np.concatenate([wx / zN, gy, [gN]])

@@ -86,7 +86,7 @@ def Q(prob, u, P=None, A=None, q=None, b=None):
 def proj_K(prob, z):
     """Pi onto K = R^n x K* x R+."""
     zx, zy, zN = split(prob, z)
-    return np.concatenate([zx, C.proj_dual(prob.cones, zy), [max(zN, 0.0)]])
+    return np.concatenate([zx, C.proj_dual(C.cone_list(prob), zy), [max(zN, 0.0)]])
 
 
 def dproj_K(prob, z):
@@ -95,7 +95,7 @@ def dproj_K(prob, z):
     zx, zy, zN = split(prob, z)
     D = np.zeros((n + m + 1, n + m + 1))
     D[:n, :n] = np.eye(n)
-    D[n:n + m, n:n + m] = C.dproj_dual(prob.cones, zy)
+    D[n:n + m, n:n + m] = C.dproj_dual(C.cone_list(prob), zy)
     D[-1, -1] = 1.0 if zN > 0 else 0.0
     return D
 
@@ -182,7 +182,7 @@ def restrict_to_patterns(prob, Pt, At):
 def phi(prob, z):
     """phi(z) = (z_x, Pi_{K*}(z_y), Pi_{K*}(z_y) - z_y) / z_N."""
     zx, zy, zN = split(prob, z)
-    py = C.proj_dual(prob.cones, zy)
+    py = C.proj_dual(C.cone_list(prob), zy)
     return np.concatenate([zx, py, py - zy]) / zN
 
 
@@ -191,8 +191,8 @@ def Dphi(prob, z):
     z_N = 1: columns -x, -y, -s in the last position)."""
     n, m = prob.n, prob.m
     zx, zy, zN = split(prob, z)
-    py = C.proj_dual(prob.cones, zy)
-    D = C.dproj_dual(prob.cones, zy)
+    py = C.proj_dual(C.cone_list(prob), zy)
+    D = C.dproj_dual(C.cone_list(prob), zy)
     J = np.zeros((n + 2 * m, n + m + 1))
     J[:n, :n] = np.eye(n) / zN
     J[n:n + m, n:n + m] = D / zN

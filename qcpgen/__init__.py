@@ -10,7 +10,7 @@ solve.  It only draws random data and assembles problem data from the drawn
 optimum (b = A x* + s*, q = -P x* - A^T y*).
 """
 from .problems import (  # noqa: F401
-    ZERO, NONNEG, SOC, PSD, EXP, CSR, QCP, Directions,
+    ZERO, NONNEG, SOC, PSD, EXP, POW, CSR, QCP, Directions,
     config1, config2, config3, config4, config5_family, paper_example, small_qcp,
     unconstrained_qp, equality_qp, make_directions, make_directions_batch,
     round_to_fp32, cone_dims_ok,

@@ -12,8 +12,9 @@ Cone blocks are listed in row order as (type, dim) with type ZERO (the cone
 {0}), NONNEG (the nonnegative orthant), SOC (the second-order cone, stored
 (t, u) with t first, Appendix A) or PSD (the positive semidefinite cone of
 order k, dim = k (k + 1) / 2, a symmetric matrix stored as its upper
-triangle column by column with the off-diagonal entries times sqrt 2) or
-EXP (the exponential cone, dim 3, Appendix A).
+triangle column by column with the off-diagonal entries times sqrt 2), EXP
+(the exponential cone, dim 3) or POW (the power cone of exponent a, dim 3,
+Appendix A; a in QCP.cone_param).
 
 The five named workloads follow the problem descriptions of the benchmark
 configurations; the readings of under-specified points are:
@@ -37,7 +38,7 @@ import numpy as np
 import scipy.sparse as sp
 from scipy.sparse.csgraph import structural_rank
 
-ZERO, NONNEG, SOC, PSD, EXP = 0, 1, 2, 3, 4
+ZERO, NONNEG, SOC, PSD, EXP, POW = 0, 1, 2, 3, 4, 5
 
 
 # --------------------------------------------------------------------------
@@ -90,6 +91,7 @@ class QCP:
     y: np.ndarray
     s: np.ndarray
     meta: dict = field(default_factory=dict)
+    cone_param: np.ndarray = None   # per block: the power cone's exponent (0 elsewhere)
 
     @property
     def N(self) -> int:
@@ -250,7 +252,7 @@ def cone_dims_ok(cone_type, cone_dim, m) -> bool:
 # --------------------------------------------------------------------------
 # optimum construction
 # --------------------------------------------------------------------------
-def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=(), exp_kind=()):
+def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=(), exp_kind=(), pow_spec=()):
     """Draw (y, s) block by block.
 
     nonneg_active: bool per row of the R+ blocks (concatenated in order).
@@ -262,6 +264,10 @@ def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=(), exp_kind=()):
         boundary of K_exp and y = a (-e^r, (r - 1) e^r, 1) on the boundary of
         K_exp*, orthogonal to it), 'sint' (s inside K_exp, y = 0) or 'yint'
         (y inside K_exp*, s = 0); r ~ U(-1, 1), a, b ~ U(0.5, 2).
+    pow_spec: per power-cone block (kind, exponent a): 'ray' (s = (u, v,
+        +-u^a v^(1-a)) on K_pow's boundary, y = c (a |s3| / u, (1 - a) |s3| / v,
+        -sign s3) on K_pow*'s boundary, orthogonal to it), 'sint' or 'yint';
+        u, v, c ~ U(0.5, 2).
     """
     m = int(sum(d for _, d in cones))
     y = np.zeros(m)
@@ -271,6 +277,7 @@ def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=(), exp_kind=()):
     isoc = 0
     ipsd = 0
     iexp = 0
+    ipow = 0
     for t, d in cones:
         if t == ZERO:
             y[r:r + d] = rng.standard_normal(d)
@@ -321,6 +328,20 @@ def _optimum(rng, cones, nonneg_active, soc_kind, psd_rank=(), exp_kind=()):
             else:
                 v = rng.standard_normal()
                 y[r:r + 3] = np.array([-al, v, al * np.exp(-v / al) / np.e * rng.uniform(1.5, 3.0)])
+        elif t == POW:
+            kind, a = pow_spec[ipow]
+            ipow += 1
+            u, v, c = rng.uniform(0.5, 2.0, 3)
+            sg = 1.0 if rng.random() < 0.5 else -1.0
+            top = u ** a * v ** (1 - a)
+            if kind == "ray":
+                s[r:r + 3] = [u, v, sg * top]
+                y[r:r + 3] = c * np.array([a * top / u, (1 - a) * top / v, -sg])
+            elif kind == "sint":
+                s[r:r + 3] = [u, v, sg * top * rng.uniform(0.2, 0.8)]
+            else:
+                w = (u / a) ** a * (v / (1 - a)) ** (1 - a)
+                y[r:r + 3] = [u, v, sg * w * rng.uniform(0.2, 0.8)]
         else:
             raise ValueError(f"unknown cone type {t}")
         r += d
@@ -376,15 +397,16 @@ def _full_row_rank(C, mode) -> bool:
     return int(structural_rank(sp.csr_matrix(C))) == C.shape[0]
 
 
-def _assemble(n, m, P, A, cones, x, y, s, meta) -> QCP:
+def _assemble(n, m, P, A, cones, x, y, s, meta, params=None) -> QCP:
     AT, perm = _transpose_with_perm(A)
     Pf = _sym_full(P)
     q = -(Pf @ x) - (A.to_scipy().T @ y)
     b = A.to_scipy() @ x + s
     ct = np.array([c[0] for c in cones], dtype=np.int32)
     cd = np.array([c[1] for c in cones], dtype=np.int32)
+    cp = np.zeros(len(cones)) if params is None else np.asarray(params, np.float64)
     return QCP(n, m, P, A, AT, perm, np.asarray(q, np.float64), np.asarray(b, np.float64),
-               ct, cd, x, y, s, meta)
+               ct, cd, x, y, s, meta, cp)
 
 
 def _soc_kinds(rng, nblocks, frac_ray, frac_yint, dims=None):
@@ -739,13 +761,14 @@ def paper_example(seed: int = 0, m: int = 2000, n: int = 1000, frac_active: floa
 
 def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_per_row: int = 4,
               p_rank: int | None = None, frac_active: float = 0.5, soc_mix=(0.4, 0.2),
-              max_attempts: int = 200, psd_orders=(), psd_ranks=None, exp_kinds=()) -> QCP:
+              max_attempts: int = 200, psd_orders=(), psd_ranks=None, exp_kinds=(), pow_blocks=()) -> QCP:
     """A small QCP with any mix of blocks, for tests.
 
     The zero block comes first, then the R+ block, then the SOC blocks, then
     the PSD blocks (orders psd_orders; psd_ranks gives the rank of s in each,
     by default a draw from 0..k), then one exponential-cone block per entry
-    of exp_kinds ('ray', 'sint' or 'yint').
+    of exp_kinds ('ray', 'sint' or 'yint'), then one power-cone block per
+    (kind, exponent) of pow_blocks.
     soc_mix = (fraction on rays, fraction with s = 0); the rest have y = 0.
     """
     cones = []
@@ -756,8 +779,10 @@ def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_pe
     cones += [(SOC, int(d)) for d in soc_dims]
     cones += [(PSD, int(k) * (int(k) + 1) // 2) for k in psd_orders]
     cones += [(EXP, 3) for _ in exp_kinds]
+    cones += [(POW, 3) for _ in pow_blocks]
+    params = [0.0] * (len(cones) - len(pow_blocks)) + [float(a) for _, a in pow_blocks]
     m = (m_zero + m_nonneg + int(sum(soc_dims)) + sum(int(k) * (int(k) + 1) // 2 for k in psd_orders)
-         + 3 * len(exp_kinds))
+         + 3 * len(exp_kinds) + 3 * len(pow_blocks))
     for attempt in range(max_attempts):
         rng = _rng(2000, seed, n, m, attempt)
         A = _sparse_rows(rng, m, n, min(nnz_per_row, n))
@@ -769,11 +794,11 @@ def small_qcp(seed: int, n: int, m_zero: int, m_nonneg: int, soc_dims=(), nnz_pe
         kinds = _soc_kinds(rng, len(soc_dims), soc_mix[0], soc_mix[1], list(soc_dims))
         ranks = list(psd_ranks) if psd_ranks is not None else [int(rng.integers(0, k + 1)) for k in psd_orders]
         x = rng.standard_normal(n)
-        y, s = _optimum(rng, cones, active, kinds, ranks, list(exp_kinds))
+        y, s = _optimum(rng, cones, active, kinds, ranks, list(exp_kinds), list(pow_blocks))
         C = _constraint_rows(A, cones, y, s)
         if not _full_row_rank(C, "dense"):
             continue
-        return _assemble(n, m, P, A, cones, x, y, s, {"seed": seed, "attempts": attempt + 1})
+        return _assemble(n, m, P, A, cones, x, y, s, {"seed": seed, "attempts": attempt + 1}, params)
     raise RuntimeError("small_qcp: no differentiable draw")
 
 

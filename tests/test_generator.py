@@ -26,13 +26,17 @@ def _check(p):
     np.testing.assert_allclose(Pf @ p.x + A.T @ p.y, -p.q, atol=1e-11 * max(1, np.abs(p.q).max(initial=0)))
     assert abs(p.s @ p.y) < 1e-12 * max(1.0, np.linalg.norm(p.s) * np.linalg.norm(p.y))
     r = 0
-    for t, d in p.cones:
+    for bi, (t, d) in enumerate(p.cones):
         yb, sb = p.y[r:r + d], p.s[r:r + d]
         if t == g.ZERO:
             assert np.all(sb == 0)
         elif t == g.NONNEG:
             assert np.all(yb >= 0) and np.all(sb >= 0)
             assert np.all((yb > 0) ^ (sb > 0)), "strict complementarity"
+        elif t == g.POW:
+            from oracle.cones import in_pow, in_pow_dual
+            a = p.cone_param[bi]
+            assert in_pow(sb, a, 1e-12) and in_pow_dual(yb, a, 1e-12)
         elif t == g.EXP:
             from oracle.cones import in_exp, in_exp_dual
             assert in_exp(sb, 1e-12) and in_exp_dual(yb, 1e-12)
@@ -140,3 +144,9 @@ def test_exp_blocks():
     C = _constraint_rows(p.A, p.cones, p.y, p.s)
     # 1 zero row, the active R+ rows, the SOC block's, 1 per boundary pair, 3 for y inside K_exp*
     assert np.linalg.matrix_rank(C.toarray()) == C.shape[0] <= p.n
+
+
+def test_pow_blocks():
+    p = g.small_qcp(41, 12, 1, 3, (3,), pow_blocks=(("ray", 0.3), ("ray", 0.5), ("sint", 0.7), ("yint", 0.4)))
+    _check(p)
+    assert p.cones[-4:] == [(g.POW, 3)] * 4 and list(p.cone_param[-4:]) == [0.3, 0.5, 0.7, 0.4]

@@ -244,3 +244,64 @@ def test_exp_special_cases():
     assert not C.in_exp(p_neg) and not C.in_exp_dual(-p_neg)
     np.testing.assert_allclose(C.proj_exp(p_neg), [-2.0, 0.0, 3.0])
     np.testing.assert_allclose(C.dproj_exp(p_neg), np.diag([1.0, 0.0, 1.0]))
+
+
+# ------------------------------------------------------------ power cone
+@pytest.mark.parametrize("a", [0.2, 0.5, 0.75])
+def test_pow_projection_characterised(a):
+    rng = np.random.default_rng(int(100 * a))
+    for _ in range(200):
+        p = rng.standard_normal(3) * rng.uniform(0.1, 4)
+        s = max(1.0, np.linalg.norm(p))
+        P = C.proj_pow(p, a)
+        assert C.in_pow(P, a, 1e-9 * s) and C.in_pow_dual(P - p, a, 1e-9 * s), (p, P)
+        assert abs(P @ (P - p)) <= 1e-10 * s * s
+        Q = C.proj_pow_dual(p, a)
+        assert C.in_pow_dual(Q, a, 1e-9 * s) and C.in_pow(Q - p, a, 1e-9 * s)
+
+
+def test_pow_projection_is_nearest_point():
+    rng = np.random.default_rng(21)
+    a = 0.35
+    u = rng.exponential(2.0, (30000, 2))
+    cand = np.concatenate([u, (u[:, :1] ** a * u[:, 1:] ** (1 - a)) * rng.uniform(-1, 1, (30000, 1))], 1)
+    for _ in range(30):
+        p = rng.standard_normal(3) * 2
+        d = np.linalg.norm(C.proj_pow(p, a) - p)
+        assert np.min(np.linalg.norm(cand - p, axis=1)) >= d - 1e-9
+
+
+@pytest.mark.parametrize("a", [0.2, 0.5, 0.75])
+def test_pow_derivative_fd_symmetry_homogeneity(a):
+    rng = np.random.default_rng(int(1000 * a))
+    seen = 0
+    for _ in range(200):
+        p = rng.standard_normal(3) * 2
+        if C.in_pow(p, a, 1e-3) or C.in_pow_dual(-p, a, 1e-3) or abs(p[2]) < 1e-3:
+            continue
+        seen += 1
+        J = C.dproj_pow(p, a)
+        h = 1e-6
+        fd = np.stack([(C.proj_pow(p + h * e, a) - C.proj_pow(p - h * e, a)) / (2 * h) for e in np.eye(3)], 1)
+        np.testing.assert_allclose(J, fd, atol=2e-6 * (1 + np.abs(fd).max()))
+        np.testing.assert_allclose(J, J.T, atol=1e-12)
+        np.testing.assert_allclose(J @ p, C.proj_pow(p, a), atol=1e-9 * (1 + np.abs(p).max()))
+    assert seen > 50
+
+
+def test_pow_special_cases():
+    a = 0.5
+    np.testing.assert_allclose(C.dproj_pow(np.array([1.0, 4.0, 1.0]), a), np.eye(3))   # 1^.5 4^.5 = 2 >= 1
+    np.testing.assert_allclose(C.dproj_pow(np.array([-1.0, -4.0, 0.5]), a), np.zeros((3, 3)))
+    # z = 0 off both cones: (x+, y+, 0); d from the case table, d_x = x / (2|y| + x) at a = 1/2
+    p = np.array([2.0, -1.0, 0.0])
+    np.testing.assert_allclose(C.proj_pow(p, a), [2.0, 0.0, 0.0])
+    np.testing.assert_allclose(C.dproj_pow(p, a), np.diag([1.0, 0.0, 2.0 / 4.0]))
+    h = 1e-6
+    fd = (C.proj_pow(p + [0, 0, h], a) - C.proj_pow(p - [0, 0, h], a)) / (2 * h)
+    np.testing.assert_allclose(fd, [0.0, 0.0, 0.5], atol=1e-4)     # the case table's d_x, by differences
+    np.testing.assert_allclose(C.dproj_pow(p, 0.7), np.diag([1.0, 0.0, 1.0]))
+    np.testing.assert_allclose(C.dproj_pow(p, 0.3), np.diag([1.0, 0.0, 0.0]))
+    for aa, want in ((0.7, 1.0), (0.3, 0.0)):
+        fd = (C.proj_pow(p + [0, 0, h], aa) - C.proj_pow(p - [0, 0, h], aa)) / (2 * h)
+        assert abs(fd[2] - want) < 1e-3, (aa, fd)

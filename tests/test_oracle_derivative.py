@@ -35,7 +35,10 @@ SOCS = [lambda: g.small_qcp(21, 10, 2, 5, (3, 4, 5)),
         lambda: g.small_qcp(24, 14, 1, 4, (3,), psd_orders=(3, 2), psd_ranks=(1, 0)),
         lambda: g.small_qcp(25, 18, 0, 3, (), psd_orders=(4, 3), psd_ranks=(2, 3)),
         # exponential-cone blocks (Appendix A): boundary pairs and both interiors
-        lambda: g.small_qcp(31, 12, 1, 3, (3,), exp_kinds=("ray", "ray", "sint", "yint"))]
+        lambda: g.small_qcp(31, 12, 1, 3, (3,), exp_kinds=("ray", "ray", "sint", "yint")),
+        # power-cone blocks of several exponents
+        lambda: g.small_qcp(41, 12, 1, 3, (3,), pow_blocks=(("ray", 0.3), ("ray", 0.5), ("sint", 0.7),
+                                                           ("yint", 0.4)))]
 
 
 @pytest.mark.parametrize("mk", QPS)
