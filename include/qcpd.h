@@ -52,9 +52,11 @@
  *             (X11, sqrt2 X12, X22, sqrt2 X13, sqrt2 X23, X33, ...), so the
  *             layout preserves inner products; k <= 64) and QCP_CONE_EXP
  *             (the exponential cone cl{(x, y, z): y > 0, y e^(x/y) <= z},
- *             dim 3, Appendix A; the method projects onto its dual).  Plans
- *             with PSD or exponential blocks run on the pass and persistent
- *             engines.
+ *             dim 3) and QCP_CONE_POW (the power cone {(x, y, z): x, y >= 0,
+ *             x^a y^(1-a) >= |z|}, dim 3, exponent a from K.param), both of
+ *             Appendix A (the method projects onto their duals).  Plans with
+ *             PSD, exponential or power blocks run on the pass and
+ *             persistent engines.
  *  Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
  *             All work of a plan is enqueued on the stream given at creation.
  *             JVP/VJP calls return when the outputs are written: they
@@ -95,7 +97,8 @@ typedef enum {
     QCP_CONE_NONNEG = 1,
     QCP_CONE_SOC = 2,
     QCP_CONE_PSD = 3,
-    QCP_CONE_EXP = 4
+    QCP_CONE_EXP = 4,
+    QCP_CONE_POW = 5
 } qcp_cone_type;
 
 /* CSR matrix; all pointers are device pointers. */
@@ -111,6 +114,8 @@ typedef struct {
     int32_t nblocks;
     const int32_t* type;      /* qcp_cone_type */
     const int32_t* dim;       /* block sizes, each >= 1, summing to m */
+    const double* param;      /* per block: the exponent a in (0, 1) of a QCP_CONE_POW block (ignored
+                                 elsewhere); may be NULL when there is none */
 } qcp_cone;
 
 typedef struct {

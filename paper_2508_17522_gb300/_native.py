@@ -26,7 +26,7 @@ class qcp_csr(ctypes.Structure):
 
 
 class qcp_cone(ctypes.Structure):
-    _fields_ = [("nblocks", c_int32), ("type", c_void_p), ("dim", c_void_p)]
+    _fields_ = [("nblocks", c_int32), ("type", c_void_p), ("dim", c_void_p), ("param", c_void_p)]
 
 
 class qcp_problem(ctypes.Structure):

@@ -59,6 +59,7 @@ class ProblemTensors:
     b: torch.Tensor
     cone_type: np.ndarray
     cone_dim: np.ndarray
+    cone_param: np.ndarray
     x: torch.Tensor
     y: torch.Tensor
     s: torch.Tensor
@@ -66,7 +67,8 @@ class ProblemTensors:
 
 def problem_tensors(prob, device="cuda", dtype=torch.float64, with_perm=True) -> ProblemTensors:
     """Copy a problem (any object with the fields n, m, P, A, AT, AT_perm, q,
-    b, cone_type, cone_dim, x, y, s; P/A/AT having indptr, indices, data) to
+    b, cone_type, cone_dim, x, y, s and optionally cone_param; P/A/AT having
+    indptr, indices, data) to
     device tensors of the given floating-point dtype."""
     i64, i32 = torch.int64, torch.int32
     return ProblemTensors(
@@ -77,6 +79,8 @@ def problem_tensors(prob, device="cuda", dtype=torch.float64, with_perm=True) ->
         _t(prob.AT_perm, device, i64) if (with_perm and prob.AT_perm is not None) else None,
         _t(prob.q, device, dtype), _t(prob.b, device, dtype),
         np.ascontiguousarray(prob.cone_type, dtype=np.int32), np.ascontiguousarray(prob.cone_dim, dtype=np.int32),
+        np.ascontiguousarray(getattr(prob, "cone_param", None) if getattr(prob, "cone_param", None) is not None
+                             else np.zeros(len(prob.cone_type)), dtype=np.float64),
         _t(prob.x, device, dtype), _t(prob.y, device, dtype), _t(prob.s, device, dtype))
 
 
@@ -84,7 +88,7 @@ def _c_problem(pt: ProblemTensors):
     def csr(nr, nc, ip, ix, v):
         return N.qcp_csr(nr, nc, int(ix.numel()), _vp(ip), _vp(ix), _vp(v))
     cone = N.qcp_cone(len(pt.cone_type), pt.cone_type.ctypes.data_as(ctypes.c_void_p),
-                      pt.cone_dim.ctypes.data_as(ctypes.c_void_p))
+                      pt.cone_dim.ctypes.data_as(ctypes.c_void_p), pt.cone_param.ctypes.data_as(ctypes.c_void_p))
     prob = N.qcp_problem(pt.n, pt.m, csr(pt.n, pt.n, pt.P_indptr, pt.P_indices, pt.P_data),
                          csr(pt.m, pt.n, pt.A_indptr, pt.A_indices, pt.A_data),
                          csr(pt.n, pt.m, pt.AT_indptr, pt.AT_indices, pt.AT_data),

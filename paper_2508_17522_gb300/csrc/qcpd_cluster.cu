@@ -91,7 +91,7 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
     }
     for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
         const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-        if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP) {
+        if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP || t == QCP_CONE_POW) {
             row += d;
             nbr += d;
             ++nsb;
@@ -142,7 +142,7 @@ static bool cluster_split(const qcp_plan* p, int pi, int C, int lcap, ClusterPro
         int nl = 0, bi = 0;
         for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
             const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP) {
+            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP || t == QCP_CONE_POW) {
                 if (bi >= cp.cb[r] && bi < cp.cb[r + 1] && d > kSocThread) ++nl;
                 ++bi;
             }

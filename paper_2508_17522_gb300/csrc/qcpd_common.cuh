@@ -98,7 +98,8 @@ struct SocBlock {
     double h, tq;    // SOC: 1 / (2 r) and t / r^2 (kase 2), so no kernel divides
     int64_t psd;     // PSD: offset of its k x k eigenvectors V and weights B in the plan's block array;
                      // dense: offset of its dim x dim D Pi (row-major)
-    int64_t pad;
+    int32_t cone;    // qcp_cone_type of the block (dense blocks: QCP_CONE_EXP or QCP_CONE_POW; t holds a pow's a)
+    int32_t pad;
 };
 
 constexpr int kPsdMaxOrder = 64;  // largest PSD block order (its scratch is 2 k^2 doubles of shared memory)

@@ -465,15 +465,89 @@ __device__ void exp_dproj(const double* p, double* Dm) {
         for (int j = 0; j < 3; ++j) Dm[i * 3 + j] = J[i][4 + j];
 }
 
-// Per exponential-cone block (one thread each): D Pi onto the dual cone at
-// z_y, by the Moreau decomposition D Pi_{K*}(z) = I - D Pi_K(-z).
+// ---- power cone K_pow,a = {(x, y, z): x, y >= 0, x^a y^(1-a) >= |z|} (Appendix A)
+__device__ bool pow_in(double x, double y, double z, double a) {
+    return x >= 0.0 && y >= 0.0 && pow(x, a) * pow(y, 1.0 - a) >= fabs(z);
+}
+
+__device__ bool pow_dual_in(double u, double v, double w, double a) {
+    return u >= 0.0 && v >= 0.0 && pow(u / a, a) * pow(v / (1.0 - a), 1.0 - a) >= fabs(w);
+}
+
+__device__ void pow_f(double x, double y, double az, double a, double r, double& fx, double& fy) {
+    fx = 0.5 * (x + sqrt(x * x + 4.0 * a * r * (az - r)));
+    fy = 0.5 * (y + sqrt(y * y + 4.0 * (1.0 - a) * r * (az - r)));
+}
+
+__device__ double pow_g(double x, double y, double az, double a, double r) {
+    double fx, fy;
+    pow_f(x, y, az, a, r, fx, fy);
+    return pow(fx, a) * pow(fy, 1.0 - a) - r;
+}
+
+// D Pi of the projection onto K_pow,a at p (3 x 3, row-major), from the
+// cases of Appendix A: I inside K, 0 inside the polar cone, the z = 0 case
+// table, else the formula of its Theorem (Hien 2015, Theorem 3.1) at the
+// root r in (0, |z|) of r = f_x(r)^a f_y(r)^(1-a).  r = 0 solves that
+// equation as well when x <= 0 or y <= 0, so the bracket starts at the
+// largest |z| 10^-k (k >= 1) with a positive residual; 200 bisections.
+__device__ void pow_dproj(const double* p, double a, double* Dm) {
+    for (int i = 0; i < 9; ++i) Dm[i] = 0.0;
+    const double x = p[0], y = p[1], z = p[2];
+    if (pow_in(x, y, z, a)) {
+        Dm[0] = Dm[4] = Dm[8] = 1.0;
+        return;
+    }
+    if (pow_dual_in(-x, -y, -z, a)) return;
+    if (z == 0.0) {
+        double d = 0.0;
+        if (x > 0.0 && y < 0.0) d = a > 0.5 ? 1.0 : (a < 0.5 ? 0.0 : x / (2.0 * fabs(y) + x));
+        else if (y > 0.0 && x < 0.0) d = a < 0.5 ? 1.0 : (a > 0.5 ? 0.0 : y / (2.0 * fabs(x) + y));
+        Dm[0] = x > 0.0 ? 1.0 : 0.0;
+        Dm[4] = y > 0.0 ? 1.0 : 0.0;
+        Dm[8] = d;
+        return;
+    }
+    const double az = fabs(z), sz = z > 0.0 ? 1.0 : -1.0;
+    double lo = -1.0, hi = az;
+    double scale = az;
+    for (int k = 1; k < 300 && lo < 0.0; ++k) {
+        scale *= 0.1;
+        if (pow_g(x, y, az, a, scale) > 0.0) lo = scale;
+    }
+    double r = 0.0;
+    if (lo > 0.0) {
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (pow_g(x, y, az, a, mid) > 0.0) lo = mid;
+            else hi = mid;
+        }
+        r = 0.5 * (lo + hi);
+    }
+    double fx, fy;
+    pow_f(x, y, az, a, r, fx, fy);
+    const double gx = 2.0 * fx - x, gy = 2.0 * fy - y;
+    const double cx = a * x / gx, cy = (1.0 - a) * y / gy;
+    const double T = -(cx + cy);
+    const double L = 2.0 * (az - r) / (az + (az - 2.0 * r) * (cx + cy));
+    Dm[0] = 0.5 + x / (2.0 * gx) + a * a * (az - 2.0 * r) * r * L / (gx * gx);
+    Dm[1] = Dm[3] = (a - a * a) * (az - 2.0 * r) * r * L / (gx * gy);
+    Dm[2] = Dm[6] = sz * a * r * L / gx;
+    Dm[4] = 0.5 + y / (2.0 * gy) + (1.0 - a) * (1.0 - a) * (az - 2.0 * r) * r * L / (gy * gy);
+    Dm[5] = Dm[7] = sz * (1.0 - a) * r * L / gy;
+    Dm[8] = r / az + r / az * T * L;
+}
+
+// Per exponential- or power-cone block (one thread each): D Pi onto the
+// dual cone at z_y, by the Moreau decomposition D Pi_{K*}(z) = I - D Pi_K(-z).
 __global__ void k_expprep(const SocBlock* blk, int64_t nb, const double* zy, double* dense) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nb || blk[b].kase != kBlockDense) return;
     const SocBlock B = blk[b];
     const double p[3] = {-zy[B.start], -zy[B.start + 1], -zy[B.start + 2]};
     double Dk[9];
-    exp_dproj(p, Dk);
+    if (B.cone == QCP_CONE_POW) pow_dproj(p, B.t, Dk);
+    else exp_dproj(p, Dk);
     double* D = dense + B.psd;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) D[i * 3 + j] = (i == j ? 1.0 : 0.0) - Dk[i * 3 + j];
@@ -760,7 +834,7 @@ static void cut_tiles(const qcp_plan* p, int pi, std::vector<Tile>& out, int& rm
     int sb = 0;
     for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
         const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
-        if (t != QCP_CONE_SOC && t != QCP_CONE_PSD && t != QCP_CONE_EXP) {  // coupled blocks stay in one tile
+        if (t != QCP_CONE_SOC && t != QCP_CONE_PSD && t != QCP_CONE_EXP && t != QCP_CONE_POW) {  // coupled blocks: one tile
             for (int r = row; r < row + d; ++r) single_row(r);
         } else {
             const int64_t nz = rp[row + d] - rp[row];
@@ -1112,9 +1186,14 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
         for (int b = 0; b < q.K.nblocks; ++b) {
             const int t = q.K.type[b], d = q.K.dim[b];
             if ((t != QCP_CONE_ZERO && t != QCP_CONE_NONNEG && t != QCP_CONE_SOC && t != QCP_CONE_PSD &&
-                 t != QCP_CONE_EXP) ||
-                d < 1 || (t == QCP_CONE_EXP && d != 3)) {
+                 t != QCP_CONE_EXP && t != QCP_CONE_POW) ||
+                d < 1 || ((t == QCP_CONE_EXP || t == QCP_CONE_POW) && d != 3)) {
                 set_error("problem %d: cone block %d has type %d dim %d", i, b, t, d);
+                return QCP_ERR_ARG;
+            }
+            const double alpha = (t == QCP_CONE_POW && q.K.param) ? q.K.param[b] : 0.0;
+            if (t == QCP_CONE_POW && !(alpha > 0.0 && alpha < 1.0)) {
+                set_error("problem %d: power-cone block %d needs an exponent in (0, 1) in K.param", i, b);
                 return QCP_ERR_ARG;
             }
             int order = 0;
@@ -1126,13 +1205,15 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
                     return QCP_ERR_ARG;
                 }
             }
-            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP) {
+            if (t == QCP_CONE_SOC || t == QCP_CONE_PSD || t == QCP_CONE_EXP || t == QCP_CONE_POW) {
                 SocBlock sb{};
                 sb.start = (int)(q.n + msum);
                 sb.dim = d;
-                if (t == QCP_CONE_EXP) {
+                sb.cone = t;
+                if (t == QCP_CONE_EXP || t == QCP_CONE_POW) {
                     sb.kase = kBlockDense;
                     sb.order = 3;
+                    sb.t = alpha;
                     sb.psd = psd_off;
                     psd_off += 9;
                     ++p->ndense;

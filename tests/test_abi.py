@@ -47,8 +47,8 @@ def test_options_defaults_without_gpu(lib):
 def test_struct_layout():
     from paper_2508_17522_gb300 import _native as N
     assert ctypes.sizeof(N.qcp_csr) == 48
-    assert ctypes.sizeof(N.qcp_cone) == 24
-    assert ctypes.sizeof(N.qcp_problem) == 16 + 3 * 48 + 24 + 24
+    assert ctypes.sizeof(N.qcp_cone) == 32
+    assert ctypes.sizeof(N.qcp_problem) == 16 + 3 * 48 + 24 + 32
     assert ctypes.sizeof(N.qcp_options) == 72
     assert ctypes.sizeof(N.qcp_info) == 40
 

@@ -1,10 +1,11 @@
-"""The exponential cone (Appendix A) on the GPU: D Pi onto the dual cone made
-at plan time per block (Moreau: I - D Pi_K(-z), the primal projection's
-nearest boundary ray found by a scan and bisection, its derivative from the
-optimality conditions' Jacobian) and applied as a dense 3 x 3 per pass, on
-the pass and persistent engines, against the CPU FP64 oracle (whose
-projection is a nearest-point search of its own, pinned by membership,
-orthogonality and finite differences)."""
+"""The exponential and power cones (Appendix A) on the GPU: D Pi onto the
+dual cone made at plan time per block (Moreau: I - D Pi_K(-z); the
+exponential cone's nearest boundary ray by a scan and bisection and its
+derivative from the optimality conditions' Jacobian; the power cone's root
+r by bisection and the printed derivative formula) and applied as a dense
+3 x 3 per pass, on the pass and persistent engines, against the CPU FP64
+oracle (its own searches, pinned by membership, orthogonality and finite
+differences)."""
 import numpy as np
 import pytest
 
@@ -20,6 +21,10 @@ EXPS = [
     ("exp_rays", lambda: g.small_qcp(32, 20, 0, 4, (), exp_kinds=("ray",) * 5)),
     ("exp_psd_soc", lambda: g.small_qcp(33, 24, 1, 4, (4,), psd_orders=(3,), psd_ranks=(1,),
                                         exp_kinds=("ray", "yint", "sint"))),
+    ("pow4", lambda: g.small_qcp(41, 12, 1, 3, (3,), pow_blocks=(("ray", 0.3), ("ray", 0.5), ("sint", 0.7),
+                                                                ("yint", 0.4)))),
+    ("pow_exp", lambda: g.small_qcp(42, 20, 0, 3, (), exp_kinds=("ray", "ray"),
+                                    pow_blocks=(("ray", 0.25), ("ray", 0.6), ("yint", 0.5)))),
 ]
 
 
@@ -52,7 +57,7 @@ def test_exp_jvp_vjp_match_oracle(q, name, mk, precond):
 
 
 def test_exp_in_a_batch(q):
-    probs = [EXPS[0][1](), g.config1(0), EXPS[2][1]()]
+    probs = [EXPS[0][1](), g.config1(0), EXPS[2][1](), EXPS[3][1]()]
     dirs = [g.make_directions(p, 9) for p in probs]
     plan = q.qcp_batch_plan_create([q.problem_tensors(p, "cuda") for p in probs], torch.float64)
     cat = lambda name: np.concatenate([getattr(dd, name) for dd in dirs])
@@ -68,3 +73,10 @@ def test_exp_in_a_batch(q):
                        D.vjp_dense(p, dd, fac)[:4]) < TOL64
         on, om, op, oa = on + p.n, om + p.m, op + p.P.nnz, oa + p.A.nnz
     plan.close()
+
+
+def test_pow_exponent_required(q):
+    prob = EXPS[3][1]()
+    bad = prob.with_values(cone_param=np.where(prob.cone_param > 0, 1.5, 0.0))
+    with pytest.raises(RuntimeError):
+        q.qcp_plan_create(q.problem_tensors(bad, "cuda"), torch.float64)
