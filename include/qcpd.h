@@ -425,8 +425,8 @@ int qcp_plan_scalings(const qcp_plan* plan, double* w, double* c);
    diagonal of D Pi; 11 log(||row of M||) / 4; 12 log(nnz(row of M) + 1) / 4;
    13 SOC block size / 32; 14 1 on an SOC block's entries after its first;
    15 feature 6 times feature 10 (0 where a feature does not apply).
-   QCP_ERR_ARG for plans with PSD blocks (the features cover the zero, R+
-   and SOC blocks). */
+   QCP_ERR_ARG for plans with PSD, exponential or power blocks (the
+   features cover the zero, R+ and SOC blocks). */
 int qcp_plan_features(qcp_plan* plan, float* out);
 
 typedef struct qcp_mlp qcp_mlp;

@@ -104,7 +104,7 @@ struct SocBlock {
 
 constexpr int kPsdMaxOrder = 64;  // largest PSD block order (its scratch is 2 k^2 doubles of shared memory)
 constexpr int kBlockPsd = 3;      // SocBlock::kase of a PSD block
-constexpr int kBlockDense = 4;    // SocBlock::kase of a block whose D Pi is a stored dense matrix (exponential cone)
+constexpr int kBlockDense = 4;    // SocBlock::kase of a block whose D Pi is a stored dense matrix (exp and power cones)
 
 // LSQR scalars of one system (Paige & Saunders' recurrences).
 struct LsqrState {

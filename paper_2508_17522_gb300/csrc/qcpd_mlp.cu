@@ -574,7 +574,7 @@ int qcp_plan_features(qcp_plan* p, float* out) {
         return QCP_ERR_ARG;
     }
     if (p->kpsd || p->ndense) {
-        set_error("qcp_plan_features: the features cover zero, R+ and SOC blocks; this plan has PSD or exp blocks");
+        set_error("qcp_plan_features: the features cover zero, R+ and SOC blocks; this plan has PSD, exp or power blocks");
         return QCP_ERR_ARG;
     }
     cudaStream_t st = p->stream;
