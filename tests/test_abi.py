@@ -56,3 +56,26 @@ def test_struct_layout():
 def test_built_for_sm103a_only():
     from paper_2508_17522_gb300 import buildlib
     assert buildlib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_argument_errors_without_gpu(lib):
+    """Calls the header documents as QCP_ERR_ARG on bad arguments return it
+    before any device work, with a message in qcp_last_error."""
+    from paper_2508_17522_gb300 import _native as N
+    QCP_ERR_ARG = 1
+    o = N.qcp_options()
+    lib.qcp_default_options(ctypes.byref(o))
+    info = (N.qcp_info * 2)()
+    assert lib.qcp_derivative_jvp(None, ctypes.byref(o), *([None] * 7), info) == QCP_ERR_ARG
+    assert lib.qcp_derivative_vjp(None, ctypes.byref(o), *([None] * 7), info) == QCP_ERR_ARG
+    assert lib.qcp_derivative_jvp_vjp_multi(None, ctypes.byref(o), 1, *([None] * 7), 1, *([None] * 7),
+                                            info) == QCP_ERR_ARG
+    assert lib.qcp_plan_set_cluster(None, 4) == QCP_ERR_ARG
+    assert lib.qcp_plan_set_schedule(None, 4096, 512, 1 << 20) == QCP_ERR_ARG
+    cnt = ctypes.c_int32()
+    assert lib.qcp_plan_autotune(None, ctypes.byref(o), 0, 1, 16, None, 0, ctypes.byref(cnt), None) == QCP_ERR_ARG
+    out = ctypes.c_void_p()
+    assert lib.qcp_plan_create(None, None, 0, 1, None, ctypes.byref(out)) == QCP_ERR_ARG
+    assert lib.qcp_plan_last_engine(None) == -1
+    assert lib.qcp_plan_last_launches(None) == 0
+    assert b"" != N.lib().qcp_last_error()
