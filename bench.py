@@ -255,6 +255,59 @@ def learned_bench(args, rank, local):
         pl.close()
 
 
+# --------------------------------------------------------------------------- batched form
+def config4_bench(args, rank, local):
+    """The batched QCP form on the first --problems problems of the uneven
+    batch (n ~ U[50, 3000], m ~ U[1.5, 3] n, R+ and SOC blocks, dense
+    P = G^T G + 1e-3 I): one batch plan, autotuned for the VJP (untimed),
+    then per step one batched JVP (one direction per problem) and one
+    batched VJP, rtol 1e-6, equilibration, engine auto.  value = solves/s of
+    the whole batch (2 x problems per step)."""
+    import torch
+    import qcpgen as g
+    import paper_2508_17522_gb300 as q
+    from paper_2508_17522_gb300.buildlib import build
+    build()
+    dev = torch.device("cuda", local)
+    probs = g.config4(seed=rank, n_problems=args.problems)
+    dirs = [g.make_directions(pr, 3) for pr in probs]
+    cat = lambda nm: torch.as_tensor(np.concatenate([getattr(d, nm) for d in dirs]), device=dev)
+    ins = {nm: cat(nm) for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
+    plan = q.qcp_batch_plan_create([q.problem_tensors(pr, dev) for pr in probs], torch.float64)
+    best, _ = plan.autotune("vjp", iters=16, opts=q.options(precond="equilibrate"))
+    opts = q.options(rtol=1e-6, maxiter=200000, precond="equilibrate", engine="auto")
+    its, stat = [], set()
+
+    def step():
+        *_, ji = q.qcp_derivative_jvp(plan, ins["dP"], ins["dA"], ins["dq"], ins["db"], opts)
+        *_, vi = q.qcp_derivative_vjp(plan, ins["wx"], ins["wy"], ins["ws"], opts)
+        return ji + vi
+
+    for _ in range(args.warmup):
+        step()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record()
+    for _ in range(args.steps):
+        info = step()
+        its += [i["iters"] for i in info]
+        stat |= {i["status"] for i in info}
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "JVP+VJP solves/sec at 1e-6 rel residual, batched", "value": 2 * len(probs) * args.steps / (ms / 1e3),
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"uneven batch, problems 0..{len(probs) - 1} of 512 (n ~ U[50, 3000], dense P)",
+                       "sum_n": int(sum(p.n for p in probs)), "sum_m": int(sum(p.m for p in probs)),
+                       "nnz_up_P": int(sum(p.P.nnz for p in probs)), "engine": plan.last_engine(), "autotuned": best,
+                       "iters_median": float(np.median(its)), "iters_max": int(max(its)), "status": sorted(stat)},
+            "gpu_launches": None, "e2e": None, "roofline": None, "cpu_baseline": None}), flush=True)
+    plan.close()
+
+
 # --------------------------------------------------------------------------- ranks
 def max_over_ranks(values, dist, device):
     """Element-wise maximum of per-rank timings over all ranks (the job
@@ -280,7 +333,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
-    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "example", "learned"])
+    ap.add_argument("--workload", default="config2",
+                    choices=["config1", "config2", "config3", "example", "learned", "config4"])
+    ap.add_argument("--problems", type=int, default=32,
+                    help="config4: how many of the batch's problems (drawn from their own streams, from 0)")
     ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
     ap.add_argument("--maxiter", type=int, default=400000,
                     help="Krylov iteration cap (lower it only for profiling runs: solves then stop early)")
@@ -323,6 +379,8 @@ def main():
     torch.cuda.set_device(local)
     if args.workload == "learned":
         return learned_bench(args, rank, local)
+    if args.workload == "config4":
+        return config4_bench(args, rank, local)
     dist = None
     if world > 1:
         import torch.distributed as dist
