@@ -163,10 +163,13 @@ typedef enum {
     QCP_ENGINE_CLUSTER = 2,     /* one thread-block cluster per system runs all of its iterations
                                    in one launch; the Krylov vectors live in the cluster's shared
                                    memory and only hardware cluster barriers separate passes.
-                                   Needs every system to fit (about 8 N + 56 N / C bytes per CTA
-                                   for C CTAs); QCP_ERR_ARG otherwise */
-    QCP_ENGINE_AUTO = 3,        /* QCP_ENGINE_CLUSTER when every system fits (and precond is not
-                                   QCP_PRECOND_DIAG), else PASSES */
+                                   Needs every system to fit (about 8 N + 60 N / C bytes per CTA
+                                   for C CTAs) and the cones to be zero, R+ and SOC blocks; LSQR
+                                   only; QCP_ERR_ARG otherwise */
+    QCP_ENGINE_AUTO = 3,        /* the plan's autotuned engine when qcp_plan_autotune has run;
+                                   PASSES for LSMR, QCP_PRECOND_DIAG / _JACOBI and plans with PSD,
+                                   exponential or power blocks; else QCP_ENGINE_CLUSTER when every
+                                   system fits, else PASSES */
     QCP_ENGINE_CLUSTER_FP64 = 4 /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,
