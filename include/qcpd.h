@@ -166,10 +166,11 @@ typedef enum {
                                    Needs every system to fit (about 8 N + 60 N / C bytes per CTA
                                    for C CTAs) and the cones to be zero, R+ and SOC blocks; LSQR
                                    only; QCP_ERR_ARG otherwise */
-    QCP_ENGINE_AUTO = 3,        /* the plan's autotuned engine when qcp_plan_autotune has run;
-                                   PASSES for LSMR, QCP_PRECOND_DIAG / _JACOBI and plans with PSD,
-                                   exponential or power blocks; else QCP_ENGINE_CLUSTER when every
-                                   system fits, else PASSES */
+    QCP_ENGINE_AUTO = 3,        /* QCP_PRECOND_DIAG / _JACOBI: PASSES.  Otherwise the plan's
+                                   autotuned engine when qcp_plan_autotune has run, else
+                                   QCP_ENGINE_CLUSTER; a cluster choice becomes PASSES for LSMR and
+                                   when a system does not fit or the plan has PSD, exponential or
+                                   power blocks */
     QCP_ENGINE_CLUSTER_FP64 = 4 /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,
