@@ -186,14 +186,21 @@ def dproj_exp(p):
     if x < 0 and y < 0:
         return np.diag([1.0, 0.0, 1.0 if z > 0 else 0.0])
     xs, ys, zs = proj_exp(p)
-    mu = zs - z
+    return np.linalg.inv(exp_kkt_jacobian(xs, ys, zs - z))[:3, :3]
+
+
+def exp_kkt_jacobian(xs, ys, mu):
+    """J of Appendix A: the Jacobian of the optimality conditions of the
+    projection onto the boundary z = y exp(x / y), at the projected point
+    (xs, ys) with multiplier mu.  The printed (2, 2) entry is garbled; it is
+    read as 1 + mu xs^2 exp(xs / ys) / ys^3, the matching entry of the
+    Hessian of y exp(x / y) - z."""
     e = np.exp(xs / ys)
-    J = np.array([
+    return np.array([
         [1.0 + mu * e / ys, -mu * xs * e / ys ** 2, 0.0, e],
         [-mu * xs * e / ys ** 2, 1.0 + mu * xs ** 2 * e / ys ** 3, 0.0, (1.0 - xs / ys) * e],
         [0.0, 0.0, 1.0, -1.0],
         [e, (1.0 - xs / ys) * e, -1.0, 0.0]])
-    return np.linalg.inv(J)[:3, :3]
 
 
 def proj_exp_dual(q):
