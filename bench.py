@@ -371,7 +371,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc, "rtol": rtol},
             "cpu_baseline": {"value": val, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} full steps of the dense-LU oracle on the host"},
+                             "sample": f"{args.steps} full step{'' if args.steps == 1 else 's'} of the dense-LU oracle on the host"},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
