@@ -232,6 +232,44 @@ def test_exp_derivative_fd_symmetry_homogeneity():
     assert seen > 50
 
 
+def _exp_by_construction(t, r, mu):
+    """A point with a known projection onto K_exp and the exact Jacobian of
+    that projection, from the boundary parametrisation alone.
+
+    a(r) = (r, 1, e^r) spans a boundary ray of K_exp and n(r) = (-e^r,
+    (r - 1) e^r, 1) lies on the boundary of K_exp* with <a, n> = 0, so for
+    t, mu > 0 the point p = t a(r) - mu n(r) projects to t a(r) (it meets the
+    three conditions of a projection onto a closed convex cone).  Along the
+    map theta = (t, r, mu) -> p the projection is theta -> t a(r), so
+    D Pi(p) = [dPi/dtheta] [dp/dtheta]^-1 exactly."""
+    e = np.exp(r)
+    a, n = np.array([r, 1.0, e]), np.array([-e, (r - 1.0) * e, 1.0])
+    da, dn = np.array([1.0, 0.0, e]), np.array([-e, r * e, 0.0])
+    dp = np.stack([a, t * da - mu * dn, -n], 1)
+    dpi = np.stack([a, t * da, np.zeros(3)], 1)
+    return t * a - mu * n, t * a, dpi @ np.linalg.inv(dp), dp
+
+
+def test_exp_projection_and_derivative_by_construction():
+    """Exact values, not finite differences: the oracle's Pi and D Pi (its
+    ray search and the J of Appendix A) agree with the boundary
+    parametrisation to rounding.  The parametrisation's own derivative is
+    checked by differences first."""
+    rng = np.random.default_rng(14)
+    for lo, hi in ((-30.0, -4.0), (-4.0, 3.0), (3.0, 8.0)):
+        for _ in range(60):
+            th = np.array([np.exp(rng.uniform(-3, 3)), rng.uniform(lo, hi), np.exp(rng.uniform(-3, 3))])
+            p, P, D, dp = _exp_by_construction(*th)
+            h = 1e-6 * (1 + np.abs(th))
+            fd = np.stack([(_exp_by_construction(*(th + h[k] * e))[0] -
+                            _exp_by_construction(*(th - h[k] * e))[0]) / (2 * h[k]) for k, e in enumerate(np.eye(3))], 1)
+            np.testing.assert_allclose(fd, dp, atol=1e-6 * (1 + np.abs(dp).max()))
+            np.testing.assert_allclose(C.proj_exp(p), P, atol=1e-12 * (1 + np.abs(P).max()))
+            np.testing.assert_allclose(C.dproj_exp(p), D, atol=1e-10)
+            # the dual cone by the Moreau decomposition: -p projects onto K* at mu n
+            np.testing.assert_allclose(C.dproj_exp_dual(-p), np.eye(3) - D, atol=1e-10)
+
+
 def test_exp_special_cases():
     """Inside K: identity; inside the polar cone: 0; x, y < 0: (x, 0, z+)."""
     p_in = np.array([0.0, 1.0, 2.0])            # 1 * exp(0) = 1 <= 2
@@ -287,6 +325,42 @@ def test_pow_derivative_fd_symmetry_homogeneity(a):
         np.testing.assert_allclose(J, J.T, atol=1e-12)
         np.testing.assert_allclose(J @ p, C.proj_pow(p, a), atol=1e-9 * (1 + np.abs(p).max()))
     assert seen > 50
+
+
+def _pow_by_construction(u, v, mu, a):
+    """The power cone's analogue of _exp_by_construction: b(u, v) = (u, v,
+    w), w = u^a v^(1-a), is on the boundary of K_pow,a; n(u, v) = (a w / u,
+    (1 - a) w / v, -1) is on the boundary of K_pow,a* with <b, n> = 0; so
+    p = b - mu n projects to b, and D Pi(p) = [dPi/dtheta] [dp/dtheta]^-1
+    along theta = (u, v, mu)."""
+    w = u ** a * v ** (1 - a)
+    b = np.array([u, v, w])
+    n = np.array([a * w / u, (1 - a) * w / v, -1.0])
+    bu, bv = np.array([1.0, 0.0, a * w / u]), np.array([0.0, 1.0, (1 - a) * w / v])
+    nu = np.array([a * (a - 1) * w / u ** 2, a * (1 - a) * w / (u * v), 0.0])
+    nv = np.array([a * (1 - a) * w / (u * v), -a * (1 - a) * w / v ** 2, 0.0])
+    dp = np.stack([bu - mu * nu, bv - mu * nv, -n], 1)
+    dpi = np.stack([bu, bv, np.zeros(3)], 1)
+    return b - mu * n, b, dpi @ np.linalg.inv(dp), dp
+
+
+@pytest.mark.parametrize("a", [0.1, 0.35, 0.5, 0.9])
+def test_pow_projection_and_derivative_by_construction(a):
+    """Exact values for the root search and Hien's formula, on both signs of
+    z (the cone is symmetric under z -> -z)."""
+    rng = np.random.default_rng(int(1000 * a) + 7)
+    S = np.diag([1.0, 1.0, -1.0])
+    for _ in range(60):
+        th = np.exp(rng.uniform(-3, 3, 3))
+        p, P, D, dp = _pow_by_construction(*th, a)
+        h = 1e-6 * th
+        fd = np.stack([(_pow_by_construction(*(th + h[k] * e), a)[0] -
+                        _pow_by_construction(*(th - h[k] * e), a)[0]) / (2 * h[k]) for k, e in enumerate(np.eye(3))], 1)
+        np.testing.assert_allclose(fd, dp, atol=1e-6 * (1 + np.abs(dp).max()))
+        np.testing.assert_allclose(C.proj_pow(p, a), P, atol=1e-12 * (1 + np.abs(P).max()))
+        np.testing.assert_allclose(C.dproj_pow(p, a), D, atol=1e-11)
+        np.testing.assert_allclose(C.proj_pow(S @ p, a), S @ P, atol=1e-12 * (1 + np.abs(P).max()))
+        np.testing.assert_allclose(C.dproj_pow(S @ p, a), S @ D @ S, atol=1e-11)
 
 
 def test_pow_special_cases():

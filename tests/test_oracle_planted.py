@@ -5,8 +5,8 @@ wrong index, a flipped sign, a lost scale factor, the other reading of a
 garbled entry) and runs an unchanged pin from test_oracle_cones.py, which
 must then fail.  The pins are properties fixed by the mathematics (finite
 differences, the conditions that define a projection, the isometry of the
-PSD layout), so a pin that let one of these through would be too weak to
-certify the oracle.
+PSD layout, exact values built from a cone's boundary), so a pin that let
+one of these through would be too weak to certify the oracle.
 """
 import numpy as np
 import pytest
@@ -102,8 +102,9 @@ def test_psd_layout_without_sqrt2(monkeypatch):
 # ---------------------------------------------------------- exponential cone
 def test_exp_other_reading_of_the_garbled_entry(monkeypatch):
     """The printed (2, 2) entry of J reads "1 + -"; taking it as
-    1 - mu x^2 e^{x/y} / y^3 fails the finite differences, which the oracle's
-    reading (the Hessian entry, with a plus) passes."""
+    1 - mu x^2 e^{x/y} / y^3 fails the finite differences and the exact
+    values, which the oracle's reading (the Hessian entry, with a plus)
+    passes."""
     orig = C.exp_kkt_jacobian
 
     def bad(xs, ys, mu):
@@ -113,6 +114,7 @@ def test_exp_other_reading_of_the_garbled_entry(monkeypatch):
 
     monkeypatch.setattr(C, "exp_kkt_jacobian", bad)
     _fails(pins.test_exp_derivative_fd_symmetry_homogeneity)
+    _fails(pins.test_exp_projection_and_derivative_by_construction)
 
 
 def test_exp_dual_moreau_sign(monkeypatch):
@@ -127,6 +129,7 @@ def test_exp_multiplier_sign(monkeypatch):
     orig = C.exp_kkt_jacobian
     monkeypatch.setattr(C, "exp_kkt_jacobian", lambda xs, ys, mu: orig(xs, ys, -mu))
     _fails(pins.test_exp_derivative_fd_symmetry_homogeneity)
+    _fails(pins.test_exp_projection_and_derivative_by_construction)
 
 
 # --------------------------------------------------------------- power cone
@@ -140,6 +143,7 @@ def test_pow_exponents_swapped_in_f_y(monkeypatch):
 
     monkeypatch.setattr(C, "_pow_f", bad)
     _fails(pins.test_pow_projection_characterised, 0.2)
+    _fails(pins.test_pow_projection_and_derivative_by_construction, 0.35)
 
 
 def test_pow_dropped_sign_of_z(monkeypatch):
@@ -157,3 +161,4 @@ def test_pow_dropped_sign_of_z(monkeypatch):
 
     monkeypatch.setattr(C, "dproj_pow", bad)
     _fails(pins.test_pow_derivative_fd_symmetry_homogeneity, 0.5)
+    _fails(pins.test_pow_projection_and_derivative_by_construction, 0.5)
