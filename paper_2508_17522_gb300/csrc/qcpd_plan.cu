@@ -1198,8 +1198,9 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
             }
             int order = 0;
             if (t == QCP_CONE_PSD) {
-                while ((order + 1) * (order + 2) / 2 <= d) ++order;
-                if (order * (order + 1) / 2 != d || order > kPsdMaxOrder) {
+                // 64-bit and capped one past the largest order, so any dim terminates
+                while (order <= kPsdMaxOrder && (int64_t)(order + 1) * (order + 2) / 2 <= d) ++order;
+                if ((int64_t)order * (order + 1) / 2 != d || order > kPsdMaxOrder) {
                     set_error("problem %d: PSD block %d has %d entries: need k (k + 1) / 2 with k <= %d", i, b, d,
                               kPsdMaxOrder);
                     return QCP_ERR_ARG;
