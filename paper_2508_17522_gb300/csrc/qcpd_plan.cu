@@ -1191,6 +1191,10 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
                 set_error("problem %d: cone block %d has type %d dim %d", i, b, t, d);
                 return QCP_ERR_ARG;
             }
+            if (msum + d > q.m) {  // before any per-row storage grows
+                set_error("problem %d: cone dimensions exceed m = %lld at block %d", i, (long long)q.m, b);
+                return QCP_ERR_ARG;
+            }
             const double alpha = (t == QCP_CONE_POW && q.K.param) ? q.K.param[b] : 0.0;
             if (t == QCP_CONE_POW && !(alpha > 0.0 && alpha < 1.0)) {
                 set_error("problem %d: power-cone block %d needs an exponent in (0, 1) in K.param", i, b);
