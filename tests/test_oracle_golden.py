@@ -76,3 +76,25 @@ def test_psd_projection_golden():
     np.testing.assert_allclose(C.dproj_psd(np.array(g["z"])) @ np.array(g["dproj_dir"]), g["dproj_times_dir"],
                                atol=1e-14)
     np.testing.assert_allclose(C.dproj_psd(np.array(g["z_diag"])), g["dproj_diag"], atol=1e-14)
+
+
+def test_exp_projection_golden():
+    """Hand-derived values on the exponential cone (fixture: its derivation)."""
+    g = GOLD["exp_projection"]
+    p = np.array(g["p"])
+    np.testing.assert_allclose(C.proj_exp(p), g["proj"], atol=1e-14)
+    np.testing.assert_allclose(C.dproj_exp(p), g["dproj"], atol=1e-13)
+    # the dual cone by the Moreau decomposition: -p projects onto K_exp* at mu n
+    np.testing.assert_allclose(C.proj_exp_dual(-p), -p + np.array(g["proj"]), atol=1e-14)
+    np.testing.assert_allclose(C.dproj_exp_dual(-p), np.eye(3) - np.array(g["dproj"]), atol=1e-13)
+
+
+def test_pow_projection_golden():
+    """Hand-derived values on the power cone at a = 1/2, both signs of z."""
+    g = GOLD["pow_projection"]
+    p, a = np.array(g["p"]), g["a"]
+    S = np.diag([1.0, 1.0, -1.0])
+    np.testing.assert_allclose(C.proj_pow(p, a), g["proj"], atol=1e-14)
+    np.testing.assert_allclose(C.dproj_pow(p, a), g["dproj"], atol=1e-13)
+    np.testing.assert_allclose(C.proj_pow(S @ p, a), S @ np.array(g["proj"]), atol=1e-14)
+    np.testing.assert_allclose(C.dproj_pow(S @ p, a), S @ np.array(g["dproj"]) @ S, atol=1e-13)
