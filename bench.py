@@ -354,9 +354,9 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        prob, dirs, rtol, desc = workload(args.workload, 0)
         if args.workload not in ("config1", "config2", "example"):
-            raise SystemExit("the oracle reference arm covers the dense-LU workloads (config2, example)")
+            raise SystemExit("the oracle reference arm covers the dense-LU workloads (config1, config2, example)")
+        prob, dirs, rtol, desc = workload(args.workload, 0)
         for _ in range(args.warmup):
             oracle_step(prob, dirs)
         t0 = time.perf_counter()

@@ -4,6 +4,7 @@ every rank's solves, and under torchrun the reference arm runs on rank 0
 alone (the other ranks exit 0 without work).  No GPU is used."""
 import json
 import os
+import shutil
 import socket
 import subprocess
 import sys
@@ -58,7 +59,14 @@ def test_reference_arm_under_torchrun_prints_once():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
            "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--workload", "config1"]
-    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    # torchrun's scratch directories go under the repository, not the system temp dir
+    tmp = os.path.join(ROOT, ".tmp", f"torchrun_{os.getpid()}")
+    os.makedirs(tmp, exist_ok=True)
+    try:
+        out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600,
+                             env=dict(os.environ, TMPDIR=tmp))
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, out.stdout
