@@ -437,9 +437,21 @@ def dproj_dual(cones, z):
 
 
 def dproj_dual_sparse(cones, z):
-    """Same Jacobian as a scipy sparse block-diagonal matrix."""
+    """Same Jacobian as a scipy sparse block-diagonal matrix.  The zero and
+    R+ blocks are diagonal, so they are built as sparse diagonals (the same
+    entries as dproj_dual_block) and never stored densely."""
     import scipy.sparse as sp
-    blocks = [sp.csr_matrix(dproj_dual_block(t, z[a:b], par)) for t, a, b, par in _blocks(cones)]
+
+    def block(t, zb, par):
+        if t == ZERO:
+            return sp.identity(zb.shape[0], format="csr")
+        if t == NONNEG:
+            Db = sp.diags((zb > 0.0).astype(np.float64), format="csr")
+            Db.eliminate_zeros()
+            return Db
+        return sp.csr_matrix(dproj_dual_block(t, zb, par))
+
+    blocks = [block(t, z[a:b], par) for t, a, b, par in _blocks(cones)]
     if not blocks:
         return sp.csr_matrix((0, 0))
     return sp.block_diag(blocks, format="csr")
