@@ -343,6 +343,8 @@ def main():
     ap.add_argument("--call", default="pair", choices=["pair", "separate"],
                     help="pair: the JVPs and VJPs in one qcp_derivative_jvp_vjp_multi call (side by side on the "
                          "cluster engine); separate: one _multi call per kind")
+    ap.add_argument("--equil-sweeps", type=int, default=1,
+                    help="sweeps of the row/column equilibration (plan setting; 1 is the plan's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -399,6 +401,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     plan = q.qcp_plan_create(q.problem_tensors(prob, dev), torch.float64, max_rhs=2 * k, stream=stream)
+    if args.equil_sweeps != 1:
+        plan.set_equilibration(args.equil_sweeps)
     opts = q.options(rtol=rtol, maxiter=args.maxiter, precond=args.precond, engine=args.engine)
     cat = lambda nm: np.concatenate([getattr(d, nm) for d in dirs])
     host = {nm: torch.as_tensor(cat(nm)).pin_memory() for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
@@ -518,7 +522,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64" if engine == "cluster" else "f64",
             "data": "synthetic",
-            "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "solver": "LSQR", "engine": engine,
+            "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "equil_sweeps": args.equil_sweeps,
+                       "solver": "LSQR", "engine": engine,
                        "arithmetic": ("vectors in double-float (binary32 pairs), LSQR scalars f64, data f64"
                                       if engine == "cluster" else "f64"),
                        "call": ("qcp_derivative_jvp_vjp_multi (16 JVP + 16 VJP systems side by side)"

@@ -359,6 +359,19 @@ int qcp_plan_autotune(qcp_plan* plan, const qcp_options* opts, int32_t mode, int
    them.  Returns QCP_ERR_ARG for other values. */
 int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas);
 
+/* Sweeps of the QCP_PRECOND_EQUILIBRATE scaling (an addition to the
+   paper's plain Krylov solve of Sec. 3.3): 1 (the default, set at plan
+   creation) to 64.  One sweep takes w = 1 / row norms of F and then
+   c = 1 / column norms of W F, with D Pi by its diagonal and c constant on
+   every coupled block; each further sweep recomputes w from the rows of F C
+   and c from the new W F.  Both systems are consistent, so the outputs do
+   not change, only the iteration count.  The plan recomputes w, c and its
+   scaled copies of M on its stream before returning.  Errors: QCP_ERR_ARG
+   for a NULL plan, sweeps outside 1 to 64, or a plan that has already run
+   a derivative or autotune call (w and c are then part of its captured
+   graphs and cluster layouts); QCP_ERR_ALLOC, QCP_ERR_CUDA. */
+int qcp_plan_set_equilibration(qcp_plan* plan, int32_t sweeps);
+
 /* The qcp_engine the most recent JVP/VJP call of the plan ran: PASSES,
    PERSISTENT, CLUSTER (double-float vector arithmetic) or CLUSTER_FP64; -1
    for a NULL plan. */

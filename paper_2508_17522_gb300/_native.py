@@ -121,6 +121,8 @@ def lib():
     L.qcp_plan_last_engine.argtypes = [c_void_p]
     L.qcp_plan_set_cluster.restype = ctypes.c_int
     L.qcp_plan_set_cluster.argtypes = [c_void_p, c_int32]
+    L.qcp_plan_set_equilibration.restype = ctypes.c_int
+    L.qcp_plan_set_equilibration.argtypes = [c_void_p, c_int32]
     L.qcp_plan_last_launches.restype = c_int64
     L.qcp_plan_last_launches.argtypes = [c_void_p]
     L.qcp_plan_last_timing.restype = ctypes.c_int

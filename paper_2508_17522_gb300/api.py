@@ -223,6 +223,12 @@ class Plan:
         """CTAs per system of the cluster engine (0: chosen per call)."""
         _check(N.lib().qcp_plan_set_cluster(self._h, int(max_ctas)), "qcp_plan_set_cluster")
 
+    def set_equilibration(self, sweeps: int = 1):
+        """Sweeps of the row/column equilibration (1 to 64, before the first
+        derivative or autotune call); more sweeps mean fewer Krylov
+        iterations on badly scaled problems, with the same outputs."""
+        _check(N.lib().qcp_plan_set_equilibration(self._h, int(sweeps)), "qcp_plan_set_equilibration")
+
     def set_schedule(self, tile_nnz: int = 4096, long_row: int = 512, long_chunk: int = 1 << 20):
         _check(N.lib().qcp_plan_set_schedule(self._h, int(tile_nnz), int(long_row), int(long_chunk)),
                "qcp_plan_set_schedule")

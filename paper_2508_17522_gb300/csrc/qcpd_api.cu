@@ -1157,6 +1157,23 @@ int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas) {
     return QCP_OK;
 }
 
+int qcp_plan_set_equilibration(qcp_plan* plan, int32_t sweeps) {
+    if (!plan || sweeps < 1 || sweeps > 64) {
+        set_error("qcp_plan_set_equilibration: null plan or sweeps outside 1 to 64");
+        return QCP_ERR_ARG;
+    }
+    // w and c are baked into captured graphs, cluster layouts and the
+    // autotuner's timings, so they may change only before any of those exist
+    if (plan->last_mode >= 0 || !plan->graphs.empty() || !plan->clusters.empty() || plan->tuned_engine >= 0) {
+        set_error("qcp_plan_set_equilibration: call it before the plan's first derivative or autotune call");
+        return QCP_ERR_ARG;
+    }
+    if (sweeps == plan->equil_sweeps) return QCP_OK;
+    const int rc = equilibrate_plan(plan, sweeps);
+    if (rc == QCP_OK) plan->equil_sweeps = sweeps;
+    return rc;
+}
+
 int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }
 
 int qcp_plan_last_engine(const qcp_plan* plan) { return plan ? plan->last_engine : -1; }

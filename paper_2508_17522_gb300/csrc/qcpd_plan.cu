@@ -659,11 +659,14 @@ __global__ void k_dd_psd(const SocBlock* blk, int64_t nb, const double* psd, dou
 //   y-row j: ||A_j||^2 + (1 - D_jj)^2 + b_j^2
 //   tau row: ||g||^2 + sum_j (D_jj b_j)^2 + kappa^2
 // w = 1 / norm.  One warp per row; tau through the tile reduction.
-template <typename T>
+// With CW, the norms are those of F C: every entry in column j is weighted
+// by cw_j (the current column scaling), for the repeated sweeps of the
+// equilibration; without CW the arithmetic is that of the plain row norms.
+template <typename T, bool CW>
 __global__ void __launch_bounds__(kThreads) k_prec_rows(const Tile* tiles, const Prob* probs, const Sys* psys,
                                                         Reduce R, const int64_t* mrowptr, const int32_t* mcol,
                                                         const T* mval, const double* coefA, const double* coefB,
-                                                        const double* dd, double* rw) {
+                                                        const double* dd, const double* cw, double* rw) {
     __shared__ Scratch scratch;
     const int ti = blockIdx.x;
     const Tile tl = tiles[ti];
@@ -672,6 +675,8 @@ __global__ void __launch_bounds__(kThreads) k_prec_rows(const Tile* tiles, const
     const int n = pr.n, N = pr.n + pr.m + 1;
     const int64_t* rp = mrowptr + pr.mrow;
     const double* d = dd + pr.doff;
+    const double* cwp = CW ? cw + pr.doff : nullptr;
+    const double cN2 = CW ? cwp[N - 1] * cwp[N - 1] : 1.0;  // the tau column's weight
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rend = (tl.kind == TILE_LONG && tl.cb0 != 0) ? tl.r0 : tl.r1;
     double ga = 0.0, gb = 0.0;
@@ -681,18 +686,35 @@ __global__ void __launch_bounds__(kThreads) k_prec_rows(const Tile* tiles, const
             const int32_t c = mcol[k];
             const double v = (double)mval[k];
             const double f = c < n ? 1.0 : d[c];
-            acc += v * v * f * f;
+            if (CW) {
+                const double vc = v * f * cwp[c];
+                acc += vc * vc;
+            } else {
+                acc += v * v * f * f;
+            }
         }
         acc = warp_sum(acc);
         if (lane == 0) {
             const double ca = (double)coefA[pr.doff + r];
-            acc += ca * ca;
-            if (r >= n) {
-                acc += (1.0 - d[r]) * (1.0 - d[r]);
-                gb += (d[r] * ca) * (d[r] * ca);
+            if (CW) {
+                const double cr2 = cwp[r] * cwp[r];  // weight of the row's own column (diagonal and tau row)
+                acc += ca * ca * cN2;
+                if (r >= n) {
+                    acc += (1.0 - d[r]) * (1.0 - d[r]) * cr2;
+                    gb += (d[r] * ca) * (d[r] * ca) * cr2;
+                } else {
+                    const double g = (double)coefB[pr.doff + r];
+                    ga += g * g * cr2;
+                }
             } else {
-                const double g = (double)coefB[pr.doff + r];
-                ga += g * g;
+                acc += ca * ca;
+                if (r >= n) {
+                    acc += (1.0 - d[r]) * (1.0 - d[r]);
+                    gb += (d[r] * ca) * (d[r] * ca);
+                } else {
+                    const double g = (double)coefB[pr.doff + r];
+                    ga += g * g;
+                }
             }
             rw[pr.doff + r] = acc > 0.0 ? 1.0 / sqrt(acc) : 1.0;
         }
@@ -701,7 +723,7 @@ __global__ void __launch_bounds__(kThreads) k_prec_rows(const Tile* tiles, const
     Part tot;
     if (!finish_tile(R, tl, sy.g0, sy.g1, ti, part, &tot, &scratch)) return;
     if (threadIdx.x == 0) {
-        const double t = tot.a + tot.b + pr.kappa * pr.kappa;
+        const double t = CW ? tot.a + tot.b + pr.kappa * pr.kappa * cN2 : tot.a + tot.b + pr.kappa * pr.kappa;
         rw[pr.doff + N - 1] = t > 0.0 ? 1.0 / sqrt(t) : 1.0;
     }
 }
@@ -1026,8 +1048,12 @@ static int run_pre(qcp_plan* p) {
 
 // Row and column scalings of F (qcp_precond QCP_PRECOND_EQUILIBRATE) and the
 // scaled copies of M's values.  Runs after k_pre (needs g and kappa).
+// One sweep: w = 1 / row norms of F, then c = 1 / column norms of W F (D by
+// its diagonal; c from the mean square over each coupled block).  Each
+// further sweep recomputes w from the row norms of F C with the current c,
+// then c from the new W F; the plan keeps the last w and c.
 template <typename T>
-static int run_equilibrate(qcp_plan* p) {
+static int run_equilibrate(qcp_plan* p, int sweeps) {
     Reduce R{p->d_ppart.as<Part>(), p->d_pgpart.as<Part>(), p->d_pgcnt.as<int32_t>(), p->d_pscnt.as<int32_t>(),
              p->d_pgroups.as<Group>()};
     int nt = 0;
@@ -1054,25 +1080,43 @@ static int run_equilibrate(qcp_plan* p) {
                 p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, p->d_psd.as<double>(), dd.as<double>() + pr.doff);
     }
     QCP_CUDA(cudaGetLastError());
-    if (nt) {
-        k_prec_rows<T><<<nt, kThreads, 0, st>>>(p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R,
-                                                p->d_mrowptr.as<int64_t>(), p->d_mcol.as<int32_t>(),
-                                                p->d_mval.as<T>(), p->d_coefA.as<double>(), p->d_coefB.as<double>(),
-                                                dd.as<double>(), p->d_rw.as<double>());
-        k_prec_cols<T><<<nt, kThreads, 0, st>>>(p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R,
-                                                p->d_mrowptr.as<int64_t>(), p->d_mcol.as<int32_t>(),
-                                                p->d_mval.as<T>(), p->d_coefA.as<double>(), p->d_coefB.as<double>(),
-                                                dd.as<double>(), p->d_rw.as<double>(), csq.as<double>());
+    // c from the column norms in csq (one value per coupled block)
+    auto columns_to_c = [&]() {
+        for (int i = 0; i < p->nprob; ++i) {
+            const Prob& pr = p->hprob[i];
+            k_cd_rows<<<grid_for((int64_t)pr.n + pr.m + 1, 256), 256, 0, st>>>(
+                csq.as<double>() + pr.doff, p->d_flag.as<int8_t>() + pr.doff, pr.n, pr.m,
+                p->d_cd.as<double>() + pr.doff);
+            if (pr.nsoc)
+                k_cd_soc<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
+                    p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, csq.as<double>() + pr.doff,
+                    p->d_cd.as<double>() + pr.doff);
+        }
+    };
+    for (int sweep = 0; sweep < sweeps; ++sweep) {
+        if (nt) {
+            if (sweep == 0)
+                k_prec_rows<T, false><<<nt, kThreads, 0, st>>>(
+                    p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R, p->d_mrowptr.as<int64_t>(),
+                    p->d_mcol.as<int32_t>(), p->d_mval.as<T>(), p->d_coefA.as<double>(), p->d_coefB.as<double>(),
+                    dd.as<double>(), nullptr, p->d_rw.as<double>());
+            else
+                k_prec_rows<T, true><<<nt, kThreads, 0, st>>>(
+                    p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R, p->d_mrowptr.as<int64_t>(),
+                    p->d_mcol.as<int32_t>(), p->d_mval.as<T>(), p->d_coefA.as<double>(), p->d_coefB.as<double>(),
+                    dd.as<double>(), p->d_cd.as<double>(), p->d_rw.as<double>());
+            k_prec_cols<T><<<nt, kThreads, 0, st>>>(p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(),
+                                                    R, p->d_mrowptr.as<int64_t>(), p->d_mcol.as<int32_t>(),
+                                                    p->d_mval.as<T>(), p->d_coefA.as<double>(),
+                                                    p->d_coefB.as<double>(), dd.as<double>(), p->d_rw.as<double>(),
+                                                    csq.as<double>());
+            QCP_CUDA(cudaGetLastError());
+        }
+        columns_to_c();
         QCP_CUDA(cudaGetLastError());
     }
     for (int i = 0; i < p->nprob; ++i) {
         const Prob& pr = p->hprob[i];
-        k_cd_rows<<<grid_for((int64_t)pr.n + pr.m + 1, 256), 256, 0, st>>>(
-            csq.as<double>() + pr.doff, p->d_flag.as<int8_t>() + pr.doff, pr.n, pr.m, p->d_cd.as<double>() + pr.doff);
-        if (pr.nsoc)
-            k_cd_soc<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
-                p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, csq.as<double>() + pr.doff,
-                p->d_cd.as<double>() + pr.doff);
         const int64_t k0 = p->h_mrowptr[pr.mrow], k1 = p->h_mrowptr[pr.mrow + pr.n + pr.m + 1];
         if (k1 > k0)
             k_scale_vals<T><<<grid_for(k1 - k0, 256), 256, 0, st>>>(
@@ -1082,6 +1126,10 @@ static int run_equilibrate(qcp_plan* p) {
     QCP_CUDA(cudaGetLastError());
     QCP_CUDA(cudaStreamSynchronize(st));
     return QCP_OK;
+}
+
+int equilibrate_plan(qcp_plan* p, int sweeps) {
+    return p->dtype == QCP_F64 ? run_equilibrate<double>(p, sweeps) : run_equilibrate<float>(p, sweeps);
 }
 
 // Column scaling of the Jacobi (column-norm) preconditioner: C = 1 / column
@@ -1492,7 +1540,7 @@ static int create_impl(qcp_plan* p, const qcp_problem* probs, const qcp_solution
     QCP_CUDA(cudaStreamSynchronize(st));
     // keep the host copy of kappa in step
     QCP_CUDA(cudaMemcpy(p->hprob.data(), p->d_prob.p, np * sizeof(Prob), cudaMemcpyDeviceToHost));
-    QCP_TRY(run_equilibrate<T>(p));
+    QCP_TRY(run_equilibrate<T>(p, p->equil_sweeps));
     return QCP_OK;
 }
 

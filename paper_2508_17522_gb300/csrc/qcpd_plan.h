@@ -146,6 +146,7 @@ struct qcp_plan {
     // cluster engine
     int cluster_cap = 0;  // CTAs per system asked for (0: per call from the number of systems)
     int tuned_engine = -1; // the autotuner's choice for QCP_ENGINE_AUTO (-1: none)
+    int equil_sweeps = 1;  // sweeps of the row/column equilibration behind d_rw and d_cd
     std::map<int, std::unique_ptr<qcpd::ClusterLayout>> clusters;  // by CTAs asked for
     qcpd::DevBuf d_csys;  // system lists of the cluster launches
     qcpd::DevBuf d_bcast; // broadcast buffers of the double-float cluster kernel
@@ -178,4 +179,7 @@ int build_schedule(qcp_plan* p);
 void drop_graphs(qcp_plan* p);
 // The Jacobi preconditioner's column scaling (N_tot doubles, device).
 int jacobi_cols(qcp_plan* p, double* out);
+// Recompute the equilibration's w and c with the given number of sweeps,
+// and the scaled copies of M's values.
+int equilibrate_plan(qcp_plan* p, int sweeps);
 }  // namespace qcpd

@@ -71,6 +71,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.qcp_derivative_jvp_vjp_multi(None, ctypes.byref(o), 1, *([None] * 7), 1, *([None] * 7),
                                             info) == QCP_ERR_ARG
     assert lib.qcp_plan_set_cluster(None, 4) == QCP_ERR_ARG
+    assert lib.qcp_plan_set_equilibration(None, 3) == QCP_ERR_ARG
     assert lib.qcp_plan_set_schedule(None, 4096, 512, 1 << 20) == QCP_ERR_ARG
     cnt = ctypes.c_int32()
     assert lib.qcp_plan_autotune(None, ctypes.byref(o), 0, 1, 16, None, 0, ctypes.byref(cnt), None) == QCP_ERR_ARG
