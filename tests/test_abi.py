@@ -80,3 +80,28 @@ def test_argument_errors_without_gpu(lib):
     assert lib.qcp_plan_last_engine(None) == -1
     assert lib.qcp_plan_last_launches(None) == 0
     assert b"" != N.lib().qcp_last_error()
+
+
+def test_header_is_plain_c():
+    """include/qcpd.h compiles as strict C99 (no C++ or torch types leak
+    into the boundary) and as C++."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    tmp = os.path.join(ROOT, ".tmp", f"hdr_{os.getpid()}")
+    os.makedirs(tmp, exist_ok=True)
+    try:
+        src = os.path.join(tmp, "use_header.c")
+        with open(src, "w") as f:
+            f.write('#include "qcpd.h"\n'
+                    "int main(void) { qcp_options o; qcp_default_options(&o); return (int)o.maxiter; }\n")
+        env = dict(os.environ, TMPDIR=tmp)
+        for cmd in ([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror"],
+                    [gcc, "-x", "c++", "-std=c++17", "-Wall", "-Werror"]):
+            out = subprocess.run(cmd + ["-I", os.path.join(ROOT, "include"), "-c", src, "-o",
+                                        os.path.join(tmp, "use_header.o")], capture_output=True, text=True, env=env)
+            assert out.returncode == 0, out.stderr
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
