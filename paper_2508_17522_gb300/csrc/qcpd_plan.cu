@@ -1051,7 +1051,10 @@ static int run_pre(qcp_plan* p) {
 // One sweep: w = 1 / row norms of F, then c = 1 / column norms of W F (D by
 // its diagonal; c from the mean square over each coupled block).  Each
 // further sweep recomputes w from the row norms of F C with the current c,
-// then c from the new W F; the plan keeps the last w and c.
+// then c from the new W F; the plan keeps the last w and c.  Everything is
+// built in buffers of its own and swapped into the plan only once every
+// kernel has run, so a failure (allocation or CUDA) leaves the plan's
+// previous scaling in place.
 template <typename T>
 static int run_equilibrate(qcp_plan* p, int sweeps) {
     Reduce R{p->d_ppart.as<Part>(), p->d_pgpart.as<Part>(), p->d_pgcnt.as<int32_t>(), p->d_pscnt.as<int32_t>(),
@@ -1059,15 +1062,15 @@ static int run_equilibrate(qcp_plan* p, int sweeps) {
     int nt = 0;
     for (auto& v : p->ptiles) nt += (int)v.size();
     cudaStream_t st = p->stream;
-    DevBuf dd, csq;
+    DevBuf dd, csq, rwb, cdb, mvalG, mvalT;
     QCP_TRY(dd.alloc(p->N_tot * sizeof(double)));
     QCP_TRY(csq.alloc(p->N_tot * sizeof(double)));
-    QCP_TRY(p->d_rw.alloc(p->N_tot * sizeof(double)));
-    QCP_TRY(p->d_cd.alloc(p->N_tot * sizeof(double)));
-    QCP_TRY(p->d_mvalG.alloc((p->mnnz + 16) * sizeof(T)));
-    QCP_TRY(p->d_mvalT.alloc((p->mnnz + 16) * sizeof(T)));
-    QCP_CUDA(cudaMemsetAsync(p->d_mvalG.p, 0, (p->mnnz + 16) * sizeof(T), st));
-    QCP_CUDA(cudaMemsetAsync(p->d_mvalT.p, 0, (p->mnnz + 16) * sizeof(T), st));
+    QCP_TRY(rwb.alloc(p->N_tot * sizeof(double)));
+    QCP_TRY(cdb.alloc(p->N_tot * sizeof(double)));
+    QCP_TRY(mvalG.alloc((p->mnnz + 16) * sizeof(T)));
+    QCP_TRY(mvalT.alloc((p->mnnz + 16) * sizeof(T)));
+    QCP_CUDA(cudaMemsetAsync(mvalG.p, 0, (p->mnnz + 16) * sizeof(T), st));
+    QCP_CUDA(cudaMemsetAsync(mvalT.p, 0, (p->mnnz + 16) * sizeof(T), st));
     for (int i = 0; i < p->nprob; ++i) {
         const Prob& pr = p->hprob[i];
         k_dd_rows<T><<<grid_for((int64_t)pr.n + pr.m + 1, 256), 256, 0, st>>>(p->d_flag.as<int8_t>() + pr.doff, pr.n,
@@ -1086,11 +1089,11 @@ static int run_equilibrate(qcp_plan* p, int sweeps) {
             const Prob& pr = p->hprob[i];
             k_cd_rows<<<grid_for((int64_t)pr.n + pr.m + 1, 256), 256, 0, st>>>(
                 csq.as<double>() + pr.doff, p->d_flag.as<int8_t>() + pr.doff, pr.n, pr.m,
-                p->d_cd.as<double>() + pr.doff);
+                cdb.as<double>() + pr.doff);
             if (pr.nsoc)
                 k_cd_soc<<<grid_for((int64_t)pr.nsoc * 32, 256), 256, 0, st>>>(
                     p->d_blocks.as<SocBlock>() + pr.soff, pr.nsoc, csq.as<double>() + pr.doff,
-                    p->d_cd.as<double>() + pr.doff);
+                    cdb.as<double>() + pr.doff);
         }
     };
     for (int sweep = 0; sweep < sweeps; ++sweep) {
@@ -1099,16 +1102,16 @@ static int run_equilibrate(qcp_plan* p, int sweeps) {
                 k_prec_rows<T, false><<<nt, kThreads, 0, st>>>(
                     p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R, p->d_mrowptr.as<int64_t>(),
                     p->d_mcol.as<int32_t>(), p->d_mval.as<T>(), p->d_coefA.as<double>(), p->d_coefB.as<double>(),
-                    dd.as<double>(), nullptr, p->d_rw.as<double>());
+                    dd.as<double>(), nullptr, rwb.as<double>());
             else
                 k_prec_rows<T, true><<<nt, kThreads, 0, st>>>(
                     p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(), R, p->d_mrowptr.as<int64_t>(),
                     p->d_mcol.as<int32_t>(), p->d_mval.as<T>(), p->d_coefA.as<double>(), p->d_coefB.as<double>(),
-                    dd.as<double>(), p->d_cd.as<double>(), p->d_rw.as<double>());
+                    dd.as<double>(), cdb.as<double>(), rwb.as<double>());
             k_prec_cols<T><<<nt, kThreads, 0, st>>>(p->d_ptiles.as<Tile>(), p->d_prob.as<Prob>(), p->d_psys.as<Sys>(),
                                                     R, p->d_mrowptr.as<int64_t>(), p->d_mcol.as<int32_t>(),
                                                     p->d_mval.as<T>(), p->d_coefA.as<double>(),
-                                                    p->d_coefB.as<double>(), dd.as<double>(), p->d_rw.as<double>(),
+                                                    p->d_coefB.as<double>(), dd.as<double>(), rwb.as<double>(),
                                                     csq.as<double>());
             QCP_CUDA(cudaGetLastError());
         }
@@ -1120,11 +1123,15 @@ static int run_equilibrate(qcp_plan* p, int sweeps) {
         const int64_t k0 = p->h_mrowptr[pr.mrow], k1 = p->h_mrowptr[pr.mrow + pr.n + pr.m + 1];
         if (k1 > k0)
             k_scale_vals<T><<<grid_for(k1 - k0, 256), 256, 0, st>>>(
-                p->d_mval.as<T>(), p->d_mcol.as<int32_t>(), k0, k1, p->d_cd.as<double>() + pr.doff,
-                p->d_rw.as<double>() + pr.doff, p->d_mvalG.as<T>(), p->d_mvalT.as<T>());
+                p->d_mval.as<T>(), p->d_mcol.as<int32_t>(), k0, k1, cdb.as<double>() + pr.doff,
+                rwb.as<double>() + pr.doff, mvalG.as<T>(), mvalT.as<T>());
     }
     QCP_CUDA(cudaGetLastError());
     QCP_CUDA(cudaStreamSynchronize(st));
+    p->d_rw.swap(rwb);
+    p->d_cd.swap(cdb);
+    p->d_mvalG.swap(mvalG);
+    p->d_mvalT.swap(mvalT);
     return QCP_OK;
 }
 

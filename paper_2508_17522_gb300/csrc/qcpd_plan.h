@@ -7,6 +7,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "qcpd_common.cuh"
@@ -55,6 +56,11 @@ struct DevBuf {
         }
         bytes = nbytes;
         return QCP_OK;
+    }
+    // exchange the allocations of two buffers (no device work)
+    void swap(DevBuf& o) {
+        std::swap(p, o.p);
+        std::swap(bytes, o.bytes);
     }
     template <typename T>
     T* as() const { return static_cast<T*>(p); }
@@ -140,6 +146,8 @@ struct qcp_plan {
     qcpd::DevBuf d_sys, d_tiles, d_groups, d_state, d_tpart, d_gpart, d_gcnt, d_scnt, d_active;
     qcpd::DevBuf d_split_cnt, d_row_part;
     qcpd::DevBuf d_pctl;     // persistent mode: barrier count, generation, stop flag, error flag
+    int64_t barrier_polls = 0;    // persistent mode: polls per barrier wait (0: the default bound)
+    int64_t barrier_hold_ns = 0;  // persistent mode: CTA 0's wait before its first barrier (a test hook)
     qcpd::DevBuf d_U, d_V, d_W, d_X, d_XI, d_RHS, d_HB;  // Krylov vectors (HB: LSMR's hbar)
     int* h_active = nullptr;  // pinned
 
