@@ -241,9 +241,3 @@ def vjp_lsmr(prob, d, rtol=1e-10, maxiter=None, op=None):
     dPv, dAv, dq, db = d_theta_N_T_sparse(prob, z, r)
     return dPv, dAv, dq, db, {"iters": int(res[2]), "istop": int(res[1]),
                               "rel_residual": float(true_res)}
-
-
-def cond_estimate(fac: DenseFactor):
-    """sigma_1 / sigma_{N-1} of F (F has one zero singular value at a root)."""
-    s = np.linalg.svd(fac.F, compute_uv=False)
-    return float(s[0] / s[-2])

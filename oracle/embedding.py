@@ -131,12 +131,14 @@ def DuQ(prob, u):
     return J
 
 
-def F_dense(prob, z):
-    """F = D_z N(z) = (1/z_N)(D_u Q(Pi z) D Pi(z) - D Pi(z) + I)  (Sec. 3.1)."""
+def F_dense(prob, z, dense_limit=3000):
+    """F = D_z N(z) = (1/z_N)(D_u Q(Pi z) D Pi(z) - D Pi(z) + I)  (Sec. 3.1).
+    Above dense_limit rows the product D_u Q D Pi is formed with D Pi held
+    sparse; both forms give the same matrix (pinned against each other)."""
     pz = proj_K(prob, z)
     DP = dproj_K(prob, z)
     N = z.shape[0]
-    if N <= 3000:
+    if N <= dense_limit:
         prod = DuQ(prob, pz) @ DP
     else:
         # the same product, with D Pi held sparse (it is block diagonal)

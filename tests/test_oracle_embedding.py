@@ -114,3 +114,21 @@ def test_matrix_free_operator(prob):
         v = rng.standard_normal(prob.N)
         np.testing.assert_allclose(op.matvec(v), F @ v, atol=1e-12 * np.linalg.norm(F) * np.linalg.norm(v))
         np.testing.assert_allclose(op.rmatvec(v), F.T @ v, atol=1e-12 * np.linalg.norm(F) * np.linalg.norm(v))
+
+
+def test_F_dense_sparse_branch():
+    """Above 3000 rows F_dense forms D_u Q D Pi with D Pi held sparse; on a
+    problem just above that size (N = 3101, SOC and R+ blocks) it equals the
+    dense product, F z = 0 at the root, and a point off the root (another
+    D Pi pattern) agrees too."""
+    prob = g.small_qcp(5, 1000, 100, 1500, (10,) * 40 + (20,) * 5)
+    z = E.solution_to_z(prob)
+    assert z.size == 3101
+    Fs = E.F_dense(prob, z)                    # the sparse branch (N > 3000)
+    Fd = E.F_dense(prob, z, dense_limit=10 ** 9)
+    assert np.max(np.abs(Fs - Fd)) <= 1e-14 * np.max(np.abs(Fd))
+    assert np.linalg.norm(Fs @ z) < 1e-12 * np.linalg.norm(Fs) * np.linalg.norm(z)
+    zp = z + 0.3 * np.random.default_rng(1).standard_normal(z.size)
+    zp[-1] = 1.0
+    assert np.max(np.abs(E.F_dense(prob, zp) - E.F_dense(prob, zp, dense_limit=10 ** 9))) <= \
+        1e-14 * np.max(np.abs(E.F_dense(prob, zp, dense_limit=10 ** 9)))

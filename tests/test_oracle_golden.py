@@ -98,3 +98,12 @@ def test_pow_projection_golden():
     np.testing.assert_allclose(C.dproj_pow(p, a), g["dproj"], atol=1e-13)
     np.testing.assert_allclose(C.proj_pow(S @ p, a), S @ np.array(g["proj"]), atol=1e-14)
     np.testing.assert_allclose(C.dproj_pow(S @ p, a), S @ np.array(g["dproj"]) @ S, atol=1e-13)
+
+
+def test_kink_margin_golden():
+    """Hand-computed distances to the kinks of D Pi (fixture: the reason for
+    each value); among them both boundary rays of the second-order cone."""
+    for case in GOLD["kink_margin"]["cases"]:
+        cones = [tuple(c) for c in case["cones"]]
+        got = C.kink_margin(cones, np.array(case["z"]))
+        assert abs(got - case["margin"]) <= 1e-14, (case, got)
