@@ -168,15 +168,25 @@ typedef enum {
                                    only; QCP_ERR_ARG otherwise */
     QCP_ENGINE_AUTO = 3,        /* QCP_PRECOND_DIAG / _JACOBI: PASSES.  Otherwise the plan's
                                    autotuned engine when qcp_plan_autotune has run, else
-                                   QCP_ENGINE_CLUSTER; a cluster choice becomes PASSES for LSMR and
-                                   when a system does not fit or the plan has PSD, exponential or
-                                   power blocks */
-    QCP_ENGINE_CLUSTER_FP64 = 4 /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
+                                   QCP_ENGINE_CLUSTER; a cluster choice becomes STREAM when a system
+                                   does not fit the cluster engine (PASSES where STREAM cannot run
+                                   the plan), and PASSES for LSMR and for plans with PSD,
+                                   exponential or power blocks */
+    QCP_ENGINE_CLUSTER_FP64 = 4, /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,
                                    which run 74 times faster than FP64 on this GPU), keeps the LSQR
                                    scalars in FP64, and itself uses FP64 when a magnitude in the
                                    data lies outside 2^-90..2^90 */
+    QCP_ENGINE_STREAM = 5       /* one launch per half-iteration for problems of any size, the
+                                   vector arithmetic in double-float pairs like the cluster engine
+                                   (Krylov vectors in device memory, LSQR scalars and the tau
+                                   entries in FP64): warp-sized work units (SELL-32 row slices,
+                                   packed second-order-cone blocks, chunks of long rows) and no
+                                   CTA-wide barrier inside a pass; replayed from CUDA graphs in
+                                   chunks of check_every.  Zero, R+ and SOC blocks (at most 256
+                                   rows each), LSQR, precond NONE or EQUILIBRATE, magnitudes in
+                                   the data within 2^-90..2^90; QCP_ERR_ARG otherwise */
 } qcp_engine;
 
 typedef struct {
@@ -360,17 +370,32 @@ int qcp_plan_autotune(qcp_plan* plan, const qcp_options* opts, int32_t mode, int
 int qcp_plan_set_cluster(qcp_plan* plan, int32_t max_ctas);
 
 /* Sweeps of the QCP_PRECOND_EQUILIBRATE scaling (an addition to the
-   paper's plain Krylov solve of Sec. 3.3): 1 (the default, set at plan
-   creation) to 64.  One sweep takes w = 1 / row norms of F and then
-   c = 1 / column norms of W F, with D Pi by its diagonal and c constant on
-   every coupled block; each further sweep recomputes w from the rows of F C
-   and c from the new W F.  Both systems are consistent, so the outputs do
-   not change, only the iteration count.  The plan recomputes w, c and its
-   scaled copies of M on its stream before returning.  Errors: QCP_ERR_ARG
-   for a NULL plan, sweeps outside 1 to 64, or a plan that has already run
-   a derivative or autotune call (w and c are then part of its captured
+   paper's plain Krylov solve of Sec. 3.3): 1 to 64; a plan starts with 16.
+   One sweep takes w = 1 / row norms of F and then c = 1 / column norms of
+   W F, with D Pi by its diagonal and c constant on every coupled block;
+   each further sweep recomputes w from the rows of F C and c from the new
+   W F.  Both systems are consistent, so the outputs do not change, only
+   the iteration count (on the 16-direction n = 2000 workload, 15 600 LSQR
+   iterations per solve at 1 sweep, 1 140 at 16).  The plan recomputes w, c
+   and its scaled copies of M on its stream before returning; if that fails
+   the plan keeps its previous scaling.  Errors: QCP_ERR_ARG for a NULL
+   plan, sweeps outside 1 to 64, or a plan that has already run a
+   derivative or autotune call (w and c are then part of its captured
    graphs and cluster layouts); QCP_ERR_ALLOC, QCP_ERR_CUDA. */
 int qcp_plan_set_equilibration(qcp_plan* plan, int32_t sweeps);
+
+/* Bound of the waits at QCP_ENGINE_PERSISTENT's grid-wide barriers (an
+   addition; the paper has no counterpart).  A CTA that waits at a barrier
+   polls at most `polls` times, about 64 ns apart, then records a timeout;
+   every CTA of the launch returns at its next barrier and the call returns
+   QCP_ERR_TIMEOUT with the outputs unspecified.  polls = 0 restores the
+   default bound (2^24 polls, about 1 s).  hold_ns > 0 (at most 1 s) makes
+   CTA 0 of the next persistent launches wait that long by the GPU's global
+   timer before its first barrier, so that the other CTAs' waits run out:
+   a way to exercise the timeout path without any fault or unbounded wait.
+   The plan stays usable after a timeout.  Errors: QCP_ERR_ARG (null plan,
+   a negative value, hold_ns above 1e9). */
+int qcp_plan_set_barrier_wait(qcp_plan* plan, int64_t polls, int64_t hold_ns);
 
 /* The qcp_engine the most recent JVP/VJP call of the plan ran: PASSES,
    PERSISTENT, CLUSTER (double-float vector arithmetic) or CLUSTER_FP64; -1
@@ -383,10 +408,12 @@ int64_t qcp_plan_last_launches(const qcp_plan* plan);
 
 /*
  * The forward product of qcp_derivative_jvp for a single-problem plan and one
- * direction, for callers that cannot allocate device memory at call time:
- * code running while its stream is captured into a CUDA graph, allocator
- * hooks, or loops whose memory comes from a pool they do not own.  The
- * paper has no counterpart; it is a deployment variant of the same kernels.
+ * direction, for callers that must not allocate device memory when they ask
+ * for a derivative: allocator hooks and callbacks that may not re-enter the
+ * allocator, real-time loops where an allocation's latency or failure is not
+ * acceptable, and hosts whose device memory is handed out by a pool they do
+ * not own.  The paper has no counterpart; it is a deployment variant of the
+ * same kernels (always the pass engine).
  *
  * All per-call scratch (Krylov vectors, LSQR scalars, reduction partials and
  * counters) lives in one 16 MiB file-scope device array of the library
@@ -398,12 +425,17 @@ int64_t qcp_plan_last_launches(const qcp_plan* plan);
  * process exits.
  *
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress, once per device); make that first
- * call before any stream capture begins.  Every call shares the one array
- * and clears it at entry, so calls whose work overlaps on the GPU (two
- * host threads, or two streams) race and must be serialised by the caller.
- * Arguments, options (check_every >= 1 is required) and outputs are those
- * of qcp_derivative_jvp; the plan must not be batched.
+ * device current (cudaGetSymbolAddress, once per device).  Every call shares
+ * the one array and clears it at entry, so calls whose work overlaps on the
+ * GPU (two host threads, or two streams) race and must be serialised by the
+ * caller.  Like qcp_derivative_jvp, the call reads convergence scalars back
+ * to the host and synchronizes the plan's stream every check_every
+ * iterations.  Arguments, options (check_every >= 1, LSQR, precond NONE or
+ * EQUILIBRATE, no warm start) and outputs are those of qcp_derivative_jvp;
+ * the plan must not be batched.  The plan's introspection queries
+ * (qcp_plan_last_solution, _last_timing, _last_engine, _last_launches)
+ * keep describing the plan's last regular call: a no-allocation call leaves
+ * them as they were.
  */
 int qcp_derivative_jvp_noalloc(qcp_plan* plan, const qcp_options* opts, const void* dP, const void* dA,
                                const void* dq, const void* db, void* dx, void* dy, void* ds,

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "QCP_OK", 1: "QCP_ERR_ARG", 2: "QCP_ERR_CUDA", 3: "QCP_ERR_AL
 QCP_F64, QCP_F32 = 0, 1
 QCP_PRECOND_NONE, QCP_PRECOND_EQUILIBRATE, QCP_PRECOND_DIAG, QCP_PRECOND_JACOBI = 0, 1, 2, 3
 QCP_ENGINE_PASSES, QCP_ENGINE_PERSISTENT, QCP_ENGINE_CLUSTER, QCP_ENGINE_AUTO, QCP_ENGINE_CLUSTER_FP64 = 0, 1, 2, 3, 4
+QCP_ENGINE_STREAM = 5
 
 
 class qcp_csr(ctypes.Structure):
@@ -123,6 +124,8 @@ def lib():
     L.qcp_plan_set_cluster.argtypes = [c_void_p, c_int32]
     L.qcp_plan_set_equilibration.restype = ctypes.c_int
     L.qcp_plan_set_equilibration.argtypes = [c_void_p, c_int32]
+    L.qcp_plan_set_barrier_wait.restype = ctypes.c_int
+    L.qcp_plan_set_barrier_wait.argtypes = [c_void_p, c_int64, c_int64]
     L.qcp_plan_last_launches.restype = c_int64
     L.qcp_plan_last_launches.argtypes = [c_void_p]
     L.qcp_plan_last_timing.restype = ctypes.c_int

@@ -102,7 +102,8 @@ _PRECOND = {"none": N.QCP_PRECOND_NONE, "equilibrate": N.QCP_PRECOND_EQUILIBRATE
 
 
 _ENGINE = {"passes": N.QCP_ENGINE_PASSES, "persistent": N.QCP_ENGINE_PERSISTENT,
-           "cluster": N.QCP_ENGINE_CLUSTER, "auto": N.QCP_ENGINE_AUTO, "cluster_fp64": N.QCP_ENGINE_CLUSTER_FP64}
+           "cluster": N.QCP_ENGINE_CLUSTER, "auto": N.QCP_ENGINE_AUTO, "cluster_fp64": N.QCP_ENGINE_CLUSTER_FP64,
+           "stream": N.QCP_ENGINE_STREAM}
 
 
 def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_residual=True, precond="none",
@@ -114,8 +115,9 @@ def options(rtol=1e-10, maxiter=100000, check_every=32, use_graph=True, compute_
     a float64 device tensor of N per system (dz for the JVP, r for the VJP).
     engine is "passes" (one launch per pass), "persistent" (one cooperative
     launch), "cluster" (one thread-block cluster per system, double-float
-    vector arithmetic), "cluster_fp64" (the same in FP64) or "auto".  The
-    returned object keeps the tensors alive."""
+    vector arithmetic), "cluster_fp64" (the same in FP64), "stream" (one
+    launch per pass, warp-sized units, double-float vector arithmetic) or
+    "auto".  The returned object keeps the tensors alive."""
     o = N.qcp_options()
     N.lib().qcp_default_options(ctypes.byref(o))
     o.rtol, o.maxiter, o.check_every = float(rtol), int(maxiter), int(check_every)
@@ -197,7 +199,7 @@ class Plan:
         return ms.value, n.value
 
     def last_engine(self) -> str:
-        """Engine of the last call: passes, persistent, cluster or cluster_fp64."""
+        """Engine of the last call: passes, persistent, cluster, cluster_fp64 or stream."""
         e = N.lib().qcp_plan_last_engine(self._h)
         return {v: k for k, v in _ENGINE.items()}.get(e, str(e))
 
@@ -228,6 +230,12 @@ class Plan:
         derivative or autotune call); more sweeps mean fewer Krylov
         iterations on badly scaled problems, with the same outputs."""
         _check(N.lib().qcp_plan_set_equilibration(self._h, int(sweeps)), "qcp_plan_set_equilibration")
+
+    def set_barrier_wait(self, polls: int = 0, hold_ns: int = 0):
+        """Bound of the persistent engine's barrier waits (0: the default) and
+        a hold of CTA 0 before its first barrier (0: none; exercises the
+        timeout path)."""
+        _check(N.lib().qcp_plan_set_barrier_wait(self._h, int(polls), int(hold_ns)), "qcp_plan_set_barrier_wait")
 
     def set_schedule(self, tile_nnz: int = 4096, long_row: int = 512, long_chunk: int = 1 << 20):
         _check(N.lib().qcp_plan_set_schedule(self._h, int(tile_nnz), int(long_row), int(long_chunk)),

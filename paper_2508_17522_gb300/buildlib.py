@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libqcpd.so")
-SOURCES = ["qcpd_plan.cu", "qcpd_api.cu", "qcpd_cluster.cu", "qcpd_mlp.cu"]
+SOURCES = ["qcpd_plan.cu", "qcpd_api.cu", "qcpd_cluster.cu", "qcpd_stream.cu", "qcpd_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

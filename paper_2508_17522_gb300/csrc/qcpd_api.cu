@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "qcpd_cluster.h"
+#include "qcpd_stream.h"
 #include "qcpd_kernels.cuh"
 #include "qcpd_plan.h"
 
@@ -130,7 +131,7 @@ static int run_chunk(qcp_plan* p, int mode, int nsys, const PlanView<T>& v, int 
         p->last_launches += 2 * chunk;
         return QCP_OK;
     }
-    GraphKey key{mode, v.tile0, nsys, chunk, p->view_precond, v.lsmr};
+    GraphKey key{QCP_ENGINE_PASSES, mode, v.tile0, nsys, chunk, p->view_precond, v.lsmr};
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -231,6 +232,8 @@ static int iterate_persistent(qcp_plan* p, int mode, const PlanView<T>& v, int n
     c.stop = ctl + 2;
     c.err = ctl + 3;
     c.max_iters = opts.maxiter + 2;
+    c.spin_limit = p->barrier_polls > 0 ? (unsigned long long)p->barrier_polls : kSpinLimit;
+    c.hold_ns = p->barrier_hold_ns;
     QCP_CUDA(cudaMemsetAsync(ctl, 0, 4 * sizeof(int32_t), st));
     PlanView<T> va = v;
     void* args[] = {(void*)&va, (void*)&c, (void*)&ntiles};
@@ -404,8 +407,8 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
         set_error("QCP_PRECOND_DIAG and _JACOBI run on the pass or persistent engine");
         return QCP_ERR_ARG;
     }
-    if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_CLUSTER_FP64) {
-        set_error("engine must be one of QCP_ENGINE_PASSES, _PERSISTENT, _CLUSTER, _AUTO, _CLUSTER_FP64");
+    if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_STREAM) {
+        set_error("engine must be one of QCP_ENGINE_PASSES, _PERSISTENT, _CLUSTER, _AUTO, _CLUSTER_FP64, _STREAM");
         return QCP_ERR_ARG;
     }
     if (nseg < 1 || nseg > kMaxSegments) {
@@ -431,8 +434,19 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
             set_error("cluster engine: a problem's vectors do not fit in the shared memory of 16 CTAs");
             return QCP_ERR_ARG;
         } else {
-            engine = QCP_ENGINE_PASSES;
+            // too large for the cluster engine: the stream engine where it can run the plan
+            bool sok = false;
+            QCP_TRY(stream_ready(p, &sok));
+            engine = sok ? QCP_ENGINE_STREAM : QCP_ENGINE_PASSES;
         }
+    } else if (engine == QCP_ENGINE_STREAM) {
+        if (opts.solver != 0 || opts.precond == QCP_PRECOND_DIAG) {
+            set_error("the stream engine runs LSQR with precond NONE or EQUILIBRATE");
+            return QCP_ERR_ARG;
+        }
+        bool sok = false;
+        QCP_TRY(stream_ready(p, &sok));
+        if (!sok) return QCP_ERR_ARG;  // stream_ready has set the reason
     }
     cudaStream_t st = p->stream;
     if (opts.precond == QCP_PRECOND_DIAG) QCP_TRY(prepare_diag<T>(p, opts.precond_d));
@@ -487,6 +501,13 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
             for (int gi = 0; gi < nseg; ++gi)
                 if (todo[gi]) cs[nc++] = ClusterSeg{segs[gi].mode, segs[gi].s0, segs[gi].ns, gi};
             return iterate_cluster<T>(p, cs, nc, nsys, v, opts);
+        }
+        if (engine == QCP_ENGINE_STREAM) {
+            for (int gi = 0; gi < nseg; ++gi)
+                if (todo[gi])
+                    QCP_TRY(iterate_stream(p, segs[gi].mode, segs[gi].s0, segs[gi].ns, p->d_active.as<int>() + gi,
+                                           v.scaled != 0, opts));
+            return QCP_OK;
         }
         for (int gi = 0; gi < nseg; ++gi) {
             if (!todo[gi]) continue;
@@ -557,7 +578,7 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
         }
         QCP_TRY(run_iterations(todo));
     }
-    if (engine != QCP_ENGINE_PASSES) {
+    if (engine != QCP_ENGINE_PASSES && engine != QCP_ENGINE_STREAM) {
         int64_t it = 0;
         for (int s = 0; s < nsys; ++s) it = std::max<int64_t>(it, hs[s].iters);
         p->pass_launches = 2 * it;  // passes the single-launch engines ran
@@ -794,9 +815,21 @@ static int autotune(qcp_plan* p, const qcp_options& base, int mode, int nsys, in
                 p->clusters.erase(c);
         }
     }
+    if (o.precond != QCP_PRECOND_DIAG && o.solver == 0) {
+        bool sok = false;
+        QCP_TRY(stream_ready(p, &sok));
+        if (sok) {
+            qcp_tune_entry e{QCP_ENGINE_STREAM, 0, 0, 0, 0.0};
+            QCP_TRY(measure(QCP_ENGINE_STREAM, e));
+            out.push_back(e);
+            if (e.us_per_pass < out[best].us_per_pass) best = (int)out.size() - 1;
+        }
+    }
     const qcp_tune_entry w = out[best];
     if (w.engine == QCP_ENGINE_CLUSTER) {
         p->cluster_cap = w.cluster_ctas;
+    } else if (w.engine == QCP_ENGINE_STREAM) {
+        p->cluster_cap = cap0;  // the stream engine uses the default tile schedule for its other kernels
     } else {
         p->cluster_cap = cap0;
         p->tile_nnz = w.tile_nnz;
@@ -861,10 +894,10 @@ static int make_plan(int np, const qcp_problem* probs, const qcp_solution* sols,
 // ---------------------------------------------------------------------------
 // JVP without device allocation.
 //
-// Some callers cannot call cudaMalloc when they need a derivative: code
-// that runs while a stream is being captured into a CUDA graph, allocator
-// hooks and real-time loops that forbid device allocation, or hosts whose
-// memory is handed out by a pool they do not own.  For them the per-call
+// Some callers cannot call cudaMalloc when they need a derivative:
+// allocator hooks and callbacks that may not re-enter the allocator,
+// real-time loops that forbid device allocation, or hosts whose memory is
+// handed out by a pool they do not own.  For them the per-call
 // scratch of the JVP (Krylov vectors, LSQR scalars, reduction partials and
 // counters) lives in one file-scope device array of fixed size instead of
 // plan memory.  Every GPU that loads the library holds the array until the
@@ -1164,7 +1197,8 @@ int qcp_plan_set_equilibration(qcp_plan* plan, int32_t sweeps) {
     }
     // w and c are baked into captured graphs, cluster layouts and the
     // autotuner's timings, so they may change only before any of those exist
-    if (plan->last_mode >= 0 || !plan->graphs.empty() || !plan->clusters.empty() || plan->tuned_engine >= 0) {
+    if (plan->last_mode >= 0 || !plan->graphs.empty() || !plan->clusters.empty() || plan->stream_lay ||
+        plan->tuned_engine >= 0) {
         set_error("qcp_plan_set_equilibration: call it before the plan's first derivative or autotune call");
         return QCP_ERR_ARG;
     }
@@ -1172,6 +1206,16 @@ int qcp_plan_set_equilibration(qcp_plan* plan, int32_t sweeps) {
     const int rc = equilibrate_plan(plan, sweeps);
     if (rc == QCP_OK) plan->equil_sweeps = sweeps;
     return rc;
+}
+
+int qcp_plan_set_barrier_wait(qcp_plan* plan, int64_t polls, int64_t hold_ns) {
+    if (!plan || polls < 0 || hold_ns < 0 || hold_ns > 1000000000LL) {
+        set_error("qcp_plan_set_barrier_wait: null plan, negative bound or hold above 1 s");
+        return QCP_ERR_ARG;
+    }
+    plan->barrier_polls = polls;
+    plan->barrier_hold_ns = hold_ns;
+    return QCP_OK;
 }
 
 int64_t qcp_plan_last_launches(const qcp_plan* plan) { return plan ? plan->last_launches : 0; }

@@ -66,9 +66,15 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Sweeps of the row/column equilibration a plan starts with: on the
+// configurations measured, 16 sweeps take 7 to 100 times fewer LSQR
+// iterations than one, and more sweeps gain little.
+constexpr int kDefaultEquilSweeps = 16;
+
 constexpr int kMaxSegments = 2;  // system ranges of one call (JVP systems, VJP systems)
 
 struct GraphKey {
+    int engine;  // qcp_engine whose launches the graph holds
     int mode;    // 0 JVP, 1 VJP
     int tile0;   // first tile of the system range
     int nsys;
@@ -76,6 +82,7 @@ struct GraphKey {
     int scaled;  // qcp_precond of the view (different kernels and value arrays)
     int solver;  // 0 LSQR, 1 LSMR (a kernel parameter of the captured launches)
     bool operator<(const GraphKey& o) const {
+        if (engine != o.engine) return engine < o.engine;
         if (mode != o.mode) return mode < o.mode;
         if (tile0 != o.tile0) return tile0 < o.tile0;
         if (nsys != o.nsys) return nsys < o.nsys;
@@ -97,6 +104,23 @@ struct ClusterLayout {
     // double-float copies for the df64 kernel (df_ok: every magnitude in range)
     bool df_ok = false;
     DevBuf d_dsval, d_dsvalG, d_dsvalT, d_dcA, d_dcB, d_drw, d_dcd, d_dzy, d_dsoc;
+};
+
+// The stream engine's copy of a plan (QCP_ENGINE_STREAM, built on first
+// use): warp units over every problem's rows, the slots of M they read as
+// df64 values, df64 per-row data and per-block constants, and the engine's
+// per-system workspace.
+struct StreamLayout {
+    bool ok = false;                 // usable: cones zero / R+ / SOC (blocks <= 256 rows), magnitudes in df64 range
+    std::string why;                 // the reason when not
+    int nunits = 0;                  // over all problems
+    int max_units = 0;               // most units of one problem
+    int nsplit = 0, nslot = 0;       // split rows and their chunk slots (plan-wide)
+    int gmax = 0;                    // CTAs per system the workspace holds
+    std::vector<int32_t> huoff, hsoff;
+    DevBuf d_units, d_uoff, d_soff, d_rows, d_lblk, d_scol, d_val, d_valG, d_valT;
+    DevBuf d_cA, d_cB, d_rw, d_cd, d_zy, d_soc;
+    DevBuf d_scal, d_ssys, d_cpart, d_ccnt, d_lchunk, d_lcnt, d_lrow;
 };
 
 }  // namespace qcpd
@@ -154,8 +178,9 @@ struct qcp_plan {
     // cluster engine
     int cluster_cap = 0;  // CTAs per system asked for (0: per call from the number of systems)
     int tuned_engine = -1; // the autotuner's choice for QCP_ENGINE_AUTO (-1: none)
-    int equil_sweeps = 1;  // sweeps of the row/column equilibration behind d_rw and d_cd
+    int equil_sweeps = qcpd::kDefaultEquilSweeps;  // sweeps of the row/column equilibration behind d_rw and d_cd
     std::map<int, std::unique_ptr<qcpd::ClusterLayout>> clusters;  // by CTAs asked for
+    std::unique_ptr<qcpd::StreamLayout> stream_lay;  // QCP_ENGINE_STREAM (built on first use)
     qcpd::DevBuf d_csys;  // system lists of the cluster launches
     qcpd::DevBuf d_bcast; // broadcast buffers of the double-float cluster kernel
     std::vector<int32_t> h_csys;

@@ -1,0 +1,505 @@
+// Host side of the stream engine (see qcpd_stream.cuh): the plan's warp
+// units, the df64 copies of M and of the per-row data, and the iteration
+// loop (two launches per LSQR iteration, replayed from CUDA graphs in chunks
+// of check_every iterations, as the pass engine does).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "qcpd_stream.cuh"
+#include "qcpd_stream.h"
+
+namespace qcpd {
+
+namespace {
+
+constexpr double kSDfMin = 0x1p-90, kSDfMax = 0x1p90;
+
+__device__ __forceinline__ bool s_df_unsafe(double x) {
+    const double a = fabs(x);
+    return !(a == 0.0 || (a >= kSDfMin && a <= kSDfMax));
+}
+
+template <typename T>
+__device__ __forceinline__ void s_put(int64_t slot, int64_t src, const int32_t* mcol, const T* mval, const T* mvalG,
+                                      const T* mvalT, int32_t* scol, df* val, df* valG, df* valT, int* bad) {
+    const double v = (double)mval[src], g = (double)mvalG[src], t = (double)mvalT[src];
+    if (s_df_unsafe(v) || s_df_unsafe(g) || s_df_unsafe(t)) atomicExch(bad, 1);
+    scol[slot] = mcol[src];
+    val[slot] = df_from(v);
+    valG[slot] = df_from(g);
+    valT[slot] = df_from(t);
+}
+
+__device__ __forceinline__ void s_pad(int64_t slot, int32_t col, int32_t* scol, df* val, df* valG, df* valT) {
+    scol[slot] = col;
+    val[slot] = df_zero();
+    valG[slot] = df_zero();
+    valT[slot] = df_zero();
+}
+
+// Slots of one SELL-32 sub-slice whose lane rows are given: the row's
+// entries, then padding that repeats its last column.
+template <typename T>
+__device__ __forceinline__ void s_fill_slice(int64_t base, int width, int row, const int64_t* rp, const int32_t* mcol,
+                                             const T* mval, const T* mvalG, const T* mvalT, int32_t* scol, df* val,
+                                             df* valG, df* valT, int* bad) {
+    const int lane = threadIdx.x & 31;
+    int64_t k0 = 0, len = 0;
+    if (row >= 0) {
+        k0 = rp[row];
+        len = rp[row + 1] - k0;
+    }
+    const int32_t last = len > 0 ? mcol[k0 + len - 1] : 0;
+    for (int k = 0; k < width; ++k) {
+        const int64_t slot = base + 32 * (int64_t)k + lane;
+        if (k < len) s_put(slot, k0 + k, mcol, mval, mvalG, mvalT, scol, val, valG, valT, bad);
+        else s_pad(slot, last, scol, val, valG, valT);
+    }
+}
+
+// One warp per unit.
+template <typename T>
+__global__ void k_stream_fill(const StreamUnit* units, int nunits, const int32_t* rows, const Prob* probs,
+                              const int64_t* mrowptr, const int32_t* mcol, const T* mval, const T* mvalG,
+                              const T* mvalT, int32_t* scol, df* val, df* valG, df* valT, int* bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ui = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (ui >= nunits) return;
+    const StreamUnit u = units[ui];
+    const int64_t* rp = mrowptr + probs[u.prob].mrow;
+    if (u.kind == SU_SLICE || u.kind == SU_SOCP) {
+        s_fill_slice(u.base, u.width, rows[u.aux + lane], rp, mcol, mval, mvalG, mvalT, scol, val, valG, valT, bad);
+    } else if (u.kind == SU_SOCB) {
+        int64_t base = u.base;
+        for (int j = 0; j < u.width; ++j) {
+            const int w = rows[u.aux + j];
+            const int i = 32 * j + lane;
+            s_fill_slice(base, w, i < u.nrows ? u.row0 + i : -1, rp, mcol, mval, mvalG, mvalT, scol, val, valG, valT,
+                         bad);
+            base += 32 * (int64_t)w;
+        }
+    } else {
+        const int64_t k0 = rp[u.aux] + (int64_t)u.chunk * kSLongChunk;
+        for (int k = lane; k < u.width; k += 32)
+            s_put(u.base + k, k0 + k, mcol, mval, mvalG, mvalT, scol, val, valG, valT, bad);
+    }
+}
+
+__global__ void k_stream_todf(const double* in, int64_t n, df* out, int* bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (s_df_unsafe(in[i])) atomicExch(bad, 1);
+        out[i] = df_from(in[i]);
+    }
+}
+
+__global__ void k_stream_soc(const SocBlock* blk, int64_t nb, StreamSoc* out, int* bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+        const SocBlock B = blk[i];
+        StreamSoc s;
+        const double htr = B.h * (B.t + B.r);
+        if (B.kase == 2 && (s_df_unsafe(B.r) || s_df_unsafe(B.h) || s_df_unsafe(B.tq) || s_df_unsafe(htr)))
+            atomicExch(bad, 1);
+        s.r = df_from(B.r);
+        s.h = df_from(B.h);
+        s.tq = df_from(B.tq);
+        s.htr = df_from(htr);
+        s.start = B.start;
+        s.dim = B.dim;
+        s.kase = B.kase;
+        s.pad = 0;
+        out[i] = s;
+    }
+}
+
+int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + 255) / 256)); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Layout.  Per problem: x-rows and zero-cone / R+ rows with at most
+// kSLongRow entries in SELL-32 slices (x and y apart, each sorted by length,
+// longest first); longer rows in chunks of kSLongChunk entries;
+// second-order-cone blocks of at most 32 rows packed in order into units of
+// at most 32 rows, larger ones (up to kSSocBig rows) one unit each.  Units
+// are sorted by cost (slots plus a per-row share for the epilogue), most
+// expensive first, for the kernel's snake order.
+static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<StreamUnit>& hu,
+                        std::vector<int32_t>& hrows, std::vector<int32_t>& hlblk, int64_t& slots) {
+    slots = 0;
+    auto take = [&](int64_t n) {
+        const int64_t b = (slots + 31) & ~(int64_t)31;  // every unit starts on a 32-slot boundary
+        slots = b + n;
+        return b;
+    };
+    lay->huoff.assign(1, 0);
+    lay->hsoff.assign(1, 0);
+    lay->nsplit = lay->nslot = 0;
+    lay->max_units = 0;
+    for (int pi = 0; pi < p->nprob; ++pi) {
+        const Prob& pr = p->hprob[pi];
+        const int64_t* rp = p->h_mrowptr.data() + pr.mrow;
+        auto len = [&](int r) { return (int)(rp[r + 1] - rp[r]); };
+        std::vector<int> xs, ys, longs;
+        struct Blk { int start, dim, idx; };
+        std::vector<Blk> socs;
+        for (int r = 0; r < pr.n; ++r) (len(r) <= kSLongRow ? xs : longs).push_back(r);
+        int row = pr.n, bi = 0;
+        for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
+            const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
+            if (t == QCP_CONE_ZERO || t == QCP_CONE_NONNEG) {
+                for (int k = 0; k < d; ++k) (len(row + k) <= kSLongRow ? ys : longs).push_back(row + k);
+            } else if (t == QCP_CONE_SOC) {
+                if (d > kSSocBig) {
+                    lay->why = "a second-order-cone block has more than 256 rows";
+                    return false;
+                }
+                socs.push_back({row, d, bi++});
+            } else {
+                lay->why = "the plan has PSD, exponential or power-cone blocks";
+                return false;
+            }
+            row += d;
+        }
+        std::vector<StreamUnit> pu;
+        std::vector<double> cost;
+        auto slice_units = [&](std::vector<int>& rows) {
+            std::stable_sort(rows.begin(), rows.end(), [&](int a, int b) { return len(a) > len(b); });
+            for (size_t i = 0; i < rows.size(); i += 32) {
+                const int nr = (int)std::min<size_t>(32, rows.size() - i);
+                StreamUnit u{};
+                u.kind = SU_SLICE;
+                u.prob = pi;
+                u.nrows = nr;
+                u.width = len(rows[i]);
+                u.aux = (int32_t)hrows.size();
+                for (int l = 0; l < 32; ++l) {
+                    hrows.push_back(l < nr ? rows[i + l] : -1);
+                    hlblk.push_back(-1);
+                }
+                u.base = take(32 * (int64_t)u.width);
+                pu.push_back(u);
+                cost.push_back(32.0 * u.width + 8.0 * nr);
+            }
+        };
+        slice_units(xs);
+        slice_units(ys);
+        for (size_t i = 0; i < socs.size();) {
+            StreamUnit u{};
+            u.prob = pi;
+            if (socs[i].dim > 32) {
+                const Blk B = socs[i++];
+                u.kind = SU_SOCB;
+                u.nrows = B.dim;
+                u.width = (B.dim + 31) / 32;
+                u.blk = B.idx;
+                u.row0 = B.start;
+                u.aux = (int32_t)hrows.size();
+                int64_t tot = 0;
+                for (int j = 0; j < u.width; ++j) {
+                    int w = 0;
+                    for (int r = B.start + 32 * j; r < std::min(B.start + B.dim, B.start + 32 * j + 32); ++r)
+                        w = std::max(w, len(r));
+                    hrows.push_back(w);
+                    hlblk.push_back(-1);
+                    tot += w;
+                }
+                u.base = take(32 * tot);
+                pu.push_back(u);
+                cost.push_back(32.0 * tot + 24.0 * B.dim);
+                continue;
+            }
+            // consecutive blocks of at most 32 rows in all, one row per lane
+            size_t j = i;
+            int total = 0;
+            while (j < socs.size() && socs[j].dim <= 32 && total + socs[j].dim <= 32) total += socs[j++].dim;
+            u.kind = SU_SOCP;
+            u.nrows = total;
+            u.aux = (int32_t)hrows.size();
+            int w = 0, lane = 0;
+            for (size_t b = i; b < j; ++b)
+                for (int k = 0; k < socs[b].dim; ++k, ++lane) {
+                    hrows.push_back(socs[b].start + k);
+                    hlblk.push_back(socs[b].idx);
+                    w = std::max(w, len(socs[b].start + k));
+                }
+            for (; lane < 32; ++lane) {
+                hrows.push_back(-1);
+                hlblk.push_back(-1);
+            }
+            u.width = w;
+            u.base = take(32 * (int64_t)w);
+            pu.push_back(u);
+            cost.push_back(32.0 * w + 24.0 * total);
+            i = j;
+        }
+        for (int r : longs) {
+            const int L = len(r);
+            const int nch = (L + kSLongChunk - 1) / kSLongChunk;
+            int split = -1, slot0 = 0;
+            if (nch > 1) {
+                split = lay->nsplit++;
+                slot0 = lay->nslot;
+                lay->nslot += nch;
+            }
+            for (int c = 0; c < nch; ++c) {
+                StreamUnit u{};
+                u.kind = SU_LONG;
+                u.prob = pi;
+                u.nrows = nch;
+                u.width = std::min(kSLongChunk, L - c * kSLongChunk);
+                u.aux = r;
+                u.blk = split;
+                u.chunk = c;
+                u.row0 = slot0;
+                u.base = take(u.width);
+                pu.push_back(u);
+                cost.push_back(u.width + 40.0);
+            }
+        }
+        std::vector<int> ord(pu.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        for (int o : ord) hu.push_back(pu[o]);
+        lay->huoff.push_back((int32_t)hu.size());
+        lay->hsoff.push_back(lay->nsplit);
+        lay->max_units = std::max(lay->max_units, (int)pu.size());
+    }
+    return true;
+}
+
+template <typename T>
+static int build_stream(qcp_plan* p, StreamLayout* lay) {
+    std::vector<StreamUnit> hu;
+    std::vector<int32_t> hrows, hlblk;
+    int64_t slots = 0;
+    if (!build_units(p, lay, hu, hrows, hlblk, slots)) return QCP_OK;  // not usable: lay->ok stays false
+    lay->nunits = (int)hu.size();
+    cudaStream_t st = p->stream;
+    auto up = [&](DevBuf& d, const void* h, size_t bytes) -> int {
+        QCP_TRY(d.alloc(bytes));
+        if (bytes) QCP_CUDA(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, st));
+        return QCP_OK;
+    };
+    QCP_TRY(up(lay->d_units, hu.data(), sizeof(StreamUnit) * hu.size()));
+    QCP_TRY(up(lay->d_uoff, lay->huoff.data(), sizeof(int32_t) * lay->huoff.size()));
+    QCP_TRY(up(lay->d_soff, lay->hsoff.data(), sizeof(int32_t) * lay->hsoff.size()));
+    QCP_TRY(up(lay->d_rows, hrows.data(), sizeof(int32_t) * hrows.size()));
+    QCP_TRY(up(lay->d_lblk, hlblk.data(), sizeof(int32_t) * hlblk.size()));
+    const int64_t ns = std::max<int64_t>(slots, 1);
+    QCP_TRY(lay->d_scol.alloc(sizeof(int32_t) * ns));
+    QCP_TRY(lay->d_val.alloc(sizeof(df) * ns));
+    QCP_TRY(lay->d_valG.alloc(sizeof(df) * ns));
+    QCP_TRY(lay->d_valT.alloc(sizeof(df) * ns));
+    DevBuf bad;
+    QCP_TRY(bad.alloc(sizeof(int)));
+    QCP_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    int* b = bad.as<int>();
+    if (!hu.empty())
+        k_stream_fill<T><<<(unsigned)((hu.size() * 32 + 255) / 256), 256, 0, st>>>(
+            lay->d_units.as<StreamUnit>(), (int)hu.size(), lay->d_rows.as<int32_t>(), p->d_prob.as<Prob>(),
+            p->d_mrowptr.as<int64_t>(), p->d_mcol.as<int32_t>(), p->d_mval.as<T>(), p->d_mvalG.as<T>(),
+            p->d_mvalT.as<T>(), lay->d_scol.as<int32_t>(), lay->d_val.as<df>(), lay->d_valG.as<df>(),
+            lay->d_valT.as<df>(), b);
+    auto todf = [&](const DevBuf& in, DevBuf& out) -> int {
+        QCP_TRY(out.alloc(sizeof(df) * (size_t)std::max<int64_t>(p->N_tot, 1)));
+        k_stream_todf<<<grid_of(p->N_tot), 256, 0, st>>>(in.as<double>(), p->N_tot, out.as<df>(), b);
+        return QCP_OK;
+    };
+    QCP_TRY(todf(p->d_coefA, lay->d_cA));
+    QCP_TRY(todf(p->d_coefB, lay->d_cB));
+    QCP_TRY(todf(p->d_rw, lay->d_rw));
+    QCP_TRY(todf(p->d_cd, lay->d_cd));
+    QCP_TRY(todf(p->d_zy, lay->d_zy));
+    QCP_TRY(lay->d_soc.alloc(sizeof(StreamSoc) * (size_t)std::max<int64_t>(p->nsoc_tot, 1)));
+    if (p->nsoc_tot > 0)
+        k_stream_soc<<<grid_of(p->nsoc_tot), 256, 0, st>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot,
+                                                            lay->d_soc.as<StreamSoc>(), b);
+    QCP_CUDA(cudaGetLastError());
+    // per-system workspace: CTAs per system up to the number resident at once
+    int dev = 0, nsm = 0, occ = 0;
+    QCP_CUDA(cudaGetDevice(&dev));
+    QCP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    QCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream<PASS_GT, ROLE_V, true>, kSThreads, 0));
+    lay->gmax = std::max(1, nsm * std::max(occ, 1));
+    const int64_t nsys = std::max(1, p->nsys_cap);
+    const int64_t per = p->batched ? 1 : nsys;  // split-row storage: per system unless each system is a problem
+    QCP_TRY(lay->d_scal.alloc(sizeof(StreamScal) * nsys));
+    QCP_TRY(lay->d_ssys.alloc(sizeof(StreamSys) * nsys));
+    QCP_CUDA(cudaMemsetAsync(lay->d_ssys.p, 0, sizeof(StreamSys) * nsys, st));
+    QCP_TRY(lay->d_cpart.alloc(sizeof(Part) * nsys * lay->gmax));
+    QCP_TRY(lay->d_ccnt.alloc(sizeof(int32_t) * nsys));
+    QCP_CUDA(cudaMemsetAsync(lay->d_ccnt.p, 0, sizeof(int32_t) * nsys, st));
+    QCP_TRY(lay->d_lchunk.alloc(sizeof(df) * per * std::max(1, lay->nslot)));
+    QCP_TRY(lay->d_lcnt.alloc(sizeof(int32_t) * per * std::max(1, lay->nsplit)));
+    QCP_CUDA(cudaMemsetAsync(lay->d_lcnt.p, 0, sizeof(int32_t) * per * std::max(1, lay->nsplit), st));
+    QCP_TRY(lay->d_lrow.alloc(sizeof(df) * 3 * per * std::max(1, lay->nsplit)));
+    int hbad = 1;
+    QCP_CUDA(cudaMemcpyAsync(&hbad, b, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QCP_CUDA(cudaStreamSynchronize(st));
+    lay->ok = hbad == 0;
+    if (!lay->ok) lay->why = "a magnitude in the data lies outside the double-float range 2^-90..2^90";
+    return QCP_OK;
+}
+
+int stream_ready(qcp_plan* p, bool* ok) {
+    if (!p->stream_lay) {
+        auto lay = std::make_unique<StreamLayout>();
+        QCP_TRY(p->dtype == QCP_F64 ? build_stream<double>(p, lay.get()) : build_stream<float>(p, lay.get()));
+        p->stream_lay = std::move(lay);
+    }
+    *ok = p->stream_lay->ok;
+    if (!*ok) set_error("stream engine: %s", p->stream_lay->why.c_str());
+    return QCP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Iterations.
+static StreamArgs stream_args(qcp_plan* p, const StreamLayout* lay, int scaled) {
+    StreamArgs a{};
+    a.units = lay->d_units.as<StreamUnit>();
+    a.uoff = lay->d_uoff.as<int32_t>();
+    a.soff = lay->d_soff.as<int32_t>();
+    a.rows = lay->d_rows.as<int32_t>();
+    a.lblk = lay->d_lblk.as<int32_t>();
+    a.scol = lay->d_scol.as<int32_t>();
+    a.valG = scaled ? lay->d_valG.as<df>() : lay->d_val.as<df>();
+    a.valT = scaled ? lay->d_valT.as<df>() : lay->d_val.as<df>();
+    a.cA = lay->d_cA.as<df>();
+    a.cB = lay->d_cB.as<df>();
+    a.rw = lay->d_rw.as<df>();
+    a.cd = lay->d_cd.as<df>();
+    a.zy = lay->d_zy.as<df>();
+    a.flag = p->d_flag.as<int8_t>();
+    a.soc = lay->d_soc.as<StreamSoc>();
+    a.rwd = p->d_rw.as<double>();
+    a.cdd = p->d_cd.as<double>();
+    a.sys = p->d_sys.as<Sys>();
+    a.probs = p->d_prob.as<Prob>();
+    a.state = p->d_state.as<LsqrState>();
+    a.scal = lay->d_scal.as<StreamScal>();
+    a.ssys = lay->d_ssys.as<StreamSys>();
+    a.U = reinterpret_cast<df*>(p->d_U.p);
+    a.V = reinterpret_cast<df*>(p->d_V.p);
+    a.W = reinterpret_cast<df*>(p->d_W.p);
+    a.X = reinterpret_cast<df*>(p->d_X.p);
+    a.XI = reinterpret_cast<df*>(p->d_XI.p);
+    a.cpart = lay->d_cpart.as<Part>();
+    a.ccnt = lay->d_ccnt.as<int32_t>();
+    a.lchunk = lay->d_lchunk.as<df>();
+    a.lcnt = lay->d_lcnt.as<int32_t>();
+    a.lrow = lay->d_lrow.as<df>();
+    a.nsplit = lay->nsplit;
+    a.nslot = lay->nslot;
+    a.batched = p->batched ? 1 : 0;
+    return a;
+}
+
+template <bool SC>
+static void launch_stream_iter_sc(int mode, const StreamArgs& a, int ns, cudaStream_t st) {
+    const dim3 grid((unsigned)a.gx, (unsigned)ns);
+    if (mode == 0) {
+        k_stream<PASS_G, ROLE_U, SC><<<grid, kSThreads, 0, st>>>(a);
+        k_stream<PASS_GT, ROLE_V, SC><<<grid, kSThreads, 0, st>>>(a);
+    } else {
+        k_stream<PASS_GT, ROLE_U, SC><<<grid, kSThreads, 0, st>>>(a);
+        k_stream<PASS_G, ROLE_V, SC><<<grid, kSThreads, 0, st>>>(a);
+    }
+}
+
+static void launch_stream_iter(int mode, const StreamArgs& a, int ns, bool scaled, cudaStream_t st) {
+    if (scaled) launch_stream_iter_sc<true>(mode, a, ns, st);
+    else launch_stream_iter_sc<false>(mode, a, ns, st);
+}
+
+static int run_stream_chunk(qcp_plan* p, int mode, int s0, int ns, const StreamArgs& a, bool scaled, int chunk,
+                            bool use_graph) {
+    cudaStream_t st = p->stream;
+    if (!use_graph || chunk < 2) {
+        for (int c = 0; c < chunk; ++c) launch_stream_iter(mode, a, ns, scaled, st);
+        QCP_CUDA(cudaGetLastError());
+        p->last_launches += 2 * chunk;
+        return QCP_OK;
+    }
+    GraphKey key{QCP_ENGINE_STREAM, mode, s0, ns, chunk, scaled ? 1 : 0, 0};
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        QCP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int c = 0; c < chunk; ++c) launch_stream_iter(mode, a, ns, scaled, st);
+        const cudaError_t le = cudaGetLastError();
+        const cudaError_t ee = cudaStreamEndCapture(st, &g);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            set_error("graph capture failed: %s", cudaGetErrorString(le != cudaSuccess ? le : ee));
+            return QCP_ERR_CUDA;
+        }
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            set_error("graph instantiation failed: %s", cudaGetErrorString(ie));
+            return QCP_ERR_CUDA;
+        }
+        it = p->graphs.emplace(key, ge).first;
+    }
+    QCP_CUDA(cudaGraphLaunch(it->second, st));
+    p->last_launches += 2 * chunk;
+    return QCP_OK;
+}
+
+int iterate_stream(qcp_plan* p, int mode, int s0, int ns, int* active, bool scaled, const qcp_options& opts) {
+    const StreamLayout* lay = p->stream_lay.get();
+    if (!lay || !lay->ok) {
+        set_error("stream engine: the plan's layout is not usable");
+        return QCP_ERR_ARG;
+    }
+    StreamArgs a = stream_args(p, lay, scaled ? 1 : 0);
+    a.s0 = s0;
+    a.active = active;
+    // CTAs per system: the GPU's resident CTAs shared by the systems, and no
+    // more than the problem's units keep busy
+    int gx = (lay->gmax + ns - 1) / ns;
+    gx = std::min(gx, std::max(1, (lay->max_units + kSWarps - 1) / kSWarps));
+    a.gx = std::max(1, gx);
+    cudaStream_t st = p->stream;
+    int maxN = 1;
+    for (int s = s0; s < s0 + ns; ++s) {
+        const Prob& pr = p->hprob[p->hsys[s].prob];
+        maxN = std::max(maxN, pr.n + pr.m + 1);
+    }
+    const dim3 vgrid((unsigned)std::min(1024, (maxN + 255) / 256), (unsigned)ns);
+    k_stream_enter_state<<<ns, 32, 0, st>>>(a, mode == 0 ? 1 : 0, scaled ? 1 : 0);
+    k_stream_enter_vec<<<vgrid, 256, 0, st>>>(a);
+    QCP_CUDA(cudaGetLastError());
+    p->last_launches += 2;
+    int64_t done = 0;
+    const int64_t cap = opts.maxiter + 1;
+    while (done < cap) {
+        int64_t chunk = opts.check_every > 0 ? opts.check_every : cap;
+        chunk = std::min<int64_t>(chunk, cap - done);
+        const bool graph_ok = opts.use_graph && opts.check_every > 0 && chunk == opts.check_every;
+        QCP_CUDA(cudaEventRecord(p->ev0, st));
+        QCP_TRY(run_stream_chunk(p, mode, s0, ns, a, scaled, (int)chunk, graph_ok));
+        QCP_CUDA(cudaEventRecord(p->ev1, st));
+        done += chunk;
+        p->pass_launches += 2 * chunk;
+        if (opts.check_every > 0) {
+            QCP_CUDA(cudaMemcpyAsync(p->h_active, active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            QCP_CUDA(cudaStreamSynchronize(st));
+        } else {
+            QCP_CUDA(cudaEventSynchronize(p->ev1));
+        }
+        float ms = 0.0f;
+        QCP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->pass_ms += ms;
+        if (opts.check_every > 0 && *p->h_active <= 0) break;
+    }
+    k_stream_exit_vec<<<vgrid, 256, 0, st>>>(a);
+    k_stream_exit_state<<<ns, 32, 0, st>>>(a);
+    QCP_CUDA(cudaGetLastError());
+    p->last_launches += 2;
+    return QCP_OK;
+}
+
+}  // namespace qcpd

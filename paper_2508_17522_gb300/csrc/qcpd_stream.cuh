@@ -1,0 +1,743 @@
+// The stream engine: one launch per pass for problems whose vectors do not
+// fit in shared memory (arXiv 2508.17522, Sec. 3.1-3.3: every LSQR
+// iteration is one product with F and one with F^T, here through
+// G = S F and the combined matrix M; see qcpd_common.cuh).
+//
+// Work is cut into warp-sized units that need no CTA barrier:
+//   SU_SLICE  up to 32 rows with no coupling inside D Pi (x-rows, or zero-
+//             cone and R+ rows), one row per lane, stored SELL-32 (slot
+//             (k, lane) at base + 32 k + lane, rows sorted by length so the
+//             slice is nearly dense);
+//   SU_SOCP   consecutive second-order-cone blocks of at most 32 rows in
+//             all, one row per lane; D Pi's dot products are segmented
+//             warp reductions (one segment per block);
+//   SU_SOCB   one second-order-cone block of 33 to kSSocBig rows, rows
+//             lane + 32 j, the block's values through a per-warp
+//             shared-memory buffer;
+//   SU_LONG   up to kSLongChunk stored entries of one long row, read
+//             lane-strided; the last chunk of a row to finish adds the
+//             chunk sums in order and runs the row's epilogue.
+// A launch has gridDim.y = systems; the warps of a system's CTAs take its
+// units in snake order (units sorted by cost, largest first).  Per-lane sums
+// of the pass (||out||^2 and the two tau-row dot products) are reduced per
+// warp, per CTA and finally, by the system's last CTA, over CTAs in a
+// fixed order, so results do not depend on scheduling.
+//
+// Arithmetic.  FP64 instructions issue at 1/64 of the FP32 rate on this
+// GPU, so every per-row operation runs in double-float (df64, about 48
+// significant bits; qcpd_df64.cuh) on df64 copies of M's values and of the
+// per-row data; the Krylov vectors U, V, W, X, XI are the plan's FP64
+// arrays reinterpreted as df64 pairs in place while the engine iterates
+// (k_stream_enter / k_stream_exit convert them, the right-hand side scaled
+// by a power of two to norm in [1/2, 1) as in the cluster engine).  Their
+// tau entries and the LSQR scalar recurrences stay in FP64 (one thread per
+// system and pass).
+#pragma once
+
+#include "qcpd_df64.cuh"
+#include "qcpd_kernels.cuh"
+
+namespace qcpd {
+
+constexpr int kSThreads = 256;
+constexpr int kSWarps = kSThreads / 32;
+constexpr int kSLongRow = 64;      // rows with more stored entries are read lane-strided (SU_LONG)
+constexpr int kSLongChunk = 1024;  // stored entries per SU_LONG unit
+constexpr int kSSocBig = 256;      // largest second-order-cone block the engine takes
+
+enum StreamKind : int32_t { SU_SLICE = 0, SU_SOCP = 1, SU_SOCB = 2, SU_LONG = 3 };
+
+struct StreamUnit {
+    int32_t kind;
+    int32_t prob;    // problem (batch plans: also the system)
+    int32_t nrows;   // SLICE / SOCP: rows (<= 32); SOCB: the block's rows; LONG: chunks of the row
+    int32_t width;   // SLICE / SOCP: SELL width; SOCB: sub-slices; LONG: entries of this chunk
+    int64_t base;    // first slot of the unit's entries
+    int32_t aux;     // SLICE / SOCP: offset of the lanes' rows in rows[] (SOCP: and block indices in
+                     // lblk[]); SOCB: offset of the sub-slices' widths in rows[]; LONG: the row
+    int32_t blk;     // SOCB: the block (problem-relative); LONG: split-row index (plan-wide, -1: one chunk)
+    int32_t chunk;   // LONG: chunk index
+    int32_t row0;    // SOCB: first row; LONG: first chunk slot (plan-wide) of the row's chunk sums
+};
+
+// df64 constants of a second-order-cone block in the formula case (Appendix A):
+// r = ||u||, h = 1/(2r), tq = t/r^2, htr = h (t + r); and the block's layout.
+struct StreamSoc {
+    df r, h, tq, htr;
+    int32_t start, dim, kase, pad;
+};
+
+// This pass's scalars for the vector work, written by the previous pass's
+// finisher (or by k_stream_enter): c1, -c2, -wcoef, xcoef and the tau
+// column's coefficient tt.
+struct StreamScal {
+    df c1, nc2, nw, xc, tt;
+    double pad;
+};
+
+// Per system while the engine iterates: the FP64 tau entries of U, V, W, X,
+// XI (they never enter a gather) and the scale of the right-hand side.
+enum { TS_U = 0, TS_V = 1, TS_W = 2, TS_X = 3, TS_XI = 4 };
+struct StreamSys {
+    double tau[5];
+    double scale;   // the right-hand side was multiplied by this power of two
+    int32_t uscaled;  // U and beta carry the scale too (no u-update yet)
+    int32_t pad;
+};
+
+struct StreamArgs {
+    const StreamUnit* units;
+    const int32_t* uoff;    // per problem: its units [uoff[p], uoff[p + 1])
+    const int32_t* rows;    // per lane row ids (SLICE, SOCP) and SOCB sub-slice widths
+    const int32_t* lblk;    // SOCP: the lane's block (problem-relative), -1 for padding lanes
+    const int32_t* scol;    // slot -> local column of M
+    const df* valG;         // slot values: M diag(c) for G-passes (M when unscaled)
+    const df* valT;         // M diag(w) for G^T-passes (M when unscaled)
+    const df* cA;           // N-indexed per-row data (plan-wide offsets): coefA, coefB, w, c, z_y
+    const df* cB;
+    const df* rw;
+    const df* cd;
+    const df* zy;
+    const int8_t* flag;
+    const StreamSoc* soc;   // per block (plan-wide)
+    const double* rwd;      // FP64 w and c (tau entries)
+    const double* cdd;
+    const Sys* sys;
+    const Prob* probs;
+    LsqrState* state;
+    StreamScal* scal;       // per system
+    StreamSys* ssys;        // per system
+    df* U;                  // plan vectors as df64 pairs (system offsets voff)
+    df* V;
+    df* W;
+    df* X;
+    df* XI;
+    Part* cpart;            // per (system, CTA) partial sums
+    int32_t* ccnt;          // per system: CTAs done in this pass
+    df* lchunk;             // per (system, chunk slot): chunk sums of split rows
+    int32_t* lcnt;          // per (system, split row): chunks done
+    df* lrow;               // per (system, split row): 3 sums of the row's epilogue
+    int32_t nsplit;         // split rows per system stride
+    int32_t nslot;          // chunk slots per system stride
+    const int32_t* soff;    // per problem: its split rows [soff[p], soff[p + 1])
+    int32_t gx;             // CTAs per system (gridDim.x)
+    int32_t s0;             // first system of the launch
+    int32_t batched;
+    int* active;
+};
+
+// ---------------------------------------------------------------------------
+// Per-CTA constants of one pass of one system.
+struct SCtx {
+    StreamScal sc;
+    int n, N;
+    const df *cA, *cB, *rw, *cd, *zy;  // problem-relative
+    const int8_t* flag;
+    const StreamSoc* soc;              // the problem's blocks
+    const df* gin;                     // the gathered vector (XI for G-passes, the input for G^T-passes)
+    df *IN, *OUT, *W, *X, *XI;         // system-relative
+};
+
+// Per-lane sums of the pass: ||out||^2 and the tau-row dot products.
+struct SAcc {
+    DfAcc ss, dtop, dbot;
+};
+
+__device__ __forceinline__ void sacc_zero(SAcc& a) {
+    a.ss = dfacc_zero();
+    a.dtop = dfacc_zero();
+    a.dbot = dfacc_zero();
+}
+
+__device__ __forceinline__ df dfl(const df* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+
+// The row sum of one lane's row in a SELL-32 slice: sum_k val[slot] g[col[slot]]
+// over slots base + 32 k + lane, k < width.  A padding slot holds the value 0
+// and repeats the row's last column (an L1 hit), so no slot needs a test.
+__device__ __forceinline__ df sell_rowsum(const int32_t* scol, const df* val, const df* g, int64_t base,
+                                          int width) {
+    const int lane = threadIdx.x & 31;
+    DfAcc acc = dfacc_zero();
+    int k = 0;
+    for (; k + 4 <= width; k += 4) {
+        int32_t c[4];
+        df v[4], x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t s = base + 32 * (int64_t)(k + j) + lane;
+            c[j] = __ldg(scol + s);
+            v[j] = dfl(val + s);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = dfl(g + c[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dfacc_fma(acc, v[j], x[j]);
+    }
+    for (; k < width; ++k) {
+        const int64_t s = base + 32 * (int64_t)k + lane;
+        dfacc_fma(acc, dfl(val + s), dfl(g + __ldg(scol + s)));
+    }
+    return dfacc_result(acc);
+}
+
+// One chunk of a long row read lane-strided (entries base .. base + cnt),
+// summed over the warp in a fixed order; every lane gets the sum.
+__device__ __forceinline__ df long_rowsum(const int32_t* scol, const df* val, const df* g, int64_t base, int cnt) {
+    const int lane = threadIdx.x & 31;
+    DfAcc acc = dfacc_zero();
+    int k = lane;
+    for (; k + 96 < cnt; k += 128) {
+        int32_t c[4];
+        df v[4], x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            c[j] = __ldg(scol + base + k + 32 * j);
+            v[j] = dfl(val + base + k + 32 * j);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = dfl(g + c[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dfacc_fma(acc, v[j], x[j]);
+    }
+    for (; k < cnt; k += 32) dfacc_fma(acc, dfl(val + base + k), dfl(g + __ldg(scol + base + k)));
+    return warp_sum_df(dfacc_result(acc));
+}
+
+// ---- row epilogues (the formulas of run_tile in qcpd_kernels.cuh, in df64)
+// G-pass, row r with row sum h: out = W (M_top xi + q t | M_bot xi - b t - c + D c) C,
+// then the u- or v-update of that row.
+template <int ROLE, bool SC>
+__device__ __forceinline__ void g_row(const SCtx& c, int r, df h, SAcc& acc) {
+    const df iv = c.IN[r];
+    df o;
+    if (r < c.n) {
+        o = df_fma(dfl(c.cA + r), c.sc.tt, h);
+        dfacc_fma(acc.dtop, dfl(c.cB + r), SC ? df_mul(dfl(c.cd + r), iv) : iv);
+    } else {
+        const df xi = c.XI[r];
+        const df dxi = SC ? df_mul(dfl(c.cd + r), df_sub(xi, iv)) : df_sub(xi, iv);
+        o = df_add(df_fma(df_neg(dfl(c.cA + r)), c.sc.tt, h), dxi);
+        dfacc_fma(acc.dbot, dfl(c.cB + r), SC ? df_mul(dfl(c.cd + r), xi) : xi);
+    }
+    if (SC) o = df_mul(o, dfl(c.rw + r));
+    const df nv = df_fma(c.sc.c1, o, df_mul(c.sc.nc2, c.OUT[r]));
+    c.OUT[r] = nv;
+    dfacc_fma(acc.ss, nv, nv);
+    if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c.sc.c1, df_mul(c.sc.nw, c.W[r]));
+    else c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
+}
+
+// G^T-pass, first half of row r: s1 = (M rho - g r3)_r on x-rows,
+// (M rho - b r3)_r + (w in)_r on y-rows; ivs = (w in)_r.
+template <bool SC>
+__device__ __forceinline__ df gt_pre(const SCtx& c, int r, df h, df& ivs, SAcc& acc) {
+    const df iv = c.IN[r];
+    ivs = SC ? df_mul(dfl(c.rw + r), iv) : iv;
+    const df h1 = df_fma(df_neg(dfl(c.cB + r)), c.sc.tt, h);
+    if (r < c.n) {
+        dfacc_fma(acc.dtop, dfl(c.cA + r), ivs);
+        return h1;
+    }
+    dfacc_fma(acc.dbot, dfl(c.cA + r), ivs);
+    return df_add(h1, ivs);
+}
+
+// G^T-pass, second half of row r given s2 = (D s1)_r: the u- or v-update;
+// returns the new out_r (whose D Pi the caller stores in XI).
+template <int ROLE, bool SC>
+__device__ __forceinline__ df gt_post(const SCtx& c, int r, df s2, df ivs, SAcc& acc) {
+    df o = (r < c.n) ? s2 : df_sub(s2, ivs);
+    if (SC) o = df_mul(o, dfl(c.cd + r));
+    const df nv = df_fma(c.sc.c1, o, df_mul(c.sc.nc2, c.OUT[r]));
+    c.OUT[r] = nv;
+    dfacc_fma(acc.ss, nv, nv);
+    if (ROLE == ROLE_U) c.W[r] = df_fma(c.IN[r], c.sc.c1, df_mul(c.sc.nw, c.W[r]));
+    else c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
+    return nv;
+}
+
+// D on a row outside second-order-cone blocks: 1 on x-rows and zero-cone
+// rows (the dual of {0} is R), the 0/1 flag on R+ rows.
+__device__ __forceinline__ df d_diag(const SCtx& c, int r, df v) {
+    if (r < c.n) return v;
+    return c.flag[r] == RF_ONE ? v : df_zero();
+}
+
+// One non-coupled row of a G^T-pass (x-rows, zero-cone and R+ rows).
+template <int ROLE, bool SC>
+__device__ __forceinline__ void gt_row(const SCtx& c, int r, df h, SAcc& acc) {
+    df ivs;
+    const df s1 = gt_pre<SC>(c, r, h, ivs, acc);
+    const df nv = gt_post<ROLE, SC>(c, r, d_diag(c, r, s1), ivs, acc);
+    c.XI[r] = d_diag(c, r, nv);
+}
+
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void plain_row(const SCtx& c, int r, df h, SAcc& acc) {
+    if (PASS == PASS_G) g_row<ROLE, SC>(c, r, h, acc);
+    else gt_row<ROLE, SC>(c, r, h, acc);
+}
+
+// ---- second-order-cone blocks (Appendix A): D Pi_{K*} at z_y = (t, u)
+// maps (c_t, c_u) to h (r c_t + u^T c_u, ...) in the formula case (kase 2),
+// to 0 inside the polar cone (kase 0) and to itself inside the cone (kase 1).
+__device__ __forceinline__ df soc_d(df v, df u, int pos, df ct, df dot, int kase, const StreamSoc& B) {
+    if (kase == 0) return df_zero();
+    if (kase != 2) return v;
+    if (pos == 0) return df_mul(B.h, df_fma(B.r, ct, dot));
+    const df aa = df_mul(B.h, df_fma(df_neg(B.tq), dot, ct));
+    return df_fma(aa, u, df_mul(B.htr, v));
+}
+
+__device__ __forceinline__ df shfl_df(df v, int src) {
+    df o;
+    o.x = __shfl_sync(0xffffffffu, v.x, src);
+    o.y = __shfl_sync(0xffffffffu, v.y, src);
+    return o;
+}
+
+// D on packed blocks, one row per lane: the lanes [head, end] hold one
+// block; u^T c_u is a segmented sum (after the doubling steps the head lane
+// holds its whole block's sum, each lane adding only from its own block).
+// Every lane calls it.
+__device__ __forceinline__ df socp_d(df v, df u, int pos, int head, int end, int kase, const StreamSoc& B) {
+    const int lane = threadIdx.x & 31;
+    df t = (kase == 2 && pos > 0) ? df_mul(u, v) : df_zero();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        df o;
+        o.x = __shfl_down_sync(0xffffffffu, t.x, d);
+        o.y = __shfl_down_sync(0xffffffffu, t.y, d);
+        if (lane + d <= end) t = df_add(t, o);
+    }
+    const df dot = shfl_df(t, head);
+    const df ct = shfl_df(v, head);
+    return soc_d(v, u, pos, ct, dot, kase, B);
+}
+
+struct SUnitCtx {
+    const int32_t* rows;
+    const int32_t* lblk;
+    const int32_t* scol;
+    const df* val;
+};
+
+// SU_SLICE and SU_SOCP units of a G-pass, and SU_SLICE units of a G^T-pass:
+// one row per lane, no coupling.
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void unit_slice(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, SAcc& acc) {
+    const int lane = threadIdx.x & 31;
+    const int r = k.rows[u.aux + lane];
+    const df h = sell_rowsum(k.scol, k.val, c.gin, u.base, u.width);
+    if (r >= 0) plain_row<PASS, ROLE, SC>(c, r, h, acc);
+}
+
+// SU_SOCB units of a G-pass: rows row0 + 32 j + lane, no coupling.
+template <int ROLE, bool SC>
+__device__ __forceinline__ void unit_socb_g(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, SAcc& acc) {
+    const int lane = threadIdx.x & 31;
+    int64_t base = u.base;
+    for (int j = 0; j < u.width; ++j) {
+        const int w = k.rows[u.aux + j];
+        const df h = sell_rowsum(k.scol, k.val, c.gin, base, w);
+        base += 32 * (int64_t)w;
+        const int i = 32 * j + lane;
+        if (i < u.nrows) g_row<ROLE, SC>(c, u.row0 + i, h, acc);
+    }
+}
+
+// SU_SOCP units of a G^T-pass.
+template <int ROLE, bool SC>
+__device__ __forceinline__ void unit_socp_gt(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, SAcc& acc) {
+    const int lane = threadIdx.x & 31;
+    const int r = k.rows[u.aux + lane];
+    const int bi = k.lblk[u.aux + lane];
+    const df h = sell_rowsum(k.scol, k.val, c.gin, u.base, u.width);
+    int head = lane, end = lane, kase = 1, pos = 0;
+    StreamSoc B{};
+    if (bi >= 0) {
+        B = c.soc[bi];
+        pos = r - B.start;
+        head = lane - pos;
+        end = head + B.dim - 1;
+        kase = B.kase;
+    }
+    df ivs = df_zero(), s1 = df_zero(), uk = df_zero();
+    if (r >= 0) {
+        s1 = gt_pre<SC>(c, r, h, ivs, acc);
+        uk = dfl(c.zy + r);
+    }
+    const df s2 = socp_d(s1, uk, pos, head, end, kase, B);
+    df nv = df_zero();
+    if (r >= 0) nv = gt_post<ROLE, SC>(c, r, s2, ivs, acc);
+    const df xi = socp_d(nv, uk, pos, head, end, kase, B);
+    if (r >= 0) c.XI[r] = xi;
+}
+
+// SU_SOCB units of a G^T-pass: the block's values go through the warp's
+// shared-memory buffer sb (kSSocBig entries).
+template <int ROLE, bool SC>
+__device__ __forceinline__ void unit_socb_gt(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, df* sb,
+                                             SAcc& acc) {
+    const int lane = threadIdx.x & 31;
+    const StreamSoc B = c.soc[u.blk];
+    const int dim = u.nrows, r0 = u.row0;
+    int64_t base = u.base;
+    df part = df_zero();
+    for (int j = 0; j < u.width; ++j) {
+        const int w = k.rows[u.aux + j];
+        const df h = sell_rowsum(k.scol, k.val, c.gin, base, w);
+        base += 32 * (int64_t)w;
+        const int i = 32 * j + lane;
+        if (i < dim) {
+            df ivs;
+            const df s1 = gt_pre<SC>(c, r0 + i, h, ivs, acc);
+            sb[i] = s1;
+            if (i > 0 && B.kase == 2) part = df_fma(dfl(c.zy + r0 + i), s1, part);
+        }
+    }
+    __syncwarp();
+    df dot = warp_sum_df(part);
+    df ct = sb[0];
+    __syncwarp();
+    part = df_zero();
+    for (int i = lane; i < dim; i += 32) {
+        const int r = r0 + i;
+        const df uk = dfl(c.zy + r);
+        const df iv = c.IN[r];
+        const df ivs = SC ? df_mul(dfl(c.rw + r), iv) : iv;
+        const df nv = gt_post<ROLE, SC>(c, r, soc_d(sb[i], uk, i, ct, dot, B.kase, B), ivs, acc);
+        sb[i] = nv;
+        if (i > 0 && B.kase == 2) part = df_fma(uk, nv, part);
+    }
+    __syncwarp();
+    dot = warp_sum_df(part);
+    ct = sb[0];
+    for (int i = lane; i < dim; i += 32) c.XI[r0 + i] = soc_d(sb[i], dfl(c.zy + r0 + i), i, ct, dot, B.kase, B);
+    __syncwarp();
+}
+
+// SU_LONG units: a chunk of one long row (never inside a coupled block).  A
+// row in one chunk is finished by lane 0; a split row's chunk sums go to
+// its slots, and the chunk that completes the row adds them in order and
+// runs the epilogue, whose contributions to the pass's sums go to the row's
+// own slot (added by the finisher in row order, so the result does not
+// depend on which chunk came last).
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void unit_long(const SCtx& c, const SUnitCtx& k, const StreamArgs& a, int si,
+                                          const StreamUnit& u, SAcc& acc) {
+    const int lane = threadIdx.x & 31;
+    const df h = long_rowsum(k.scol, k.val, c.gin, u.base, u.width);
+    if (lane != 0) return;
+    const int r = u.aux;
+    if (u.blk < 0) {
+        plain_row<PASS, ROLE, SC>(c, r, h, acc);
+        return;
+    }
+    const int64_t so = a.batched ? 0 : (int64_t)si * a.nslot;
+    const int64_t sr = a.batched ? 0 : (int64_t)si * a.nsplit;
+    a.lchunk[so + u.row0 + u.chunk] = h;
+    __threadfence();
+    const int prev = atomicAdd(a.lcnt + sr + u.blk, 1);
+    if (prev != u.nrows - 1) return;
+    __threadfence();
+    df t = df_zero();
+    for (int q = 0; q < u.nrows; ++q)
+        t = df_add(t, __ldcg(reinterpret_cast<const float2*>(a.lchunk + so + u.row0 + q)));
+    a.lcnt[sr + u.blk] = 0;
+    SAcc racc;
+    sacc_zero(racc);
+    plain_row<PASS, ROLE, SC>(c, r, t, racc);
+    df* o = a.lrow + 3 * (sr + u.blk);
+    o[0] = dfacc_result(racc.ss);
+    o[1] = dfacc_result(racc.dtop);
+    o[2] = dfacc_result(racc.dbot);
+}
+
+// ---------------------------------------------------------------------------
+// The system's finisher (one thread): the tau entry of the pass's output and
+// the LSQR scalars, in FP64 as in run_tile, then the next pass's scalars.
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only_x) {
+    LsqrState* st = a.state + si;
+    double* tau = a.ssys[si].tau;
+    const int rN = pr.n + pr.m;
+    const double rwN = a.rwd[pr.doff + rN], cdN = a.cdd[pr.doff + rN];
+    if (only_x) {
+        tau[TS_X] = fma(st->xcoef, tau[TS_W], tau[TS_X]);
+        st->status = S_DONE;
+        atomicSub(a.active, 1);
+        return;
+    }
+    const double c1 = ROLE == ROLE_U ? st->uc1 : st->vc1;
+    const double c2 = ROLE == ROLE_U ? st->uc2 : st->vc2;
+    const double wcoef = st->wcoef, xcoef = st->xcoef;
+    const int tin_i = ROLE == ROLE_U ? TS_V : TS_U, tout_i = ROLE == ROLE_U ? TS_U : TS_V;
+    const double tin = tau[tin_i];
+    const double tt = SC ? (PASS == PASS_G ? cdN : rwN) * tin : tin;
+    double oN;
+    if (PASS == PASS_G) {
+        oN = -tot.b - tot.c + pr.kappa * tt;
+        if (SC) oN *= rwN;
+    } else {
+        oN = tot.b - tot.c + pr.kappa * tt;
+        if (SC) oN *= cdN;
+    }
+    // gauge dz_N = 0: G^T-passes leave the tau entry at 0 (see run_tile)
+    const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * tau[tout_i];
+    tau[tout_i] = nvN;
+    if (PASS == PASS_GT) tau[TS_XI] = 0.0;
+    const double nsq = fma(nvN, nvN, tot.a);
+    double nrm, inv;
+    norm_and_inverse(nsq, nrm, inv);
+    if (ROLE == ROLE_U) {
+        tau[TS_W] = tin * c1 - wcoef * tau[TS_W];
+        lsqr_step_u(st, nrm, inv, nsq);
+    } else {
+        tau[TS_X] = fma(xcoef, tau[TS_W], tau[TS_X]);
+        if (lsqr_step_v(st, nrm, inv)) atomicSub(a.active, 1);
+    }
+    // the next pass: the other product, the other update
+    constexpr int NPASS = PASS == PASS_G ? PASS_GT : PASS_G;
+    const double nc1 = ROLE == ROLE_U ? st->vc1 : st->uc1;
+    const double nc2 = ROLE == ROLE_U ? st->vc2 : st->uc2;
+    const double ntin = tau[ROLE == ROLE_U ? TS_U : TS_V];
+    const double ntt = SC ? (NPASS == PASS_G ? cdN : rwN) * ntin : ntin;
+    StreamScal q;
+    q.c1 = df_from(nc1);
+    q.nc2 = df_from(-nc2);
+    q.nw = df_from(-st->wcoef);
+    q.xc = df_from(st->xcoef);
+    q.tt = df_from(ntt);
+    q.pad = 0.0;
+    a.scal[si] = q;
+}
+
+// One pass of the systems [s0, s0 + gridDim.y): PASS_G or PASS_GT, ROLE_U or
+// ROLE_V (the product and update of run_tile), SC = diagonal scaling.
+template <int PASS, int ROLE, bool SC>
+__global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
+    __shared__ df sbuf[kSWarps][kSSocBig];
+    __shared__ df red[kSWarps][3];
+    __shared__ int s_last;
+    const int si = a.s0 + (int)blockIdx.y;
+    const int status = a.state[si].status;
+    if (status == S_DONE) return;
+    const Sys sy = a.sys[si];
+    const Prob pr = a.probs[sy.prob];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    SCtx c;
+    c.sc = a.scal[si];
+    c.n = pr.n;
+    c.N = pr.n + pr.m + 1;
+    c.cA = a.cA + pr.doff;
+    c.cB = a.cB + pr.doff;
+    c.rw = a.rw + pr.doff;
+    c.cd = a.cd + pr.doff;
+    c.zy = a.zy + pr.doff;
+    c.flag = a.flag + pr.doff;
+    c.soc = a.soc + pr.soff;
+    c.IN = (ROLE == ROLE_U ? a.V : a.U) + sy.voff;
+    c.OUT = (ROLE == ROLE_U ? a.U : a.V) + sy.voff;
+    c.W = a.W + sy.voff;
+    c.X = a.X + sy.voff;
+    c.XI = a.XI + sy.voff;
+    c.gin = PASS == PASS_G ? c.XI : c.IN;
+    SUnitCtx k{a.rows, a.lblk, a.scol, PASS == PASS_G ? a.valG : a.valT};
+    const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
+    SAcc acc;
+    sacc_zero(acc);
+    if (only_x) {  // the last x-update of a stopped system
+        for (int r = blockIdx.x * kSThreads + threadIdx.x; r < c.N - 1; r += a.gx * kSThreads)
+            c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
+    } else {
+        const int wt = a.gx * kSWarps, wg = blockIdx.x * kSWarps + warp;
+        const int u0 = a.uoff[sy.prob], nu = a.uoff[sy.prob + 1] - u0;
+        for (int j = 0;; ++j) {  // snake order over the units (sorted by cost, largest first)
+            const int idx = j * wt + ((j & 1) ? wt - 1 - wg : wg);
+            if (idx >= nu) break;
+            const StreamUnit u = a.units[u0 + idx];
+            if (u.kind == SU_LONG) {
+                unit_long<PASS, ROLE, SC>(c, k, a, si, u, acc);
+            } else if (PASS == PASS_G) {
+                if (u.kind == SU_SOCB) unit_socb_g<ROLE, SC>(c, k, u, acc);
+                else unit_slice<PASS, ROLE, SC>(c, k, u, acc);
+            } else {
+                if (u.kind == SU_SLICE) unit_slice<PASS, ROLE, SC>(c, k, u, acc);
+                else if (u.kind == SU_SOCP) unit_socp_gt<ROLE, SC>(c, k, u, acc);
+                else unit_socb_gt<ROLE, SC>(c, k, u, sbuf[warp], acc);
+            }
+        }
+    }
+    // the CTA's sums in a fixed order: lanes, then warps
+    const df v0 = warp_sum_df(dfacc_result(acc.ss));
+    const df v1 = warp_sum_df(dfacc_result(acc.dtop));
+    const df v2 = warp_sum_df(dfacc_result(acc.dbot));
+    if (lane == 0) {
+        red[warp][0] = v0;
+        red[warp][1] = v1;
+        red[warp][2] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        df t0 = red[0][0], t1 = red[0][1], t2 = red[0][2];
+        for (int w = 1; w < kSWarps; ++w) {
+            t0 = df_add(t0, red[w][0]);
+            t1 = df_add(t1, red[w][1]);
+            t2 = df_add(t2, red[w][2]);
+        }
+        a.cpart[(int64_t)si * a.gx + blockIdx.x] = Part{df_to(t0), df_to(t1), df_to(t2), 0.0};
+        __threadfence();
+        const int prev = atomicAdd(a.ccnt + si, 1);
+        s_last = prev == a.gx - 1;
+    }
+    __syncthreads();
+    if (!s_last || warp != 0) return;
+    // the system's last CTA: CTA partials in order, then the split rows' sums
+    __threadfence();
+    Part t = pzero();
+    for (int i = lane; i < a.gx; i += 32) t = padd(t, ld_part(a.cpart + (int64_t)si * a.gx + i));
+    const int64_t sr = a.batched ? 0 : (int64_t)si * a.nsplit;
+    if (!only_x) {
+        for (int i = a.soff[sy.prob] + lane; i < a.soff[sy.prob + 1]; i += 32) {
+            const float2* o = reinterpret_cast<const float2*>(a.lrow + 3 * (sr + i));
+            t = padd(t, Part{df_to(__ldcg(o)), df_to(__ldcg(o + 1)), df_to(__ldcg(o + 2)), 0.0});
+        }
+    }
+    t = warp_sum_part(t);
+    if (lane == 0) {
+        a.ccnt[si] = 0;
+        stream_finish<PASS, ROLE, SC>(a, si, pr, t, only_x);
+    }
+}
+
+// ---- entering and leaving the engine (per call and continuation round)
+// State: the right-hand side's scale (a power of two putting ||b|| in
+// [1/2, 1)), the tau entries into StreamSys, the scaled LSQR scalars
+// (x, phibar, xcoef and bnorm are proportional to the right-hand side, and
+// so are u, beta and 1/uc2 before the first u-update) and the first u-pass's
+// df64 scalars.  One thread per system.
+__global__ void k_stream_enter_state(StreamArgs a, int upass_g, int sc) {
+    const int si = a.s0 + (int)blockIdx.x;
+    if (threadIdx.x != 0) return;
+    LsqrState* st = a.state + si;
+    StreamSys* ss = a.ssys + si;
+    ss->pad = st->status != S_DONE;
+    if (!ss->pad) return;
+    const Sys sy = a.sys[si];
+    const Prob pr = a.probs[sy.prob];
+    const int rN = pr.n + pr.m;
+    const double* U = reinterpret_cast<const double*>(a.U + sy.voff);
+    const double* V = reinterpret_cast<const double*>(a.V + sy.voff);
+    const double* W = reinterpret_cast<const double*>(a.W + sy.voff);
+    const double* X = reinterpret_cast<const double*>(a.X + sy.voff);
+    const double* XI = reinterpret_cast<const double*>(a.XI + sy.voff);
+    double s = 1.0;
+    if (st->bnorm > 0.0 && finite64(st->bnorm)) {
+        int e = 0;
+        frexp(st->bnorm, &e);
+        s = ldexp(1.0, -e);
+    }
+    const int us = st->iters == 0;
+    ss->scale = s;
+    ss->uscaled = us;
+    st->phibar *= s;
+    st->xcoef *= s;
+    st->bnorm *= s;
+    if (us) {
+        st->beta *= s;
+        st->uc2 /= s;
+    }
+    ss->tau[TS_U] = U[rN] * (us ? s : 1.0);
+    ss->tau[TS_V] = V[rN];
+    ss->tau[TS_W] = W[rN];
+    ss->tau[TS_X] = X[rN] * s;
+    ss->tau[TS_XI] = XI[rN];
+    const double tin = ss->tau[TS_V];
+    const double tt = sc ? (upass_g ? a.cdd[pr.doff + rN] : a.rwd[pr.doff + rN]) * tin : tin;
+    StreamScal q;
+    q.c1 = df_from(st->uc1);
+    q.nc2 = df_from(-st->uc2);
+    q.nw = df_from(-st->wcoef);
+    q.xc = df_from(st->xcoef);
+    q.tt = df_from(tt);
+    q.pad = 0.0;
+    a.scal[si] = q;
+}
+
+// Vectors: FP64 -> df64 pairs in place (rows below the tau entry), with the
+// scale.  blockIdx.y = system.
+__global__ void k_stream_enter_vec(StreamArgs a) {
+    const int si = a.s0 + (int)blockIdx.y;
+    const StreamSys ss = a.ssys[si];
+    if (!ss.pad) return;
+    const Sys sy = a.sys[si];
+    const Prob pr = a.probs[sy.prob];
+    const int rN = pr.n + pr.m;
+    const double su = ss.uscaled ? ss.scale : 1.0;
+    double* U = reinterpret_cast<double*>(a.U + sy.voff);
+    double* V = reinterpret_cast<double*>(a.V + sy.voff);
+    double* W = reinterpret_cast<double*>(a.W + sy.voff);
+    double* X = reinterpret_cast<double*>(a.X + sy.voff);
+    double* XI = reinterpret_cast<double*>(a.XI + sy.voff);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rN; r += gridDim.x * blockDim.x) {
+        a.U[sy.voff + r] = df_from(U[r] * su);
+        a.V[sy.voff + r] = df_from(V[r]);
+        a.W[sy.voff + r] = df_from(W[r]);
+        a.X[sy.voff + r] = df_from(X[r] * ss.scale);
+        a.XI[sy.voff + r] = df_from(XI[r]);
+    }
+}
+
+// df64 pairs -> FP64 in place, the scale undone (U only while no u-update
+// has happened since entering).  Runs before k_stream_exit_state.
+__global__ void k_stream_exit_vec(StreamArgs a) {
+    const int si = a.s0 + (int)blockIdx.y;
+    const StreamSys ss = a.ssys[si];
+    if (!ss.pad) return;
+    const Sys sy = a.sys[si];
+    const Prob pr = a.probs[sy.prob];
+    const int rN = pr.n + pr.m;
+    const bool u_still = ss.uscaled && a.state[si].iters == 0;
+    const double iu = u_still ? 1.0 / ss.scale : 1.0, ix = 1.0 / ss.scale;
+    double* U = reinterpret_cast<double*>(a.U + sy.voff);
+    double* V = reinterpret_cast<double*>(a.V + sy.voff);
+    double* W = reinterpret_cast<double*>(a.W + sy.voff);
+    double* X = reinterpret_cast<double*>(a.X + sy.voff);
+    double* XI = reinterpret_cast<double*>(a.XI + sy.voff);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rN; r += gridDim.x * blockDim.x) {
+        U[r] = df_to(a.U[sy.voff + r]) * iu;
+        V[r] = df_to(a.V[sy.voff + r]);
+        W[r] = df_to(a.W[sy.voff + r]);
+        X[r] = df_to(a.X[sy.voff + r]) * ix;
+        XI[r] = df_to(a.XI[sy.voff + r]);
+    }
+}
+
+__global__ void k_stream_exit_state(StreamArgs a) {
+    const int si = a.s0 + (int)blockIdx.x;
+    if (threadIdx.x != 0) return;
+    StreamSys* ss = a.ssys + si;
+    if (!ss->pad) return;
+    LsqrState* st = a.state + si;
+    const Sys sy = a.sys[si];
+    const Prob pr = a.probs[sy.prob];
+    const int rN = pr.n + pr.m;
+    const bool u_still = ss->uscaled && st->iters == 0;
+    const double iu = u_still ? 1.0 / ss->scale : 1.0, ix = 1.0 / ss->scale;
+    st->phibar *= ix;
+    st->xcoef *= ix;
+    st->bnorm *= ix;
+    if (u_still) {
+        st->beta *= iu;
+        st->uc2 /= iu;
+    }
+    reinterpret_cast<double*>(a.U + sy.voff)[rN] = ss->tau[TS_U] * iu;
+    reinterpret_cast<double*>(a.V + sy.voff)[rN] = ss->tau[TS_V];
+    reinterpret_cast<double*>(a.W + sy.voff)[rN] = ss->tau[TS_W];
+    reinterpret_cast<double*>(a.X + sy.voff)[rN] = ss->tau[TS_X] * ix;
+    reinterpret_cast<double*>(a.XI + sy.voff)[rN] = ss->tau[TS_XI];
+    ss->pad = 0;
+}
+
+}  // namespace qcpd

@@ -238,7 +238,8 @@ def test_cluster_sizes_agree(q, ctas):
 
 def test_cluster_engine_limits(q):
     """A system too large for 16 CTAs' shared memory: the cluster engine
-    refuses it, the automatic choice runs the pass engine instead."""
+    refuses it, the automatic choice runs the stream engine instead (the
+    same bits as asking for it)."""
     from paper_2508_17522_gb300._native import QCPError
     prob = g.config3(3, scale=0.1)
     d = g.make_directions(prob, 4)
@@ -246,7 +247,8 @@ def test_cluster_engine_limits(q):
     with pytest.raises(QCPError, match="ERR_ARG"):
         gpu_jvp(q, plan, d, q.options(rtol=1e-8, engine="cluster"))
     a, ai = gpu_jvp(q, plan, d, q.options(rtol=1e-8, engine="auto", precond="equilibrate"))
-    b, bi = gpu_jvp(q, plan, d, q.options(rtol=1e-8, engine="passes", precond="equilibrate"))
+    assert plan.last_engine() == "stream"
+    b, bi = gpu_jvp(q, plan, d, q.options(rtol=1e-8, engine="stream", precond="equilibrate"))
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
     for bad in (-1, 17):
