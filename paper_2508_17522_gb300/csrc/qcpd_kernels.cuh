@@ -781,17 +781,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(PlanView<T> a) {
 // launch.  Each CTA owns the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // and runs them pass after pass; a grid barrier separates the passes (the
 // CTA that completes a system still updates its scalars inside the pass).
-// Every wait is bounded: after kSpinLimit polls the waiting CTA records a
-// timeout in *err and returns, and so do the others at their next barrier.
+// Every wait is bounded: after spin_limit polls (kSpinLimit unless the plan
+// sets another bound) the waiting CTA records a timeout in *err and returns,
+// and so do the others at their next barrier.  hold_ns > 0 makes CTA 0 wait
+// that long, by the global timer, before its first barrier: a test of the
+// timeout path that needs no fault and no unbounded wait.
 struct PersistCtl {
     unsigned* bar_count;
     unsigned* bar_gen;
     int* stop;
     int* err;
     int64_t max_iters;
+    unsigned long long spin_limit;
+    long long hold_ns;
 };
 
 constexpr unsigned long long kSpinLimit = 1ull << 24;  // about 1 s with 64 ns naps
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ bool grid_sync(const PersistCtl& c, const int* active) {
     __shared__ int s_ok;
@@ -810,7 +821,7 @@ __device__ __forceinline__ bool grid_sync(const PersistCtl& c, const int* active
         } else {
             unsigned long long spins = 0;
             while (*gen == g0) {
-                if (++spins > kSpinLimit) {
+                if (++spins > c.spin_limit) {
                     atomicExch(c.err, 1);
                     ok = 0;
                     break;
@@ -835,6 +846,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_persist(PlanView<T> a, PersistC
         for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
             run_tile<PU, ROLE_U, SC, false, T>(a, a.tile0 + ti, smem, scratch);
             __syncthreads();
+        }
+        if (c.hold_ns > 0 && it == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+            const unsigned long long t0 = global_ns();
+            while (global_ns() - t0 < (unsigned long long)c.hold_ns) __nanosleep(1000);
         }
         if (!grid_sync(c, a.active)) return;
         for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {

@@ -13,5 +13,5 @@ from .problems import (  # noqa: F401
     ZERO, NONNEG, SOC, PSD, EXP, POW, CSR, QCP, Directions,
     config1, config2, config3, config4, config5_family, paper_example, small_qcp,
     unconstrained_qp, equality_qp, make_directions, make_directions_batch,
-    round_to_fp32, cone_dims_ok,
+    round_to_fp32, with_optimum, cone_dims_ok,
 )

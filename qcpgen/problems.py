@@ -833,6 +833,16 @@ def make_directions_batch(qcp: QCP, seed: int, k: int):
     return [make_directions(qcp, seed, i) for i in range(k)]
 
 
+def with_optimum(qcp: QCP, x, y, s) -> QCP:
+    """The same P, A and cones with another constructed optimum (x, y, s):
+    q = -P x - A^T y and b = A x + s are rebuilt so that (x, y, s) solves the
+    pair.  The caller keeps y in K*, s in K and y^T s = 0 blockwise."""
+    x, y, s = (np.asarray(a, np.float64).copy() for a in (x, y, s))
+    q = -(_sym_full(qcp.P) @ x) - (qcp.A.to_scipy().T @ y)
+    b = qcp.A.to_scipy() @ x + s
+    return dataclasses.replace(qcp, x=x, y=y, s=s, q=np.asarray(q, np.float64), b=np.asarray(b, np.float64))
+
+
 def round_to_fp32(qcp: QCP) -> QCP:
     """The same problem with every floating-point array rounded to binary32
     (round to nearest even) and held again in float64."""
