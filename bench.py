@@ -1,16 +1,19 @@
 #!/usr/bin/env python
 """Throughput benchmark of the QCP solution-map derivative (JVP + VJP).
 
-Workload (default): the single second-order-cone QCP with n=2000, m=5500
-(cone {0}^500 x R+^2000 x SOC(10)^300), 16 forward and 16 adjoint directions,
-relative residual tolerance 1e-10, FP64, synthetic seeded data with an
-optimum built by construction.  One step = the 16 JVPs plus the 16 VJPs in
-one qcp_derivative_jvp_vjp_multi call (the cluster engine runs the two
-groups side by side; --call separate makes one multi-direction call per
-group).
+Workload (default): the large sparse QCP (n = 100 000, m = 220 000; cone
+{0}^20000 x R+^150000 x lognormal second-order-cone blocks on 50 000 rows;
+A with 2.2 M entries in power-law columns, P banded plus 200 k random upper
+entries), one forward and one adjoint direction, relative residual
+tolerance 1e-6, FP64 data, synthetic seeded data with an optimum built by
+construction.  One step = the JVP and the VJP in one
+qcp_derivative_jvp_vjp_multi call (engine auto: the stream engine for a
+problem this size).  --workload config2 runs the n = 2000 SOC problem with
+16 + 16 directions at rtol 1e-10 (cluster engine), --workload example the
+paper's example shape, config4 / learned the batched and learned forms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--precond equilibrate|none] [--workload config2|config3|example]
+                    [--workload config3|config2|example|config1|config4|learned]
 
 Prints one JSON line (rank 0).  `value` counts JVP+VJP solves per second
 over all ranks with inputs resident in device memory; `e2e` measures the
@@ -18,7 +21,9 @@ same through the public API with the inputs copied from pinned host memory
 and the outputs copied back inside the timed region.  With N > 1 (torchrun)
 every rank solves its own instance (replicas, weak scaling); there is no
 collective on the data path.  `--impl reference` times the CPU FP64 oracle
-(dense LU of the bordered derivative system) on the same workload.
+on the same workload: dense LU of the bordered derivative system where it
+fits (configs 1, 2, example), else a bounded sample of its matrix-free
+LSMR iterations.
 """
 import argparse
 import hashlib
@@ -37,6 +42,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20
+# mean LSQR iterations per solve of config 3 at rtol 1e-6 with 16
+# equilibration sweeps (GB300 runs: 2727 JVP, 3093 VJP), for the CPU
+# oracle's per-iteration sample when the GPU's own count is not at hand
+CONFIG3_ITERS_PER_SOLVE = 2910.0
 
 
 def log(*a):
@@ -83,6 +92,7 @@ def algorithmic_bytes_per_pass(prob):
 
 # the dominant kernel of each engine and the sources it is built from
 KERNELS = {
+    "stream": ("k_stream", ("qcpd_stream.cuh", "qcpd_df64.cuh", "qcpd_kernels.cuh", "qcpd_common.cuh")),
     "passes": ("k_pass", ("qcpd_kernels.cuh", "qcpd_common.cuh")),
     "persistent": ("k_persist", ("qcpd_kernels.cuh", "qcpd_common.cuh")),
     "cluster": ("k_cluster_df", ("qcpd_cluster_df.cuh", "qcpd_cluster.cuh", "qcpd_df64.cuh", "qcpd_kernels.cuh",
@@ -176,15 +186,62 @@ def oracle_step(prob, dirs):
     return 2 * len(dirs)
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def dense_workload(name):
+    """Workloads whose (N+1)^2 bordered system the dense-LU oracle factors."""
+    return name in ("config1", "config2", "example")
+
+
 def oracle_sample(prob, dirs, budget_s=30.0):
-    """A bounded sample of the oracle on this workload (rank 0 only)."""
+    """A bounded sample of the dense-LU oracle on this workload (rank 0 only)."""
     t0 = time.perf_counter()
     solves = oracle_step(prob, dirs[:16])
     dt = time.perf_counter() - t0
     return {"value": solves / dt, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": (f"one full step on the host: dense LU of the bordered (N+1)x(N+1) derivative "
                        f"system (N={prob.N}) plus {len(dirs[:16])} JVP and {len(dirs[:16])} VJP solves, "
                        f"{dt:.1f} s; numpy/scipy FP64 with the BLAS threads of all {os.cpu_count()} cores")}
+
+
+def oracle_lsmr_sample(prob, dirs, iters_per_solve, target_s=15.0):
+    """A bounded sample of the oracle's matrix-free LSMR on this workload (dense
+    LU does not fit): the seconds per iteration of scipy's LSMR on the JVP
+    system (F and F^T products through scipy sparse matrices, FP64, one
+    core), scaled to a solve of `iters_per_solve` iterations."""
+    from oracle import derivative as D
+    op = D.FOperator(prob)
+    t0 = time.perf_counter()
+    D.jvp_lsmr(prob, dirs[0], rtol=1e-30, maxiter=5, op=op)
+    per = (time.perf_counter() - t0) / 5
+    k = int(max(10, min(2000, target_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    D.jvp_lsmr(prob, dirs[0], rtol=1e-30, maxiter=k, op=op)
+    dt = time.perf_counter() - t0
+    s_iter = dt / k
+    return {"value": 1.0 / (s_iter * iters_per_solve), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": (f"{k} iterations of the oracle's matrix-free LSMR on the JVP system (N={prob.N}; scipy "
+                       f"sparse F and F^T products, FP64, single-threaded) in {dt:.1f} s = {1e3 * s_iter:.1f} ms "
+                       f"per iteration, scaled to {iters_per_solve:.0f} iterations per solve (the mean the GPU's "
+                       f"equilibrated LSQR took); {os.cpu_count()} cores on the host")}
 
 
 # --------------------------------------------------------------------------- learned form
@@ -333,7 +390,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
-    ap.add_argument("--workload", default="config2",
+    ap.add_argument("--workload", default="config3",
                     choices=["config1", "config2", "config3", "example", "learned", "config4"])
     ap.add_argument("--problems", type=int, default=32,
                     help="config4: how many of the batch's problems (drawn from their own streams, from 0)")
@@ -343,8 +400,8 @@ def main():
     ap.add_argument("--call", default="pair", choices=["pair", "separate"],
                     help="pair: the JVPs and VJPs in one qcp_derivative_jvp_vjp_multi call (side by side on the "
                          "cluster engine); separate: one _multi call per kind")
-    ap.add_argument("--equil-sweeps", type=int, default=1,
-                    help="sweeps of the row/column equilibration (plan setting; 1 is the plan's default)")
+    ap.add_argument("--equil-sweeps", type=int, default=16,
+                    help="sweeps of the row/column equilibration (plan setting; 16 is the plan's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -356,24 +413,36 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        if args.workload not in ("config1", "config2", "example"):
-            raise SystemExit("the oracle reference arm covers the dense-LU workloads (config1, config2, example)")
+        if args.workload not in ("config1", "config2", "config3", "example"):
+            raise SystemExit("the oracle reference arm covers config1, config2, config3 and example")
         prob, dirs, rtol, desc = workload(args.workload, 0)
-        for _ in range(args.warmup):
-            oracle_step(prob, dirs)
-        t0 = time.perf_counter()
-        solves = 0
-        for _ in range(args.steps):
-            solves += oracle_step(prob, dirs)
-        dt = time.perf_counter() - t0
-        val = solves / dt
+        if dense_workload(args.workload):
+            for _ in range(args.warmup):
+                oracle_step(prob, dirs)
+            t0 = time.perf_counter()
+            solves = 0
+            for _ in range(args.steps):
+                solves += oracle_step(prob, dirs)
+            dt = time.perf_counter() - t0
+            val = solves / dt
+            cores = os.cpu_count()
+            sample = f"{args.steps} full step{'' if args.steps == 1 else 's'} of the dense-LU oracle on the host"
+        else:
+            # each step: a bounded sample of the matrix-free oracle, scaled to
+            # the iterations a solve of this workload takes with 16
+            # equilibration sweeps (measured on the GPU: about 2900)
+            rec = None
+            for _ in range(args.warmup + args.steps):
+                rec = oracle_lsmr_sample(prob, dirs, CONFIG3_ITERS_PER_SOLVE, target_s=10.0)
+            val, cores, sample = rec["value"], rec["cores"], rec["sample"]
+            dt = 2 * len(dirs) * args.steps / val
         print(json.dumps({
             "impl": "reference", "metric": metric, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc, "rtol": rtol},
-            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} full step{'' if args.steps == 1 else 's'} of the dense-LU oracle on the host"},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
@@ -394,15 +463,14 @@ def main():
     prob, dirs, rtol, desc = workload(args.workload, rank)
     k = len(dirs)
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and args.workload in ("config2", "example"):
+    if rank == 0 and not args.no_cpu_baseline and dense_workload(args.workload):
         log("timing the CPU oracle sample ...")
         cpu = oracle_sample(prob, dirs)
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     plan = q.qcp_plan_create(q.problem_tensors(prob, dev), torch.float64, max_rhs=2 * k, stream=stream)
-    if args.equil_sweeps != 1:
-        plan.set_equilibration(args.equil_sweeps)
+    plan.set_equilibration(args.equil_sweeps)
     opts = q.options(rtol=rtol, maxiter=args.maxiter, precond=args.precond, engine=args.engine)
     cat = lambda nm: np.concatenate([getattr(d, nm) for d in dirs])
     host = {nm: torch.as_tensor(cat(nm)).pin_memory() for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
@@ -499,6 +567,11 @@ def main():
     value = whole_job_rate(2 * k, world, args.steps, total_ms)
     e2e = whole_job_rate(2 * k, world, args.steps, e2e_ms)
 
+    mean_iters = float(np.mean([i["iters"] for pair in infos for grp in pair for i in grp]))
+    if rank == 0 and not args.no_cpu_baseline and not dense_workload(args.workload):
+        log("timing a sample of the matrix-free CPU oracle ...")
+        cpu = oracle_lsmr_sample(prob, dirs, mean_iters)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -520,18 +593,24 @@ def main():
         line = {
             "metric": metric, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "df64" if engine == "cluster" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64" if engine in ("cluster", "stream") else "f64",
             "data": "synthetic",
             "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "equil_sweeps": args.equil_sweeps,
                        "solver": "LSQR", "engine": engine,
                        "arithmetic": ("vectors in double-float (binary32 pairs), LSQR scalars f64, data f64"
-                                      if engine == "cluster" else "f64"),
-                       "call": ("qcp_derivative_jvp_vjp_multi (16 JVP + 16 VJP systems side by side)"
+                                      if engine in ("cluster", "stream") else "f64"),
+                       "call": (f"qcp_derivative_jvp_vjp_multi ({k} JVP + {k} VJP systems in one call)"
                                 if args.call == "pair" else "qcp_derivative_jvp_multi then qcp_derivative_vjp_multi"),
+                       "mean_iters_per_solve": mean_iters,
                        "parallelism": f"replicas x{world}", "l2": "flushed before every timed step "
                        f"({L2_FLUSH_BYTES >> 20} MiB write)", "status": statuses,
                        "max_true_rel_residual": max_res},
-            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm" if args.workload in ("config3", "config4") else "l2",
+                         "bound_note": ("M and the vectors (about 145 MB per iteration) exceed the 129 MB L2"
+                                        if args.workload in ("config3", "config4") else
+                                        "the matrix is L2- and shared-memory-resident: the fraction is of algorithmic "
+                                        "bytes over time, not of DRAM traffic"),
+                         "kernel": kname, "achieved": achieved, "peak": peak,
                          "peak_source": peak_note, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "traffic_per": "system pass (dram read + write bytes, ncu)",
                          "per": "algorithmic bytes of all passes of all systems (one pass = one product with F "
