@@ -151,55 +151,91 @@ __device__ __forceinline__ void sacc_zero(SAcc& a) {
 
 __device__ __forceinline__ df dfl(const df* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
 
+// M's slots are read once per pass: streaming loads (evict first), so L1 keeps
+// the gathered vector's entries.
+__device__ __forceinline__ df dfl_cs(const df* p) { return __ldcs(reinterpret_cast<const float2*>(p)); }
+
 // The row sum of one lane's row in a SELL-32 slice: sum_k val[slot] g[col[slot]]
 // over slots base + 32 k + lane, k < width.  A padding slot holds the value 0
 // and repeats the row's last column (an L1 hit), so no slot needs a test.
+// The sum is software-pipelined in batches of kSB slots: the next batch's
+// columns and values are loaded while the current batch's gathers are in
+// flight, so a lane has up to 3 kSB loads outstanding instead of waiting
+// for the columns and then for the gathers of every batch.
+constexpr int kSB = 4;
+
+__device__ __forceinline__ void sell_load(const int32_t* scol, const df* val, int64_t base, int k, int width,
+                                          int32_t (&c)[kSB], df (&v)[kSB]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kSB; ++j) {
+        const bool ok = k + j < width;
+        const int64_t s = base + 32 * (int64_t)(k + j) + lane;
+        c[j] = ok ? __ldcs(scol + s) : 0;
+        v[j] = ok ? dfl_cs(val + s) : df_zero();
+    }
+}
+
 __device__ __forceinline__ df sell_rowsum(const int32_t* scol, const df* val, const df* g, int64_t base,
                                           int width) {
-    const int lane = threadIdx.x & 31;
     DfAcc acc = dfacc_zero();
-    int k = 0;
-    for (; k + 4 <= width; k += 4) {
-        int32_t c[4];
-        df v[4], x[4];
+    if (width <= 0) return dfacc_result(acc);
+    int32_t c[kSB];
+    df v[kSB];
+    sell_load(scol, val, base, 0, width, c, v);
+    for (int k = 0; k < width; k += kSB) {
+        df x[kSB];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t s = base + 32 * (int64_t)(k + j) + lane;
-            c[j] = __ldg(scol + s);
-            v[j] = dfl(val + s);
+        for (int j = 0; j < kSB; ++j) x[j] = (k + j < width) ? dfl(g + c[j]) : df_zero();
+        int32_t cn[kSB];
+        df vn[kSB];
+        sell_load(scol, val, base, k + kSB, width, cn, vn);
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) dfacc_fma(acc, v[j], x[j]);
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) {
+            c[j] = cn[j];
+            v[j] = vn[j];
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = dfl(g + c[j]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dfacc_fma(acc, v[j], x[j]);
-    }
-    for (; k < width; ++k) {
-        const int64_t s = base + 32 * (int64_t)k + lane;
-        dfacc_fma(acc, dfl(val + s), dfl(g + __ldg(scol + s)));
     }
     return dfacc_result(acc);
 }
 
 // One chunk of a long row read lane-strided (entries base .. base + cnt),
-// summed over the warp in a fixed order; every lane gets the sum.
+// pipelined as sell_rowsum, summed over the warp in a fixed order; every
+// lane gets the sum.
+__device__ __forceinline__ void long_load(const int32_t* scol, const df* val, int64_t base, int k, int cnt,
+                                          int32_t (&c)[kSB], df (&v)[kSB]) {
+#pragma unroll
+    for (int j = 0; j < kSB; ++j) {
+        const int e = k + 32 * j;
+        const bool ok = e < cnt;
+        c[j] = ok ? __ldcs(scol + base + e) : 0;
+        v[j] = ok ? dfl_cs(val + base + e) : df_zero();
+    }
+}
+
 __device__ __forceinline__ df long_rowsum(const int32_t* scol, const df* val, const df* g, int64_t base, int cnt) {
     const int lane = threadIdx.x & 31;
     DfAcc acc = dfacc_zero();
-    int k = lane;
-    for (; k + 96 < cnt; k += 128) {
-        int32_t c[4];
-        df v[4], x[4];
+    int32_t c[kSB];
+    df v[kSB];
+    long_load(scol, val, base, lane, cnt, c, v);
+    for (int k = lane; k < cnt; k += 32 * kSB) {
+        df x[kSB];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            c[j] = __ldg(scol + base + k + 32 * j);
-            v[j] = dfl(val + base + k + 32 * j);
+        for (int j = 0; j < kSB; ++j) x[j] = (k + 32 * j < cnt) ? dfl(g + c[j]) : df_zero();
+        int32_t cn[kSB];
+        df vn[kSB];
+        long_load(scol, val, base, k + 32 * kSB, cnt, cn, vn);
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) dfacc_fma(acc, v[j], x[j]);
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) {
+            c[j] = cn[j];
+            v[j] = vn[j];
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) x[j] = dfl(g + c[j]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dfacc_fma(acc, v[j], x[j]);
     }
-    for (; k < cnt; k += 32) dfacc_fma(acc, dfl(val + base + k), dfl(g + __ldg(scol + base + k)));
     return warp_sum_df(dfacc_result(acc));
 }
 
@@ -519,6 +555,7 @@ template <int PASS, int ROLE, bool SC>
 __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
     __shared__ df sbuf[kSWarps][kSSocBig];
     __shared__ df red[kSWarps][3];
+    __shared__ double fin_red[3 * kSThreads];
     __shared__ int s_last;
     const int si = a.s0 + (int)blockIdx.y;
     const int status = a.state[si].status;
@@ -592,22 +629,25 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
         s_last = prev == a.gx - 1;
     }
     __syncthreads();
-    if (!s_last || warp != 0) return;
-    // the system's last CTA: CTA partials in order, then the split rows' sums
+    if (!s_last) return;
+    // the system's last CTA: every thread adds a fixed share of the CTA
+    // partials and the split rows' sums (independent loads in flight), then
+    // a fixed-order tree over the CTA; thread 0 finishes
     __threadfence();
     Part t = pzero();
-    for (int i = lane; i < a.gx; i += 32) t = padd(t, ld_part(a.cpart + (int64_t)si * a.gx + i));
+    for (int i = threadIdx.x; i < a.gx; i += kSThreads) t = padd(t, ld_part(a.cpart + (int64_t)si * a.gx + i));
     const int64_t sr = a.batched ? 0 : (int64_t)si * a.nsplit;
     if (!only_x) {
-        for (int i = a.soff[sy.prob] + lane; i < a.soff[sy.prob + 1]; i += 32) {
+        for (int i = a.soff[sy.prob] + threadIdx.x; i < a.soff[sy.prob + 1]; i += kSThreads) {
             const float2* o = reinterpret_cast<const float2*>(a.lrow + 3 * (sr + i));
             t = padd(t, Part{df_to(__ldcg(o)), df_to(__ldcg(o + 1)), df_to(__ldcg(o + 2)), 0.0});
         }
     }
-    t = warp_sum_part(t);
-    if (lane == 0) {
+    double v[3] = {t.a, t.b, t.c};
+    block_reduce<3, kSThreads>(v, fin_red);
+    if (threadIdx.x == 0) {
         a.ccnt[si] = 0;
-        stream_finish<PASS, ROLE, SC>(a, si, pr, t, only_x);
+        stream_finish<PASS, ROLE, SC>(a, si, pr, Part{v[0], v[1], v[2], 0.0}, only_x);
     }
 }
 
