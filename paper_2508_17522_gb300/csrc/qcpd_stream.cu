@@ -38,12 +38,12 @@ __device__ __forceinline__ void s_pad(int64_t slot, int32_t col, int32_t* scol, 
     valT[slot] = df_zero();
 }
 
-// Slots of one SELL-32 sub-slice whose lane rows are given: the row's
-// entries, then padding that repeats its last column.
+// Slots of one SELL-32 sub-slice: this lane holds entries k G + sub
+// (k < width) of `row`, then padding that repeats the row's last column.
 template <typename T>
-__device__ __forceinline__ void s_fill_slice(int64_t base, int width, int row, const int64_t* rp, const int32_t* mcol,
-                                             const T* mval, const T* mvalG, const T* mvalT, int32_t* scol, df* val,
-                                             df* valG, df* valT, int* bad) {
+__device__ __forceinline__ void s_fill_slice(int64_t base, int width, int row, int G, int sub, const int64_t* rp,
+                                             const int32_t* mcol, const T* mval, const T* mvalG, const T* mvalT,
+                                             int32_t* scol, df* val, df* valG, df* valT, int* bad) {
     const int lane = threadIdx.x & 31;
     int64_t k0 = 0, len = 0;
     if (row >= 0) {
@@ -53,7 +53,8 @@ __device__ __forceinline__ void s_fill_slice(int64_t base, int width, int row, c
     const int32_t last = len > 0 ? mcol[k0 + len - 1] : 0;
     for (int k = 0; k < width; ++k) {
         const int64_t slot = base + 32 * (int64_t)k + lane;
-        if (k < len) s_put(slot, k0 + k, mcol, mval, mvalG, mvalT, scol, val, valG, valT, bad);
+        const int64_t e = (int64_t)k * G + sub;
+        if (e < len) s_put(slot, k0 + e, mcol, mval, mvalG, mvalT, scol, val, valG, valT, bad);
         else s_pad(slot, last, scol, val, valG, valT);
     }
 }
@@ -68,15 +69,20 @@ __global__ void k_stream_fill(const StreamUnit* units, int nunits, const int32_t
     if (ui >= nunits) return;
     const StreamUnit u = units[ui];
     const int64_t* rp = mrowptr + probs[u.prob].mrow;
-    if (u.kind == SU_SLICE || u.kind == SU_SOCP) {
-        s_fill_slice(u.base, u.width, rows[u.aux + lane], rp, mcol, mval, mvalG, mvalT, scol, val, valG, valT, bad);
+    if (u.kind == SU_SLICE) {
+        const int G = u.chunk;
+        s_fill_slice(u.base, u.width, rows[u.aux + lane / G], G, lane & (G - 1), rp, mcol, mval, mvalG, mvalT, scol,
+                     val, valG, valT, bad);
+    } else if (u.kind == SU_SOCP) {
+        s_fill_slice(u.base, u.width, rows[u.aux + lane], 1, 0, rp, mcol, mval, mvalG, mvalT, scol, val, valG, valT,
+                     bad);
     } else if (u.kind == SU_SOCB) {
         int64_t base = u.base;
         for (int j = 0; j < u.width; ++j) {
             const int w = rows[u.aux + j];
             const int i = 32 * j + lane;
-            s_fill_slice(base, w, i < u.nrows ? u.row0 + i : -1, rp, mcol, mval, mvalG, mvalT, scol, val, valG, valT,
-                         bad);
+            s_fill_slice(base, w, i < u.nrows ? u.row0 + i : -1, 1, 0, rp, mcol, mval, mvalG, mvalT, scol, val, valG,
+                         valT, bad);
             base += 32 * (int64_t)w;
         }
     } else {
@@ -118,12 +124,13 @@ int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(4096
 
 // ---------------------------------------------------------------------------
 // Layout.  Per problem: x-rows and zero-cone / R+ rows with at most
-// kSLongRow entries in SELL-32 slices (x and y apart, each sorted by length,
-// longest first); longer rows in chunks of kSLongChunk entries;
+// kSLongChunk entries in SELL-32 slices of G lanes per row (x and y apart,
+// each sorted by length, longest first, one G per slice); longer rows in
+// chunks of kSLongChunk entries;
 // second-order-cone blocks of at most 32 rows packed in order into units of
 // at most 32 rows, larger ones (up to kSSocBig rows) one unit each.  Units
-// are sorted by cost (slots plus a per-row share for the epilogue), most
-// expensive first, for the kernel's snake order.
+// are sorted by their per-lane chain of dependent loads (plus a share for
+// the epilogue), longest first, for the kernel's snake order.
 static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<StreamUnit>& hu,
                         std::vector<int32_t>& hrows, std::vector<int32_t>& hlblk, int64_t& slots) {
     slots = 0;
@@ -143,12 +150,12 @@ static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<Stream
         std::vector<int> xs, ys, longs;
         struct Blk { int start, dim, idx; };
         std::vector<Blk> socs;
-        for (int r = 0; r < pr.n; ++r) (len(r) <= kSLongRow ? xs : longs).push_back(r);
+        for (int r = 0; r < pr.n; ++r) (len(r) <= kSLongChunk ? xs : longs).push_back(r);
         int row = pr.n, bi = 0;
         for (size_t b = 0; b < p->cone_type[pi].size(); ++b) {
             const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
             if (t == QCP_CONE_ZERO || t == QCP_CONE_NONNEG) {
-                for (int k = 0; k < d; ++k) (len(row + k) <= kSLongRow ? ys : longs).push_back(row + k);
+                for (int k = 0; k < d; ++k) (len(row + k) <= kSLongChunk ? ys : longs).push_back(row + k);
             } else if (t == QCP_CONE_SOC) {
                 if (d > kSSocBig) {
                     lay->why = "a second-order-cone block has more than 256 rows";
@@ -163,23 +170,37 @@ static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<Stream
         }
         std::vector<StreamUnit> pu;
         std::vector<double> cost;
+        // G lanes per row: the smallest power of two that leaves a lane at
+        // most kSSteps entries; one slice holds 32 / G rows of one G
+        auto lanes_for = [&](int L) {
+            int G = 1;
+            while (G < 32 && (L + G - 1) / G > kSSteps) G <<= 1;
+            return G;
+        };
         auto slice_units = [&](std::vector<int>& rows) {
             std::stable_sort(rows.begin(), rows.end(), [&](int a, int b) { return len(a) > len(b); });
-            for (size_t i = 0; i < rows.size(); i += 32) {
-                const int nr = (int)std::min<size_t>(32, rows.size() - i);
-                StreamUnit u{};
-                u.kind = SU_SLICE;
-                u.prob = pi;
-                u.nrows = nr;
-                u.width = len(rows[i]);
-                u.aux = (int32_t)hrows.size();
-                for (int l = 0; l < 32; ++l) {
-                    hrows.push_back(l < nr ? rows[i + l] : -1);
-                    hlblk.push_back(-1);
+            for (int G = 32; G >= 1; G >>= 1) {
+                std::vector<int> cls;
+                for (int r : rows)
+                    if (lanes_for(len(r)) == G) cls.push_back(r);
+                const int R = 32 / G;
+                for (size_t i = 0; i < cls.size(); i += R) {
+                    const int nr = (int)std::min<size_t>(R, cls.size() - i);
+                    StreamUnit u{};
+                    u.kind = SU_SLICE;
+                    u.prob = pi;
+                    u.nrows = nr;
+                    u.chunk = G;
+                    u.width = (len(cls[i]) + G - 1) / G;
+                    u.aux = (int32_t)hrows.size();
+                    for (int l = 0; l < 32; ++l) {
+                        hrows.push_back(l < nr ? cls[i + l] : -1);
+                        hlblk.push_back(-1);
+                    }
+                    u.base = take(32 * (int64_t)u.width);
+                    pu.push_back(u);
+                    cost.push_back(u.width + 3.0);
                 }
-                u.base = take(32 * (int64_t)u.width);
-                pu.push_back(u);
-                cost.push_back(32.0 * u.width + 8.0 * nr);
             }
         };
         slice_units(xs);
@@ -206,7 +227,7 @@ static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<Stream
                 }
                 u.base = take(32 * tot);
                 pu.push_back(u);
-                cost.push_back(32.0 * tot + 24.0 * B.dim);
+                cost.push_back(tot + 6.0);
                 continue;
             }
             // consecutive blocks of at most 32 rows in all, one row per lane
@@ -230,7 +251,7 @@ static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<Stream
             u.width = w;
             u.base = take(32 * (int64_t)w);
             pu.push_back(u);
-            cost.push_back(32.0 * w + 24.0 * total);
+            cost.push_back(w + 5.0);
             i = j;
         }
         for (int r : longs) {
@@ -254,7 +275,7 @@ static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<Stream
                 u.row0 = slot0;
                 u.base = take(u.width);
                 pu.push_back(u);
-                cost.push_back(u.width + 40.0);
+                cost.push_back((u.width + 31) / 32 + 4.0);
             }
         }
         std::vector<int> ord(pu.size());

@@ -4,21 +4,26 @@
 // G = S F and the combined matrix M; see qcpd_common.cuh).
 //
 // Work is cut into warp-sized units that need no CTA barrier:
-//   SU_SLICE  up to 32 rows with no coupling inside D Pi (x-rows, or zero-
-//             cone and R+ rows), one row per lane, stored SELL-32 (slot
-//             (k, lane) at base + 32 k + lane, rows sorted by length so the
-//             slice is nearly dense);
+//   SU_SLICE  32 / G rows with no coupling inside D Pi (x-rows, or zero-
+//             cone and R+ rows), G lanes per row (G a power of two chosen so
+//             that no lane holds more than kSSteps entries), stored SELL-32:
+//             slot (k, lane) at base + 32 k + lane holds entry k G + (lane
+//             mod G) of row lane / G (rows sorted by length, so a slice is
+//             nearly dense); the G partial sums of a row are added in a fixed
+//             butterfly;
 //   SU_SOCP   consecutive second-order-cone blocks of at most 32 rows in
 //             all, one row per lane; D Pi's dot products are segmented
 //             warp reductions (one segment per block);
 //   SU_SOCB   one second-order-cone block of 33 to kSSocBig rows, rows
 //             lane + 32 j, the block's values through a per-warp
 //             shared-memory buffer;
-//   SU_LONG   up to kSLongChunk stored entries of one long row, read
+//   SU_LONG   up to kSLongChunk stored entries of a row longer than that, read
 //             lane-strided; the last chunk of a row to finish adds the
 //             chunk sums in order and runs the row's epilogue.
 // A launch has gridDim.y = systems; the warps of a system's CTAs take its
-// units in snake order (units sorted by cost, largest first).  Per-lane sums
+// units in snake order (units sorted by their per-lane chain of dependent
+// loads, longest first: the passes are bound by latency, so that chain, not
+// the slot count, is what to balance).  Per-lane sums
 // of the pass (||out||^2 and the two tau-row dot products) are reduced per
 // warp, per CTA and finally, by the system's last CTA, over CTAs in a
 // fixed order, so results do not depend on scheduling.
@@ -41,8 +46,8 @@ namespace qcpd {
 
 constexpr int kSThreads = 256;
 constexpr int kSWarps = kSThreads / 32;
-constexpr int kSLongRow = 64;      // rows with more stored entries are read lane-strided (SU_LONG)
-constexpr int kSLongChunk = 1024;  // stored entries per SU_LONG unit
+constexpr int kSSteps = 16;        // most entries of one lane in a slice (its chain of dependent loads)
+constexpr int kSLongChunk = 32 * kSSteps;  // rows with more entries are cut into SU_LONG units of this many
 constexpr int kSSocBig = 256;      // largest second-order-cone block the engine takes
 
 enum StreamKind : int32_t { SU_SLICE = 0, SU_SOCP = 1, SU_SOCB = 2, SU_LONG = 3 };
@@ -56,7 +61,7 @@ struct StreamUnit {
     int32_t aux;     // SLICE / SOCP: offset of the lanes' rows in rows[] (SOCP: and block indices in
                      // lblk[]); SOCB: offset of the sub-slices' widths in rows[]; LONG: the row
     int32_t blk;     // SOCB: the block (problem-relative); LONG: split-row index (plan-wide, -1: one chunk)
-    int32_t chunk;   // LONG: chunk index
+    int32_t chunk;   // LONG: chunk index; SLICE: G, the lanes per row
     int32_t row0;    // SOCB: first row; LONG: first chunk slot (plan-wide) of the row's chunk sums
 };
 
@@ -325,6 +330,13 @@ __device__ __forceinline__ df soc_d(df v, df u, int pos, df ct, df dot, int kase
     return df_fma(aa, u, df_mul(B.htr, v));
 }
 
+__device__ __forceinline__ df shfl_xor_df(df v, int o) {
+    df w;
+    w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+    w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+    return w;
+}
+
 __device__ __forceinline__ df shfl_df(df v, int src) {
     df o;
     o.x = __shfl_sync(0xffffffffu, v.x, src);
@@ -358,13 +370,16 @@ struct SUnitCtx {
     const df* val;
 };
 
-// SU_SLICE and SU_SOCP units of a G-pass, and SU_SLICE units of a G^T-pass:
-// one row per lane, no coupling.
+// SU_SLICE units (either pass) and SU_SOCP units of a G-pass: row i of the
+// unit on lanes [G i, G i + G) (SU_SOCP: G = 1), no coupling.
 template <int PASS, int ROLE, bool SC>
 __device__ __forceinline__ void unit_slice(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, SAcc& acc) {
     const int lane = threadIdx.x & 31;
-    const int r = k.rows[u.aux + lane];
-    const df h = sell_rowsum(k.scol, k.val, c.gin, u.base, u.width);
+    const int G = u.kind == SU_SLICE ? u.chunk : 1;
+    df h = sell_rowsum(k.scol, k.val, c.gin, u.base, u.width);
+    for (int o = G >> 1; o > 0; o >>= 1) h = df_add(h, shfl_xor_df(h, o));
+    if ((lane & (G - 1)) != 0) return;
+    const int r = k.rows[u.aux + lane / G];
     if (r >= 0) plain_row<PASS, ROLE, SC>(c, r, h, acc);
 }
 
@@ -464,22 +479,28 @@ __device__ __forceinline__ void unit_long(const SCtx& c, const SUnitCtx& k, cons
                                           const StreamUnit& u, SAcc& acc) {
     const int lane = threadIdx.x & 31;
     const df h = long_rowsum(k.scol, k.val, c.gin, u.base, u.width);
-    if (lane != 0) return;
     const int r = u.aux;
     if (u.blk < 0) {
-        plain_row<PASS, ROLE, SC>(c, r, h, acc);
+        if (lane == 0) plain_row<PASS, ROLE, SC>(c, r, h, acc);
         return;
     }
     const int64_t so = a.batched ? 0 : (int64_t)si * a.nslot;
     const int64_t sr = a.batched ? 0 : (int64_t)si * a.nsplit;
-    a.lchunk[so + u.row0 + u.chunk] = h;
+    int last = 0;
+    if (lane == 0) {
+        a.lchunk[so + u.row0 + u.chunk] = h;
+        __threadfence();
+        last = atomicAdd(a.lcnt + sr + u.blk, 1) == u.nrows - 1;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
     __threadfence();
-    const int prev = atomicAdd(a.lcnt + sr + u.blk, 1);
-    if (prev != u.nrows - 1) return;
-    __threadfence();
+    // the chunk sums: a fixed share per lane (independent loads), then a
+    // fixed butterfly, so the sum does not depend on which chunk came last
     df t = df_zero();
-    for (int q = 0; q < u.nrows; ++q)
+    for (int q = lane; q < u.nrows; q += 32)
         t = df_add(t, __ldcg(reinterpret_cast<const float2*>(a.lchunk + so + u.row0 + q)));
+    t = warp_sum_df(t);
+    if (lane != 0) return;
     a.lcnt[sr + u.blk] = 0;
     SAcc racc;
     sacc_zero(racc);
@@ -488,6 +509,7 @@ __device__ __forceinline__ void unit_long(const SCtx& c, const SUnitCtx& k, cons
     o[0] = dfacc_result(racc.ss);
     o[1] = dfacc_result(racc.dtop);
     o[2] = dfacc_result(racc.dbot);
+    __threadfence();  // read by the system's last CTA within this launch
 }
 
 // ---------------------------------------------------------------------------
