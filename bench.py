@@ -314,12 +314,17 @@ def learned_bench(args, rank, local):
 
 # --------------------------------------------------------------------------- batched form
 def config4_bench(args, rank, local):
-    """The batched QCP form on the first --problems problems of the uneven
-    batch (n ~ U[50, 3000], m ~ U[1.5, 3] n, R+ and SOC blocks, dense
-    P = G^T G + 1e-3 I): one batch plan, autotuned for the VJP (untimed),
-    then per step one batched JVP (one direction per problem) and one
-    batched VJP, rtol 1e-6, equilibration, engine auto.  value = solves/s of
-    the whole batch (2 x problems per step)."""
+    """The batched QCP form against the plain per-problem form on the same
+    problems: the first --problems problems of the uneven batch (n ~ U[50,
+    3000], m ~ U[1.5, 3] n, R+ and SOC blocks, dense P = G^T G + 1e-3 I), one
+    JVP and one VJP direction each, rtol 1e-6, equilibration.
+    Batched: one batch plan (autotuned for the VJP, untimed), per step one
+    batched JVP and one batched VJP (engine auto).  Plain: one plan per
+    problem, per step each problem's JVP and VJP in turn (engine auto: the
+    cluster engine where a problem fits, else the stream engine).
+    value = batched solves/s; the plain rate, their ratio and both
+    rooflines (algorithmic bytes of every pass of every problem over the
+    device time of the iteration launches) ride along."""
     import torch
     import qcpgen as g
     import paper_2508_17522_gb300 as q
@@ -331,37 +336,85 @@ def config4_bench(args, rank, local):
     cat = lambda nm: torch.as_tensor(np.concatenate([getattr(d, nm) for d in dirs]), device=dev)
     ins = {nm: cat(nm) for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
     plan = q.qcp_batch_plan_create([q.problem_tensors(pr, dev) for pr in probs], torch.float64)
+    plan.set_equilibration(args.equil_sweeps)
     best, _ = plan.autotune("vjp", iters=16, opts=q.options(precond="equilibrate"))
-    opts = q.options(rtol=1e-6, maxiter=200000, precond="equilibrate", engine="auto")
-    its, stat = [], set()
+    opts = q.options(rtol=1e-6, maxiter=args.maxiter, precond="equilibrate", engine="auto")
+    plans = []
+    for pr in probs:
+        pl = q.qcp_plan_create(q.problem_tensors(pr, dev), torch.float64)
+        pl.set_equilibration(args.equil_sweeps)
+        plans.append(pl)
+    pins = [{nm: torch.as_tensor(getattr(d, nm), device=dev) for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
+            for d in dirs]
+    bpp = [algorithmic_bytes_per_pass(pr) for pr in probs]
+    acct = {"batched": [0.0, 0.0, [], set(), set()], "plain": [0.0, 0.0, [], set(), set()]}
 
-    def step():
+    def record(kind, pl, info, which):
+        ms, _ = pl.last_timing()
+        a = acct[kind]
+        a[0] += ms
+        a[1] += sum(2 * i["iters"] * bpp[p] for p, i in zip(which, info))
+        a[2] += [i["iters"] for i in info]
+        a[3] |= {i["status"] for i in info}
+        a[4].add(pl.last_engine())
+
+    def step_batched():
         *_, ji = q.qcp_derivative_jvp(plan, ins["dP"], ins["dA"], ins["dq"], ins["db"], opts)
+        record("batched", plan, ji, range(len(probs)))
         *_, vi = q.qcp_derivative_vjp(plan, ins["wx"], ins["wy"], ins["ws"], opts)
-        return ji + vi
+        record("batched", plan, vi, range(len(probs)))
+
+    def step_plain():
+        for p, (pl, d) in enumerate(zip(plans, pins)):
+            *_, ji = q.qcp_derivative_jvp(pl, d["dP"], d["dA"], d["dq"], d["db"], opts)
+            record("plain", pl, ji, [p])
+            *_, vi = q.qcp_derivative_vjp(pl, d["wx"], d["wy"], d["ws"], opts)
+            record("plain", pl, vi, [p])
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record()
+        for _ in range(args.steps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1)
 
     for _ in range(args.warmup):
-        step()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    ev0.record()
-    for _ in range(args.steps):
-        info = step()
-        its += [i["iters"] for i in info]
-        stat |= {i["status"] for i in info}
-    ev1.record()
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1)
+        step_batched()
+        step_plain()
+    for a in acct.values():
+        a[:] = [0.0, 0.0, [], set(), set()]
+    ms_b = timed(step_batched)
+    ms_p = timed(step_plain)
+    peak = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None) or 6800.0
+
+    def roof(kind):
+        a = acct[kind]
+        gbs = a[1] / (a[0] / 1e3) / 1e9 if a[0] > 0 else None
+        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                "frac": gbs / peak if gbs else None, "traffic": None,
+                "engines": sorted(a[4]), "iters_median": float(np.median(a[2])), "iters_max": int(max(a[2])),
+                "status": sorted(a[3])}
+    n_solves = 2 * len(probs) * args.steps
+    vb, vp = n_solves / (ms_b / 1e3), n_solves / (ms_p / 1e3)
     if rank == 0:
         print(json.dumps({
-            "metric": "JVP+VJP solves/sec at 1e-6 rel residual, batched", "value": 2 * len(probs) * args.steps / (ms / 1e3),
-            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "metric": "JVP+VJP solves/sec at 1e-6 rel residual, batched vs plain", "value": vb,
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"uneven batch, problems 0..{len(probs) - 1} of 512 (n ~ U[50, 3000], dense P)",
                        "sum_n": int(sum(p.n for p in probs)), "sum_m": int(sum(p.m for p in probs)),
-                       "nnz_up_P": int(sum(p.P.nnz for p in probs)), "engine": plan.last_engine(), "autotuned": best,
-                       "iters_median": float(np.median(its)), "iters_max": int(max(its)), "status": sorted(stat)},
-            "gpu_launches": None, "e2e": None, "roofline": None, "cpu_baseline": None}), flush=True)
+                       "nnz_up_P": int(sum(p.P.nnz for p in probs)), "autotuned": best,
+                       "equil_sweeps": args.equil_sweeps,
+                       "plain_solves_per_s": vp, "batched_over_plain": vb / vp,
+                       "plain_ms_per_step": ms_p / args.steps},
+            "roofline": roof("batched"), "roofline_plain": roof("plain"),
+            "gpu_launches": None, "e2e": None, "cpu_baseline": None}), flush=True)
+    for pl in plans:
+        pl.close()
     plan.close()
 
 

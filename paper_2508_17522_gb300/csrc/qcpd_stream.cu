@@ -348,7 +348,7 @@ static int build_stream(qcp_plan* p, StreamLayout* lay) {
     QCP_TRY(lay->d_scal.alloc(sizeof(StreamScal) * nsys));
     QCP_TRY(lay->d_ssys.alloc(sizeof(StreamSys) * nsys));
     QCP_CUDA(cudaMemsetAsync(lay->d_ssys.p, 0, sizeof(StreamSys) * nsys, st));
-    QCP_TRY(lay->d_cpart.alloc(sizeof(Part) * nsys * lay->gmax));
+    QCP_TRY(lay->d_cpart.alloc(2 * sizeof(float4) * nsys * lay->gmax));
     QCP_TRY(lay->d_ccnt.alloc(sizeof(int32_t) * nsys));
     QCP_CUDA(cudaMemsetAsync(lay->d_ccnt.p, 0, sizeof(int32_t) * nsys, st));
     QCP_TRY(lay->d_lchunk.alloc(sizeof(df) * per * std::max(1, lay->nslot)));
@@ -405,7 +405,7 @@ static StreamArgs stream_args(qcp_plan* p, const StreamLayout* lay, int scaled) 
     a.W = reinterpret_cast<df*>(p->d_W.p);
     a.X = reinterpret_cast<df*>(p->d_X.p);
     a.XI = reinterpret_cast<df*>(p->d_XI.p);
-    a.cpart = lay->d_cpart.as<Part>();
+    a.cpart = lay->d_cpart.as<float4>();
     a.ccnt = lay->d_ccnt.as<int32_t>();
     a.lchunk = lay->d_lchunk.as<df>();
     a.lcnt = lay->d_lcnt.as<int32_t>();

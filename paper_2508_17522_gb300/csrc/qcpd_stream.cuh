@@ -117,7 +117,7 @@ struct StreamArgs {
     df* W;
     df* X;
     df* XI;
-    Part* cpart;            // per (system, CTA) partial sums
+    float4* cpart;          // per (system, CTA): the three df64 partial sums as (a, b), (c, 0) pairs
     int32_t* ccnt;          // per system: CTAs done in this pass
     df* lchunk;             // per (system, chunk slot): chunk sums of split rows
     int32_t* lcnt;          // per (system, split row): chunks done
@@ -468,6 +468,16 @@ __device__ __forceinline__ void unit_socb_gt(const SCtx& c, const SUnitCtx& k, c
     __syncwarp();
 }
 
+// Arrival at a counter (a CTA at the end of its pass, a chunk of a split
+// row): add 1 with release semantics (the partial sums the arriving thread
+// wrote before become visible with it) and acquire semantics (the last to
+// arrive sees every earlier arrival's partials); returns the previous count.
+__device__ __forceinline__ int arrive_acq_rel(int* cnt) {
+    int prev;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(prev) : "l"(cnt) : "memory");
+    return prev;
+}
+
 // SU_LONG units: a chunk of one long row (never inside a coupled block).  A
 // row in one chunk is finished by lane 0; a split row's chunk sums go to
 // its slots, and the chunk that completes the row adds them in order and
@@ -489,11 +499,10 @@ __device__ __forceinline__ void unit_long(const SCtx& c, const SUnitCtx& k, cons
     int last = 0;
     if (lane == 0) {
         a.lchunk[so + u.row0 + u.chunk] = h;
-        __threadfence();
-        last = atomicAdd(a.lcnt + sr + u.blk, 1) == u.nrows - 1;
+        last = arrive_acq_rel(a.lcnt + sr + u.blk) == u.nrows - 1;
     }
     if (!__shfl_sync(0xffffffffu, last, 0)) return;
-    __threadfence();
+    __syncwarp();  // the lanes' reads below come after lane 0's acquire
     // the chunk sums: a fixed share per lane (independent loads), then a
     // fixed butterfly, so the sum does not depend on which chunk came last
     df t = df_zero();
@@ -531,7 +540,7 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
     const double c2 = ROLE == ROLE_U ? st->uc2 : st->vc2;
     const double wcoef = st->wcoef, xcoef = st->xcoef;
     const int tin_i = ROLE == ROLE_U ? TS_V : TS_U, tout_i = ROLE == ROLE_U ? TS_U : TS_V;
-    const double tin = tau[tin_i];
+    const double tin = tau[tin_i], tout = tau[tout_i], tw = tau[TS_W], tx = tau[TS_X];
     const double tt = SC ? (PASS == PASS_G ? cdN : rwN) * tin : tin;
     double oN;
     if (PASS == PASS_G) {
@@ -542,24 +551,24 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
         if (SC) oN *= cdN;
     }
     // gauge dz_N = 0: G^T-passes leave the tau entry at 0 (see run_tile)
-    const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * tau[tout_i];
+    const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * tout;
     tau[tout_i] = nvN;
     if (PASS == PASS_GT) tau[TS_XI] = 0.0;
     const double nsq = fma(nvN, nvN, tot.a);
     double nrm, inv;
     norm_and_inverse(nsq, nrm, inv);
     if (ROLE == ROLE_U) {
-        tau[TS_W] = tin * c1 - wcoef * tau[TS_W];
+        tau[TS_W] = tin * c1 - wcoef * tw;
         lsqr_step_u(st, nrm, inv, nsq);
     } else {
-        tau[TS_X] = fma(xcoef, tau[TS_W], tau[TS_X]);
+        tau[TS_X] = fma(xcoef, tw, tx);
         if (lsqr_step_v(st, nrm, inv)) atomicSub(a.active, 1);
     }
     // the next pass: the other product, the other update
     constexpr int NPASS = PASS == PASS_G ? PASS_GT : PASS_G;
     const double nc1 = ROLE == ROLE_U ? st->vc1 : st->uc1;
     const double nc2 = ROLE == ROLE_U ? st->vc2 : st->uc2;
-    const double ntin = tau[ROLE == ROLE_U ? TS_U : TS_V];
+    const double ntin = nvN;  // the next pass's input is this pass's output (U after a u-pass, V after a v-pass)
     const double ntt = SC ? (NPASS == PASS_G ? cdN : rwN) * ntin : ntin;
     StreamScal q;
     q.c1 = df_from(nc1);
@@ -571,37 +580,43 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
     a.scal[si] = q;
 }
 
+
 // One pass of the systems [s0, s0 + gridDim.y): PASS_G or PASS_GT, ROLE_U or
 // ROLE_V (the product and update of run_tile), SC = diagonal scaling.
 template <int PASS, int ROLE, bool SC>
 __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
     __shared__ df sbuf[kSWarps][kSSocBig];
     __shared__ df red[kSWarps][3];
-    __shared__ double fin_red[3 * kSThreads];
     __shared__ int s_last;
     const int si = a.s0 + (int)blockIdx.y;
     const int status = a.state[si].status;
     if (status == S_DONE) return;
+    // the pass's per-CTA constants live in shared memory, not in registers
+    __shared__ SCtx s_ctx;
     const Sys sy = a.sys[si];
     const Prob pr = a.probs[sy.prob];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    SCtx c;
-    c.sc = a.scal[si];
-    c.n = pr.n;
-    c.N = pr.n + pr.m + 1;
-    c.cA = a.cA + pr.doff;
-    c.cB = a.cB + pr.doff;
-    c.rw = a.rw + pr.doff;
-    c.cd = a.cd + pr.doff;
-    c.zy = a.zy + pr.doff;
-    c.flag = a.flag + pr.doff;
-    c.soc = a.soc + pr.soff;
-    c.IN = (ROLE == ROLE_U ? a.V : a.U) + sy.voff;
-    c.OUT = (ROLE == ROLE_U ? a.U : a.V) + sy.voff;
-    c.W = a.W + sy.voff;
-    c.X = a.X + sy.voff;
-    c.XI = a.XI + sy.voff;
-    c.gin = PASS == PASS_G ? c.XI : c.IN;
+    if (threadIdx.x == 0) {
+        SCtx& c = s_ctx;
+        c.sc = a.scal[si];
+        c.n = pr.n;
+        c.N = pr.n + pr.m + 1;
+        c.cA = a.cA + pr.doff;
+        c.cB = a.cB + pr.doff;
+        c.rw = a.rw + pr.doff;
+        c.cd = a.cd + pr.doff;
+        c.zy = a.zy + pr.doff;
+        c.flag = a.flag + pr.doff;
+        c.soc = a.soc + pr.soff;
+        c.IN = (ROLE == ROLE_U ? a.V : a.U) + sy.voff;
+        c.OUT = (ROLE == ROLE_U ? a.U : a.V) + sy.voff;
+        c.W = a.W + sy.voff;
+        c.X = a.X + sy.voff;
+        c.XI = a.XI + sy.voff;
+        c.gin = PASS == PASS_G ? c.XI : c.IN;
+    }
+    __syncthreads();
+    const SCtx& c = s_ctx;
     SUnitCtx k{a.rows, a.lblk, a.scol, PASS == PASS_G ? a.valG : a.valT};
     const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
     SAcc acc;
@@ -628,10 +643,11 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
             }
         }
     }
-    // the CTA's sums in a fixed order: lanes, then warps
-    const df v0 = warp_sum_df(dfacc_result(acc.ss));
-    const df v1 = warp_sum_df(dfacc_result(acc.dtop));
-    const df v2 = warp_sum_df(dfacc_result(acc.dbot));
+    // the CTA's sums in a fixed order: lanes, then warps (df64 throughout;
+    // FP64 only for the three totals, in the finisher's thread)
+    df v0 = warp_sum_df(dfacc_result(acc.ss));
+    df v1 = warp_sum_df(dfacc_result(acc.dtop));
+    df v2 = warp_sum_df(dfacc_result(acc.dbot));
     if (lane == 0) {
         red[warp][0] = v0;
         red[warp][1] = v1;
@@ -645,31 +661,52 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
             t1 = df_add(t1, red[w][1]);
             t2 = df_add(t2, red[w][2]);
         }
-        a.cpart[(int64_t)si * a.gx + blockIdx.x] = Part{df_to(t0), df_to(t1), df_to(t2), 0.0};
-        __threadfence();
-        const int prev = atomicAdd(a.ccnt + si, 1);
-        s_last = prev == a.gx - 1;
+        float4* o = a.cpart + 2 * ((int64_t)si * a.gx + blockIdx.x);
+        o[0] = make_float4(t0.x, t0.y, t1.x, t1.y);
+        o[1] = make_float4(t2.x, t2.y, 0.f, 0.f);
+        s_last = arrive_acq_rel(a.ccnt + si) == a.gx - 1;
     }
     __syncthreads();
     if (!s_last) return;
-    // the system's last CTA: every thread adds a fixed share of the CTA
-    // partials and the split rows' sums (independent loads in flight), then
-    // a fixed-order tree over the CTA; thread 0 finishes
-    __threadfence();
-    Part t = pzero();
-    for (int i = threadIdx.x; i < a.gx; i += kSThreads) t = padd(t, ld_part(a.cpart + (int64_t)si * a.gx + i));
+    // the system's last CTA (thread 0 acquired every other CTA's partials;
+    // the barrier orders this CTA's reads after that): every thread adds a
+    // fixed share of the CTA partials and of the split rows' sums, then lanes
+    // and warps in a fixed order; thread 0 finishes
+    v0 = v1 = v2 = df_zero();
+    for (int i = threadIdx.x; i < a.gx; i += kSThreads) {
+        const float4* o = a.cpart + 2 * ((int64_t)si * a.gx + i);
+        const float4 p0 = __ldcg(o), p1 = __ldcg(o + 1);
+        v0 = df_add(v0, make_float2(p0.x, p0.y));
+        v1 = df_add(v1, make_float2(p0.z, p0.w));
+        v2 = df_add(v2, make_float2(p1.x, p1.y));
+    }
     const int64_t sr = a.batched ? 0 : (int64_t)si * a.nsplit;
     if (!only_x) {
         for (int i = a.soff[sy.prob] + threadIdx.x; i < a.soff[sy.prob + 1]; i += kSThreads) {
             const float2* o = reinterpret_cast<const float2*>(a.lrow + 3 * (sr + i));
-            t = padd(t, Part{df_to(__ldcg(o)), df_to(__ldcg(o + 1)), df_to(__ldcg(o + 2)), 0.0});
+            v0 = df_add(v0, __ldcg(o));
+            v1 = df_add(v1, __ldcg(o + 1));
+            v2 = df_add(v2, __ldcg(o + 2));
         }
     }
-    double v[3] = {t.a, t.b, t.c};
-    block_reduce<3, kSThreads>(v, fin_red);
+    v0 = warp_sum_df(v0);
+    v1 = warp_sum_df(v1);
+    v2 = warp_sum_df(v2);
+    if (lane == 0) {
+        red[warp][0] = v0;
+        red[warp][1] = v1;
+        red[warp][2] = v2;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        df t0 = red[0][0], t1 = red[0][1], t2 = red[0][2];
+        for (int w = 1; w < kSWarps; ++w) {
+            t0 = df_add(t0, red[w][0]);
+            t1 = df_add(t1, red[w][1]);
+            t2 = df_add(t2, red[w][2]);
+        }
         a.ccnt[si] = 0;
-        stream_finish<PASS, ROLE, SC>(a, si, pr, Part{v[0], v[1], v[2], 0.0}, only_x);
+        stream_finish<PASS, ROLE, SC>(a, si, pr, Part{df_to(t0), df_to(t1), df_to(t2), 0.0}, only_x);
     }
 }
 
