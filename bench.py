@@ -341,8 +341,8 @@ def config4_bench(args, rank, local):
     JVP and one VJP direction each, rtol 1e-6, equilibration.
     Batched: one batch plan (autotuned for the VJP, untimed), per step one
     batched JVP and one batched VJP (engine auto).  Plain: one plan per
-    problem, per step each problem's JVP and VJP in turn (engine auto: the
-    cluster engine where a problem fits, else the stream engine).
+    problem, each autotuned for the VJP (untimed), per step each problem's
+    JVP and VJP in turn on its own fastest engine.
     value = batched solves/s; the plain rate, their ratio and both
     rooflines (algorithmic bytes of every pass of every problem over the
     device time of the iteration launches) ride along."""
@@ -361,9 +361,10 @@ def config4_bench(args, rank, local):
     best, _ = plan.autotune("vjp", iters=16, opts=q.options(precond="equilibrate"))
     opts = q.options(rtol=1e-6, maxiter=args.maxiter, precond="equilibrate", engine="auto")
     plans = []
-    for pr in probs:
+    for pr in probs:  # each problem on its own fastest engine (autotuned, untimed)
         pl = q.qcp_plan_create(q.problem_tensors(pr, dev), torch.float64)
         pl.set_equilibration(args.equil_sweeps)
+        pl.autotune("vjp", iters=16, opts=q.options(precond="equilibrate"))
         plans.append(pl)
     pins = [{nm: torch.as_tensor(getattr(d, nm), device=dev) for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
             for d in dirs]

@@ -32,10 +32,9 @@ def q():
     return lib()
 
 
-def _plan(q, prob, dtype=torch.float64, max_rhs=1, sweeps=1):
+def _plan(q, prob, dtype=torch.float64, max_rhs=1, sweeps=16):
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda", dtype), dtype, max_rhs=max_rhs)
-    if sweeps != 1:
-        plan.set_equilibration(sweeps)
+    plan.set_equilibration(sweeps)
     return plan
 
 
@@ -139,7 +138,8 @@ def test_more_sweeps_fewer_iterations(q):
 
 def test_set_equilibration_rules(q):
     """Out-of-range sweeps are refused and leave the plan as it was; the
-    setting is refused once the plan has run a derivative call."""
+    setting is refused once the plan has run a derivative call; a plan
+    starts with 16 sweeps (setting 16 again changes nothing)."""
     from paper_2508_17522_gb300._native import QCPError
     prob = g.small_qcp(21, 10, 2, 5, (3, 4, 5))
     d = g.make_directions(prob, 34)
