@@ -250,17 +250,14 @@ def learned_bench(args, rank, local):
     pattern, shrunk to n = 500, m = 801): train on the method's own solves of
     40 instances (untimed), then time, on 8 held-out instances, the adjoint
     solve of ||x*||^2 to rtol 1e-6 by
-      plain       zero start, no scaling (the method of Sec. 3.1), pass engine;
+      plain       zero start, no scaling (the method of Sec. 3.1);
       c_alpha     zero start, the column scaling c^alpha the training chose
-                  (the network's preconditioner target without the network),
-                  pass engine;
-      equilibrate the plan's 16-sweep row/column equilibration, pass engine;
+                  (the network's preconditioner target without the network);
       learned     network features + forward + decode, warm start and
-                  diagonal preconditioner, pass engine (the engine the
-                  diagonal preconditioner runs on);
-      best_plain  the fastest plain GPU form: equilibration, engine auto.
-    value = learned solves/s; every row's rate and mean iterations ride
-    along."""
+                  diagonal preconditioner;
+      best_plain  the fastest plain GPU form: the 16-sweep equilibration,
+    all on engine auto (the cluster engine for this size).  value = learned
+    solves/s; every row's rate and mean iterations ride along."""
     import torch
     import qcpgen as g
     import paper_2508_17522_gb300 as q
@@ -276,9 +273,8 @@ def learned_bench(args, rank, local):
     dirs = [L.adjoint_direction(pr) for pr in held]
     calpha = [(L.plan_scalings(pl)[1] ** lp.alpha).contiguous() for pl in plans]
     kinds = {
-        "plain": lambda i: q.options(rtol=1e-6, engine="passes"),
-        "c_alpha": lambda i: q.options(rtol=1e-6, engine="passes", precond="diag", precond_d=calpha[i]),
-        "equilibrate": lambda i: q.options(rtol=1e-6, engine="passes", precond="equilibrate"),
+        "plain": lambda i: q.options(rtol=1e-6, engine="auto"),
+        "c_alpha": lambda i: q.options(rtol=1e-6, engine="auto", precond="diag", precond_d=calpha[i]),
         "best_plain": lambda i: q.options(rtol=1e-6, engine="auto", precond="equilibrate"),
     }
 
@@ -299,7 +295,7 @@ def learned_bench(args, rank, local):
         torch.cuda.synchronize(dev)
         return ev0.elapsed_time(ev1), its, stat, eng
 
-    names = ["plain", "c_alpha", "equilibrate", "learned", "best_plain"]
+    names = ["plain", "c_alpha", "learned", "best_plain"]
     for _ in range(max(args.warmup, 1)):
         for k in names:
             run(k)
@@ -327,7 +323,8 @@ def learned_bench(args, rank, local):
                        "alpha": lp.alpha, "rows": rows,
                        "learned_over_plain": rate["learned"] / rate["plain"],
                        "learned_over_c_alpha": rate["learned"] / rate["c_alpha"],
-                       "learned_over_best_plain": rate["learned"] / rate["best_plain"]},
+                       "learned_over_best_plain": rate["learned"] / rate["best_plain"],
+                       "training": "40 instances, 800 Adam steps on the GPU (untimed)"},
             "gpu_launches": None, "e2e": None, "roofline": None, "cpu_baseline": None}), flush=True)
     for pl in plans:
         pl.close()

@@ -143,12 +143,13 @@ typedef enum {
                                    left out of the norms (any positive diagonal is a valid choice) */
     QCP_PRECOND_DIAG = 2,       /* LSQR on F C with C = diag(opts->precond_d), a caller-given positive
                                    right preconditioner (for instance the learned one), averaged
-                                   over each SOC block (C must commute with D Pi); pass or
-                                   persistent engine */
+                                   over each SOC block (C must commute with D Pi); pass,
+                                   persistent and cluster engines (the cluster engine refills its
+                                   copy of M diag(C) on every such call) */
     QCP_PRECOND_JACOBI = 3      /* the classical column-norm (Jacobi) preconditioner: LSQR on F C with
                                    C = 1/(column norms of F), D Pi by its diagonal in the norms, C
                                    constant on each SOC block; computed on the plan's first such call;
-                                   pass or persistent engine (as QCP_PRECOND_DIAG) */
+                                   the engines of QCP_PRECOND_DIAG */
 } qcp_precond;
 
 /* How the Krylov iterations are run on the GPU (all give the same iterates up
@@ -165,13 +166,12 @@ typedef enum {
                                    memory and only hardware cluster barriers separate passes.
                                    Needs every system to fit (about 8 N + 60 N / C bytes per CTA
                                    for C CTAs) and the cones to be zero, R+ and SOC blocks; LSQR
-                                   only; QCP_ERR_ARG otherwise */
-    QCP_ENGINE_AUTO = 3,        /* QCP_PRECOND_DIAG / _JACOBI: PASSES.  Otherwise the plan's
-                                   autotuned engine when qcp_plan_autotune has run, else
+                                   only (any qcp_precond); QCP_ERR_ARG otherwise */
+    QCP_ENGINE_AUTO = 3,        /* the plan's autotuned engine when qcp_plan_autotune has run, else
                                    QCP_ENGINE_CLUSTER; a cluster choice becomes STREAM when a system
                                    does not fit the cluster engine (PASSES where STREAM cannot run
-                                   the plan), and PASSES for LSMR and for plans with PSD,
-                                   exponential or power blocks */
+                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI), and PASSES for LSMR
+                                   and for plans with PSD, exponential or power blocks */
     QCP_ENGINE_CLUSTER_FP64 = 4, /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,

@@ -162,6 +162,19 @@ class FOperator:
     def rmatvec(self, u):
         return (self._DPi_T(self._DuQ_T(u)) - self._DPi_T(u) + u) / self.zN
 
+    def sparse(self):
+        """F assembled as a scipy CSR matrix from the same pieces (D_u Q with
+        its dense tau row and column, the block-diagonal D Pi), for the
+        column-scaled LSMR below."""
+        import scipy.sparse as sp
+        p, n, m = self.prob, self.n, self.m
+        DuQ = sp.bmat([[self.P, self.AT, sp.csr_matrix(p.q.reshape(-1, 1))],
+                       [-self.A, None, sp.csr_matrix(p.b.reshape(-1, 1))],
+                       [sp.csr_matrix(self.last_x.reshape(1, -1)), sp.csr_matrix(-p.b.reshape(1, -1)),
+                        sp.csr_matrix([[self.last_t]])]], format="csr")
+        DPi = sp.block_diag([sp.identity(n), self.Dy, sp.csr_matrix([[self.dtau]])], format="csr")
+        return ((DuQ @ DPi - DPi + sp.identity(self.N)) / self.zN).tocsr()
+
     def linear_operator(self, transpose=False):
         mv, rmv = (self.rmatvec, self.matvec) if transpose else (self.matvec, self.rmatvec)
         return spla.LinearOperator((self.N, self.N), matvec=mv, rmatvec=rmv, dtype=np.float64)
@@ -216,27 +229,66 @@ def _phi_apply_T(prob, z, wx, wy, ws):
     return np.concatenate([wx / zN, gy, [gN]])
 
 
-def jvp_lsmr(prob, d, rtol=1e-10, maxiter=None, op=None):
-    """Matrix-free JVP: LSMR on min ||F dz + dN|| (Sec. 3.1)."""
+def _ruiz(F, sweeps=16):
+    """Row and column scalings (r, c) of a sparse matrix by Ruiz's iterated
+    equilibration in the 2-norm (Ruiz 2001): each sweep divides every row
+    of diag(r) F diag(c) by the square root of its norm, then every column
+    likewise.  Both linear systems are consistent, so the scaled problem
+    min ||diag(r) (F diag(c) y - b)|| has the same solution dz = c y; only
+    the Krylov iterates change."""
+    import scipy.sparse as sp
+    F = sp.csr_matrix(F)
+    r = np.ones(F.shape[0])
+    c = np.ones(F.shape[1])
+    for _ in range(sweeps):
+        G = sp.diags(r) @ F @ sp.diags(c)
+        rn = np.sqrt(np.asarray(G.multiply(G).sum(axis=1)).ravel())
+        r = r / np.sqrt(np.where(rn > 0, rn, 1.0))
+        G = sp.diags(r) @ F @ sp.diags(c)
+        cn = np.sqrt(np.asarray(G.multiply(G).sum(axis=0)).ravel())
+        c = c / np.sqrt(np.where(cn > 0, cn, 1.0))
+    return r, c
+
+
+def _scaled_lsmr(F, b, rtol, maxiter):
+    """LSMR on diag(r) F diag(c) y = diag(r) b (Ruiz scalings), x = c y."""
+    import scipy.sparse as sp
+    r, c = _ruiz(F)
+    res = spla.lsmr(sp.diags(r) @ F @ sp.diags(c), r * b, atol=0.0, btol=rtol, conlim=0.0, maxiter=maxiter)
+    return c * res[0], res
+
+
+def jvp_lsmr(prob, d, rtol=1e-10, maxiter=None, op=None, scale=False):
+    """Matrix-free JVP: LSMR on min ||F dz + dN|| (Sec. 3.1).  scale=True
+    runs it on the assembled sparse F with Ruiz's row and column scalings
+    (dz = C y; F dz = -dN is consistent, so the solution is the same).  rtol
+    bounds the scaled problem's residual; info reports the true one."""
     op = op or FOperator(prob)
     z = op.z
     dN = d_theta_N_sparse(prob, z, d.dP, d.dA, d.dq, d.db)
-    res = spla.lsmr(op.linear_operator(), -dN, atol=0.0, btol=rtol, conlim=0.0,
-                    maxiter=maxiter or 20 * op.N)
-    dz = res[0]
+    if scale:
+        dz, res = _scaled_lsmr(op.sparse(), -dN, rtol, maxiter or 20 * op.N)
+    else:
+        res = spla.lsmr(op.linear_operator(), -dN, atol=0.0, btol=rtol, conlim=0.0,
+                        maxiter=maxiter or 20 * op.N)
+        dz = res[0]
     true_res = np.linalg.norm(op.matvec(dz) + dN) / max(np.linalg.norm(dN), 1e-300)
     dx, dy, ds = _phi_apply(prob, z, dz)
     return dx, dy, ds, {"iters": int(res[2]), "istop": int(res[1]), "rel_residual": float(true_res)}
 
 
-def vjp_lsmr(prob, d, rtol=1e-10, maxiter=None, op=None):
-    """Matrix-free VJP: LSMR on min ||F^T r + g|| (Sec. 3.2)."""
+def vjp_lsmr(prob, d, rtol=1e-10, maxiter=None, op=None, scale=False):
+    """Matrix-free VJP: LSMR on min ||F^T r + g|| (Sec. 3.2); scale=True as
+    in jvp_lsmr, on F^T."""
     op = op or FOperator(prob)
     z = op.z
     g = _phi_apply_T(prob, z, d.wx, d.wy, d.ws)
-    res = spla.lsmr(op.linear_operator(transpose=True), -g, atol=0.0, btol=rtol, conlim=0.0,
-                    maxiter=maxiter or 20 * op.N)
-    r = res[0]
+    if scale:
+        r, res = _scaled_lsmr(op.sparse().T.tocsr(), -g, rtol, maxiter or 20 * op.N)
+    else:
+        res = spla.lsmr(op.linear_operator(transpose=True), -g, atol=0.0, btol=rtol, conlim=0.0,
+                        maxiter=maxiter or 20 * op.N)
+        r = res[0]
     true_res = np.linalg.norm(op.rmatvec(r) + g) / max(np.linalg.norm(g), 1e-300)
     dPv, dAv, dq, db = d_theta_N_T_sparse(prob, z, r)
     return dPv, dAv, dq, db, {"iters": int(res[2]), "istop": int(res[1]),

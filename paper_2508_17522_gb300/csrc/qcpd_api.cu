@@ -402,11 +402,6 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
         set_error("QCP_PRECOND_DIAG needs opts->precond_d");
         return QCP_ERR_ARG;
     }
-    if (opts.precond == QCP_PRECOND_DIAG &&
-        (opts.engine == QCP_ENGINE_CLUSTER || opts.engine == QCP_ENGINE_CLUSTER_FP64)) {
-        set_error("QCP_PRECOND_DIAG and _JACOBI run on the pass or persistent engine");
-        return QCP_ERR_ARG;
-    }
     if (opts.engine < QCP_ENGINE_PASSES || opts.engine > QCP_ENGINE_STREAM) {
         set_error("engine must be one of QCP_ENGINE_PASSES, _PERSISTENT, _CLUSTER, _AUTO, _CLUSTER_FP64, _STREAM");
         return QCP_ERR_ARG;
@@ -422,8 +417,10 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
     int nsys = 0;
     for (int gi = 0; gi < nseg; ++gi) nsys = std::max(nsys, segs[gi].s0 + segs[gi].ns);
     int engine = opts.engine;
-    if (engine == QCP_ENGINE_AUTO && opts.precond == QCP_PRECOND_DIAG) engine = QCP_ENGINE_PASSES;
     if (engine == QCP_ENGINE_AUTO && p->tuned_engine >= 0) engine = p->tuned_engine;
+    // the stream engine takes no diagonal preconditioner: an autotuned choice of it becomes AUTO
+    if (engine == QCP_ENGINE_STREAM && opts.engine == QCP_ENGINE_AUTO && opts.precond == QCP_PRECOND_DIAG)
+        engine = QCP_ENGINE_AUTO;
     if (opts.solver == 1 && (engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER)) engine = QCP_ENGINE_PASSES;
     if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER_FP64) {
         bool fits = false;
@@ -433,6 +430,8 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
         } else if (engine != QCP_ENGINE_AUTO) {
             set_error("cluster engine: a problem's vectors do not fit in the shared memory of 16 CTAs");
             return QCP_ERR_ARG;
+        } else if (opts.precond == QCP_PRECOND_DIAG) {
+            engine = QCP_ENGINE_PASSES;  // the stream engine takes no diagonal preconditioner
         } else {
             // too large for the cluster engine: the stream engine where it can run the plan
             bool sok = false;

@@ -242,12 +242,15 @@ static int fill_sell(qcp_plan* p, ClusterLayout* lay, const std::vector<SellSlic
     QCP_TRY(lay->d_sval.alloc(sizeof(T) * (size_t)slots));
     QCP_TRY(lay->d_svalG.alloc(sizeof(T) * (size_t)slots));
     QCP_TRY(lay->d_svalT.alloc(sizeof(T) * (size_t)slots));
-    DevBuf d_sp, d_sr;
+    DevBuf& d_sp = lay->d_sp;
+    DevBuf& d_sr = lay->d_sr;
     QCP_TRY(d_sp.alloc(sizeof(int32_t) * hsp.size()));
     QCP_TRY(d_sr.alloc(sizeof(int32_t) * hsr.size()));
     QCP_CUDA(cudaMemcpyAsync(d_sp.p, hsp.data(), sizeof(int32_t) * hsp.size(), cudaMemcpyHostToDevice, p->stream));
     QCP_CUDA(cudaMemcpyAsync(d_sr.p, hsr.data(), sizeof(int32_t) * hsr.size(), cudaMemcpyHostToDevice, p->stream));
     const int64_t nsl = (int64_t)hs.size();
+    lay->nslices = nsl;
+    lay->slots = slots;
     if (nsl > 0) {
         const int64_t blocks = (nsl * 32 + 255) / 256;
         k_sell_fill<T><<<(unsigned)blocks, 256, 0, p->stream>>>(
@@ -327,6 +330,45 @@ static int build_df(qcp_plan* p, ClusterLayout* lay, int64_t slots) {
     QCP_CUDA(cudaMemcpyAsync(&hbad, b, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     QCP_CUDA(cudaStreamSynchronize(p->stream));
     lay->df_ok = hbad == 0;
+    return QCP_OK;
+}
+
+// QCP_PRECOND_DIAG on the cluster engine: the caller's C (block-averaged by
+// prepare_diag into p->d_cdD, with M diag(C) in p->d_mvalD) changes from
+// call to call, so every such call refills the layout's M diag(C) slots
+// (the same slot map as the other value arrays; the plain values serve the
+// G^T-passes, W = I) and the df64 copies of M diag(C), W = 1 and C.
+template <typename T>
+static int refresh_diag(qcp_plan* p, ClusterLayout* lay) {
+    const int64_t slots = std::max<int64_t>(lay->slots, 1), nt = std::max<int64_t>(p->N_tot, 1);
+    if (!lay->d_svalDG.p) {
+        QCP_TRY(lay->d_svalDG.alloc(sizeof(T) * (size_t)slots));
+        QCP_TRY(lay->d_dsvalDG.alloc(sizeof(df) * (size_t)slots));
+        QCP_TRY(lay->d_drwD.alloc(sizeof(df) * (size_t)nt));
+        QCP_TRY(lay->d_dcdD.alloc(sizeof(df) * (size_t)nt));
+        QCP_TRY(lay->d_diag_bad.alloc(sizeof(int)));
+    }
+    cudaStream_t st = p->stream;
+    int* b = lay->d_diag_bad.as<int>();
+    QCP_CUDA(cudaMemsetAsync(b, 0, sizeof(int), st));
+    if (lay->nslices > 0) {
+        const int64_t blocks = (lay->nslices * 32 + 255) / 256;
+        // scol and sval are rewritten with the values they already hold
+        k_sell_fill<T><<<(unsigned)blocks, 256, 0, st>>>(
+            lay->d_slices.as<SellSlice>(), lay->nslices, lay->d_perm.as<int32_t>(), lay->d_sp.as<int32_t>(),
+            lay->d_sr.as<int32_t>(), lay->d_cprob.as<ClusterProb>(), p->d_prob.as<Prob>(), p->d_mrowptr.as<int64_t>(),
+            p->d_mcol.as<int32_t>(), p->d_mval.as<T>(), p->d_mvalD.as<T>(), p->d_mval.as<T>(),
+            lay->d_scol.as<int32_t>(), lay->d_sval.as<T>(), lay->d_svalDG.as<T>(), lay->d_sval.as<T>());
+    }
+    const int g1 = (int)std::min<int64_t>(4096, (slots + 255) / 256), g2 = (int)std::min<int64_t>(4096, (nt + 255) / 256);
+    k_to_df<T><<<g1, 256, 0, st>>>(lay->d_svalDG.as<T>(), slots, lay->d_dsvalDG.as<df>(), b);
+    k_to_df<double><<<g2, 256, 0, st>>>(p->d_onesD.as<double>(), p->N_tot, lay->d_drwD.as<df>(), b);
+    k_to_df<double><<<g2, 256, 0, st>>>(p->d_cdD.as<double>(), p->N_tot, lay->d_dcdD.as<df>(), b);
+    QCP_CUDA(cudaGetLastError());
+    int hbad = 1;
+    QCP_CUDA(cudaMemcpyAsync(&hbad, b, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QCP_CUDA(cudaStreamSynchronize(st));
+    lay->diag_df_ok = hbad == 0;
     return QCP_OK;
 }
 
@@ -501,7 +543,9 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
     }
     const size_t ncs = std::max<size_t>(1, p->h_csys.size());
     if (p->d_csys.bytes < sizeof(int32_t) * ncs) QCP_TRY(p->d_csys.alloc(sizeof(int32_t) * ncs));
-    const bool use_df = lay->df_ok && opts.engine != QCP_ENGINE_CLUSTER_FP64;
+    const bool diag = p->view_precond == QCP_PRECOND_DIAG;
+    if (diag) QCP_TRY(refresh_diag<T>(p, lay));
+    const bool use_df = lay->df_ok && (!diag || lay->diag_df_ok) && opts.engine != QCP_ENGINE_CLUSTER_FP64;
     if (use_df && p->d_bcast.bytes < bneed) QCP_TRY(p->d_bcast.alloc(bneed));
     QCP_CUDA(cudaMemcpyAsync(p->d_csys.p, p->h_csys.data(), sizeof(int32_t) * p->h_csys.size(),
                              cudaMemcpyHostToDevice, st));
@@ -543,8 +587,8 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
         ca.perm = lay->d_perm.as<int32_t>();
         ca.scol = lay->d_scol.as<int32_t>();
         ca.sval = lay->d_sval.p;
-        ca.svalG = lay->d_svalG.p;
-        ca.svalT = lay->d_svalT.p;
+        ca.svalG = diag ? lay->d_svalDG.p : lay->d_svalG.p;
+        ca.svalT = diag ? lay->d_sval.p : lay->d_svalT.p;
         ca.sys_list = p->d_csys.as<int32_t>() + L.start;
         ca.C = C;
         ca.FN = L.FN;
@@ -556,12 +600,12 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
             da.bhalf = even_up(L.FN);
             da.bcast = reinterpret_cast<df*>(static_cast<unsigned char*>(p->d_bcast.p) + L.boff);
             da.sval = lay->d_dsval.as<df>();
-            da.svalG = lay->d_dsvalG.as<df>();
-            da.svalT = lay->d_dsvalT.as<df>();
+            da.svalG = diag ? lay->d_dsvalDG.as<df>() : lay->d_dsvalG.as<df>();
+            da.svalT = diag ? lay->d_dsval.as<df>() : lay->d_dsvalT.as<df>();
             da.cA = lay->d_dcA.as<df>();
             da.cB = lay->d_dcB.as<df>();
-            da.rw = lay->d_drw.as<df>();
-            da.cd = lay->d_dcd.as<df>();
+            da.rw = diag ? lay->d_drwD.as<df>() : lay->d_drw.as<df>();
+            da.cd = diag ? lay->d_dcdD.as<df>() : lay->d_dcd.as<df>();
             da.zy = lay->d_dzy.as<df>();
             da.soc = lay->d_dsoc.as<SocDf>();
             auto fn = mode == 0 ? cluster_kernel_df<0, T>(vs.scaled != 0) : cluster_kernel_df<1, T>(vs.scaled != 0);

@@ -101,9 +101,15 @@ struct ClusterLayout {
     // SELL-32 copy of M by CTA: slices, row permutation, gather-buffer
     // columns and the plain / column-scaled / row-scaled values per slot
     DevBuf d_slices, d_perm, d_scol, d_sval, d_svalG, d_svalT;
+    DevBuf d_sp, d_sr;          // per slice: its problem and the first row of its CTA
+    int64_t nslices = 0, slots = 0;
     // double-float copies for the df64 kernel (df_ok: every magnitude in range)
     bool df_ok = false;
     DevBuf d_dsval, d_dsvalG, d_dsvalT, d_dcA, d_dcB, d_drw, d_dcd, d_dzy, d_dsoc;
+    // QCP_PRECOND_DIAG (refilled on every such call, the caller's C changes):
+    // M diag(C) per slot and its df64 copy, df64 copies of W = 1 and of C
+    bool diag_df_ok = false;
+    DevBuf d_svalDG, d_dsvalDG, d_drwD, d_dcdD, d_diag_bad;
 };
 
 // The stream engine's copy of a plan (QCP_ENGINE_STREAM, built on first

@@ -225,7 +225,7 @@ class LearnedPreconditioner:
         y = self.net.forward(plan_features(plan))
         return decode(y, scale, self.offset)
 
-    def vjp(self, plan: api.Plan, prob, rtol=1e-6, engine="passes"):
+    def vjp(self, plan: api.Plan, prob, rtol=1e-6, engine="auto"):
         """The learned adjoint solve of ||x*||^2 on a new instance."""
         wx, wy, ws = adjoint_direction(prob)
         warm, d = self.predict(plan, float(np.linalg.norm(wx)) or 1.0)

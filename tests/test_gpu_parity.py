@@ -439,17 +439,22 @@ def test_warm_start_and_diag_preconditioner(q):
             assert ji[0]["iters"] <= 1 and rel_err(jv, ref_j) < TOL64, (engine, precond, ji)
             vv, vi = gpu_vjp(q, plan, d, q.options(rtol=1e-9, warm_start=cuda(r), engine=engine, precond=precond))
             assert vi[0]["iters"] <= 1 and rel_err(vv, ref_v) < TOL64, (engine, precond, vi)
-    for dd in (np.ones(N), np.exp(rng.uniform(-1.0, 1.0, N))):
-        for engine in ("passes", "persistent", "auto"):
-            opts = q.options(rtol=1e-11, precond="diag", precond_d=cuda(dd), engine=engine)
-            jv, ji = gpu_jvp(q, plan, d, opts)
-            assert rel_err(jv, ref_j) < TOL64, (engine, rel_err(jv, ref_j), ji)
-            vv, vi = gpu_vjp(q, plan, d, opts)
-            assert rel_err(vv, ref_v) < TOL64, (engine, rel_err(vv, ref_v), vi)
-            assert plan.last_engine() in ("passes", "persistent")
+    # the caller's diagonal preconditioner, changing from call to call (the
+    # cluster engine refills its copy of M diag(C) each time), with and
+    # without a warm start
+    for dd in (np.ones(N), np.exp(rng.uniform(-1.0, 1.0, N)), np.exp(rng.uniform(-2.0, 2.0, N))):
+        for engine in ("passes", "persistent", "cluster", "cluster_fp64", "auto"):
+            for ws in (None, cuda(rng.standard_normal(N))):
+                opts = q.options(rtol=1e-11, precond="diag", precond_d=cuda(dd), engine=engine, warm_start=ws)
+                jv, ji = gpu_jvp(q, plan, d, opts)
+                assert rel_err(jv, ref_j) < TOL64, (engine, rel_err(jv, ref_j), ji)
+                vv, vi = gpu_vjp(q, plan, d, opts)
+                assert rel_err(vv, ref_v) < TOL64, (engine, rel_err(vv, ref_v), vi)
+                if engine == "auto":
+                    assert plan.last_engine() in ("cluster", "cluster_fp64"), plan.last_engine()
     from paper_2508_17522_gb300._native import QCPError
     with pytest.raises(QCPError, match="ERR_ARG"):
-        gpu_jvp(q, plan, d, q.options(precond="diag", precond_d=cuda(np.ones(N)), engine="cluster"))
+        gpu_jvp(q, plan, d, q.options(precond="diag", precond_d=cuda(np.ones(N)), engine="stream"))
     with pytest.raises(QCPError, match="ERR_ARG"):
         gpu_jvp(q, plan, d, q.options(precond="diag"))
     plan.close()
@@ -551,5 +556,6 @@ def test_jacobi_preconditioner(q, name, mk, solver):
     vv, vi = gpu_vjp(q, plan, d, opts)
     assert rel_err(jv, D.jvp_dense(prob, d, fac)[:3]) < TOL64, ji
     assert rel_err(vv, D.vjp_dense(prob, d, fac)[:4]) < TOL64, vi
-    assert plan.last_engine() == "passes"
+    # LSMR runs on the pass engine; LSQR with the Jacobi scaling on the cluster engine where it fits
+    assert plan.last_engine() in (("passes",) if solver == "lsmr" else ("cluster", "cluster_fp64")), plan.last_engine()
     plan.close()

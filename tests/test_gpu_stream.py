@@ -1,12 +1,13 @@
 """The stream engine (QCP_ENGINE_STREAM) against the CPU oracle.
 
 The engine cuts every problem's rows into warp-sized units: SELL-32 slices
-of x-rows and of zero-cone / R+ rows, packed second-order-cone blocks of at
-most 32 rows (segmented warp sums for D Pi, Appendix A), single blocks of
-33 to 256 rows, and 1024-entry chunks of long rows (a row of more chunks is
-completed by whichever chunk finishes last).  The problems below reach each
-kind: SOC mixes with blocks of dimension 1 to 200, dense P rows of 1300+
-entries (two chunks), power-law columns (config 3, scaled), m = 0.
+of x-rows and of zero-cone / R+ rows with 1 to 32 lanes per row, packed
+second-order-cone blocks of at most 32 rows (segmented warp sums for D Pi,
+Appendix A), single blocks of 33 to 256 rows, and 512-entry chunks of
+longer rows (a row of several chunks is completed by whichever chunk
+finishes last).  The problems below reach each kind: SOC mixes with blocks
+of dimension 1 to 200, dense P rows of 1300+ entries (three chunks),
+power-law columns (config 3, scaled), m = 0.
 Tolerances: FP64 1e-6, FP32 storage 1e-4 against the oracle on the
 FP32-rounded data; every output block is checked on its own.
 """
@@ -173,3 +174,27 @@ def test_stream_engine_rules(q):
     with pytest.raises(QCPError, match="ERR_ARG"):
         gpu_jvp(q, pl, g.make_directions(psd, 1), q.options(engine="stream"))
     pl.close()
+
+
+@pytest.mark.slow
+def test_config3_tenth_against_matrix_free_oracle(q):
+    """Configuration 3's structure at a tenth of its size (N = 32 001: power-law
+    columns, lognormal SOC blocks, 1000+-entry rows), too large for the dense
+    oracle: the outputs of the stream and pass engines against the oracle's
+    own matrix-free solve (Ruiz-scaled LSMR on the assembled sparse F, to a
+    relative residual of 1e-12), element by element in every output block."""
+    prob = g.config3(0, scale=0.1)
+    d = g.make_directions(prob, 61)
+    op = D.FOperator(prob)
+    rj = D.jvp_lsmr(prob, d, rtol=1e-12, scale=True, maxiter=40000, op=op)
+    rv = D.vjp_lsmr(prob, d, rtol=1e-12, scale=True, maxiter=40000, op=op)
+    assert rj[3]["rel_residual"] < 1e-10 and rv[4]["rel_residual"] < 1e-10, (rj[3], rv[4])
+    plan = _plan(q, prob)
+    for engine in ("stream", "passes"):
+        opts = q.options(rtol=1e-11, maxiter=400000, precond="equilibrate", engine=engine)
+        jv, ji = gpu_jvp(q, plan, d, opts)
+        vv, vi = gpu_vjp(q, plan, d, opts)
+        assert plan.last_engine() == engine
+        _check_blocks(jv, rj[:3], TOL64, (engine, "jvp", ji))
+        _check_blocks(vv, rv[:4], TOL64, (engine, "vjp", vi))
+    plan.close()

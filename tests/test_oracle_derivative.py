@@ -176,3 +176,31 @@ def test_linearized_kkt_pins_dense_jvp(mk):
     rng = np.random.default_rng(0)
     bad = dy + 1e-4 * np.linalg.norm(dy) * rng.standard_normal(dy.size) / np.sqrt(dy.size)
     assert KL.relative_residual(p, d, dx, bad, ds) > 1e-7
+
+
+@pytest.mark.parametrize("mk", [lambda: g.config1(0), lambda: g.small_qcp(2, 14, 0, 6, (3, 5, 2, 6)),
+                                lambda: g.small_qcp(25, 60, 3, 10, (40, 5), soc_mix=(0.5, 0.0))])
+def test_assembled_F_and_scaled_lsmr(mk):
+    """The matrix-free oracle's assembled sparse F equals the dense F (at the
+    root and off it), and its Ruiz-scaled LSMR reaches the dense-LU JVP and
+    VJP: the scaling changes the iterates, not the solution of the
+    consistent systems.  This is the oracle the large GPU parity cases use."""
+    from oracle import embedding as E
+    prob = mk()
+    z = E.solution_to_z(prob)
+    op = D.FOperator(prob)
+    assert np.max(np.abs(op.sparse().toarray() - E.F_dense(prob, z))) < 1e-13 * max(1.0, np.abs(E.F_dense(prob, z)).max())
+    zp = z + 0.3 * np.random.default_rng(5).standard_normal(z.size)
+    zp[-1] = 1.0
+    opp = D.FOperator(prob, zp)
+    assert np.max(np.abs(opp.sparse().toarray() - E.F_dense(prob, zp))) < 1e-12 * max(1.0, np.abs(E.F_dense(prob, zp)).max())
+    d = g.make_directions(prob, 8)
+    fac = D.DenseFactor(prob)
+    rj = D.jvp_dense(prob, d, fac)[:3]
+    rv = D.vjp_dense(prob, d, fac)[:4]
+    j = D.jvp_lsmr(prob, d, rtol=1e-13, scale=True, op=op)
+    v = D.vjp_lsmr(prob, d, rtol=1e-13, scale=True, op=op)
+    for a, b in zip(j[:3], rj):
+        assert np.linalg.norm(a - b) <= 1e-9 * max(np.linalg.norm(b), 1e-300)
+    for a, b in zip(v[:4], rv):
+        assert np.linalg.norm(a - b) <= 1e-9 * max(np.linalg.norm(b), 1e-300)
