@@ -127,6 +127,7 @@ struct StreamLayout {
     DevBuf d_units, d_uoff, d_soff, d_rows, d_lblk, d_scol, d_val, d_valG, d_valT;
     DevBuf d_cA, d_cB, d_rw, d_cd, d_zy, d_soc;
     DevBuf d_scal, d_ssys, d_cpart, d_ccnt, d_lchunk, d_lcnt, d_lrow;
+    DevBuf d_slist, d_scount;        // the systems still iterating, their number
 };
 
 }  // namespace qcpd

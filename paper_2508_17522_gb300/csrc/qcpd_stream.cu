@@ -355,6 +355,8 @@ static int build_stream(qcp_plan* p, StreamLayout* lay) {
     QCP_TRY(lay->d_lcnt.alloc(sizeof(int32_t) * per * std::max(1, lay->nsplit)));
     QCP_CUDA(cudaMemsetAsync(lay->d_lcnt.p, 0, sizeof(int32_t) * per * std::max(1, lay->nsplit), st));
     QCP_TRY(lay->d_lrow.alloc(sizeof(df) * 3 * per * std::max(1, lay->nsplit)));
+    QCP_TRY(lay->d_slist.alloc(sizeof(int32_t) * nsys));
+    QCP_TRY(lay->d_scount.alloc(sizeof(int32_t)));
     int hbad = 1;
     QCP_CUDA(cudaMemcpyAsync(&hbad, b, sizeof(int), cudaMemcpyDeviceToHost, st));
     QCP_CUDA(cudaStreamSynchronize(st));
@@ -435,6 +437,8 @@ static void launch_stream_iter(int mode, const StreamArgs& a, int ns, bool scale
 
 static int run_stream_chunk(qcp_plan* p, int mode, int s0, int ns, const StreamArgs& a, bool scaled, int chunk,
                             bool use_graph) {
+    // ns: the systems in a.slist this chunk (graphs are kept per count: the
+    // list's contents change between chunks, the launch shape does not)
     cudaStream_t st = p->stream;
     if (!use_graph || chunk < 2) {
         for (int c = 0; c < chunk; ++c) launch_stream_iter(mode, a, ns, scaled, st);
@@ -478,11 +482,8 @@ int iterate_stream(qcp_plan* p, int mode, int s0, int ns, int* active, bool scal
     StreamArgs a = stream_args(p, lay, scaled ? 1 : 0);
     a.s0 = s0;
     a.active = active;
-    // CTAs per system: the GPU's resident CTAs shared by the systems, and no
-    // more than the problem's units keep busy
-    int gx = (lay->gmax + ns - 1) / ns;
-    gx = std::min(gx, std::max(1, (lay->max_units + kSWarps - 1) / kSWarps));
-    a.gx = std::max(1, gx);
+    a.slist = lay->d_slist.as<int32_t>();
+    a.gstride = lay->gmax;
     cudaStream_t st = p->stream;
     int maxN = 1;
     for (int s = s0; s < s0 + ns; ++s) {
@@ -494,14 +495,32 @@ int iterate_stream(qcp_plan* p, int mode, int s0, int ns, int* active, bool scal
     k_stream_enter_vec<<<vgrid, 256, 0, st>>>(a);
     QCP_CUDA(cudaGetLastError());
     p->last_launches += 2;
+    // The launches cover the range's systems still iterating (a device list,
+    // rebuilt whenever the host's check sees fewer of them), and the GPU's
+    // resident CTAs are shared among those: a system left alone gets them all.
+    auto compact = [&](int* nact) -> int {
+        k_stream_compact<<<1, 32, 0, st>>>(p->d_state.as<LsqrState>(), s0, ns, lay->d_slist.as<int32_t>(),
+                                           lay->d_scount.as<int32_t>());
+        QCP_CUDA(cudaGetLastError());
+        QCP_CUDA(cudaMemcpyAsync(p->h_active, lay->d_scount.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        QCP_CUDA(cudaStreamSynchronize(st));
+        *nact = *p->h_active;
+        p->last_launches += 1;
+        return QCP_OK;
+    };
+    int nact = 0;
+    QCP_TRY(compact(&nact));
     int64_t done = 0;
     const int64_t cap = opts.maxiter + 1;
-    while (done < cap) {
+    while (done < cap && nact > 0) {
+        int gx = (lay->gmax + nact - 1) / nact;
+        gx = std::min(gx, std::max(1, (lay->max_units + kSWarps - 1) / kSWarps));
+        a.gx = std::max(1, gx);
         int64_t chunk = opts.check_every > 0 ? opts.check_every : cap;
         chunk = std::min<int64_t>(chunk, cap - done);
         const bool graph_ok = opts.use_graph && opts.check_every > 0 && chunk == opts.check_every;
         QCP_CUDA(cudaEventRecord(p->ev0, st));
-        QCP_TRY(run_stream_chunk(p, mode, s0, ns, a, scaled, (int)chunk, graph_ok));
+        QCP_TRY(run_stream_chunk(p, mode, s0, nact, a, scaled, (int)chunk, graph_ok));
         QCP_CUDA(cudaEventRecord(p->ev1, st));
         done += chunk;
         p->pass_launches += 2 * chunk;
@@ -514,7 +533,11 @@ int iterate_stream(qcp_plan* p, int mode, int s0, int ns, int* active, bool scal
         float ms = 0.0f;
         QCP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
         p->pass_ms += ms;
-        if (opts.check_every > 0 && *p->h_active <= 0) break;
+        if (opts.check_every > 0) {
+            const int still = *p->h_active;
+            if (still <= 0) break;
+            if (still < nact) QCP_TRY(compact(&nact));
+        }
     }
     k_stream_exit_vec<<<vgrid, 256, 0, st>>>(a);
     k_stream_exit_state<<<ns, 32, 0, st>>>(a);

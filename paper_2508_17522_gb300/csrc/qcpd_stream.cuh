@@ -126,7 +126,9 @@ struct StreamArgs {
     int32_t nslot;          // chunk slots per system stride
     const int32_t* soff;    // per problem: its split rows [soff[p], soff[p + 1])
     int32_t gx;             // CTAs per system (gridDim.x)
-    int32_t s0;             // first system of the launch
+    int32_t gstride;        // CTA partials per system in cpart (>= gx)
+    int32_t s0;             // first system of the range (enter / exit kernels)
+    const int32_t* slist;   // the pass kernels' systems: slist[blockIdx.y] (the range's systems still iterating)
     int32_t batched;
     int* active;
 };
@@ -588,7 +590,7 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
     __shared__ df sbuf[kSWarps][kSSocBig];
     __shared__ df red[kSWarps][3];
     __shared__ int s_last;
-    const int si = a.s0 + (int)blockIdx.y;
+    const int si = a.slist[blockIdx.y];
     const int status = a.state[si].status;
     if (status == S_DONE) return;
     // the pass's per-CTA constants live in shared memory, not in registers
@@ -661,7 +663,7 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
             t1 = df_add(t1, red[w][1]);
             t2 = df_add(t2, red[w][2]);
         }
-        float4* o = a.cpart + 2 * ((int64_t)si * a.gx + blockIdx.x);
+        float4* o = a.cpart + 2 * ((int64_t)si * a.gstride + blockIdx.x);
         o[0] = make_float4(t0.x, t0.y, t1.x, t1.y);
         o[1] = make_float4(t2.x, t2.y, 0.f, 0.f);
         s_last = arrive_acq_rel(a.ccnt + si) == a.gx - 1;
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
     // and warps in a fixed order; thread 0 finishes
     v0 = v1 = v2 = df_zero();
     for (int i = threadIdx.x; i < a.gx; i += kSThreads) {
-        const float4* o = a.cpart + 2 * ((int64_t)si * a.gx + i);
+        const float4* o = a.cpart + 2 * ((int64_t)si * a.gstride + i);
         const float4 p0 = __ldcg(o), p1 = __ldcg(o + 1);
         v0 = df_add(v0, make_float2(p0.x, p0.y));
         v1 = df_add(v1, make_float2(p0.z, p0.w));
@@ -708,6 +710,21 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
         a.ccnt[si] = 0;
         stream_finish<PASS, ROLE, SC>(a, si, pr, Part{df_to(t0), df_to(t1), df_to(t2), 0.0}, only_x);
     }
+}
+
+// The systems of [s0, s0 + ns) still iterating (status other than
+// S_DONE), in order, into slist; their number into *count.  One warp.
+__global__ void k_stream_compact(const LsqrState* state, int s0, int ns, int32_t* slist, int32_t* count) {
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    for (int i0 = 0; i0 < ns; i0 += 32) {
+        const int i = i0 + lane;
+        const bool live = i < ns && state[s0 + i].status != S_DONE;
+        const unsigned m = __ballot_sync(0xffffffffu, live);
+        if (live) slist[base + __popc(m & ((1u << lane) - 1u))] = s0 + i;
+        base += __popc(m);
+    }
+    if (lane == 0) *count = base;
 }
 
 // ---- entering and leaving the engine (per call and continuation round)
