@@ -80,19 +80,29 @@ def workload(name, rank):
     raise SystemExit(f"unknown workload {name}")
 
 
-def algorithmic_bytes_per_pass(prob):
+def algorithmic_bytes_split(prob):
     """Bytes one product with F or F^T must move (FP64 values 8 B, indices
-    4 B): half of B_iter = 2 [12 (2 nnz(A) + nnz_up(P)) + 4 (m + 2n + 3)]
-    + 8 (8n + 14m + 9N), the per-iteration traffic of one F and one F^T
-    product plus the LSQR vector updates."""
+    4 B), as (matrix, vectors): half of B_iter = 2 [12 (2 nnz(A) + nnz_up(P))
+    + 4 (m + 2n + 3)] + 8 (8n + 14m + 9N), the per-iteration traffic of one F
+    and one F^T product (the matrix part) plus the LSQR vector updates (the
+    vector part).  Two systems whose passes share a launch's read of the
+    matrix (paired stream iterations) move the matrix part once."""
     n, m, N = prob.n, prob.m, prob.N
-    b_iter = 2 * (12 * (2 * prob.A.nnz + prob.P.nnz) + 4 * (m + 2 * n + 3)) + 8 * (8 * n + 14 * m + 9 * N)
-    return b_iter / 2.0
+    mat = 12 * (2 * prob.A.nnz + prob.P.nnz) + 4 * (m + 2 * n + 3)
+    vec = 8 * (8 * n + 14 * m + 9 * N) / 2.0
+    return float(mat), vec
+
+
+def algorithmic_bytes_per_pass(prob):
+    mat, vec = algorithmic_bytes_split(prob)
+    return mat + vec
 
 
 # the dominant kernel of each engine and the sources it is built from
 KERNELS = {
     "stream": ("k_stream", ("qcpd_stream.cuh", "qcpd_df64.cuh", "qcpd_kernels.cuh", "qcpd_common.cuh")),
+    # the stream engine's paired launches (a JVP and a VJP system in step)
+    "stream_pair": ("k_stream2", ("qcpd_stream.cuh", "qcpd_df64.cuh", "qcpd_kernels.cuh", "qcpd_common.cuh")),
     "passes": ("k_pass", ("qcpd_kernels.cuh", "qcpd_common.cuh")),
     "persistent": ("k_persist", ("qcpd_kernels.cuh", "qcpd_common.cuh")),
     "cluster": ("k_cluster_df", ("qcpd_cluster_df.cuh", "qcpd_cluster.cuh", "qcpd_df64.cuh", "qcpd_kernels.cuh",
@@ -555,6 +565,7 @@ def main():
     pass_ms = [0.0]
     passes = [0]
     sys_passes = [0]  # sum over systems of the passes each ran (2 per LSQR iteration)
+    shared = [0]  # system passes that shared a launch's read of M with another system's
     infos = []
 
     def account(info):
@@ -563,6 +574,7 @@ def main():
         pass_ms[0] += ms
         passes[0] += n_
         sys_passes[0] += sum(2 * i["iters"] for i in info)
+        shared[0] += plan.last_shared_passes()
 
     def step(inputs):
         if args.call == "pair":
@@ -584,7 +596,7 @@ def main():
     torch.cuda.synchronize(dev)
 
     # ---- device-resident timed region (L2 flushed before every step)
-    launches[0], pass_ms[0], passes[0], sys_passes[0] = 0, 0.0, 0, 0
+    launches[0], pass_ms[0], passes[0], sys_passes[0], shared[0] = 0, 0.0, 0, 0, 0
     infos.clear()
     sampler = ClockSampler(local)
     if dist is not None:
@@ -607,7 +619,7 @@ def main():
     if dist is not None:
         dist.barrier()
     dev_launches = launches[0]
-    dev_pass_ms, dev_passes, dev_sys_passes = pass_ms[0], passes[0], sys_passes[0]
+    dev_pass_ms, dev_passes, dev_sys_passes, dev_shared = pass_ms[0], passes[0], sys_passes[0], shared[0]
     statuses = sorted({i["status"] for pair in infos for grp in pair for i in grp})
     max_res = max(i["rel_residual"] for pair in infos for grp in pair for i in grp)
 
@@ -653,13 +665,16 @@ def main():
     peak_note = "measured" if peak else "fallback"
     peak = peak or 6800.0
     engine = plan.last_engine()
-    kname = KERNELS[engine][0]
+    kkey = "stream_pair" if engine == "stream" and dev_shared > 0 else engine
+    kname = KERNELS[kkey][0]
     # algorithmic bytes of every pass every system ran, over the device time
     # of the iteration launches
-    bsys = algorithmic_bytes_per_pass(prob)
-    achieved = bsys * dev_sys_passes / (dev_pass_ms / 1e3) / 1e9
+    bmat, bvec = algorithmic_bytes_split(prob)
+    bsys = bmat + bvec
+    alg_bytes = bsys * dev_sys_passes - bmat * dev_shared
+    achieved = alg_bytes / (dev_pass_ms / 1e3) / 1e9
     avg_pass_s = (dev_pass_ms / 1e3) / max(dev_passes, 1)
-    traffic = recorded_traffic(engine, args.workload)
+    traffic = recorded_traffic(kkey, args.workload)
 
     if rank == 0:
         line = {
@@ -686,9 +701,11 @@ def main():
                          "peak_source": peak_note, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "traffic_per": "system pass (dram read + write bytes, ncu)",
                          "per": "algorithmic bytes of all passes of all systems (one pass = one product with F "
-                                "or F^T of one system) over the device time of the iteration launches; a "
-                                "cluster-engine launch runs every pass of its systems",
-                         "bytes_per_system_pass": bsys, "system_passes": dev_sys_passes,
+                                "or F^T of one system; a pass that shared its launch's read of M with another "
+                                "system's counts the vector part only) over the device time of the iteration "
+                                "launches; a cluster-engine launch runs every pass of its systems",
+                         "bytes_per_system_pass": bsys, "matrix_bytes_per_pass": bmat,
+                         "system_passes": dev_sys_passes, "shared_passes": dev_shared,
                          "avg_pass_us": avg_pass_s * 1e6, "passes": dev_passes},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -397,6 +397,18 @@ int qcp_plan_set_equilibration(qcp_plan* plan, int32_t sweeps);
    a negative value, hold_ns above 1e9). */
 int qcp_plan_set_barrier_wait(qcp_plan* plan, int64_t polls, int64_t hold_ns);
 
+/* Stream-engine scheduling of a call with one JVP range and one VJP range of
+   equal size on one problem (qcp_derivative_jvp_vjp_multi on a plan that is
+   not a batch plan); an addition, the paper solves the two systems
+   separately.  on = 1 (the default): the two ranges iterate in step, the
+   VJP systems one pass behind, so that every launch runs the same product
+   (with G, then with G^T) for JVP system i and VJP system i and reads M's
+   stored entries once for both.  on = 0: one range after the other.  Each
+   system takes the same sequence of passes either way, so the outputs
+   agree to rounding order (the CTA partial sums are grouped by the launch
+   shape).  Errors: QCP_ERR_ARG (null plan, on not 0 or 1). */
+int qcp_plan_set_stream_pairing(qcp_plan* plan, int32_t on);
+
 /* The qcp_engine the most recent JVP/VJP call of the plan ran: PASSES,
    PERSISTENT, CLUSTER (double-float vector arithmetic) or CLUSTER_FP64; -1
    for a NULL plan. */
@@ -446,6 +458,13 @@ int qcp_derivative_jvp_noalloc(qcp_plan* plan, const qcp_options* opts, const vo
    (products with F or F^T over all systems) they contain; their ratio is
    the average duration of one pass.  Errors: QCP_ERR_ARG (null plan). */
 int qcp_plan_last_timing(const qcp_plan* plan, double* pass_ms, int64_t* passes);
+
+/* The system passes of the plan's most recent call that shared their read
+   of M with another system's pass in the same launch (paired stream
+   iterations, qcp_plan_set_stream_pairing; 0 otherwise): one per launch in
+   which both systems of a pair ran a product.  Errors: QCP_ERR_ARG (null
+   plan or output). */
+int qcp_plan_last_shared_passes(const qcp_plan* plan, int64_t* shared);
 
 /* The embedding-space solution of the plan's most recent call: dz (JVP) or
    r (VJP; F^T r = -g_phi), N = n + m + 1 doubles per system of that call

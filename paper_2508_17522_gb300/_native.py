@@ -126,6 +126,10 @@ def lib():
     L.qcp_plan_set_equilibration.argtypes = [c_void_p, c_int32]
     L.qcp_plan_set_barrier_wait.restype = ctypes.c_int
     L.qcp_plan_set_barrier_wait.argtypes = [c_void_p, c_int64, c_int64]
+    L.qcp_plan_set_stream_pairing.restype = ctypes.c_int
+    L.qcp_plan_set_stream_pairing.argtypes = [c_void_p, ctypes.c_int32]
+    L.qcp_plan_last_shared_passes.restype = ctypes.c_int
+    L.qcp_plan_last_shared_passes.argtypes = [c_void_p, ctypes.POINTER(c_int64)]
     L.qcp_plan_last_launches.restype = c_int64
     L.qcp_plan_last_launches.argtypes = [c_void_p]
     L.qcp_plan_last_timing.restype = ctypes.c_int

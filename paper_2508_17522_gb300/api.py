@@ -198,6 +198,13 @@ class Plan:
         _check(N.lib().qcp_plan_last_timing(self._h, ctypes.byref(ms), ctypes.byref(n)), "qcp_plan_last_timing")
         return ms.value, n.value
 
+    def last_shared_passes(self) -> int:
+        """System passes of the last call that shared a launch's read of M
+        (paired stream iterations; 0 otherwise)."""
+        n = ctypes.c_int64()
+        _check(N.lib().qcp_plan_last_shared_passes(self._h, ctypes.byref(n)), "qcp_plan_last_shared_passes")
+        return n.value
+
     def last_engine(self) -> str:
         """Engine of the last call: passes, persistent, cluster, cluster_fp64 or stream."""
         e = N.lib().qcp_plan_last_engine(self._h)
@@ -236,6 +243,12 @@ class Plan:
         a hold of CTA 0 before its first barrier (0: none; exercises the
         timeout path)."""
         _check(N.lib().qcp_plan_set_barrier_wait(self._h, int(polls), int(hold_ns)), "qcp_plan_set_barrier_wait")
+
+    def set_stream_pairing(self, on: bool = True):
+        """Stream engine: iterate a call's JVP and VJP ranges in step, one
+        read of M per launch for both (True, the default), or one range
+        after the other (False)."""
+        _check(N.lib().qcp_plan_set_stream_pairing(self._h, 1 if on else 0), "qcp_plan_set_stream_pairing")
 
     def set_schedule(self, tile_nnz: int = 4096, long_row: int = 512, long_chunk: int = 1 << 20):
         _check(N.lib().qcp_plan_set_schedule(self._h, int(tile_nnz), int(long_row), int(long_chunk)),

@@ -461,6 +461,7 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
     p->last_jvp_sys = segs[0].mode == 0 ? segs[0].s0 + segs[0].ns : 0;
     p->pass_ms = 0.0;
     p->pass_launches = 0;
+    p->shared_passes = 0;
     QCP_CUDA(cudaMemsetAsync(p->d_active.p, 0, kMaxSegments * sizeof(int), st));
     for (int gi = 0; gi < nseg; ++gi) {
         const Seg<T>& g = segs[gi];
@@ -502,6 +503,15 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
             return iterate_cluster<T>(p, cs, nc, nsys, v, opts);
         }
         if (engine == QCP_ENGINE_STREAM) {
+            // a JVP range and a VJP range of equal size on one problem: in step
+            if (p->stream_pairing && nseg == 2 && todo[0] && todo[1] && segs[0].mode != segs[1].mode &&
+                segs[0].ns == segs[1].ns) {
+                const int ja = segs[0].mode == 0 ? 0 : 1, vb = 1 - ja;
+                if (stream_can_pair(p, segs[ja].s0, segs[vb].s0, segs[ja].ns))
+                    return iterate_stream_pair(p, segs[ja].s0, segs[vb].s0, segs[ja].ns,
+                                               p->d_active.as<int>() + ja, p->d_active.as<int>() + vb,
+                                               v.scaled != 0, opts);
+            }
             for (int gi = 0; gi < nseg; ++gi)
                 if (todo[gi])
                     QCP_TRY(iterate_stream(p, segs[gi].mode, segs[gi].s0, segs[gi].ns, p->d_active.as<int>() + gi,
@@ -876,7 +886,7 @@ static int make_plan(int np, const qcp_problem* probs, const qcp_solution* sols,
         qcp_plan_destroy(p);
         return QCP_ERR_CUDA;
     }
-    if (cudaMallocHost(&p->h_active, sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost(&p->h_active, 2 * sizeof(int)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         qcp_plan_destroy(p);
         return QCP_ERR_ALLOC;
@@ -1214,6 +1224,24 @@ int qcp_plan_set_barrier_wait(qcp_plan* plan, int64_t polls, int64_t hold_ns) {
     }
     plan->barrier_polls = polls;
     plan->barrier_hold_ns = hold_ns;
+    return QCP_OK;
+}
+
+int qcp_plan_set_stream_pairing(qcp_plan* plan, int32_t on) {
+    if (!plan || (on != 0 && on != 1)) {
+        set_error("qcp_plan_set_stream_pairing: null plan or a value other than 0 and 1");
+        return QCP_ERR_ARG;
+    }
+    plan->stream_pairing = on;
+    return QCP_OK;
+}
+
+int qcp_plan_last_shared_passes(const qcp_plan* plan, int64_t* shared) {
+    if (!plan || !shared) {
+        set_error("qcp_plan_last_shared_passes: null plan or output");
+        return QCP_ERR_ARG;
+    }
+    *shared = plan->shared_passes;
     return QCP_OK;
 }
 

@@ -75,13 +75,15 @@ constexpr int kMaxSegments = 2;  // system ranges of one call (JVP systems, VJP 
 
 struct GraphKey {
     int engine;  // qcp_engine whose launches the graph holds
-    int mode;    // 0 JVP, 1 VJP
+    int mode;    // 0 JVP, 1 VJP, 2 a JVP range and a VJP range in step (stream engine)
     int tile0;   // first tile of the system range
     int nsys;
     int chunk;
     int scaled;  // qcp_precond of the view (different kernels and value arrays)
     int solver;  // 0 LSQR, 1 LSMR (a kernel parameter of the captured launches)
+    int pair = 0;  // paired stream launches: 1 + the first system of the VJP range (mode 2); else 0
     bool operator<(const GraphKey& o) const {
+        if (pair != o.pair) return pair < o.pair;
         if (engine != o.engine) return engine < o.engine;
         if (mode != o.mode) return mode < o.mode;
         if (tile0 != o.tile0) return tile0 < o.tile0;
@@ -122,12 +124,14 @@ struct StreamLayout {
     int nunits = 0;                  // over all problems
     int max_units = 0;               // most units of one problem
     int nsplit = 0, nslot = 0;       // split rows and their chunk slots (plan-wide)
-    int gmax = 0;                    // CTAs per system the workspace holds
+    int gmax = 0;                    // CTAs per system the workspace holds (all resident k_stream CTAs)
+    int gmax2 = 0;                   // resident k_stream2 CTAs (<= gmax)
     std::vector<int32_t> huoff, hsoff;
     DevBuf d_units, d_uoff, d_soff, d_rows, d_lblk, d_scol, d_val, d_valG, d_valT;
     DevBuf d_cA, d_cB, d_rw, d_cd, d_zy, d_soc;
     DevBuf d_scal, d_ssys, d_cpart, d_ccnt, d_lchunk, d_lcnt, d_lrow;
-    DevBuf d_slist, d_scount;        // the systems still iterating, their number
+    DevBuf d_slist, d_scount;        // the systems (or pairs) still iterating, their number
+    DevBuf d_pshared;                // paired launches: system passes that shared their read of M
 };
 
 }  // namespace qcpd
@@ -180,7 +184,7 @@ struct qcp_plan {
     int64_t barrier_polls = 0;    // persistent mode: polls per barrier wait (0: the default bound)
     int64_t barrier_hold_ns = 0;  // persistent mode: CTA 0's wait before its first barrier (a test hook)
     qcpd::DevBuf d_U, d_V, d_W, d_X, d_XI, d_RHS, d_HB;  // Krylov vectors (HB: LSMR's hbar)
-    int* h_active = nullptr;  // pinned
+    int* h_active = nullptr;  // pinned, two counters (a paired stream iteration reads both of its ranges')
 
     // cluster engine
     int cluster_cap = 0;  // CTAs per system asked for (0: per call from the number of systems)
@@ -208,6 +212,8 @@ struct qcp_plan {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double pass_ms = 0.0;
     int64_t pass_launches = 0;
+    int stream_pairing = 1;  // stream engine: iterate a JVP range and a VJP range in step
+    int64_t shared_passes = 0;  // of the last call: system passes that shared a launch's read of M
 
     ~qcp_plan();
 };

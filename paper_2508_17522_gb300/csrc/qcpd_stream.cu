@@ -343,6 +343,8 @@ static int build_stream(qcp_plan* p, StreamLayout* lay) {
     QCP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     QCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream<PASS_GT, ROLE_V, true>, kSThreads, 0));
     lay->gmax = std::max(1, nsm * std::max(occ, 1));
+    QCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream2<PASS_GT, true>, kSThreads, 0));
+    lay->gmax2 = std::max(1, std::min(lay->gmax, nsm * std::max(occ, 1)));
     const int64_t nsys = std::max(1, p->nsys_cap);
     const int64_t per = p->batched ? 1 : nsys;  // split-row storage: per system unless each system is a problem
     QCP_TRY(lay->d_scal.alloc(sizeof(StreamScal) * nsys));
@@ -357,6 +359,7 @@ static int build_stream(qcp_plan* p, StreamLayout* lay) {
     QCP_TRY(lay->d_lrow.alloc(sizeof(df) * 3 * per * std::max(1, lay->nsplit)));
     QCP_TRY(lay->d_slist.alloc(sizeof(int32_t) * nsys));
     QCP_TRY(lay->d_scount.alloc(sizeof(int32_t)));
+    QCP_TRY(lay->d_pshared.alloc(sizeof(unsigned long long)));
     int hbad = 1;
     QCP_CUDA(cudaMemcpyAsync(&hbad, b, sizeof(int), cudaMemcpyDeviceToHost, st));
     QCP_CUDA(cudaStreamSynchronize(st));
@@ -543,6 +546,196 @@ int iterate_stream(qcp_plan* p, int mode, int s0, int ns, int* active, bool scal
     k_stream_exit_state<<<ns, 32, 0, st>>>(a);
     QCP_CUDA(cudaGetLastError());
     p->last_launches += 2;
+    return QCP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Paired iterations: a JVP range and a VJP range of equal size on one
+// problem advance in step, the VJP systems one pass behind, so that every
+// launch runs one product for both systems of each pair (k_stream2).
+template <bool SC>
+static void launch_stream_pair_iter_sc(const StreamArgs& a, int npairs, cudaStream_t st) {
+    const dim3 grid((unsigned)a.gx, (unsigned)npairs);
+    k_stream2<PASS_G, SC><<<grid, kSThreads, 0, st>>>(a);
+    k_stream2<PASS_GT, SC><<<grid, kSThreads, 0, st>>>(a);
+}
+
+static void launch_stream_pair_iter(const StreamArgs& a, int npairs, bool scaled, cudaStream_t st) {
+    if (scaled) launch_stream_pair_iter_sc<true>(a, npairs, st);
+    else launch_stream_pair_iter_sc<false>(a, npairs, st);
+}
+
+static int run_stream_pair_chunk(qcp_plan* p, int sa0, int sb0, int npairs, const StreamArgs& a, bool scaled,
+                                 int chunk, bool use_graph) {
+    cudaStream_t st = p->stream;
+    if (!use_graph || chunk < 2) {
+        for (int c = 0; c < chunk; ++c) launch_stream_pair_iter(a, npairs, scaled, st);
+        QCP_CUDA(cudaGetLastError());
+        p->last_launches += 2 * chunk;
+        return QCP_OK;
+    }
+    GraphKey key{QCP_ENGINE_STREAM, 2, sa0, npairs, chunk, scaled ? 1 : 0, 0, 1 + sb0};
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        QCP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int c = 0; c < chunk; ++c) launch_stream_pair_iter(a, npairs, scaled, st);
+        const cudaError_t le = cudaGetLastError();
+        const cudaError_t ee = cudaStreamEndCapture(st, &g);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            set_error("graph capture failed: %s", cudaGetErrorString(le != cudaSuccess ? le : ee));
+            return QCP_ERR_CUDA;
+        }
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            set_error("graph instantiation failed: %s", cudaGetErrorString(ie));
+            return QCP_ERR_CUDA;
+        }
+        it = p->graphs.emplace(key, ge).first;
+    }
+    QCP_CUDA(cudaGraphLaunch(it->second, st));
+    p->last_launches += 2 * chunk;
+    return QCP_OK;
+}
+
+bool stream_can_pair(const qcp_plan* p, int sa0, int sb0, int ns) {
+    if (p->batched || ns <= 0) return false;
+    for (int i = 0; i < ns; ++i)
+        if (p->hsys[sa0 + i].prob != p->hsys[sb0 + i].prob) return false;
+    return true;
+}
+
+int iterate_stream_pair(qcp_plan* p, int sa0, int sb0, int ns, int* active_a, int* active_b, bool scaled,
+                        const qcp_options& opts) {
+    const StreamLayout* lay = p->stream_lay.get();
+    if (!lay || !lay->ok) {
+        set_error("stream engine: the plan's layout is not usable");
+        return QCP_ERR_ARG;
+    }
+    StreamArgs a = stream_args(p, lay, scaled ? 1 : 0);
+    a.active = active_a;
+    a.active2 = active_b;
+    a.pshared = lay->d_pshared.as<unsigned long long>();
+    a.slist = lay->d_slist.as<int32_t>();
+    a.gstride = lay->gmax;
+    cudaStream_t st = p->stream;
+    int maxN = 1;
+    for (int i = 0; i < ns; ++i)
+        for (int s : {sa0 + i, sb0 + i}) {
+            const Prob& pr = p->hprob[p->hsys[s].prob];
+            maxN = std::max(maxN, pr.n + pr.m + 1);
+        }
+    const dim3 vgrid((unsigned)std::min(1024, (maxN + 255) / 256), (unsigned)ns);
+    a.s0 = sa0;
+    k_stream_enter_state<<<ns, 32, 0, st>>>(a, 1, scaled ? 1 : 0);  // JVP: the first u-pass is a G-pass
+    k_stream_enter_vec<<<vgrid, 256, 0, st>>>(a);
+    a.s0 = sb0;
+    k_stream_enter_state<<<ns, 32, 0, st>>>(a, 0, scaled ? 1 : 0);  // VJP: a G^T-pass
+    k_stream_enter_vec<<<vgrid, 256, 0, st>>>(a);
+    QCP_CUDA(cudaMemsetAsync(lay->d_pshared.p, 0, sizeof(unsigned long long), st));
+    QCP_CUDA(cudaGetLastError());
+    p->last_launches += 4;
+    auto sync_read = [&](const void* src, int n) -> int {
+        QCP_CUDA(cudaMemcpyAsync(p->h_active, src, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+        QCP_CUDA(cudaStreamSynchronize(st));
+        return QCP_OK;
+    };
+    auto grid_x = [&](int nunits, int gmax) {
+        int gx = (gmax + nunits - 1) / nunits;
+        return std::max(1, std::min(gx, std::max(1, (lay->max_units + kSWarps - 1) / kSWarps)));
+    };
+    // the VJP systems' first u-pass, alone: afterwards both ranges need the
+    // same product at every launch
+    k_stream_compact<<<1, 32, 0, st>>>(p->d_state.as<LsqrState>(), sb0, ns, lay->d_slist.as<int32_t>(),
+                                       lay->d_scount.as<int32_t>());
+    QCP_CUDA(cudaGetLastError());
+    QCP_TRY(sync_read(lay->d_scount.p, 1));
+    p->last_launches += 1;
+    const int nb = p->h_active[0];
+    if (nb > 0) {
+        StreamArgs b = a;
+        b.active = active_b;
+        b.gx = grid_x(nb, lay->gmax);
+        QCP_CUDA(cudaEventRecord(p->ev0, st));
+        const dim3 grid((unsigned)b.gx, (unsigned)nb);
+        if (scaled) k_stream<PASS_GT, ROLE_U, true><<<grid, kSThreads, 0, st>>>(b);
+        else k_stream<PASS_GT, ROLE_U, false><<<grid, kSThreads, 0, st>>>(b);
+        QCP_CUDA(cudaGetLastError());
+        QCP_CUDA(cudaEventRecord(p->ev1, st));
+        QCP_CUDA(cudaEventSynchronize(p->ev1));
+        float ms = 0.0f;
+        QCP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->pass_ms += ms;
+        p->pass_launches += 1;
+        p->last_launches += 1;
+    }
+    auto compact = [&](int* npairs) -> int {
+        k_stream_compact2<<<1, 32, 0, st>>>(p->d_state.as<LsqrState>(), sa0, sb0, ns, lay->d_slist.as<int32_t>(),
+                                            lay->d_scount.as<int32_t>());
+        QCP_CUDA(cudaGetLastError());
+        QCP_TRY(sync_read(lay->d_scount.p, 1));
+        *npairs = p->h_active[0];
+        p->last_launches += 1;
+        return QCP_OK;
+    };
+    int npairs = 0;
+    QCP_TRY(compact(&npairs));
+    // active_a and active_b are adjacent counters (one per range of the call)
+    const bool adjacent = active_b == active_a + 1;
+    int live_a = ns, live_b = ns;
+    int64_t done = 0;
+    const int64_t cap = opts.maxiter + 1;
+    while (done < cap && npairs > 0) {
+        a.gx = grid_x(npairs, lay->gmax2);
+        int64_t chunk = opts.check_every > 0 ? opts.check_every : cap;
+        chunk = std::min<int64_t>(chunk, cap - done);
+        const bool graph_ok = opts.use_graph && opts.check_every > 0 && chunk == opts.check_every;
+        QCP_CUDA(cudaEventRecord(p->ev0, st));
+        QCP_TRY(run_stream_pair_chunk(p, sa0, sb0, npairs, a, scaled, (int)chunk, graph_ok));
+        QCP_CUDA(cudaEventRecord(p->ev1, st));
+        done += chunk;
+        p->pass_launches += 2 * chunk;
+        int still_a = 0, still_b = 0;
+        if (opts.check_every > 0) {
+            if (adjacent) {
+                QCP_TRY(sync_read(active_a, 2));
+                still_a = p->h_active[0];
+                still_b = p->h_active[1];
+            } else {
+                QCP_TRY(sync_read(active_a, 1));
+                still_a = p->h_active[0];
+                QCP_TRY(sync_read(active_b, 1));
+                still_b = p->h_active[0];
+            }
+        } else {
+            QCP_CUDA(cudaEventSynchronize(p->ev1));
+        }
+        float ms = 0.0f;
+        QCP_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->pass_ms += ms;
+        if (opts.check_every > 0) {
+            if (still_a <= 0 && still_b <= 0) break;
+            if (still_a < live_a || still_b < live_b) QCP_TRY(compact(&npairs));
+            live_a = still_a;
+            live_b = still_b;
+        }
+    }
+    unsigned long long shared = 0;
+    QCP_CUDA(cudaMemcpyAsync(&shared, lay->d_pshared.p, sizeof(shared), cudaMemcpyDeviceToHost, st));
+    a.s0 = sa0;
+    k_stream_exit_vec<<<vgrid, 256, 0, st>>>(a);
+    k_stream_exit_state<<<ns, 32, 0, st>>>(a);
+    a.s0 = sb0;
+    k_stream_exit_vec<<<vgrid, 256, 0, st>>>(a);
+    k_stream_exit_state<<<ns, 32, 0, st>>>(a);
+    QCP_CUDA(cudaGetLastError());
+    QCP_CUDA(cudaStreamSynchronize(st));
+    p->shared_passes += (int64_t)shared;
+    p->last_launches += 4;
     return QCP_OK;
 }
 

@@ -45,6 +45,7 @@
 namespace qcpd {
 
 constexpr int kSThreads = 256;
+constexpr int kS2Ctas = 4;  // resident CTAs per SM of the paired kernel (its register budget)
 constexpr int kSWarps = kSThreads / 32;
 constexpr int kSSteps = 16;        // most entries of one lane in a slice (its chain of dependent loads)
 constexpr int kSLongChunk = 32 * kSSteps;  // rows with more entries are cut into SU_LONG units of this many
@@ -130,7 +131,9 @@ struct StreamArgs {
     int32_t s0;             // first system of the range (enter / exit kernels)
     const int32_t* slist;   // the pass kernels' systems: slist[blockIdx.y] (the range's systems still iterating)
     int32_t batched;
-    int* active;
+    int* active;            // running systems of the range (paired launches: of the JVP range)
+    int* active2;           // paired launches: running systems of the VJP range
+    unsigned long long* pshared;  // paired launches: system passes that shared their read of M
 };
 
 // ---------------------------------------------------------------------------
@@ -246,12 +249,113 @@ __device__ __forceinline__ df long_rowsum(const int32_t* scol, const df* val, co
     return warp_sum_df(dfacc_result(acc));
 }
 
+// Row sums of two systems over the same slots (a paired launch: the two
+// systems' passes share one read of M's columns and values; g and g2 are
+// their gathered vectors).  Each system's adds come in the order of
+// sell_rowsum / long_rowsum, so either sum equals the one-system result.
+__device__ __forceinline__ void sell_rowsum2(const int32_t* scol, const df* val, const df* g, const df* g2,
+                                             int64_t base, int width, df& h, df& h2) {
+    DfAcc acc = dfacc_zero(), acc2 = dfacc_zero();
+    if (width > 0) {
+        int32_t c[kSB];
+        df v[kSB];
+        sell_load(scol, val, base, 0, width, c, v);
+        for (int k = 0; k < width; k += kSB) {
+            df x[kSB], x2[kSB];
+#pragma unroll
+            for (int j = 0; j < kSB; ++j) {
+                const bool ok = k + j < width;
+                x[j] = ok ? dfl(g + c[j]) : df_zero();
+                x2[j] = ok ? dfl(g2 + c[j]) : df_zero();
+            }
+            int32_t cn[kSB];
+            df vn[kSB];
+            sell_load(scol, val, base, k + kSB, width, cn, vn);
+#pragma unroll
+            for (int j = 0; j < kSB; ++j) {
+                dfacc_fma(acc, v[j], x[j]);
+                dfacc_fma(acc2, v[j], x2[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < kSB; ++j) {
+                c[j] = cn[j];
+                v[j] = vn[j];
+            }
+        }
+    }
+    h = dfacc_result(acc);
+    h2 = dfacc_result(acc2);
+}
+
+__device__ __forceinline__ void long_rowsum2(const int32_t* scol, const df* val, const df* g, const df* g2,
+                                             int64_t base, int cnt, df& h, df& h2) {
+    const int lane = threadIdx.x & 31;
+    DfAcc acc = dfacc_zero(), acc2 = dfacc_zero();
+    int32_t c[kSB];
+    df v[kSB];
+    long_load(scol, val, base, lane, cnt, c, v);
+    for (int k = lane; k < cnt; k += 32 * kSB) {
+        df x[kSB], x2[kSB];
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) {
+            const bool ok = k + 32 * j < cnt;
+            x[j] = ok ? dfl(g + c[j]) : df_zero();
+            x2[j] = ok ? dfl(g2 + c[j]) : df_zero();
+        }
+        int32_t cn[kSB];
+        df vn[kSB];
+        long_load(scol, val, base, k + 32 * kSB, cnt, cn, vn);
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) {
+            dfacc_fma(acc, v[j], x[j]);
+            dfacc_fma(acc2, v[j], x2[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) {
+            c[j] = cn[j];
+            v[j] = vn[j];
+        }
+    }
+    h = warp_sum_df(dfacc_result(acc));
+    h2 = warp_sum_df(dfacc_result(acc2));
+}
+
 // ---- row epilogues (the formulas of run_tile in qcpd_kernels.cuh, in df64)
+// The vector entries of row r that a pass's update reads, loaded together
+// before the row's first store (the arrays are distinct, but the compiler
+// cannot know that and would reload them after each store).
+struct SRowV {
+    df in, out, w, x;
+};
+
+template <int ROLE>
+__device__ __forceinline__ SRowV row_vecs(const SCtx& c, int r) {
+    SRowV v;
+    v.in = c.IN[r];
+    v.out = c.OUT[r];
+    v.w = c.W[r];
+    v.x = ROLE == ROLE_V ? c.X[r] : df_zero();
+    return v;
+}
+
+// The u- or v-update of row r given its new product value o: out = c1 o -
+// c2 out, then w (u-update) or x (v-update); returns the new out.
+template <int ROLE>
+__device__ __forceinline__ df row_update(const SCtx& c, int r, df o, const SRowV& v, SAcc& acc) {
+    const df nv = df_fma(c.sc.c1, o, df_mul(c.sc.nc2, v.out));
+    c.OUT[r] = nv;
+    dfacc_fma(acc.ss, nv, nv);
+    if (ROLE == ROLE_U) c.W[r] = df_fma(v.in, c.sc.c1, df_mul(c.sc.nw, v.w));
+    else c.X[r] = df_fma(c.sc.xc, v.w, v.x);
+    return nv;
+}
+
 // G-pass, row r with row sum h: out = W (M_top xi + q t | M_bot xi - b t - c + D c) C,
 // then the u- or v-update of that row.
 template <int ROLE, bool SC>
 __device__ __forceinline__ void g_row(const SCtx& c, int r, df h, SAcc& acc) {
-    const df iv = c.IN[r];
+    const SRowV v = row_vecs<ROLE>(c, r);
+    const df iv = v.in;
     df o;
     if (r < c.n) {
         o = df_fma(dfl(c.cA + r), c.sc.tt, h);
@@ -263,18 +367,13 @@ __device__ __forceinline__ void g_row(const SCtx& c, int r, df h, SAcc& acc) {
         dfacc_fma(acc.dbot, dfl(c.cB + r), SC ? df_mul(dfl(c.cd + r), xi) : xi);
     }
     if (SC) o = df_mul(o, dfl(c.rw + r));
-    const df nv = df_fma(c.sc.c1, o, df_mul(c.sc.nc2, c.OUT[r]));
-    c.OUT[r] = nv;
-    dfacc_fma(acc.ss, nv, nv);
-    if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c.sc.c1, df_mul(c.sc.nw, c.W[r]));
-    else c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
+    row_update<ROLE>(c, r, o, v, acc);
 }
 
-// G^T-pass, first half of row r: s1 = (M rho - g r3)_r on x-rows,
-// (M rho - b r3)_r + (w in)_r on y-rows; ivs = (w in)_r.
+// G^T-pass, first half of row r (iv = in_r): s1 = (M rho - g r3)_r on
+// x-rows, (M rho - b r3)_r + (w in)_r on y-rows; ivs = (w in)_r.
 template <bool SC>
-__device__ __forceinline__ df gt_pre(const SCtx& c, int r, df h, df& ivs, SAcc& acc) {
-    const df iv = c.IN[r];
+__device__ __forceinline__ df gt_pre(const SCtx& c, int r, df h, df iv, df& ivs, SAcc& acc) {
     ivs = SC ? df_mul(dfl(c.rw + r), iv) : iv;
     const df h1 = df_fma(df_neg(dfl(c.cB + r)), c.sc.tt, h);
     if (r < c.n) {
@@ -288,15 +387,10 @@ __device__ __forceinline__ df gt_pre(const SCtx& c, int r, df h, df& ivs, SAcc& 
 // G^T-pass, second half of row r given s2 = (D s1)_r: the u- or v-update;
 // returns the new out_r (whose D Pi the caller stores in XI).
 template <int ROLE, bool SC>
-__device__ __forceinline__ df gt_post(const SCtx& c, int r, df s2, df ivs, SAcc& acc) {
+__device__ __forceinline__ df gt_post(const SCtx& c, int r, df s2, df ivs, const SRowV& v, SAcc& acc) {
     df o = (r < c.n) ? s2 : df_sub(s2, ivs);
     if (SC) o = df_mul(o, dfl(c.cd + r));
-    const df nv = df_fma(c.sc.c1, o, df_mul(c.sc.nc2, c.OUT[r]));
-    c.OUT[r] = nv;
-    dfacc_fma(acc.ss, nv, nv);
-    if (ROLE == ROLE_U) c.W[r] = df_fma(c.IN[r], c.sc.c1, df_mul(c.sc.nw, c.W[r]));
-    else c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
-    return nv;
+    return row_update<ROLE>(c, r, o, v, acc);
 }
 
 // D on a row outside second-order-cone blocks: 1 on x-rows and zero-cone
@@ -309,9 +403,10 @@ __device__ __forceinline__ df d_diag(const SCtx& c, int r, df v) {
 // One non-coupled row of a G^T-pass (x-rows, zero-cone and R+ rows).
 template <int ROLE, bool SC>
 __device__ __forceinline__ void gt_row(const SCtx& c, int r, df h, SAcc& acc) {
+    const SRowV v = row_vecs<ROLE>(c, r);
     df ivs;
-    const df s1 = gt_pre<SC>(c, r, h, ivs, acc);
-    const df nv = gt_post<ROLE, SC>(c, r, d_diag(c, r, s1), ivs, acc);
+    const df s1 = gt_pre<SC>(c, r, h, v.in, ivs, acc);
+    const df nv = gt_post<ROLE, SC>(c, r, d_diag(c, r, s1), ivs, v, acc);
     c.XI[r] = d_diag(c, r, nv);
 }
 
@@ -372,13 +467,13 @@ struct SUnitCtx {
     const df* val;
 };
 
-// SU_SLICE units (either pass) and SU_SOCP units of a G-pass: row i of the
-// unit on lanes [G i, G i + G) (SU_SOCP: G = 1), no coupling.
+// SU_SLICE units (either pass) and SU_SOCP units of a G-pass, given each
+// lane's row sum h: row i of the unit on lanes [G i, G i + G) (SU_SOCP:
+// G = 1), no coupling.
 template <int PASS, int ROLE, bool SC>
-__device__ __forceinline__ void unit_slice(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, SAcc& acc) {
+__device__ __forceinline__ void slice_rows(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, df h, SAcc& acc) {
     const int lane = threadIdx.x & 31;
     const int G = u.kind == SU_SLICE ? u.chunk : 1;
-    df h = sell_rowsum(k.scol, k.val, c.gin, u.base, u.width);
     for (int o = G >> 1; o > 0; o >>= 1) h = df_add(h, shfl_xor_df(h, o));
     if ((lane & (G - 1)) != 0) return;
     const int r = k.rows[u.aux + lane / G];
@@ -399,13 +494,13 @@ __device__ __forceinline__ void unit_socb_g(const SCtx& c, const SUnitCtx& k, co
     }
 }
 
-// SU_SOCP units of a G^T-pass.
+// SU_SOCP units of a G^T-pass, given each lane's row sum h.
 template <int ROLE, bool SC>
-__device__ __forceinline__ void unit_socp_gt(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, SAcc& acc) {
+__device__ __forceinline__ void socp_gt_rows(const SCtx& c, const SUnitCtx& k, const StreamUnit& u, df h,
+                                             SAcc& acc) {
     const int lane = threadIdx.x & 31;
     const int r = k.rows[u.aux + lane];
     const int bi = k.lblk[u.aux + lane];
-    const df h = sell_rowsum(k.scol, k.val, c.gin, u.base, u.width);
     int head = lane, end = lane, kase = 1, pos = 0;
     StreamSoc B{};
     if (bi >= 0) {
@@ -415,14 +510,16 @@ __device__ __forceinline__ void unit_socp_gt(const SCtx& c, const SUnitCtx& k, c
         end = head + B.dim - 1;
         kase = B.kase;
     }
+    SRowV v{};
     df ivs = df_zero(), s1 = df_zero(), uk = df_zero();
     if (r >= 0) {
-        s1 = gt_pre<SC>(c, r, h, ivs, acc);
+        v = row_vecs<ROLE>(c, r);
+        s1 = gt_pre<SC>(c, r, h, v.in, ivs, acc);
         uk = dfl(c.zy + r);
     }
     const df s2 = socp_d(s1, uk, pos, head, end, kase, B);
     df nv = df_zero();
-    if (r >= 0) nv = gt_post<ROLE, SC>(c, r, s2, ivs, acc);
+    if (r >= 0) nv = gt_post<ROLE, SC>(c, r, s2, ivs, v, acc);
     const df xi = socp_d(nv, uk, pos, head, end, kase, B);
     if (r >= 0) c.XI[r] = xi;
 }
@@ -444,7 +541,7 @@ __device__ __forceinline__ void unit_socb_gt(const SCtx& c, const SUnitCtx& k, c
         const int i = 32 * j + lane;
         if (i < dim) {
             df ivs;
-            const df s1 = gt_pre<SC>(c, r0 + i, h, ivs, acc);
+            const df s1 = gt_pre<SC>(c, r0 + i, h, c.IN[r0 + i], ivs, acc);
             sb[i] = s1;
             if (i > 0 && B.kase == 2) part = df_fma(dfl(c.zy + r0 + i), s1, part);
         }
@@ -457,9 +554,9 @@ __device__ __forceinline__ void unit_socb_gt(const SCtx& c, const SUnitCtx& k, c
     for (int i = lane; i < dim; i += 32) {
         const int r = r0 + i;
         const df uk = dfl(c.zy + r);
-        const df iv = c.IN[r];
-        const df ivs = SC ? df_mul(dfl(c.rw + r), iv) : iv;
-        const df nv = gt_post<ROLE, SC>(c, r, soc_d(sb[i], uk, i, ct, dot, B.kase, B), ivs, acc);
+        const SRowV v = row_vecs<ROLE>(c, r);
+        const df ivs = SC ? df_mul(dfl(c.rw + r), v.in) : v.in;
+        const df nv = gt_post<ROLE, SC>(c, r, soc_d(sb[i], uk, i, ct, dot, B.kase, B), ivs, v, acc);
         sb[i] = nv;
         if (i > 0 && B.kase == 2) part = df_fma(uk, nv, part);
     }
@@ -480,17 +577,16 @@ __device__ __forceinline__ int arrive_acq_rel(int* cnt) {
     return prev;
 }
 
-// SU_LONG units: a chunk of one long row (never inside a coupled block).  A
-// row in one chunk is finished by lane 0; a split row's chunk sums go to
+// SU_LONG units, given the chunk's sum h: a chunk of one long row (never
+// inside a coupled block).  A row in one chunk is finished by lane 0; a split row's chunk sums go to
 // its slots, and the chunk that completes the row adds them in order and
 // runs the epilogue, whose contributions to the pass's sums go to the row's
 // own slot (added by the finisher in row order, so the result does not
 // depend on which chunk came last).
 template <int PASS, int ROLE, bool SC>
-__device__ __forceinline__ void unit_long(const SCtx& c, const SUnitCtx& k, const StreamArgs& a, int si,
-                                          const StreamUnit& u, SAcc& acc) {
+__device__ __forceinline__ void long_rows(const SCtx& c, const StreamArgs& a, int si, const StreamUnit& u, df h,
+                                          SAcc& acc) {
     const int lane = threadIdx.x & 31;
-    const df h = long_rowsum(k.scol, k.val, c.gin, u.base, u.width);
     const int r = u.aux;
     if (u.blk < 0) {
         if (lane == 0) plain_row<PASS, ROLE, SC>(c, r, h, acc);
@@ -527,7 +623,8 @@ __device__ __forceinline__ void unit_long(const SCtx& c, const SUnitCtx& k, cons
 // The system's finisher (one thread): the tau entry of the pass's output and
 // the LSQR scalars, in FP64 as in run_tile, then the next pass's scalars.
 template <int PASS, int ROLE, bool SC>
-__device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only_x) {
+__device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only_x,
+                                              int* active) {
     LsqrState* st = a.state + si;
     double* tau = a.ssys[si].tau;
     const int rN = pr.n + pr.m;
@@ -535,7 +632,7 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
     if (only_x) {
         tau[TS_X] = fma(st->xcoef, tau[TS_W], tau[TS_X]);
         st->status = S_DONE;
-        atomicSub(a.active, 1);
+        atomicSub(active, 1);
         return;
     }
     const double c1 = ROLE == ROLE_U ? st->uc1 : st->vc1;
@@ -564,7 +661,7 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
         lsqr_step_u(st, nrm, inv, nsq);
     } else {
         tau[TS_X] = fma(xcoef, tw, tx);
-        if (lsqr_step_v(st, nrm, inv)) atomicSub(a.active, 1);
+        if (lsqr_step_v(st, nrm, inv)) atomicSub(active, 1);
     }
     // the next pass: the other product, the other update
     constexpr int NPASS = PASS == PASS_G ? PASS_GT : PASS_G;
@@ -583,98 +680,130 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
 }
 
 
-// One pass of the systems [s0, s0 + gridDim.y): PASS_G or PASS_GT, ROLE_U or
-// ROLE_V (the product and update of run_tile), SC = diagonal scaling.
+// ---------------------------------------------------------------------------
+// The pieces of a pass.  The per-CTA constants live in shared memory, not in
+// registers; thread 0 fills them.
+template <int PASS, int ROLE>
+__device__ __forceinline__ void stream_ctx(const StreamArgs& a, const Sys& sy, const Prob& pr, int si, SCtx& c) {
+    c.sc = a.scal[si];
+    c.n = pr.n;
+    c.N = pr.n + pr.m + 1;
+    c.cA = a.cA + pr.doff;
+    c.cB = a.cB + pr.doff;
+    c.rw = a.rw + pr.doff;
+    c.cd = a.cd + pr.doff;
+    c.zy = a.zy + pr.doff;
+    c.flag = a.flag + pr.doff;
+    c.soc = a.soc + pr.soff;
+    c.IN = (ROLE == ROLE_U ? a.V : a.U) + sy.voff;
+    c.OUT = (ROLE == ROLE_U ? a.U : a.V) + sy.voff;
+    c.W = a.W + sy.voff;
+    c.X = a.X + sy.voff;
+    c.XI = a.XI + sy.voff;
+    c.gin = PASS == PASS_G ? c.XI : c.IN;
+}
+
+// The units of one system in snake order (sorted by cost, largest first).
 template <int PASS, int ROLE, bool SC>
-__global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
-    __shared__ df sbuf[kSWarps][kSSocBig];
-    __shared__ df red[kSWarps][3];
-    __shared__ int s_last;
-    const int si = a.slist[blockIdx.y];
-    const int status = a.state[si].status;
-    if (status == S_DONE) return;
-    // the pass's per-CTA constants live in shared memory, not in registers
-    __shared__ SCtx s_ctx;
-    const Sys sy = a.sys[si];
-    const Prob pr = a.probs[sy.prob];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        SCtx& c = s_ctx;
-        c.sc = a.scal[si];
-        c.n = pr.n;
-        c.N = pr.n + pr.m + 1;
-        c.cA = a.cA + pr.doff;
-        c.cB = a.cB + pr.doff;
-        c.rw = a.rw + pr.doff;
-        c.cd = a.cd + pr.doff;
-        c.zy = a.zy + pr.doff;
-        c.flag = a.flag + pr.doff;
-        c.soc = a.soc + pr.soff;
-        c.IN = (ROLE == ROLE_U ? a.V : a.U) + sy.voff;
-        c.OUT = (ROLE == ROLE_U ? a.U : a.V) + sy.voff;
-        c.W = a.W + sy.voff;
-        c.X = a.X + sy.voff;
-        c.XI = a.XI + sy.voff;
-        c.gin = PASS == PASS_G ? c.XI : c.IN;
+__device__ __forceinline__ void stream_units(const StreamArgs& a, int si, int prob, const SCtx& c, df* sb,
+                                             SAcc& acc) {
+    const int warp = threadIdx.x >> 5;
+    const SUnitCtx k{a.rows, a.lblk, a.scol, PASS == PASS_G ? a.valG : a.valT};
+    const int wt = a.gx * kSWarps, wg = blockIdx.x * kSWarps + warp;
+    const int u0 = a.uoff[prob], nu = a.uoff[prob + 1] - u0;
+    for (int j = 0;; ++j) {
+        const int idx = j * wt + ((j & 1) ? wt - 1 - wg : wg);
+        if (idx >= nu) break;
+        const StreamUnit u = a.units[u0 + idx];
+        if (u.kind == SU_LONG) {
+            long_rows<PASS, ROLE, SC>(c, a, si, u, long_rowsum(k.scol, k.val, c.gin, u.base, u.width), acc);
+        } else if (u.kind == SU_SOCB) {
+            if (PASS == PASS_G) unit_socb_g<ROLE, SC>(c, k, u, acc);
+            else unit_socb_gt<ROLE, SC>(c, k, u, sb, acc);
+        } else {
+            const df h = sell_rowsum(k.scol, k.val, c.gin, u.base, u.width);
+            if (PASS == PASS_G || u.kind == SU_SLICE) slice_rows<PASS, ROLE, SC>(c, k, u, h, acc);
+            else socp_gt_rows<ROLE, SC>(c, k, u, h, acc);
+        }
     }
-    __syncthreads();
-    const SCtx& c = s_ctx;
-    SUnitCtx k{a.rows, a.lblk, a.scol, PASS == PASS_G ? a.valG : a.valT};
-    const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
-    SAcc acc;
-    sacc_zero(acc);
-    if (only_x) {  // the last x-update of a stopped system
-        for (int r = blockIdx.x * kSThreads + threadIdx.x; r < c.N - 1; r += a.gx * kSThreads)
-            c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
-    } else {
-        const int wt = a.gx * kSWarps, wg = blockIdx.x * kSWarps + warp;
-        const int u0 = a.uoff[sy.prob], nu = a.uoff[sy.prob + 1] - u0;
-        for (int j = 0;; ++j) {  // snake order over the units (sorted by cost, largest first)
-            const int idx = j * wt + ((j & 1) ? wt - 1 - wg : wg);
-            if (idx >= nu) break;
-            const StreamUnit u = a.units[u0 + idx];
-            if (u.kind == SU_LONG) {
-                unit_long<PASS, ROLE, SC>(c, k, a, si, u, acc);
-            } else if (PASS == PASS_G) {
-                if (u.kind == SU_SOCB) unit_socb_g<ROLE, SC>(c, k, u, acc);
-                else unit_slice<PASS, ROLE, SC>(c, k, u, acc);
+}
+
+// The units of two systems of one problem in one pass: A in role RA, B in
+// role RB; slices, packed blocks and chunks of long rows read their slots
+// once for both (SU_SOCB units, rare, run once per system).
+template <int PASS, int RA, int RB, bool SC>
+__device__ __forceinline__ void stream_units2(const StreamArgs& a, int sa, int sb2, int prob, const SCtx& ca,
+                                              const SCtx& cb, df* sb, SAcc& acca, SAcc& accb) {
+    const int warp = threadIdx.x >> 5;
+    const SUnitCtx k{a.rows, a.lblk, a.scol, PASS == PASS_G ? a.valG : a.valT};
+    const int wt = a.gx * kSWarps, wg = blockIdx.x * kSWarps + warp;
+    const int u0 = a.uoff[prob], nu = a.uoff[prob + 1] - u0;
+    for (int j = 0;; ++j) {
+        const int idx = j * wt + ((j & 1) ? wt - 1 - wg : wg);
+        if (idx >= nu) break;
+        const StreamUnit u = a.units[u0 + idx];
+        if (u.kind == SU_LONG) {
+            df h, h2;
+            long_rowsum2(k.scol, k.val, ca.gin, cb.gin, u.base, u.width, h, h2);
+            long_rows<PASS, RA, SC>(ca, a, sa, u, h, acca);
+            long_rows<PASS, RB, SC>(cb, a, sb2, u, h2, accb);
+        } else if (u.kind == SU_SOCB) {
+            if (PASS == PASS_G) {
+                unit_socb_g<RA, SC>(ca, k, u, acca);
+                unit_socb_g<RB, SC>(cb, k, u, accb);
             } else {
-                if (u.kind == SU_SLICE) unit_slice<PASS, ROLE, SC>(c, k, u, acc);
-                else if (u.kind == SU_SOCP) unit_socp_gt<ROLE, SC>(c, k, u, acc);
-                else unit_socb_gt<ROLE, SC>(c, k, u, sbuf[warp], acc);
+                unit_socb_gt<RA, SC>(ca, k, u, sb, acca);
+                unit_socb_gt<RB, SC>(cb, k, u, sb, accb);
+            }
+        } else {
+            df h, h2;
+            sell_rowsum2(k.scol, k.val, ca.gin, cb.gin, u.base, u.width, h, h2);
+            if (PASS == PASS_G || u.kind == SU_SLICE) {
+                slice_rows<PASS, RA, SC>(ca, k, u, h, acca);
+                slice_rows<PASS, RB, SC>(cb, k, u, h2, accb);
+            } else {
+                socp_gt_rows<RA, SC>(ca, k, u, h, acca);
+                socp_gt_rows<RB, SC>(cb, k, u, h2, accb);
             }
         }
     }
-    // the CTA's sums in a fixed order: lanes, then warps (df64 throughout;
-    // FP64 only for the three totals, in the finisher's thread)
-    df v0 = warp_sum_df(dfacc_result(acc.ss));
-    df v1 = warp_sum_df(dfacc_result(acc.dtop));
-    df v2 = warp_sum_df(dfacc_result(acc.dbot));
+}
+
+// The end of a system's pass, in pieces.  cta_partial: the CTA's sums in a
+// fixed order (lanes, then warps; df64 throughout) into the system's CTA
+// slot, then its arrival; true in the system's last CTA (one thread).
+__device__ __forceinline__ bool cta_partial(const StreamArgs& a, int si, df (*red)[3]) {
+    df t0 = red[0][0], t1 = red[0][1], t2 = red[0][2];
+    for (int w = 1; w < kSWarps; ++w) {
+        t0 = df_add(t0, red[w][0]);
+        t1 = df_add(t1, red[w][1]);
+        t2 = df_add(t2, red[w][2]);
+    }
+    float4* o = a.cpart + 2 * ((int64_t)si * a.gstride + blockIdx.x);
+    o[0] = make_float4(t0.x, t0.y, t1.x, t1.y);
+    o[1] = make_float4(t2.x, t2.y, 0.f, 0.f);
+    return arrive_acq_rel(a.ccnt + si) == a.gx - 1;
+}
+
+__device__ __forceinline__ void warp_sums_to(const SAcc& acc, df (*red)[3]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const df v0 = warp_sum_df(dfacc_result(acc.ss));
+    const df v1 = warp_sum_df(dfacc_result(acc.dtop));
+    const df v2 = warp_sum_df(dfacc_result(acc.dbot));
     if (lane == 0) {
         red[warp][0] = v0;
         red[warp][1] = v1;
         red[warp][2] = v2;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        df t0 = red[0][0], t1 = red[0][1], t2 = red[0][2];
-        for (int w = 1; w < kSWarps; ++w) {
-            t0 = df_add(t0, red[w][0]);
-            t1 = df_add(t1, red[w][1]);
-            t2 = df_add(t2, red[w][2]);
-        }
-        float4* o = a.cpart + 2 * ((int64_t)si * a.gstride + blockIdx.x);
-        o[0] = make_float4(t0.x, t0.y, t1.x, t1.y);
-        o[1] = make_float4(t2.x, t2.y, 0.f, 0.f);
-        s_last = arrive_acq_rel(a.ccnt + si) == a.gx - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    // the system's last CTA (thread 0 acquired every other CTA's partials;
-    // the barrier orders this CTA's reads after that): every thread adds a
-    // fixed share of the CTA partials and of the split rows' sums, then lanes
-    // and warps in a fixed order; thread 0 finishes
-    v0 = v1 = v2 = df_zero();
+}
+
+// In the system's last CTA (every thread; thread 0 of some warp acquired
+// every other CTA's partials and a barrier orders these reads after that):
+// a fixed share of the CTA partials and of the split rows' sums per thread,
+// then lanes, into red.
+__device__ __forceinline__ void last_partials(const StreamArgs& a, int si, int prob, bool only_x, df (*red)[3]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    df v0 = df_zero(), v1 = df_zero(), v2 = df_zero();
     for (int i = threadIdx.x; i < a.gx; i += kSThreads) {
         const float4* o = a.cpart + 2 * ((int64_t)si * a.gstride + i);
         const float4 p0 = __ldcg(o), p1 = __ldcg(o + 1);
@@ -684,7 +813,7 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
     }
     const int64_t sr = a.batched ? 0 : (int64_t)si * a.nsplit;
     if (!only_x) {
-        for (int i = a.soff[sy.prob] + threadIdx.x; i < a.soff[sy.prob + 1]; i += kSThreads) {
+        for (int i = a.soff[prob] + threadIdx.x; i < a.soff[prob + 1]; i += kSThreads) {
             const float2* o = reinterpret_cast<const float2*>(a.lrow + 3 * (sr + i));
             v0 = df_add(v0, __ldcg(o));
             v1 = df_add(v1, __ldcg(o + 1));
@@ -699,17 +828,138 @@ __global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
         red[warp][1] = v1;
         red[warp][2] = v2;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        df t0 = red[0][0], t1 = red[0][1], t2 = red[0][2];
-        for (int w = 1; w < kSWarps; ++w) {
-            t0 = df_add(t0, red[w][0]);
-            t1 = df_add(t1, red[w][1]);
-            t2 = df_add(t2, red[w][2]);
-        }
-        a.ccnt[si] = 0;
-        stream_finish<PASS, ROLE, SC>(a, si, pr, Part{df_to(t0), df_to(t1), df_to(t2), 0.0}, only_x);
+}
+
+// One thread of the system's last CTA: the warps' totals in order, then the
+// finisher.
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void last_finish(const StreamArgs& a, int si, const Prob& pr, bool only_x, int* active,
+                                            df (*red)[3], unsigned long long* shared) {
+    df t0 = red[0][0], t1 = red[0][1], t2 = red[0][2];
+    for (int w = 1; w < kSWarps; ++w) {
+        t0 = df_add(t0, red[w][0]);
+        t1 = df_add(t1, red[w][1]);
+        t2 = df_add(t2, red[w][2]);
     }
+    a.ccnt[si] = 0;
+    stream_finish<PASS, ROLE, SC>(a, si, pr, Part{df_to(t0), df_to(t1), df_to(t2), 0.0}, only_x, active);
+    if (shared) atomicAdd(shared, 1ull);
+}
+
+// The end of a system's pass in every CTA: its partials and arrival; the
+// system's last CTA adds every CTA's partials and the split rows' sums and
+// finishes (FP64 only for the three totals, in the finisher's thread).
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void stream_tail(const StreamArgs& a, int si, int prob, const Prob& pr, SAcc& acc,
+                                            bool only_x, int* active, df (*red)[3], int* s_last) {
+    __syncthreads();  // red and s_last may still be read by an earlier tail of this CTA
+    warp_sums_to(acc, red);
+    __syncthreads();
+    if (threadIdx.x == 0) *s_last = cta_partial(a, si, red);
+    __syncthreads();
+    if (!*s_last) return;
+    last_partials(a, si, prob, only_x, red);
+    __syncthreads();
+    if (threadIdx.x == 0) last_finish<PASS, ROLE, SC>(a, si, pr, only_x, active, red, nullptr);
+}
+
+// The same for the two systems of a paired launch: both arrivals first
+// (threads 0 and 32), then in a CTA that is last for either system the
+// partial sums of each such system, and the two finishers at once in two
+// warps.
+template <int PASS, int RA, int RB, bool SC>
+__device__ __forceinline__ void stream_tail2(const StreamArgs& a, int sa, int sb, int prob, const Prob& pr,
+                                             SAcc& acca, SAcc& accb, df (*red)[kSWarps][3], int* s_last) {
+    __syncthreads();
+    warp_sums_to(acca, red[0]);
+    warp_sums_to(accb, red[1]);
+    __syncthreads();
+    if (threadIdx.x == 0) s_last[0] = cta_partial(a, sa, red[0]);
+    if (threadIdx.x == 32) s_last[1] = cta_partial(a, sb, red[1]);
+    __syncthreads();
+    const bool la = s_last[0], lb = s_last[1];
+    if (!la && !lb) return;
+    if (la) last_partials(a, sa, prob, false, red[0]);
+    if (lb) last_partials(a, sb, prob, false, red[1]);
+    __syncthreads();
+    if (la && threadIdx.x == 0) last_finish<PASS, RA, SC>(a, sa, pr, false, a.active, red[0], a.pshared);
+    if (lb && threadIdx.x == 32) last_finish<PASS, RB, SC>(a, sb, pr, false, a.active2, red[1], nullptr);
+}
+
+// One system's whole pass (status: its LSQR status, read at launch).
+template <int PASS, int ROLE, bool SC>
+__device__ __forceinline__ void stream_pass(const StreamArgs& a, int si, int status, int* active, SCtx& s_ctx,
+                                            df* sb, df (*red)[3], int* s_last) {
+    const Sys sy = a.sys[si];
+    const Prob pr = a.probs[sy.prob];
+    __syncthreads();  // s_ctx may still be read by an earlier pass of this CTA
+    if (threadIdx.x == 0) stream_ctx<PASS, ROLE>(a, sy, pr, si, s_ctx);
+    __syncthreads();
+    const SCtx& c = s_ctx;
+    const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
+    SAcc acc;
+    sacc_zero(acc);
+    if (only_x) {  // the last x-update of a stopped system
+        for (int r = blockIdx.x * kSThreads + threadIdx.x; r < c.N - 1; r += a.gx * kSThreads)
+            c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
+    } else {
+        stream_units<PASS, ROLE, SC>(a, si, sy.prob, c, sb, acc);
+    }
+    stream_tail<PASS, ROLE, SC>(a, si, sy.prob, pr, acc, only_x, active, red, s_last);
+}
+
+// One pass of the systems a.slist[blockIdx.y]: PASS_G or PASS_GT, ROLE_U or
+// ROLE_V (the product and update of run_tile), SC = diagonal scaling.
+template <int PASS, int ROLE, bool SC>
+__global__ void __launch_bounds__(kSThreads, 4) k_stream(StreamArgs a) {
+    __shared__ df sbuf[kSWarps][kSSocBig];
+    __shared__ df red[kSWarps][3];
+    __shared__ int s_last;
+    __shared__ SCtx s_ctx;
+    const int si = a.slist[blockIdx.y];
+    const int status = a.state[si].status;
+    if (status == S_DONE) return;
+    stream_pass<PASS, ROLE, SC>(a, si, status, a.active, s_ctx, sbuf[threadIdx.x >> 5], red, &s_last);
+}
+
+// One pass of pairs of systems of one problem that iterate in step: a
+// JVP system (mode 0) a.slist[2 y] and a VJP system (mode 1) a.slist[2 y + 1]
+// whose own passes run one pass behind, so that both need the same product
+// now (PASS_G: the JVP's u-update and the VJP's v-update; PASS_GT: the JVP's
+// v-update and the VJP's next u-update) and read M once.  A pair with one
+// system stopped (or in its last x-update) runs the one-system pass for
+// each system still iterating.  The JVP systems count down a.active, the
+// VJP systems a.active2.
+template <int PASS, bool SC>
+__global__ void __launch_bounds__(kSThreads, kS2Ctas) k_stream2(StreamArgs a) {
+    constexpr int RA = PASS == PASS_G ? ROLE_U : ROLE_V;
+    constexpr int RB = PASS == PASS_G ? ROLE_V : ROLE_U;
+    __shared__ df sbuf[kSWarps][kSSocBig];
+    __shared__ df red[2][kSWarps][3];
+    __shared__ int s_last[2];
+    __shared__ SCtx s_ctx[2];
+    const int sa = a.slist[2 * blockIdx.y], sb = a.slist[2 * blockIdx.y + 1];
+    const int ta = a.state[sa].status, tb = a.state[sb].status;
+    const bool la = ta != S_DONE, lb = tb != S_DONE;
+    const bool xa = RA == ROLE_V && ta == S_FINAL, xb = RB == ROLE_V && tb == S_FINAL;
+    df* sbw = sbuf[threadIdx.x >> 5];
+    if (!(la && lb) || xa || xb) {
+        if (la) stream_pass<PASS, RA, SC>(a, sa, ta, a.active, s_ctx[0], sbw, red[0], &s_last[0]);
+        if (lb) stream_pass<PASS, RB, SC>(a, sb, tb, a.active2, s_ctx[1], sbw, red[0], &s_last[0]);
+        return;
+    }
+    const Sys sya = a.sys[sa], syb = a.sys[sb];
+    const Prob pr = a.probs[sya.prob];
+    if (threadIdx.x == 0) {
+        stream_ctx<PASS, RA>(a, sya, pr, sa, s_ctx[0]);
+        stream_ctx<PASS, RB>(a, syb, pr, sb, s_ctx[1]);
+    }
+    __syncthreads();
+    SAcc acca, accb;
+    sacc_zero(acca);
+    sacc_zero(accb);
+    stream_units2<PASS, RA, RB, SC>(a, sa, sb, sya.prob, s_ctx[0], s_ctx[1], sbw, acca, accb);
+    stream_tail2<PASS, RA, RB, SC>(a, sa, sb, sya.prob, pr, acca, accb, red, s_last);
 }
 
 // The systems of [s0, s0 + ns) still iterating (status other than
@@ -722,6 +972,26 @@ __global__ void k_stream_compact(const LsqrState* state, int s0, int ns, int32_t
         const bool live = i < ns && state[s0 + i].status != S_DONE;
         const unsigned m = __ballot_sync(0xffffffffu, live);
         if (live) slist[base + __popc(m & ((1u << lane) - 1u))] = s0 + i;
+        base += __popc(m);
+    }
+    if (lane == 0) *count = base;
+}
+
+// The pairs (sa0 + i, sb0 + i), i < ns, with a system still iterating, in
+// order, into slist (two entries a pair); their number into *count.  One warp.
+__global__ void k_stream_compact2(const LsqrState* state, int sa0, int sb0, int ns, int32_t* slist,
+                                  int32_t* count) {
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    for (int i0 = 0; i0 < ns; i0 += 32) {
+        const int i = i0 + lane;
+        const bool live = i < ns && (state[sa0 + i].status != S_DONE || state[sb0 + i].status != S_DONE);
+        const unsigned m = __ballot_sync(0xffffffffu, live);
+        if (live) {
+            const int o = 2 * (base + __popc(m & ((1u << lane) - 1u)));
+            slist[o] = sa0 + i;
+            slist[o + 1] = sb0 + i;
+        }
         base += __popc(m);
     }
     if (lane == 0) *count = base;

@@ -19,4 +19,18 @@ int stream_ready(qcp_plan* p, bool* ok);
 // the device time of the chunks to p->pass_ms.
 int iterate_stream(qcp_plan* p, int mode, int s0, int ns, int* active, bool scaled, const qcp_options& opts);
 
+// Whether the JVP range [sa0, sa0 + ns) and the VJP range [sb0, sb0 + ns)
+// can iterate in step: system sa0 + i and system sb0 + i on one problem (a
+// plan that is not a batch plan).
+bool stream_can_pair(const qcp_plan* p, int sa0, int sb0, int ns);
+
+// Runs the remaining LSQR iterations of the JVP range and the VJP range in
+// step: the VJP systems' first u-pass alone, then launches that each run one
+// product (with G, then with G^T) for both systems of every pair, reading
+// M's slots once for the two; each range's active counter at active_a /
+// active_b.  Adds the device time to p->pass_ms and the system passes that
+// shared a read of M to p->shared_passes.
+int iterate_stream_pair(qcp_plan* p, int sa0, int sb0, int ns, int* active_a, int* active_b, bool scaled,
+                        const qcp_options& opts);
+
 }  // namespace qcpd

@@ -74,6 +74,9 @@ def test_argument_errors_without_gpu(lib):
     assert lib.qcp_plan_set_equilibration(None, 3) == QCP_ERR_ARG
     assert lib.qcp_plan_set_schedule(None, 4096, 512, 1 << 20) == QCP_ERR_ARG
     assert lib.qcp_plan_set_barrier_wait(None, 16, 0) == QCP_ERR_ARG
+    assert lib.qcp_plan_set_stream_pairing(None, 1) == QCP_ERR_ARG
+    shared = ctypes.c_int64()
+    assert lib.qcp_plan_last_shared_passes(None, ctypes.byref(shared)) == QCP_ERR_ARG
     cnt = ctypes.c_int32()
     assert lib.qcp_plan_autotune(None, ctypes.byref(o), 0, 1, 16, None, 0, ctypes.byref(cnt), None) == QCP_ERR_ARG
     out = ctypes.c_void_p()
