@@ -325,7 +325,8 @@ __device__ __forceinline__ int tile_rowsums(const Tile& tl, int ti, const int64_
 // The LSQR scalar recurrences (Paige & Saunders 1982) after a u-update with
 // ||u_{k+1}|| = nrm (inv_nrm = 1/nrm, 0 when nrm = 0): the plane rotation
 // eliminating beta_{k+1}, the coefficients of the next v-update and
-// x-update, and the stopping tests.  S is LsqrState or volatile LsqrState.
+// x-update, and the stopping tests.  S is LsqrState, volatile LsqrState or a
+// register copy of the fields used here (the stream engine's LsqrHot).
 // One thread runs this and every FP64 instruction here costs a full
 // warp-wide issue, so the square root and the reciprocal of the rotation
 // share one rsqrt_fast.

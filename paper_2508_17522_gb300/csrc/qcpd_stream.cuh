@@ -620,18 +620,77 @@ __device__ __forceinline__ void long_rows(const SCtx& c, const StreamArgs& a, in
 }
 
 // ---------------------------------------------------------------------------
+// The LSQR fields the finisher reads and writes, copied into registers with
+// one batch of loads and written back at the end: on the state in global
+// memory every read after a write would wait for its own round trip (the
+// compiler cannot tell the fields and the tau entries apart).
+struct LsqrHot {
+    double alpha, beta, rhobar, phibar, inv_rho, uc1, uc2, vc1, vc2, wcoef, xcoef, c, s, bnorm, rtol;
+    int64_t iters, maxiter;
+    int32_t status, outcome, first;
+};
+
+__device__ __forceinline__ void hot_load(LsqrHot& h, const LsqrState* st) {
+    h.alpha = st->alpha;
+    h.beta = st->beta;
+    h.rhobar = st->rhobar;
+    h.phibar = st->phibar;
+    h.inv_rho = st->inv_rho;
+    h.uc1 = st->uc1;
+    h.uc2 = st->uc2;
+    h.vc1 = st->vc1;
+    h.vc2 = st->vc2;
+    h.wcoef = st->wcoef;
+    h.xcoef = st->xcoef;
+    h.c = st->c;
+    h.s = st->s;
+    h.bnorm = st->bnorm;
+    h.rtol = st->rtol;
+    h.iters = st->iters;
+    h.maxiter = st->maxiter;
+    h.status = st->status;
+    h.outcome = st->outcome;
+    h.first = st->first;
+}
+
+__device__ __forceinline__ void hot_store(LsqrState* st, const LsqrHot& h) {
+    st->alpha = h.alpha;
+    st->beta = h.beta;
+    st->rhobar = h.rhobar;
+    st->phibar = h.phibar;
+    st->inv_rho = h.inv_rho;
+    st->uc1 = h.uc1;
+    st->uc2 = h.uc2;
+    st->vc1 = h.vc1;
+    st->vc2 = h.vc2;
+    st->wcoef = h.wcoef;
+    st->xcoef = h.xcoef;
+    st->c = h.c;
+    st->s = h.s;
+    st->iters = h.iters;
+    st->status = h.status;
+    st->outcome = h.outcome;
+    st->first = h.first;
+}
+
 // The system's finisher (one thread): the tau entry of the pass's output and
 // the LSQR scalars, in FP64 as in run_tile, then the next pass's scalars.
 template <int PASS, int ROLE, bool SC>
 __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only_x,
                                               int* active) {
-    LsqrState* st = a.state + si;
-    double* tau = a.ssys[si].tau;
+    LsqrState* gst = a.state + si;
+    double* gtau = a.ssys[si].tau;
     const int rN = pr.n + pr.m;
     const double rwN = a.rwd[pr.doff + rN], cdN = a.cdd[pr.doff + rN];
+    double tau[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tau[i] = gtau[i];
+    LsqrHot h;
+    hot_load(h, gst);
+    LsqrHot* st = &h;
     if (only_x) {
-        tau[TS_X] = fma(st->xcoef, tau[TS_W], tau[TS_X]);
-        st->status = S_DONE;
+        gtau[TS_X] = fma(st->xcoef, tau[TS_W], tau[TS_X]);
+        gst->status = S_DONE;
         atomicSub(active, 1);
         return;
     }
@@ -656,12 +715,13 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
     const double nsq = fma(nvN, nvN, tot.a);
     double nrm, inv;
     norm_and_inverse(nsq, nrm, inv);
+    bool stopped = false;
     if (ROLE == ROLE_U) {
         tau[TS_W] = tin * c1 - wcoef * tw;
         lsqr_step_u(st, nrm, inv, nsq);
     } else {
         tau[TS_X] = fma(xcoef, tw, tx);
-        if (lsqr_step_v(st, nrm, inv)) atomicSub(active, 1);
+        stopped = lsqr_step_v(st, nrm, inv);
     }
     // the next pass: the other product, the other update
     constexpr int NPASS = PASS == PASS_G ? PASS_GT : PASS_G;
@@ -677,6 +737,10 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
     q.tt = df_from(ntt);
     q.pad = 0.0;
     a.scal[si] = q;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gtau[i] = tau[i];
+    hot_store(gst, h);
+    if (stopped) atomicSub(active, 1);
 }
 
 
@@ -830,6 +894,64 @@ __device__ __forceinline__ void last_partials(const StreamArgs& a, int si, int p
     }
 }
 
+// last_partials for the two systems of a paired launch (either or both
+// last in this CTA), their loads issued together.
+__device__ __forceinline__ void last_partials2(const StreamArgs& a, int sa, int sb, bool la, bool lb, int prob,
+                                               df (*red)[kSWarps][3]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    df v[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) v[h][0] = v[h][1] = v[h][2] = df_zero();
+    const int sys[2] = {sa, sb};
+    const bool on[2] = {la, lb};
+    for (int i = threadIdx.x; i < a.gx; i += kSThreads) {
+        float4 p0[2], p1[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            const float4* o = a.cpart + 2 * ((int64_t)sys[h] * a.gstride + i);
+            p0[h] = __ldcg(o);
+            p1[h] = __ldcg(o + 1);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            v[h][0] = df_add(v[h][0], make_float2(p0[h].x, p0[h].y));
+            v[h][1] = df_add(v[h][1], make_float2(p0[h].z, p0[h].w));
+            v[h][2] = df_add(v[h][2], make_float2(p1[h].x, p1[h].y));
+        }
+    }
+    for (int i = a.soff[prob] + threadIdx.x; i < a.soff[prob + 1]; i += kSThreads) {
+        float2 q[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            const int64_t sr = a.batched ? 0 : (int64_t)sys[h] * a.nsplit;
+            const float2* o = reinterpret_cast<const float2*>(a.lrow + 3 * (sr + i));
+            q[h][0] = __ldcg(o);
+            q[h][1] = __ldcg(o + 1);
+            q[h][2] = __ldcg(o + 2);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            v[h][0] = df_add(v[h][0], q[h][0]);
+            v[h][1] = df_add(v[h][1], q[h][1]);
+            v[h][2] = df_add(v[h][2], q[h][2]);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!on[h]) continue;
+        const df w0 = warp_sum_df(v[h][0]), w1 = warp_sum_df(v[h][1]), w2 = warp_sum_df(v[h][2]);
+        if (lane == 0) {
+            red[h][warp][0] = w0;
+            red[h][warp][1] = w1;
+            red[h][warp][2] = w2;
+        }
+    }
+}
+
 // One thread of the system's last CTA: the warps' totals in order, then the
 // finisher.
 template <int PASS, int ROLE, bool SC>
@@ -879,8 +1001,7 @@ __device__ __forceinline__ void stream_tail2(const StreamArgs& a, int sa, int sb
     __syncthreads();
     const bool la = s_last[0], lb = s_last[1];
     if (!la && !lb) return;
-    if (la) last_partials(a, sa, prob, false, red[0]);
-    if (lb) last_partials(a, sb, prob, false, red[1]);
+    last_partials2(a, sa, sb, la, lb, prob, red);
     __syncthreads();
     if (la && threadIdx.x == 0) last_finish<PASS, RA, SC>(a, sa, pr, false, a.active, red[0], a.pshared);
     if (lb && threadIdx.x == 32) last_finish<PASS, RB, SC>(a, sb, pr, false, a.active2, red[1], nullptr);
