@@ -10,10 +10,12 @@ construction.  One step = the JVP and the VJP in one
 qcp_derivative_jvp_vjp_multi call (engine auto: the stream engine for a
 problem this size).  --workload config2 runs the n = 2000 SOC problem with
 16 + 16 directions at rtol 1e-10 (cluster engine), --workload example the
-paper's example shape, config4 / learned the batched and learned forms.
+paper's example shape, cones a problem with every cone family (PSD,
+exponential and power blocks: the pass engine), config4 / learned the
+batched and learned forms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload config3|config2|example|config1|config4|learned]
+                    [--workload config3|config2|example|cones|config1|config4|learned]
 
 Prints one JSON line (rank 0).  `value` counts JVP+VJP solves per second
 over all ranks with inputs resident in device memory; `e2e` measures the
@@ -22,7 +24,7 @@ and the outputs copied back inside the timed region.  With N > 1 (torchrun)
 every rank solves its own instance (replicas, weak scaling); there is no
 collective on the data path.  `--impl reference` times the CPU FP64 oracle
 on the same workload: dense LU of the bordered derivative system where it
-fits (configs 1, 2, example), else a bounded sample of its matrix-free
+fits (configs 1, 2, example, cones), else a bounded sample of its matrix-free
 LSMR iterations.
 """
 import argparse
@@ -77,6 +79,14 @@ def workload(name, rank):
         return prob, dirs, 1e-9, ("the paper's example shape (Sec. 4): x in R^1000, r in R^2000, "
                                    "[C D; E 0; f^T 0] with C 2000x1000 dense, {0}^2000 x R+^1000 x {0}, "
                                    "P diagonal on r; 16 JVP + 16 VJP directions")
+    if name == "cones":
+        prob = g.small_qcp(11 + rank, 1500, 100, 600, (5,) * 40, nnz_per_row=8, psd_orders=(8,) * 30,
+                           exp_kinds=("ray", "sint", "yint") * 33 + ("ray",),
+                           pow_blocks=(("ray", 0.3), ("sint", 0.6), ("yint", 0.45), ("ray", 0.7)) * 25)
+        dirs = g.make_directions_batch(prob, 5 + 1000 * rank, 8)
+        return prob, dirs, 1e-9, ("every cone family: QCP n=1500 m=2580 {0}^100 x R+^600 x SOC(5)^40 x "
+                                  "PSD(8)^30 x EXP^100 x POW^100 (exponents 0.3-0.7), dense P, "
+                                  "8 JVP + 8 VJP directions")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -216,7 +226,7 @@ def cpu_model():
 
 def dense_workload(name):
     """Workloads whose (N+1)^2 bordered system the dense-LU oracle factors."""
-    return name in ("config1", "config2", "example")
+    return name in ("config1", "config2", "example", "cones")
 
 
 def oracle_sample(prob, dirs, budget_s=30.0):
@@ -473,7 +483,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
     ap.add_argument("--workload", default="config3",
-                    choices=["config1", "config2", "config3", "example", "learned", "config4"])
+                    choices=["config1", "config2", "config3", "example", "cones", "learned", "config4"])
     ap.add_argument("--problems", type=int, default=32,
                     help="config4: how many of the batch's problems (drawn from their own streams, from 0)")
     ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
@@ -495,8 +505,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        if args.workload not in ("config1", "config2", "config3", "example"):
-            raise SystemExit("the oracle reference arm covers config1, config2, config3 and example")
+        if args.workload not in ("config1", "config2", "config3", "example", "cones"):
+            raise SystemExit("the oracle reference arm covers config1, config2, config3, example and cones")
         prob, dirs, rtol, desc = workload(args.workload, 0)
         if dense_workload(args.workload):
             for _ in range(args.warmup):
