@@ -56,7 +56,8 @@
  *             x^a y^(1-a) >= |z|}, dim 3, exponent a from K.param), both of
  *             Appendix A (the method projects onto their duals).  Plans with
  *             PSD, exponential or power blocks run on the pass and
- *             persistent engines.
+ *             persistent engines, and on the stream engine (LSQR; PSD
+ *             orders up to 22) with each such block's D Pi stored dense.
  *  Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
  *             All work of a plan is enqueued on the stream given at creation.
  *             JVP/VJP calls return when the outputs are written: they
@@ -170,8 +171,9 @@ typedef enum {
     QCP_ENGINE_AUTO = 3,        /* the plan's autotuned engine when qcp_plan_autotune has run, else
                                    QCP_ENGINE_CLUSTER; a cluster choice becomes STREAM when a system
                                    does not fit the cluster engine (PASSES where STREAM cannot run
-                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI), and PASSES for LSMR
-                                   and for plans with PSD, exponential or power blocks */
+                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI), and PASSES for LSMR.
+                                   Plans with PSD, exponential or power blocks never fit the cluster
+                                   engine, so they run on STREAM where it can run them */
     QCP_ENGINE_CLUSTER_FP64 = 4, /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,
@@ -182,11 +184,13 @@ typedef enum {
                                    vector arithmetic in double-float pairs like the cluster engine
                                    (Krylov vectors in device memory, LSQR scalars and the tau
                                    entries in FP64): warp-sized work units (SELL-32 row slices,
-                                   packed second-order-cone blocks, chunks of long rows) and no
-                                   CTA-wide barrier inside a pass; replayed from CUDA graphs in
-                                   chunks of check_every.  Zero, R+ and SOC blocks (at most 256
-                                   rows each), LSQR, precond NONE or EQUILIBRATE, magnitudes in
-                                   the data within 2^-90..2^90; QCP_ERR_ARG otherwise */
+                                   packed cone blocks, chunks of long rows) and no CTA-wide
+                                   barrier inside a pass; replayed from CUDA graphs in chunks of
+                                   check_every.  Zero, R+, SOC and PSD blocks of at most 256 rows,
+                                   exponential and power blocks (the last three with D Pi stored
+                                   as a dense matrix per block, made at plan time), LSQR, precond
+                                   NONE or EQUILIBRATE, magnitudes in the data within
+                                   2^-90..2^90; QCP_ERR_ARG otherwise */
 } qcp_engine;
 
 typedef struct {

@@ -132,6 +132,7 @@ struct StreamLayout {
     DevBuf d_scal, d_ssys, d_cpart, d_ccnt, d_lchunk, d_lcnt, d_lrow;
     DevBuf d_slist, d_scount;        // the systems (or pairs) still iterating, their number
     DevBuf d_pshared;                // paired launches: system passes that shared their read of M
+    DevBuf d_doff, d_dense;          // per coupled block: offset of its stored dense D Pi (-1: none); the D Pi
 };
 
 }  // namespace qcpd

@@ -99,10 +99,58 @@ __global__ void k_stream_todf(const double* in, int64_t n, df* out, int* bad) {
     }
 }
 
-__global__ void k_stream_soc(const SocBlock* blk, int64_t nb, StreamSoc* out, int* bad) {
+// A stored D Pi entry as df64: entries below the double-float range are
+// dropped (D Pi is nonexpansive, so they are far below the others), entries
+// above it make the plan unusable for the engine.
+__device__ __forceinline__ df s_dense_entry(double v, int* bad) {
+    if (fabs(v) < kSDfMin) return df_zero();
+    if (s_df_unsafe(v)) atomicExch(bad, 1);
+    return df_from(v);
+}
+
+// The dense D Pi of every exponential, power and PSD block (doff[b] >= 0),
+// row-major at out + doff[b] as df64 pairs: exponential and power blocks copy
+// their stored 3 x 3; a PSD block (order <= 22) applies its
+// V (B o (V^T dZ V)) V^T to each unit vector of its entries, one column at a
+// time (apply_D_psd, the pass engine's map).  One CTA per block.
+__global__ void k_stream_dense(const SocBlock* blk, int64_t nb, const int64_t* doff, const double* psd, df* out,
+                               int* bad) {
+    __shared__ double src[kSSocBig], dst[kSSocBig], scr[2 * 22 * 22];
+    const int64_t b = blockIdx.x;
+    if (b >= nb || doff[b] < 0) return;
+    const SocBlock B = blk[b];
+    const int d = B.dim;
+    df* D = out + doff[b];
+    if (B.kase == kBlockDense) {
+        for (int e = threadIdx.x; e < d * d; e += blockDim.x) D[e] = s_dense_entry(psd[B.psd + e], bad);
+        return;
+    }
+    if (B.kase != kBlockPsd || B.order > 22) {
+        if (threadIdx.x == 0) atomicExch(bad, 1);
+        return;
+    }
+    for (int c = 0; c < d; ++c) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x) src[i] = i == c ? 1.0 : 0.0;
+        __syncthreads();
+        apply_D_psd(src, dst, B.start, blk, (int)b, (int)b + 1, psd, scr);
+        for (int i = threadIdx.x; i < d; i += blockDim.x) D[(int64_t)i * d + c] = s_dense_entry(dst[i], bad);
+        __syncthreads();
+    }
+}
+
+__global__ void k_stream_soc(const SocBlock* blk, int64_t nb, const int64_t* doff, StreamSoc* out, int* bad) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
         const SocBlock B = blk[i];
         StreamSoc s;
+        if (doff[i] >= 0) {  // a stored dense D Pi
+            s.r = s.h = s.tq = s.htr = df_zero();
+            s.start = B.start;
+            s.dim = B.dim;
+            s.kase = kSDense;
+            s.pad = (int32_t)doff[i];
+            out[i] = s;
+            continue;
+        }
         const double htr = B.h * (B.t + B.r);
         if (B.kase == 2 && (s_df_unsafe(B.r) || s_df_unsafe(B.h) || s_df_unsafe(B.tq) || s_df_unsafe(htr)))
             atomicExch(bad, 1);
@@ -156,15 +204,12 @@ static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<Stream
             const int t = p->cone_type[pi][b], d = p->cone_dim[pi][b];
             if (t == QCP_CONE_ZERO || t == QCP_CONE_NONNEG) {
                 for (int k = 0; k < d; ++k) (len(row + k) <= kSLongChunk ? ys : longs).push_back(row + k);
-            } else if (t == QCP_CONE_SOC) {
+            } else {  // a coupled block: second-order, PSD, exponential or power cone
                 if (d > kSSocBig) {
-                    lay->why = "a second-order-cone block has more than 256 rows";
+                    lay->why = "a second-order-cone or PSD block has more than 256 rows";
                     return false;
                 }
                 socs.push_back({row, d, bi++});
-            } else {
-                lay->why = "the plan has PSD, exponential or power-cone blocks";
-                return false;
             }
             row += d;
         }
@@ -332,10 +377,37 @@ static int build_stream(qcp_plan* p, StreamLayout* lay) {
     QCP_TRY(todf(p->d_rw, lay->d_rw));
     QCP_TRY(todf(p->d_cd, lay->d_cd));
     QCP_TRY(todf(p->d_zy, lay->d_zy));
+    // the coupled blocks' constants; exponential, power and PSD blocks get a
+    // dense D Pi (offsets in block order, problems in order)
+    std::vector<int64_t> hdoff((size_t)std::max<int64_t>(p->nsoc_tot, 1), -1);
+    int64_t ndense = 0;
+    for (int pi = 0; pi < p->nprob; ++pi) {
+        int64_t bi = p->hprob[pi].soff;
+        for (size_t c = 0; c < p->cone_type[pi].size(); ++c) {
+            const int t = p->cone_type[pi][c], d = p->cone_dim[pi][c];
+            if (t == QCP_CONE_ZERO || t == QCP_CONE_NONNEG) continue;
+            if (t != QCP_CONE_SOC) {
+                hdoff[bi] = ndense;
+                ndense += (int64_t)d * d;
+            }
+            ++bi;
+        }
+    }
+    if (ndense > (int64_t)1 << 28) {
+        lay->why = "the stored D Pi of the exponential, power and PSD blocks would exceed 2 GB";
+        return QCP_OK;
+    }
+    QCP_TRY(up(lay->d_doff, hdoff.data(), sizeof(int64_t) * hdoff.size()));
+    QCP_TRY(lay->d_dense.alloc(sizeof(df) * (size_t)std::max<int64_t>(ndense, 1)));
     QCP_TRY(lay->d_soc.alloc(sizeof(StreamSoc) * (size_t)std::max<int64_t>(p->nsoc_tot, 1)));
-    if (p->nsoc_tot > 0)
+    if (p->nsoc_tot > 0) {
         k_stream_soc<<<grid_of(p->nsoc_tot), 256, 0, st>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot,
-                                                            lay->d_soc.as<StreamSoc>(), b);
+                                                            lay->d_doff.as<int64_t>(), lay->d_soc.as<StreamSoc>(), b);
+        if (ndense > 0)
+            k_stream_dense<<<(unsigned)p->nsoc_tot, 128, 0, st>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot,
+                                                                  lay->d_doff.as<int64_t>(), p->d_psd.as<double>(),
+                                                                  lay->d_dense.as<df>(), b);
+    }
     QCP_CUDA(cudaGetLastError());
     // per-system workspace: CTAs per system up to the number resident at once
     int dev = 0, nsm = 0, occ = 0;
@@ -398,6 +470,7 @@ static StreamArgs stream_args(qcp_plan* p, const StreamLayout* lay, int scaled) 
     a.zy = lay->d_zy.as<df>();
     a.flag = p->d_flag.as<int8_t>();
     a.soc = lay->d_soc.as<StreamSoc>();
+    a.dense = lay->d_dense.as<df>();
     a.rwd = p->d_rw.as<double>();
     a.cdd = p->d_cd.as<double>();
     a.sys = p->d_sys.as<Sys>();

@@ -11,12 +11,14 @@
 //             mod G) of row lane / G (rows sorted by length, so a slice is
 //             nearly dense); the G partial sums of a row are added in a fixed
 //             butterfly;
-//   SU_SOCP   consecutive second-order-cone blocks of at most 32 rows in
-//             all, one row per lane; D Pi's dot products are segmented
-//             warp reductions (one segment per block);
-//   SU_SOCB   one second-order-cone block of 33 to kSSocBig rows, rows
-//             lane + 32 j, the block's values through a per-warp
-//             shared-memory buffer;
+//   SU_SOCP   consecutive coupled blocks (second-order, PSD, exponential,
+//             power cone) of at most 32 rows in all, one row per lane; an SOC
+//             block's D Pi dot products are segmented warp reductions (one
+//             segment per block), the other cones' D Pi is a dense matrix
+//             per block (made at plan time; Appendix A's maps are linear in
+//             the direction) applied through shuffles inside the block;
+//   SU_SOCB   one coupled block of 33 to kSSocBig rows, rows lane + 32 j, the
+//             block's values through a per-warp shared-memory buffer;
 //   SU_LONG   up to kSLongChunk stored entries of a row longer than that, read
 //             lane-strided; the last chunk of a row to finish adds the
 //             chunk sums in order and runs the row's epilogue.
@@ -49,7 +51,8 @@ constexpr int kS2Ctas = 4;  // resident CTAs per SM of the paired kernel (its re
 constexpr int kSWarps = kSThreads / 32;
 constexpr int kSSteps = 16;        // most entries of one lane in a slice (its chain of dependent loads)
 constexpr int kSLongChunk = 32 * kSSteps;  // rows with more entries are cut into SU_LONG units of this many
-constexpr int kSSocBig = 256;      // largest second-order-cone block the engine takes
+constexpr int kSSocBig = 256;      // largest coupled block (second-order, PSD) the engine takes
+constexpr int kSDense = 4;         // StreamSoc::kase of a block whose D Pi is stored dense (exp, power, PSD)
 
 enum StreamKind : int32_t { SU_SLICE = 0, SU_SOCP = 1, SU_SOCB = 2, SU_LONG = 3 };
 
@@ -106,6 +109,7 @@ struct StreamArgs {
     const df* zy;
     const int8_t* flag;
     const StreamSoc* soc;   // per block (plan-wide)
+    const df* dense;        // row-major dim x dim D Pi of each block of kase kSDense (offset StreamSoc::pad)
     const double* rwd;      // FP64 w and c (tau entries)
     const double* cdd;
     const Sys* sys;
@@ -144,6 +148,7 @@ struct SCtx {
     const df *cA, *cB, *rw, *cd, *zy;  // problem-relative
     const int8_t* flag;
     const StreamSoc* soc;              // the problem's blocks
+    const df* dense;                   // dense D Pi of the blocks that store one (plan-wide offsets)
     const df* gin;                     // the gathered vector (XI for G-passes, the input for G^T-passes)
     df *IN, *OUT, *W, *X, *XI;         // system-relative
 };
@@ -445,8 +450,22 @@ __device__ __forceinline__ df shfl_df(df v, int src) {
 // block; u^T c_u is a segmented sum (after the doubling steps the head lane
 // holds its whole block's sum, each lane adding only from its own block).
 // Every lane calls it.
-__device__ __forceinline__ df socp_d(df v, df u, int pos, int head, int end, int kase, const StreamSoc& B) {
+__device__ __forceinline__ df socp_d(df v, df u, int pos, int head, int end, int kase, const StreamSoc& B,
+                                     const df* dense) {
     const int lane = threadIdx.x & 31;
+    // blocks with a stored D Pi (exponential and power cones, PSD blocks of
+    // at most 32 entries): out_pos = sum_j D[pos][j] v_{head + j}, in j order
+    const bool dn = kase == kSDense;
+    if (__any_sync(0xffffffffu, dn)) {
+        const int dim = end - head + 1;
+        const int jmax = __reduce_max_sync(0xffffffffu, dn ? dim : 0);
+        df acc = df_zero();
+        for (int j = 0; j < jmax; ++j) {
+            const df vj = shfl_df(v, dn && j < dim ? head + j : lane);
+            if (dn && j < dim) acc = df_fma(dfl(dense + B.pad + pos * dim + j), vj, acc);
+        }
+        if (dn) v = acc;
+    }
     df t = (kase == 2 && pos > 0) ? df_mul(u, v) : df_zero();
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -517,10 +536,10 @@ __device__ __forceinline__ void socp_gt_rows(const SCtx& c, const SUnitCtx& k, c
         s1 = gt_pre<SC>(c, r, h, v.in, ivs, acc);
         uk = dfl(c.zy + r);
     }
-    const df s2 = socp_d(s1, uk, pos, head, end, kase, B);
+    const df s2 = socp_d(s1, uk, pos, head, end, kase, B, c.dense);
     df nv = df_zero();
     if (r >= 0) nv = gt_post<ROLE, SC>(c, r, s2, ivs, v, acc);
-    const df xi = socp_d(nv, uk, pos, head, end, kase, B);
+    const df xi = socp_d(nv, uk, pos, head, end, kase, B, c.dense);
     if (r >= 0) c.XI[r] = xi;
 }
 
@@ -547,6 +566,25 @@ __device__ __forceinline__ void unit_socb_gt(const SCtx& c, const SUnitCtx& k, c
         }
     }
     __syncwarp();
+    if (B.kase == kSDense) {  // a stored D Pi: dense products in j order, the second on the new OUT entries
+        const df* D = c.dense + B.pad;
+        for (int i = lane; i < dim; i += 32) {
+            df s2 = df_zero();
+            for (int j = 0; j < dim; ++j) s2 = df_fma(dfl(D + (int64_t)i * dim + j), sb[j], s2);
+            const int r = r0 + i;
+            const SRowV v = row_vecs<ROLE>(c, r);
+            const df ivs = SC ? df_mul(dfl(c.rw + r), v.in) : v.in;
+            gt_post<ROLE, SC>(c, r, s2, ivs, v, acc);
+        }
+        __syncwarp();  // the lanes' new OUT entries are visible to the whole warp
+        for (int i = lane; i < dim; i += 32) {
+            df x = df_zero();
+            for (int j = 0; j < dim; ++j) x = df_fma(dfl(D + (int64_t)i * dim + j), c.OUT[r0 + j], x);
+            c.XI[r0 + i] = x;
+        }
+        __syncwarp();
+        return;
+    }
     df dot = warp_sum_df(part);
     df ct = sb[0];
     __syncwarp();
@@ -759,6 +797,7 @@ __device__ __forceinline__ void stream_ctx(const StreamArgs& a, const Sys& sy, c
     c.zy = a.zy + pr.doff;
     c.flag = a.flag + pr.doff;
     c.soc = a.soc + pr.soff;
+    c.dense = a.dense;
     c.IN = (ROLE == ROLE_U ? a.V : a.U) + sy.voff;
     c.OUT = (ROLE == ROLE_U ? a.U : a.V) + sy.voff;
     c.W = a.W + sy.voff;

@@ -3,8 +3,8 @@ dual cone made at plan time per block (Moreau: I - D Pi_K(-z); the
 exponential cone's nearest boundary ray by a scan and bisection and its
 derivative from the optimality conditions' Jacobian; the power cone's root
 r by bisection and the printed derivative formula) and applied as a dense
-3 x 3 per pass, on the pass and persistent engines, against the CPU FP64
-oracle (its own searches, pinned by membership, orthogonality and finite
+3 x 3 per pass, on the pass, persistent and stream engines (the stream
+engine in double-float), against the CPU FP64 oracle (its own searches, pinned by membership, orthogonality and finite
 differences)."""
 import numpy as np
 import pytest
@@ -42,12 +42,18 @@ def test_exp_jvp_vjp_match_oracle(q, name, mk, precond):
     rj = D.jvp_dense(prob, d, fac)[:3]
     rv = D.vjp_dense(prob, d, fac)[:4]
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
-    for engine in ("auto", "persistent"):
+    for engine in ("auto", "persistent", "stream"):
         for solver in ("lsqr", "lsmr"):
+            if engine == "stream" and solver == "lsmr":
+                continue  # the stream engine runs LSQR
             opts = q.options(rtol=1e-11, precond=precond, engine=engine, solver=solver)
             jv, ji = gpu_jvp(q, plan, d, opts)
             vv, vi = gpu_vjp(q, plan, d, opts)
-            assert plan.last_engine() in ("passes", "persistent")
+            # auto: the stream engine for LSQR (double-float, the cones' D Pi
+            # stored dense), the pass engine for LSMR (and the Jacobi scaling)
+            want = {"persistent": "persistent", "stream": "stream"}.get(
+                engine, "stream" if solver == "lsqr" and precond != "jacobi" else "passes")
+            assert plan.last_engine() == want, (engine, solver, plan.last_engine())
             assert rel_err(jv, rj) < TOL64, (engine, solver, rel_err(jv, rj), ji)
             assert rel_err(vv, rv) < TOL64, (engine, solver, rel_err(vv, rv), vi)
             assert adjoint_gap(prob, d, jv, vv) < 1e-8

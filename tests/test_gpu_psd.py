@@ -1,6 +1,8 @@
 """The positive semidefinite cone (Appendix A) on the GPU: D Pi_psd = V (B o
 (V^T dZ V)) V^T with the eigendecomposition made at plan time, on the pass
-and persistent engines, against the CPU FP64 oracle (which uses its own
+and persistent engines, and on the stream engine as the dense matrix of
+that map (made at plan time from the same V and B, applied in
+double-float), against the CPU FP64 oracle (which uses its own
 eigendecomposition and the same formula, and is pinned by finite
 differences of re-solves)."""
 import numpy as np
@@ -35,12 +37,18 @@ def test_psd_jvp_vjp_match_oracle(q, name, mk, precond):
     rj = D.jvp_dense(prob, d, fac)[:3]
     rv = D.vjp_dense(prob, d, fac)[:4]
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
-    for engine in ("auto", "persistent"):
+    for engine in ("auto", "persistent", "stream"):
         for solver in ("lsqr", "lsmr"):
+            if engine == "stream" and (solver == "lsmr" or precond == "jacobi"):
+                continue  # the stream engine runs LSQR, unscaled or equilibrated
             opts = q.options(rtol=1e-11, precond=precond, engine=engine, solver=solver)
             jv, ji = gpu_jvp(q, plan, d, opts)
             vv, vi = gpu_vjp(q, plan, d, opts)
-            assert plan.last_engine() in ("passes", "persistent")
+            # auto: the stream engine for LSQR (double-float, the cones' D Pi
+            # stored dense), the pass engine for LSMR (and the Jacobi scaling)
+            want = {"persistent": "persistent", "stream": "stream"}.get(
+                engine, "stream" if solver == "lsqr" and precond != "jacobi" else "passes")
+            assert plan.last_engine() == want, (engine, solver, plan.last_engine())
             assert rel_err(jv, rj) < TOL64, (engine, solver, rel_err(jv, rj), ji)
             assert rel_err(vv, rv) < TOL64, (engine, solver, rel_err(vv, rv), vi)
             for inf in (ji[0], vi[0]):

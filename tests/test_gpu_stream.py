@@ -151,7 +151,8 @@ def test_stream_batched_uneven_problems(q):
 def test_stream_engine_rules(q):
     """auto runs the stream engine when a system does not fit the cluster
     engine; the stream engine refuses LSMR, the diagonal preconditioner and
-    PSD blocks, and agrees with the pass engine on a larger problem."""
+    PSD blocks of more than 256 entries, and agrees with the pass engine on
+    a larger problem."""
     from paper_2508_17522_gb300._native import QCPError
     prob = g.config3(3, scale=0.1)
     d = g.make_directions(prob, 4)
@@ -169,7 +170,8 @@ def test_stream_engine_rules(q):
         gpu_jvp(q, plan, d, q.options(precond="diag", precond_d=torch.ones(N, device="cuda", dtype=torch.float64),
                                       engine="stream"))
     plan.close()
-    psd = g.small_qcp(31, 12, 0, 4, (3,), psd_orders=(3,))
+    # a PSD block of order 23 (276 entries) is beyond the engine's 256-row blocks
+    psd = g.small_qcp(31, 300, 0, 4, (3,), psd_orders=(23,))
     pl = _plan(q, psd)
     with pytest.raises(QCPError, match="ERR_ARG"):
         gpu_jvp(q, pl, g.make_directions(psd, 1), q.options(engine="stream"))
