@@ -489,6 +489,8 @@ def main():
     ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
     ap.add_argument("--maxiter", type=int, default=400000,
                     help="Krylov iteration cap (lower it only for profiling runs: solves then stop early)")
+    ap.add_argument("--solver", default="lsqr", choices=["lsqr", "lsmr"],
+                    help="Krylov solver: LSQR (default) or the paper's LSMR")
     ap.add_argument("--call", default="pair", choices=["pair", "separate"],
                     help="pair: the JVPs and VJPs in one qcp_derivative_jvp_vjp_multi call (side by side on the "
                          "cluster engine); separate: one _multi call per kind")
@@ -563,7 +565,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     plan = q.qcp_plan_create(q.problem_tensors(prob, dev), torch.float64, max_rhs=2 * k, stream=stream)
     plan.set_equilibration(args.equil_sweeps)
-    opts = q.options(rtol=rtol, maxiter=args.maxiter, precond=args.precond, engine=args.engine)
+    opts = q.options(rtol=rtol, maxiter=args.maxiter, precond=args.precond, engine=args.engine, solver=args.solver)
     cat = lambda nm: np.concatenate([getattr(d, nm) for d in dirs])
     host = {nm: torch.as_tensor(cat(nm)).pin_memory() for nm in ("dP", "dA", "dq", "db", "wx", "wy", "ws")}
     with torch.cuda.stream(stream):
@@ -693,8 +695,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "df64" if engine in ("cluster", "stream") else "f64",
             "data": "synthetic",
             "config": {"workload": desc, "rtol": rtol, "precond": args.precond, "equil_sweeps": args.equil_sweeps,
-                       "solver": "LSQR", "engine": engine,
-                       "arithmetic": ("vectors in double-float (binary32 pairs), LSQR scalars f64, data f64"
+                       "solver": args.solver.upper(), "engine": engine,
+                       "arithmetic": ("vectors in double-float (binary32 pairs), Krylov scalars f64, data f64"
                                       if engine in ("cluster", "stream") else "f64"),
                        "call": (f"qcp_derivative_jvp_vjp_multi ({k} JVP + {k} VJP systems in one call)"
                                 if args.call == "pair" else "qcp_derivative_jvp_multi then qcp_derivative_vjp_multi"),

@@ -171,9 +171,9 @@ typedef enum {
     QCP_ENGINE_AUTO = 3,        /* the plan's autotuned engine when qcp_plan_autotune has run, else
                                    QCP_ENGINE_CLUSTER; a cluster choice becomes STREAM when a system
                                    does not fit the cluster engine (PASSES where STREAM cannot run
-                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI), and PASSES for LSMR.
-                                   Plans with PSD, exponential or power blocks never fit the cluster
-                                   engine, so they run on STREAM where it can run them */
+                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI); LSMR and plans with
+                                   PSD, exponential or power blocks never run on the cluster engine,
+                                   so they go to STREAM where it can run them, else PASSES */
     QCP_ENGINE_CLUSTER_FP64 = 4, /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,
@@ -188,16 +188,17 @@ typedef enum {
                                    barrier inside a pass; replayed from CUDA graphs in chunks of
                                    check_every.  Zero, R+, SOC and PSD blocks of at most 256 rows,
                                    exponential and power blocks (the last three with D Pi stored
-                                   as a dense matrix per block, made at plan time), LSQR, precond
-                                   NONE or EQUILIBRATE, magnitudes in the data within
+                                   as a dense matrix per block, made at plan time), precond
+                                   NONE or EQUILIBRATE, LSQR or LSMR, magnitudes in the data within
                                    2^-90..2^90; QCP_ERR_ARG otherwise */
 } qcp_engine;
 
 typedef struct {
     int32_t solver;           /* 0 = LSQR (Paige & Saunders 1982), 1 = LSMR (Fong & Saunders 2011; the
-                                 pass and persistent engines: AUTO then runs the pass engine, CLUSTER
-                                 is an error).  Both minimise the same ||Op x - b|| and stop on the
-                                 same estimate of ||r|| <= rtol ||b|| */
+                                 pass, persistent and stream engines: AUTO then runs the stream engine
+                                 where it can run the plan, else the pass engine; CLUSTER is an
+                                 error).  Both minimise the same ||Op x - b|| and stop on the same
+                                 estimate of ||r|| <= rtol ||b|| */
     double rtol;              /* target for ||F dz + dN|| / ||dN|| (JVP) or ||F^T r + g|| / ||g|| (VJP) */
     int64_t maxiter;          /* iteration cap per system (counted over all restarts) */
     int32_t check_every;      /* iterations between host convergence checks; 0 = none */

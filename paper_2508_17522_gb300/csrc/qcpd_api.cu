@@ -377,7 +377,7 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
         return QCP_ERR_ARG;
     }
     if (opts.solver == 1 && (opts.engine == QCP_ENGINE_CLUSTER || opts.engine == QCP_ENGINE_CLUSTER_FP64)) {
-        set_error("LSMR runs on the pass or persistent engine");
+        set_error("LSMR runs on the pass, persistent or stream engine");
         return QCP_ERR_ARG;
     }
     if (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE &&
@@ -421,7 +421,13 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
     // the stream engine takes no diagonal preconditioner: an autotuned choice of it becomes AUTO
     if (engine == QCP_ENGINE_STREAM && opts.engine == QCP_ENGINE_AUTO && opts.precond == QCP_PRECOND_DIAG)
         engine = QCP_ENGINE_AUTO;
-    if (opts.solver == 1 && (engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER)) engine = QCP_ENGINE_PASSES;
+    if (opts.solver == 1 && engine == QCP_ENGINE_CLUSTER) engine = QCP_ENGINE_PASSES;
+    if (opts.solver == 1 && engine == QCP_ENGINE_AUTO) {
+        // LSMR: the cluster engine runs LSQR only; the stream engine where it can run the plan
+        bool sok = false;
+        if (opts.precond != QCP_PRECOND_DIAG) QCP_TRY(stream_ready(p, &sok));
+        engine = sok ? QCP_ENGINE_STREAM : QCP_ENGINE_PASSES;
+    }
     if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER_FP64) {
         bool fits = false;
         QCP_TRY(cluster_ready(p, nsys, &fits));
@@ -439,8 +445,8 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
             engine = sok ? QCP_ENGINE_STREAM : QCP_ENGINE_PASSES;
         }
     } else if (engine == QCP_ENGINE_STREAM) {
-        if (opts.solver != 0 || opts.precond == QCP_PRECOND_DIAG) {
-            set_error("the stream engine runs LSQR with precond NONE or EQUILIBRATE");
+        if (opts.precond == QCP_PRECOND_DIAG) {
+            set_error("the stream engine runs with precond NONE or EQUILIBRATE");
             return QCP_ERR_ARG;
         }
         bool sok = false;

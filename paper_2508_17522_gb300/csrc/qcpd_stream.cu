@@ -483,6 +483,7 @@ static StreamArgs stream_args(qcp_plan* p, const StreamLayout* lay, int scaled) 
     a.W = reinterpret_cast<df*>(p->d_W.p);
     a.X = reinterpret_cast<df*>(p->d_X.p);
     a.XI = reinterpret_cast<df*>(p->d_XI.p);
+    a.HB = reinterpret_cast<df*>(p->d_HB.p);
     a.cpart = lay->d_cpart.as<float4>();
     a.ccnt = lay->d_ccnt.as<int32_t>();
     a.lchunk = lay->d_lchunk.as<df>();
@@ -522,7 +523,7 @@ static int run_stream_chunk(qcp_plan* p, int mode, int s0, int ns, const StreamA
         p->last_launches += 2 * chunk;
         return QCP_OK;
     }
-    GraphKey key{QCP_ENGINE_STREAM, mode, s0, ns, chunk, scaled ? 1 : 0, 0};
+    GraphKey key{QCP_ENGINE_STREAM, mode, s0, ns, chunk, scaled ? 1 : 0, a.lsmr};
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -556,6 +557,7 @@ int iterate_stream(qcp_plan* p, int mode, int s0, int ns, int* active, bool scal
         return QCP_ERR_ARG;
     }
     StreamArgs a = stream_args(p, lay, scaled ? 1 : 0);
+    a.lsmr = opts.solver == 1 ? 1 : 0;
     a.s0 = s0;
     a.active = active;
     a.slist = lay->d_slist.as<int32_t>();
@@ -648,7 +650,7 @@ static int run_stream_pair_chunk(qcp_plan* p, int sa0, int sb0, int npairs, cons
         p->last_launches += 2 * chunk;
         return QCP_OK;
     }
-    GraphKey key{QCP_ENGINE_STREAM, 2, sa0, npairs, chunk, scaled ? 1 : 0, 0, 1 + sb0};
+    GraphKey key{QCP_ENGINE_STREAM, 2, sa0, npairs, chunk, scaled ? 1 : 0, a.lsmr, 1 + sb0};
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -690,6 +692,7 @@ int iterate_stream_pair(qcp_plan* p, int sa0, int sb0, int ns, int* active_a, in
         return QCP_ERR_ARG;
     }
     StreamArgs a = stream_args(p, lay, scaled ? 1 : 0);
+    a.lsmr = opts.solver == 1 ? 1 : 0;
     a.active = active_a;
     a.active2 = active_b;
     a.pshared = lay->d_pshared.as<unsigned long long>();

@@ -81,14 +81,16 @@ struct StreamSoc {
 // column's coefficient tt.
 struct StreamScal {
     df c1, nc2, nw, xc, tt;
-    double pad;
+    df nhc;        // LSMR: -hcoef (hbar <- h - hcoef hbar)
+    int32_t upd;   // LSMR: this u-pass applies the deferred (hbar, x, h) updates
+    int32_t lsmr;  // 1: LSMR's vector updates, 0: LSQR's
 };
 
 // Per system while the engine iterates: the FP64 tau entries of U, V, W, X,
 // XI (they never enter a gather) and the scale of the right-hand side.
-enum { TS_U = 0, TS_V = 1, TS_W = 2, TS_X = 3, TS_XI = 4 };
+enum { TS_U = 0, TS_V = 1, TS_W = 2, TS_X = 3, TS_XI = 4, TS_HB = 5 };
 struct StreamSys {
-    double tau[5];
+    double tau[6];
     double scale;   // the right-hand side was multiplied by this power of two
     int32_t uscaled;  // U and beta carry the scale too (no u-update yet)
     int32_t pad;
@@ -122,6 +124,8 @@ struct StreamArgs {
     df* W;
     df* X;
     df* XI;
+    df* HB;                 // LSMR's hbar (W holds h)
+    int32_t lsmr;           // 1: LSMR (Fong & Saunders 2011), 0: LSQR
     float4* cpart;          // per (system, CTA): the three df64 partial sums as (a, b), (c, 0) pairs
     int32_t* ccnt;          // per system: CTAs done in this pass
     df* lchunk;             // per (system, chunk slot): chunk sums of split rows
@@ -150,7 +154,7 @@ struct SCtx {
     const StreamSoc* soc;              // the problem's blocks
     const df* dense;                   // dense D Pi of the blocks that store one (plan-wide offsets)
     const df* gin;                     // the gathered vector (XI for G-passes, the input for G^T-passes)
-    df *IN, *OUT, *W, *X, *XI;         // system-relative
+    df *IN, *OUT, *W, *X, *XI, *HB;    // system-relative
 };
 
 // Per-lane sums of the pass: ||out||^2 and the tau-row dot products.
@@ -330,7 +334,7 @@ __device__ __forceinline__ void long_rowsum2(const int32_t* scol, const df* val,
 // before the row's first store (the arrays are distinct, but the compiler
 // cannot know that and would reload them after each store).
 struct SRowV {
-    df in, out, w, x;
+    df in, out, w, x, hb;
 };
 
 template <int ROLE>
@@ -339,19 +343,31 @@ __device__ __forceinline__ SRowV row_vecs(const SCtx& c, int r) {
     v.in = c.IN[r];
     v.out = c.OUT[r];
     v.w = c.W[r];
-    v.x = ROLE == ROLE_V ? c.X[r] : df_zero();
+    const bool upd = ROLE == ROLE_U && c.sc.upd;
+    v.x = (ROLE == ROLE_V && !c.sc.lsmr) || upd ? c.X[r] : df_zero();
+    v.hb = upd ? c.HB[r] : df_zero();
     return v;
 }
 
 // The u- or v-update of row r given its new product value o: out = c1 o -
-// c2 out, then w (u-update) or x (v-update); returns the new out.
+// c2 out, then LSQR's w (u-update) or x (v-update), or in LSMR's u-update
+// the deferred hbar <- h - hcoef hbar, x <- x + xcoef hbar, h <- v / alpha -
+// wcoef h (run_tile's lsmr_update); returns the new out.
 template <int ROLE>
 __device__ __forceinline__ df row_update(const SCtx& c, int r, df o, const SRowV& v, SAcc& acc) {
     const df nv = df_fma(c.sc.c1, o, df_mul(c.sc.nc2, v.out));
     c.OUT[r] = nv;
     dfacc_fma(acc.ss, nv, nv);
-    if (ROLE == ROLE_U) c.W[r] = df_fma(v.in, c.sc.c1, df_mul(c.sc.nw, v.w));
-    else c.X[r] = df_fma(c.sc.xc, v.w, v.x);
+    if (ROLE == ROLE_U) {
+        if (c.sc.upd) {
+            const df hb = df_fma(c.sc.nhc, v.hb, v.w);
+            c.HB[r] = hb;
+            c.X[r] = df_fma(c.sc.xc, hb, v.x);
+        }
+        if (!c.sc.lsmr || c.sc.upd) c.W[r] = df_fma(v.in, c.sc.c1, df_mul(c.sc.nw, v.w));
+    } else if (!c.sc.lsmr) {
+        c.X[r] = df_fma(c.sc.xc, v.w, v.x);
+    }
     return nv;
 }
 
@@ -658,6 +674,76 @@ __device__ __forceinline__ void long_rows(const SCtx& c, const StreamArgs& a, in
 }
 
 // ---------------------------------------------------------------------------
+// The finisher of an LSMR system (one thread): the tau entries with the
+// pass's vector updates, then lsmr_step_u / lsmr_step_v (Fong & Saunders
+// 2011, the pass engine's finisher) on the state in global memory, then the
+// next pass's scalars.  only: a stopped system's last deferred updates.
+template <int PASS, int ROLE, bool SC>
+__device__ __noinline__ void stream_finish_lsmr(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only,
+                                                int* active) {
+    LsqrState* st = a.state + si;
+    double* tau = a.ssys[si].tau;
+    const int rN = pr.n + pr.m;
+    const double rwN = a.rwd[pr.doff + rN], cdN = a.cdd[pr.doff + rN];
+    const double c1 = ROLE == ROLE_U ? st->uc1 : st->vc1;
+    const double c2 = ROLE == ROLE_U ? st->uc2 : st->vc2;
+    const double wcoef = st->wcoef, xcoef = st->xcoef, hcoef = st->hcoef;
+    const int tin_i = ROLE == ROLE_U ? TS_V : TS_U, tout_i = ROLE == ROLE_U ? TS_U : TS_V;
+    const double tin = tau[tin_i];
+    auto tau_upd = [&]() {  // run_tile's lsmr_update on the tau entries
+        const double h = tau[TS_W];
+        const double hb = fma(-hcoef, tau[TS_HB], h);
+        tau[TS_HB] = hb;
+        tau[TS_X] = fma(xcoef, hb, tau[TS_X]);
+        tau[TS_W] = fma(tin, c1, -wcoef * h);
+    };
+    if (only) {
+        tau_upd();
+        st->upd = 0;  // applied: a continuation starts with a plain u-pass
+        st->status = S_DONE;
+        atomicSub(active, 1);
+        return;
+    }
+    const double tt = SC ? (PASS == PASS_G ? cdN : rwN) * tin : tin;
+    double oN;
+    if (PASS == PASS_G) {
+        oN = -tot.b - tot.c + pr.kappa * tt;
+        if (SC) oN *= rwN;
+    } else {
+        oN = tot.b - tot.c + pr.kappa * tt;
+        if (SC) oN *= cdN;
+    }
+    // gauge dz_N = 0: G^T-passes leave the tau entry at 0 (see run_tile)
+    const double nvN = (PASS == PASS_GT) ? 0.0 : c1 * oN - c2 * tau[tout_i];
+    tau[tout_i] = nvN;
+    if (PASS == PASS_GT) tau[TS_XI] = 0.0;
+    const double nsq = fma(nvN, nvN, tot.a);
+    double nrm, inv;
+    norm_and_inverse(nsq, nrm, inv);
+    bool stopped;
+    if (ROLE == ROLE_U) {
+        if (st->upd) tau_upd();
+        stopped = lsmr_step_u(st, nrm, inv);
+    } else {
+        stopped = lsmr_step_v(st, nrm, inv);
+    }
+    constexpr int NPASS = PASS == PASS_G ? PASS_GT : PASS_G;
+    const double nc1 = ROLE == ROLE_U ? st->vc1 : st->uc1;
+    const double nc2 = ROLE == ROLE_U ? st->vc2 : st->uc2;
+    const double ntt = SC ? (NPASS == PASS_G ? cdN : rwN) * nvN : nvN;
+    StreamScal q;
+    q.c1 = df_from(nc1);
+    q.nc2 = df_from(-nc2);
+    q.nw = df_from(-st->wcoef);
+    q.xc = df_from(st->xcoef);
+    q.tt = df_from(ntt);
+    q.nhc = df_from(-st->hcoef);
+    q.upd = st->upd;
+    q.lsmr = 1;
+    a.scal[si] = q;
+    if (stopped) atomicSub(active, 1);
+}
+
 // The LSQR fields the finisher reads and writes, copied into registers with
 // one batch of loads and written back at the end: on the state in global
 // memory every read after a write would wait for its own round trip (the
@@ -716,6 +802,10 @@ __device__ __forceinline__ void hot_store(LsqrState* st, const LsqrHot& h) {
 template <int PASS, int ROLE, bool SC>
 __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only_x,
                                               int* active) {
+    if (a.lsmr) {
+        stream_finish_lsmr<PASS, ROLE, SC>(a, si, pr, tot, only_x, active);
+        return;
+    }
     LsqrState* gst = a.state + si;
     double* gtau = a.ssys[si].tau;
     const int rN = pr.n + pr.m;
@@ -773,7 +863,9 @@ __device__ __forceinline__ void stream_finish(const StreamArgs& a, int si, const
     q.nw = df_from(-st->wcoef);
     q.xc = df_from(st->xcoef);
     q.tt = df_from(ntt);
-    q.pad = 0.0;
+    q.nhc = df_zero();
+    q.upd = 0;
+    q.lsmr = 0;
     a.scal[si] = q;
 #pragma unroll
     for (int i = 0; i < 5; ++i) gtau[i] = tau[i];
@@ -803,6 +895,7 @@ __device__ __forceinline__ void stream_ctx(const StreamArgs& a, const Sys& sy, c
     c.W = a.W + sy.voff;
     c.X = a.X + sy.voff;
     c.XI = a.XI + sy.voff;
+    c.HB = a.HB + sy.voff;
     c.gin = PASS == PASS_G ? c.XI : c.IN;
 }
 
@@ -1056,12 +1149,23 @@ __device__ __forceinline__ void stream_pass(const StreamArgs& a, int si, int sta
     if (threadIdx.x == 0) stream_ctx<PASS, ROLE>(a, sy, pr, si, s_ctx);
     __syncthreads();
     const SCtx& c = s_ctx;
-    const bool only_x = (ROLE == ROLE_V && status == S_FINAL);
+    // a stopped system's last deferred update: LSQR's x-update in its
+    // v-pass, LSMR's (hbar, x, h) updates in its u-pass
+    const bool only_x = status == S_FINAL && (ROLE == ROLE_V) == !a.lsmr;
     SAcc acc;
     sacc_zero(acc);
-    if (only_x) {  // the last x-update of a stopped system
-        for (int r = blockIdx.x * kSThreads + threadIdx.x; r < c.N - 1; r += a.gx * kSThreads)
-            c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
+    if (only_x) {
+        for (int r = blockIdx.x * kSThreads + threadIdx.x; r < c.N - 1; r += a.gx * kSThreads) {
+            if (ROLE == ROLE_V) {
+                c.X[r] = df_fma(c.sc.xc, c.W[r], c.X[r]);
+            } else {
+                const df h = c.W[r];
+                const df hb = df_fma(c.sc.nhc, c.HB[r], h);
+                c.HB[r] = hb;
+                c.X[r] = df_fma(c.sc.xc, hb, c.X[r]);
+                c.W[r] = df_fma(c.IN[r], c.sc.c1, df_mul(c.sc.nw, h));
+            }
+        }
     } else {
         stream_units<PASS, ROLE, SC>(a, si, sy.prob, c, sb, acc);
     }
@@ -1101,7 +1205,9 @@ __global__ void __launch_bounds__(kSThreads, kS2Ctas) k_stream2(StreamArgs a) {
     const int sa = a.slist[2 * blockIdx.y], sb = a.slist[2 * blockIdx.y + 1];
     const int ta = a.state[sa].status, tb = a.state[sb].status;
     const bool la = ta != S_DONE, lb = tb != S_DONE;
-    const bool xa = RA == ROLE_V && ta == S_FINAL, xb = RB == ROLE_V && tb == S_FINAL;
+    // a stopped system's last update pass (LSQR: a v-pass, LSMR: a u-pass)
+    const bool xa = ta == S_FINAL && (RA == ROLE_V) == !a.lsmr;
+    const bool xb = tb == S_FINAL && (RB == ROLE_V) == !a.lsmr;
     df* sbw = sbuf[threadIdx.x >> 5];
     if (!(la && lb) || xa || xb) {
         if (la) stream_pass<PASS, RA, SC>(a, sa, ta, a.active, s_ctx[0], sbw, red[0], &s_last[0]);
@@ -1179,7 +1285,9 @@ __global__ void k_stream_enter_state(StreamArgs a, int upass_g, int sc) {
     const double* X = reinterpret_cast<const double*>(a.X + sy.voff);
     const double* XI = reinterpret_cast<const double*>(a.XI + sy.voff);
     double s = 1.0;
-    if (st->bnorm > 0.0 && finite64(st->bnorm)) {
+    // LSMR keeps its scalars unscaled (its recurrences carry many quantities
+    // proportional to ||b||); LSQR's right-hand side goes to norm [1/2, 1)
+    if (!a.lsmr && st->bnorm > 0.0 && finite64(st->bnorm)) {
         int e = 0;
         frexp(st->bnorm, &e);
         s = ldexp(1.0, -e);
@@ -1199,6 +1307,7 @@ __global__ void k_stream_enter_state(StreamArgs a, int upass_g, int sc) {
     ss->tau[TS_W] = W[rN];
     ss->tau[TS_X] = X[rN] * s;
     ss->tau[TS_XI] = XI[rN];
+    ss->tau[TS_HB] = reinterpret_cast<const double*>(a.HB + sy.voff)[rN];
     const double tin = ss->tau[TS_V];
     const double tt = sc ? (upass_g ? a.cdd[pr.doff + rN] : a.rwd[pr.doff + rN]) * tin : tin;
     StreamScal q;
@@ -1207,7 +1316,9 @@ __global__ void k_stream_enter_state(StreamArgs a, int upass_g, int sc) {
     q.nw = df_from(-st->wcoef);
     q.xc = df_from(st->xcoef);
     q.tt = df_from(tt);
-    q.pad = 0.0;
+    q.nhc = df_from(a.lsmr ? -st->hcoef : 0.0);
+    q.upd = a.lsmr ? st->upd : 0;
+    q.lsmr = a.lsmr;
     a.scal[si] = q;
 }
 
@@ -1233,6 +1344,10 @@ __global__ void k_stream_enter_vec(StreamArgs a) {
         a.X[sy.voff + r] = df_from(X[r] * ss.scale);
         a.XI[sy.voff + r] = df_from(XI[r]);
     }
+    if (!a.lsmr) return;
+    double* HB = reinterpret_cast<double*>(a.HB + sy.voff);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rN; r += gridDim.x * blockDim.x)
+        a.HB[sy.voff + r] = df_from(HB[r]);
 }
 
 // df64 pairs -> FP64 in place, the scale undone (U only while no u-update
@@ -1258,6 +1373,10 @@ __global__ void k_stream_exit_vec(StreamArgs a) {
         X[r] = df_to(a.X[sy.voff + r]) * ix;
         XI[r] = df_to(a.XI[sy.voff + r]);
     }
+    if (!a.lsmr) return;
+    double* HB = reinterpret_cast<double*>(a.HB + sy.voff);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rN; r += gridDim.x * blockDim.x)
+        HB[r] = df_to(a.HB[sy.voff + r]);
 }
 
 __global__ void k_stream_exit_state(StreamArgs a) {
@@ -1283,6 +1402,7 @@ __global__ void k_stream_exit_state(StreamArgs a) {
     reinterpret_cast<double*>(a.W + sy.voff)[rN] = ss->tau[TS_W];
     reinterpret_cast<double*>(a.X + sy.voff)[rN] = ss->tau[TS_X] * ix;
     reinterpret_cast<double*>(a.XI + sy.voff)[rN] = ss->tau[TS_XI];
+    if (a.lsmr) reinterpret_cast<double*>(a.HB + sy.voff)[rN] = ss->tau[TS_HB];
     ss->pad = 0;
 }
 

@@ -490,14 +490,14 @@ def test_lsmr_matches_oracle(q, name, mk, precond):
 
 def test_lsmr_config2_and_engine_rules(q, cfg2):
     """Configuration 2 with LSMR: four directions each way at rtol 1e-10;
-    auto runs LSMR on the pass engine and the cluster engines refuse it."""
+    auto runs LSMR on the stream engine (the cluster engines refuse it)."""
     prob, dirs, ref_j, ref_v = cfg2
     k = 4
     plan = _plan(q, prob, max_rhs=k)
     opts = q.options(rtol=1e-10, precond="equilibrate", solver="lsmr")
     cat = lambda name: np.concatenate([getattr(d, name) for d in dirs[:k]])
     dx, dy, ds, ji = q.qcp_derivative_jvp_multi(plan, k, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
-    assert plan.last_engine() == "passes"
+    assert plan.last_engine() == "stream"
     dx, dy, ds = to_np(dx, dy, ds)
     n, m = prob.n, prob.m
     for i in range(k):

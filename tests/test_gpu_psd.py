@@ -39,15 +39,15 @@ def test_psd_jvp_vjp_match_oracle(q, name, mk, precond):
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
     for engine in ("auto", "persistent", "stream"):
         for solver in ("lsqr", "lsmr"):
-            if engine == "stream" and (solver == "lsmr" or precond == "jacobi"):
-                continue  # the stream engine runs LSQR, unscaled or equilibrated
+            if engine == "stream" and precond == "jacobi":
+                continue  # the stream engine runs unscaled or equilibrated
             opts = q.options(rtol=1e-11, precond=precond, engine=engine, solver=solver)
             jv, ji = gpu_jvp(q, plan, d, opts)
             vv, vi = gpu_vjp(q, plan, d, opts)
-            # auto: the stream engine for LSQR (double-float, the cones' D Pi
-            # stored dense), the pass engine for LSMR (and the Jacobi scaling)
+            # auto: the stream engine (double-float, the cones' D Pi stored
+            # dense), the pass engine with the Jacobi scaling
             want = {"persistent": "persistent", "stream": "stream"}.get(
-                engine, "stream" if solver == "lsqr" and precond != "jacobi" else "passes")
+                engine, "stream" if precond != "jacobi" else "passes")
             assert plan.last_engine() == want, (engine, solver, plan.last_engine())
             assert rel_err(jv, rj) < TOL64, (engine, solver, rel_err(jv, rj), ji)
             assert rel_err(vv, rv) < TOL64, (engine, solver, rel_err(vv, rv), vi)

@@ -79,6 +79,35 @@ def test_stream_matches_oracle(q, name, mk, precond):
     plan.close()
 
 
+@pytest.mark.parametrize("precond", ["none", "equilibrate"])
+@pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
+def test_stream_lsmr_matches_oracle(q, name, mk, precond):
+    """LSMR (Fong & Saunders 2011) on the stream engine: the deferred
+    (hbar, x, h) updates in the u-passes, the last ones in a stopped
+    system's final u-pass; the oracle per output block, and the same bits on
+    a second call."""
+    prob = mk()
+    d = g.make_directions(prob, 53)
+    fac = D.DenseFactor(prob)
+    ref_j = D.jvp_dense(prob, d, fac)[:3]
+    ref_v = D.vjp_dense(prob, d, fac)[:4]
+    plan = _plan(q, prob)
+    opts = q.options(rtol=1e-11, maxiter=400000, precond=precond, engine="stream", solver="lsmr")
+    jv, ji = gpu_jvp(q, plan, d, opts)
+    assert plan.last_engine() == "stream"
+    vv, vi = gpu_vjp(q, plan, d, opts)
+    _check_blocks(jv, ref_j, TOL64, (name, precond, "jvp", ji))
+    _check_blocks(vv, ref_v, TOL64, (name, precond, "vjp", vi))
+    for inf in (ji[0], vi[0]):
+        assert inf["status"] in ("QCP_OK", "QCP_NOT_CONVERGED"), inf
+        assert inf["rel_residual"] <= (1e-11 if inf["status"] == "QCP_OK" else 1e-8), inf
+    assert adjoint_gap(prob, d, jv, vv) < 1e-8
+    jv2, _ = gpu_jvp(q, plan, d, opts)
+    for a, b in zip(jv, jv2):
+        assert np.array_equal(a, b)
+    plan.close()
+
+
 @pytest.mark.parametrize("name,mk", [PROBS[1], PROBS[3], PROBS[5]], ids=[PROBS[1][0], PROBS[3][0], PROBS[5][0]])
 def test_stream_fp32_storage(q, name, mk):
     prob = mk()
@@ -150,9 +179,9 @@ def test_stream_batched_uneven_problems(q):
 
 def test_stream_engine_rules(q):
     """auto runs the stream engine when a system does not fit the cluster
-    engine; the stream engine refuses LSMR, the diagonal preconditioner and
-    PSD blocks of more than 256 entries, and agrees with the pass engine on
-    a larger problem."""
+    engine (LSQR and LSMR); the stream engine refuses the diagonal
+    preconditioner and PSD blocks of more than 256 entries, and agrees with
+    the pass engine on a larger problem."""
     from paper_2508_17522_gb300._native import QCPError
     prob = g.config3(3, scale=0.1)
     d = g.make_directions(prob, 4)
@@ -163,8 +192,11 @@ def test_stream_engine_rules(q):
     b, bi = gpu_jvp(q, plan, d, q.options(rtol=1e-10, maxiter=400000, precond="equilibrate", engine="passes"))
     assert ai[0]["status"] == "QCP_OK" and bi[0]["status"] == "QCP_OK", (ai, bi)
     assert rel_err(a, b) < 1e-7, rel_err(a, b)
-    with pytest.raises(QCPError, match="ERR_ARG"):
-        gpu_jvp(q, plan, d, q.options(solver="lsmr", engine="stream"))
+    # LSMR runs on the stream engine too, and auto picks it for LSMR here
+    c, ci = gpu_jvp(q, plan, d, q.options(rtol=1e-10, maxiter=400000, precond="equilibrate", solver="lsmr"))
+    assert plan.last_engine() == "stream", plan.last_engine()
+    assert ci[0]["status"] == "QCP_OK", ci
+    assert rel_err(c, b) < 1e-7, rel_err(c, b)
     N = prob.N
     with pytest.raises(QCPError, match="ERR_ARG"):
         gpu_jvp(q, plan, d, q.options(precond="diag", precond_d=torch.ones(N, device="cuda", dtype=torch.float64),

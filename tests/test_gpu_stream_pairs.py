@@ -127,6 +127,26 @@ def test_paired_iteration_cap_same_passes(q, cap):
     plan.close()
 
 
+@pytest.mark.parametrize("name,mk", [PROBS[1], PROBS[2], PROBS[4]], ids=[PROBS[1][0], PROBS[2][0], PROBS[4][0]])
+def test_paired_lsmr(q, name, mk):
+    """LSMR in paired launches: the oracle, and the unpaired schedule."""
+    prob = mk()
+    dirs = g.make_directions_batch(prob, 65, 2)
+    fac = D.DenseFactor(prob)
+    plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64, max_rhs=4)
+    opts = q.options(rtol=1e-11, maxiter=400000, precond="equilibrate", engine="stream", solver="lsmr")
+    jv, vv, info = _pair_call(q, plan, prob, dirs, opts)
+    assert plan.last_shared_passes() > 0
+    for i, d in enumerate(dirs):
+        _check_blocks(jv[i], D.jvp_dense(prob, d, fac)[:3], TOL64, (name, "jvp", i, info[i]))
+        _check_blocks(vv[i], D.vjp_dense(prob, d, fac)[:4], TOL64, (name, "vjp", i, info[2 + i]))
+    plan.set_stream_pairing(False)
+    ju, vu, _ = _pair_call(q, plan, prob, dirs, opts)
+    for i in range(2):
+        assert rel_err(jv[i], ju[i]) < 1e-8 and rel_err(vv[i], vu[i]) < 1e-8
+    plan.close()
+
+
 def test_paired_fp32_storage(q):
     prob = g.small_qcp(27, 1300, 100, 400, (10,) * 10, nnz_per_row=6)
     r = g.round_to_fp32(prob)
