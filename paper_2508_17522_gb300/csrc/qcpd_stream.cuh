@@ -679,7 +679,7 @@ __device__ __forceinline__ void long_rows(const SCtx& c, const StreamArgs& a, in
 // 2011, the pass engine's finisher) on the state in global memory, then the
 // next pass's scalars.  only: a stopped system's last deferred updates.
 template <int PASS, int ROLE, bool SC>
-__device__ __noinline__ void stream_finish_lsmr(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only,
+__device__ __forceinline__ void stream_finish_lsmr(const StreamArgs& a, int si, const Prob& pr, Part tot, bool only,
                                                 int* active) {
     LsqrState* st = a.state + si;
     double* tau = a.ssys[si].tau;
