@@ -267,16 +267,16 @@ def oracle_lsmr_sample(prob, dirs, iters_per_solve, target_s=15.0):
 # --------------------------------------------------------------------------- learned form
 def learned_bench(args, rank, local):
     """The learned preconditioner's family (the parametric family with a fixed
-    pattern, shrunk to n = 500, m = 801): train on the method's own solves of
-    40 instances (untimed), then time, on 8 held-out instances, the adjoint
-    solve of ||x*||^2 to rtol 1e-6 by
+    pattern, n = 5000, m = 8000 times --scale, 0.1 by default): train on the
+    method's own solves of --train instances (untimed), then time, on --held
+    held-out instances, the adjoint solve of ||x*||^2 to rtol 1e-6 by
       plain       zero start, no scaling (the method of Sec. 3.1);
       c_alpha     zero start, the column scaling c^alpha the training chose
                   (the network's preconditioner target without the network);
       learned     network features + forward + decode, warm start and
                   diagonal preconditioner;
       best_plain  the fastest plain GPU form: the 16-sweep equilibration,
-    all on engine auto (the cluster engine for this size).  value = learned
+    all on engine auto (the cluster engine up to the full size).  value = learned
     solves/s; every row's rate and mean iterations ride along."""
     import torch
     import qcpgen as g
@@ -285,10 +285,12 @@ def learned_bench(args, rank, local):
     from paper_2508_17522_gb300.buildlib import build
     build()
     dev = torch.device("cuda", local)
-    fam = g.config5_family(2 + 1000 * rank, scale=0.1)
-    train = [fam.instance(j) for j in range(40)]
-    held = [fam.instance(1000 + j) for j in range(8)]
+    fam = g.config5_family(2 + 1000 * rank, scale=args.scale)
+    train = [fam.instance(j) for j in range(args.train)]
+    held = [fam.instance(1000 + j) for j in range(args.held)]
+    t0 = time.time()
     lp = L.LearnedPreconditioner(seed=3, device=dev).fit(train, steps=800, lr=1e-3)
+    log(f"learned: trained on {len(train)} instances (n={fam.n}) in {time.time() - t0:.1f} s")
     plans = [q.qcp_plan_create(q.problem_tensors(pr, dev), torch.float64) for pr in held]
     dirs = [L.adjoint_direction(pr) for pr in held]
     calpha = [(L.plan_scalings(pl)[1] ** lp.alpha).contiguous() for pl in plans]
@@ -318,7 +320,8 @@ def learned_bench(args, rank, local):
     names = ["plain", "c_alpha", "learned", "best_plain"]
     for _ in range(max(args.warmup, 1)):
         for k in names:
-            run(k)
+            t, its_k, _, _ = run(k)
+            log(f"learned: warm-up {k}: {t:.1f} ms, mean iterations {np.mean(its_k):.0f}")
     tot = {k: [0.0, [], set(), set()] for k in names}
     for _ in range(args.steps):
         for k in names:
@@ -337,14 +340,15 @@ def learned_bench(args, rank, local):
             "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot["learned"][0] / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "learned-preconditioner family shrunk to n=500 m=801 (1 zero row, R+ blocks, "
-                                   "one SOC of 20% of the rows, dense P); 40 training and 8 held-out instances; "
-                                   "VJP of ||x*||^2 at rtol 1e-6",
+            "config": {"workload": (f"learned-preconditioner family n={fam.n} m={fam.m} (scale {args.scale} of "
+                                    "n=5000 m=8000: 1 zero row, R+ blocks, one SOC of 25% of the rows, dense "
+                                    f"P = F^T F + diag); {args.train} training and {args.held} held-out instances; "
+                                    "VJP of ||x*||^2 at rtol 1e-6"),
                        "alpha": lp.alpha, "rows": rows,
                        "learned_over_plain": rate["learned"] / rate["plain"],
                        "learned_over_c_alpha": rate["learned"] / rate["c_alpha"],
                        "learned_over_best_plain": rate["learned"] / rate["best_plain"],
-                       "training": "40 instances, 800 Adam steps on the GPU (untimed)"},
+                       "training": f"{args.train} instances, 800 Adam steps on the GPU (untimed)"},
             "gpu_launches": None, "e2e": None, "roofline": None, "cpu_baseline": None}), flush=True)
     for pl in plans:
         pl.close()
@@ -484,6 +488,10 @@ def main():
     ap.add_argument("--precond", default="equilibrate", choices=["equilibrate", "none"])
     ap.add_argument("--workload", default="config3",
                     choices=["config1", "config2", "config3", "example", "cones", "learned", "config4"])
+    ap.add_argument("--scale", type=float, default=0.1,
+                    help="learned: size of the family relative to n=5000, m=8000 (1.0: the full size)")
+    ap.add_argument("--train", type=int, default=40, help="learned: training instances")
+    ap.add_argument("--held", type=int, default=8, help="learned: held-out instances timed")
     ap.add_argument("--problems", type=int, default=32,
                     help="config4: how many of the batch's problems (drawn from their own streams, from 0)")
     ap.add_argument("--engine", default="auto", choices=["auto", "cluster", "cluster_fp64", "passes", "persistent"])
