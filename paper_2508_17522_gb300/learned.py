@@ -11,8 +11,8 @@ mean and spread, minibatch indices) with torch tensor operations:
 
 1. For each training instance of a family (fixed sparsity pattern, the
    rows line up across instances), solve the adjoint problem of ||x*||^2
-   with the plain method and read back its solution r and the plan's column
-   equilibration c.
+   (equilibrated, on the fastest engine) and read back its solution r and
+   the plan's column equilibration c.
 2. Choose the preconditioner C = c^alpha: alpha in {0, 1/4, 1/2, 3/4, 1}
    with the fewest iterations on the first training instances (on this
    family full equilibration is slower than none, c^(1/2) faster).
@@ -161,10 +161,12 @@ def adjoint_direction(prob):
 
 def training_rows(prob, device="cuda", rtol=1e-10):
     """(features, r / ||w||, c, info) of one instance from the method's own
-    plain adjoint solve."""
+    adjoint solve (equilibrated, on the fastest engine: the solution r does
+    not depend on how the solve is preconditioned)."""
     plan = api.qcp_plan_create(api.problem_tensors(prob, device), torch.float64)
     wx, wy, ws = adjoint_direction(prob)
-    _, _, _, _, info = api.qcp_derivative_vjp(plan, wx, wy, ws, api.options(rtol=rtol, engine="passes"))
+    _, _, _, _, info = api.qcp_derivative_vjp(plan, wx, wy, ws,
+                                              api.options(rtol=rtol, precond="equilibrate", engine="auto"))
     r = last_solution(plan)
     _, c = plan_scalings(plan)
     f = plan_features(plan)
@@ -176,7 +178,7 @@ def training_rows(prob, device="cuda", rtol=1e-10):
 def _iterations(prob, device, **opts):
     plan = api.qcp_plan_create(api.problem_tensors(prob, device), torch.float64)
     wx, wy, ws = adjoint_direction(prob)
-    *_, info = api.qcp_derivative_vjp(plan, wx, wy, ws, api.options(rtol=1e-6, engine="passes", **opts))
+    *_, info = api.qcp_derivative_vjp(plan, wx, wy, ws, api.options(rtol=1e-6, engine="auto", **opts))
     plan.close()
     return info[0]["iters"] if info[0]["status"] == "QCP_OK" else 10 ** 9
 
