@@ -56,8 +56,9 @@
  *             x^a y^(1-a) >= |z|}, dim 3, exponent a from K.param), both of
  *             Appendix A (the method projects onto their duals).  Plans with
  *             PSD, exponential or power blocks run on the pass and
- *             persistent engines, and on the stream engine (LSQR; PSD
- *             orders up to 22) with each such block's D Pi stored dense.
+ *             persistent engines, and on the stream and (double-float)
+ *             cluster engines with each such block's D Pi stored dense
+ *             (PSD orders up to 22).
  *  Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
  *             All work of a plan is enqueued on the stream given at creation.
  *             JVP/VJP calls return when the outputs are written: they
@@ -166,14 +167,16 @@ typedef enum {
                                    in one launch; the Krylov vectors live in the cluster's shared
                                    memory and only hardware cluster barriers separate passes.
                                    Needs every system to fit (about 8 N + 60 N / C bytes per CTA
-                                   for C CTAs) and the cones to be zero, R+ and SOC blocks; LSQR
-                                   only (any qcp_precond); QCP_ERR_ARG otherwise */
+                                   for C CTAs); zero, R+ and SOC blocks, and PSD (order <= 22),
+                                   exponential and power blocks through their dense D Pi (the
+                                   double-float kernel only); LSQR only (any qcp_precond);
+                                   QCP_ERR_ARG otherwise */
     QCP_ENGINE_AUTO = 3,        /* the plan's autotuned engine when qcp_plan_autotune has run, else
                                    QCP_ENGINE_CLUSTER; a cluster choice becomes STREAM when a system
                                    does not fit the cluster engine (PASSES where STREAM cannot run
-                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI); LSMR and plans with
-                                   PSD, exponential or power blocks never run on the cluster engine,
-                                   so they go to STREAM where it can run them, else PASSES */
+                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI); LSMR never runs on
+                                   the cluster engine, so it goes to STREAM where that can run the
+                                   plan, else PASSES */
     QCP_ENGINE_CLUSTER_FP64 = 4, /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "qcpd_cluster.h"
+#include "qcpd_stream.h"
 
 namespace qcpd {
 
@@ -441,7 +442,10 @@ static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
     QCP_TRY(cluster_smem_limit(&limit));
     std::unique_ptr<ClusterLayout> lay(new ClusterLayout());
     lay->hp.resize(p->nprob);
-    lay->fits = p->kpsd == 0 && p->ndense == 0;  // the cluster kernels apply D Pi to R+, zero and SOC blocks only
+    // exponential, power and PSD blocks: their dense D Pi (df64, the
+    // double-float kernel only)
+    lay->fits = true;
+    if (p->kpsd || p->ndense) QCP_TRY(dense_dpi_ready(p, &lay->fits));
     for (int pi = 0; pi < p->nprob; ++pi) {
         bool ok = false;
         const Prob& pr = p->hprob[pi];
@@ -461,6 +465,7 @@ static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
         if (!ok) lay->fits = false;
     }
     if (lay->fits) QCP_TRY(build_sell(p, lay.get()));
+    if (lay->fits && (p->kpsd || p->ndense) && !lay->df_ok) lay->fits = false;  // the FP64 kernel has no dense D Pi
     *out = lay.get();
     p->clusters.emplace(cap, std::move(lay));
     return QCP_OK;
@@ -546,6 +551,10 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
     const bool diag = p->view_precond == QCP_PRECOND_DIAG;
     if (diag) QCP_TRY(refresh_diag<T>(p, lay));
     const bool use_df = lay->df_ok && (!diag || lay->diag_df_ok) && opts.engine != QCP_ENGINE_CLUSTER_FP64;
+    if (!use_df && (p->kpsd || p->ndense)) {
+        set_error("the FP64 cluster kernel applies D Pi to zero, R+ and SOC blocks only");
+        return QCP_ERR_ARG;
+    }
     if (use_df && p->d_bcast.bytes < bneed) QCP_TRY(p->d_bcast.alloc(bneed));
     QCP_CUDA(cudaMemcpyAsync(p->d_csys.p, p->h_csys.data(), sizeof(int32_t) * p->h_csys.size(),
                              cudaMemcpyHostToDevice, st));
@@ -608,6 +617,9 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
             da.cd = diag ? lay->d_dcdD.as<df>() : lay->d_dcd.as<df>();
             da.zy = lay->d_dzy.as<df>();
             da.soc = lay->d_dsoc.as<SocDf>();
+            const bool dense = p->kpsd || p->ndense;
+            da.dense = dense ? p->d_dpi.as<df>() : nullptr;
+            da.doff = dense ? p->d_dpi_off.as<int64_t>() : nullptr;
             auto fn = mode == 0 ? cluster_kernel_df<0, T>(vs.scaled != 0) : cluster_kernel_df<1, T>(vs.scaled != 0);
             QCP_TRY(prepare_launch(fn, C, bytes, cfg));
             QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, vs, ca, da));

@@ -48,6 +48,8 @@ struct ClusterDfArgs {
     const df* cd;
     const df* zy;
     const SocDf* soc;  // per SOC block (plan-wide indices)
+    const df* dense;        // the exponential, power and PSD blocks' dense D Pi (row-major; null: none)
+    const int64_t* doff;    // per coupled block (plan-wide): its offset in dense, -1 for SOC blocks
 };
 
 // This pass's scalars: FP64 for the finisher, df64 for the vector work.
@@ -73,6 +75,7 @@ struct CCtxDf {
     const int8_t* flag;
     const SocBlock* blocks;
     const SocDf* soc;
+    const df* dense;  // the stored dense D Pi (offsets in bs[].w)
     df* W;  // the plan's w and x rows of this system, as df64 pairs
     df* X;
     df* B;  // the system's broadcast buffers (bhalf entries each)
@@ -128,7 +131,12 @@ __device__ __forceinline__ void apply_D_rows_df(const CCtxDf& c, const df* src, 
             dst[i] = df_zero();
         } else {
             const int4 B = c.bs[rb];
-            if (B.z == 0) {
+            if (B.w >= 0) {  // exponential, power or PSD block: its stored dense D Pi, in j order
+                const df* D = c.dense + B.w + (int64_t)(i - B.x) * B.y;
+                df acc = df_zero();
+                for (int j = 0; j < B.y; ++j) acc = df_fma(__ldg(reinterpret_cast<const float2*>(D + j)), src[B.x + j], acc);
+                dst[i] = acc;
+            } else if (B.z == 0) {
                 dst[i] = df_zero();
             } else if (B.z == 1) {
                 dst[i] = src[i];
@@ -539,6 +547,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
     c.flag = a.flag + pr.doff;
     c.blocks = a.blocks + pr.soff;
     c.soc = da.soc + pr.soff;
+    c.dense = da.dense;
     c.W = reinterpret_cast<df*>(gW);
     c.X = reinterpret_cast<df*>(gX);
     c.B = da.bcast + (int64_t)(blockIdx.x / C) * 2 * da.bhalf;
@@ -583,7 +592,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
         }
         for (int j = tid; j < c.cb1 - c.cb0; j += kCThreads) {
             const SocBlock B = c.blocks[c.cb0 + j];
-            c.bs[j] = make_int4(B.start - c.R0, B.dim, B.kase, 0);
+            c.bs[j] = make_int4(B.start - c.R0, B.dim, B.kase, da.doff ? (int)da.doff[pr.soff + c.cb0 + j] : -1);
             c.bsdf[j] = c.soc[c.cb0 + j];
         }
         __syncthreads();

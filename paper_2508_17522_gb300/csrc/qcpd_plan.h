@@ -132,7 +132,6 @@ struct StreamLayout {
     DevBuf d_scal, d_ssys, d_cpart, d_ccnt, d_lchunk, d_lcnt, d_lrow;
     DevBuf d_slist, d_scount;        // the systems (or pairs) still iterating, their number
     DevBuf d_pshared;                // paired launches: system passes that shared their read of M
-    DevBuf d_doff, d_dense;          // per coupled block: offset of its stored dense D Pi (-1: none); the D Pi
 };
 
 }  // namespace qcpd
@@ -158,6 +157,13 @@ struct qcp_plan {
     qcpd::DevBuf d_psd;   // PSD blocks: eigenvectors V and D Pi weights B, 2 k^2 doubles each; exp blocks: D Pi
     int kpsd = 0;         // largest PSD block order (0: no PSD block)
     int ndense = 0;       // exponential-cone blocks (D Pi stored as a dense 3 x 3 in d_psd)
+    // the exponential, power and PSD blocks' D Pi as dense df64 matrices for the
+    // double-float engines (stream, cluster): offsets per coupled block (-1 for
+    // SOC blocks) and the row-major matrices; dpi_state 0 not built, 1 built,
+    // -1 unusable (dpi_why says why)
+    qcpd::DevBuf d_dpi_off, d_dpi;
+    int dpi_state = 0;
+    std::string dpi_why;
     qcpd::DevBuf d_rw, d_cd, d_mvalG, d_mvalT;   // equilibration: row/column scalings, scaled values
     qcpd::DevBuf d_cdD, d_onesD, d_mvalD;        // QCP_PRECOND_DIAG: the caller's C, unit W, M diag(C)
     qcpd::DevBuf d_cdJ;                          // QCP_PRECOND_JACOBI: 1 / column norms of F (made on first use)

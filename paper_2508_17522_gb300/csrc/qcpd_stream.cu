@@ -334,6 +334,55 @@ static bool build_units(const qcp_plan* p, StreamLayout* lay, std::vector<Stream
     return true;
 }
 
+int dense_dpi_ready(qcp_plan* p, bool* ok) {
+    if (p->dpi_state == 0) {
+        std::vector<int64_t> hoff((size_t)std::max<int64_t>(p->nsoc_tot, 1), -1);
+        int64_t total = 0;
+        bool fit = true;
+        for (int pi = 0; pi < p->nprob; ++pi) {
+            int64_t bi = p->hprob[pi].soff;
+            for (size_t c = 0; c < p->cone_type[pi].size(); ++c) {
+                const int t = p->cone_type[pi][c], d = p->cone_dim[pi][c];
+                if (t == QCP_CONE_ZERO || t == QCP_CONE_NONNEG) continue;
+                if (t != QCP_CONE_SOC) {
+                    if (d > kSSocBig) fit = false;
+                    hoff[bi] = total;
+                    total += (int64_t)d * d;
+                }
+                ++bi;
+            }
+        }
+        p->dpi_state = -1;
+        if (!fit) {
+            p->dpi_why = "a PSD block has more than 256 entries (order above 22)";
+        } else if (total > (int64_t)1 << 28) {
+            p->dpi_why = "the dense D Pi of the exponential, power and PSD blocks would exceed 2 GB";
+        } else {
+            cudaStream_t st = p->stream;
+            QCP_TRY(p->d_dpi_off.alloc(sizeof(int64_t) * hoff.size()));
+            QCP_CUDA(cudaMemcpyAsync(p->d_dpi_off.p, hoff.data(), sizeof(int64_t) * hoff.size(),
+                                     cudaMemcpyHostToDevice, st));
+            QCP_TRY(p->d_dpi.alloc(sizeof(df) * (size_t)std::max<int64_t>(total, 1)));
+            DevBuf bad;
+            QCP_TRY(bad.alloc(sizeof(int)));
+            QCP_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            if (total > 0)
+                k_stream_dense<<<(unsigned)p->nsoc_tot, 128, 0, st>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot,
+                                                                      p->d_dpi_off.as<int64_t>(),
+                                                                      p->d_psd.as<double>(), p->d_dpi.as<df>(),
+                                                                      bad.as<int>());
+            QCP_CUDA(cudaGetLastError());
+            int hbad = 1;
+            QCP_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            QCP_CUDA(cudaStreamSynchronize(st));
+            if (hbad == 0) p->dpi_state = 1;
+            else p->dpi_why = "an entry of a stored D Pi lies above the double-float range";
+        }
+    }
+    *ok = p->dpi_state > 0;
+    return QCP_OK;
+}
+
 template <typename T>
 static int build_stream(qcp_plan* p, StreamLayout* lay) {
     std::vector<StreamUnit> hu;
@@ -377,37 +426,22 @@ static int build_stream(qcp_plan* p, StreamLayout* lay) {
     QCP_TRY(todf(p->d_rw, lay->d_rw));
     QCP_TRY(todf(p->d_cd, lay->d_cd));
     QCP_TRY(todf(p->d_zy, lay->d_zy));
-    // the coupled blocks' constants; exponential, power and PSD blocks get a
-    // dense D Pi (offsets in block order, problems in order)
-    std::vector<int64_t> hdoff((size_t)std::max<int64_t>(p->nsoc_tot, 1), -1);
-    int64_t ndense = 0;
-    for (int pi = 0; pi < p->nprob; ++pi) {
-        int64_t bi = p->hprob[pi].soff;
-        for (size_t c = 0; c < p->cone_type[pi].size(); ++c) {
-            const int t = p->cone_type[pi][c], d = p->cone_dim[pi][c];
-            if (t == QCP_CONE_ZERO || t == QCP_CONE_NONNEG) continue;
-            if (t != QCP_CONE_SOC) {
-                hdoff[bi] = ndense;
-                ndense += (int64_t)d * d;
-            }
-            ++bi;
-        }
-    }
-    if (ndense > (int64_t)1 << 28) {
-        lay->why = "the stored D Pi of the exponential, power and PSD blocks would exceed 2 GB";
+    // the coupled blocks' constants; exponential, power and PSD blocks get
+    // their dense D Pi (plan-wide, shared with the cluster engine)
+    bool dok = true;
+    if (p->kpsd || p->ndense) QCP_TRY(dense_dpi_ready(p, &dok));
+    if (!dok) {
+        lay->why = p->dpi_why;
         return QCP_OK;
     }
-    QCP_TRY(up(lay->d_doff, hdoff.data(), sizeof(int64_t) * hdoff.size()));
-    QCP_TRY(lay->d_dense.alloc(sizeof(df) * (size_t)std::max<int64_t>(ndense, 1)));
-    QCP_TRY(lay->d_soc.alloc(sizeof(StreamSoc) * (size_t)std::max<int64_t>(p->nsoc_tot, 1)));
-    if (p->nsoc_tot > 0) {
-        k_stream_soc<<<grid_of(p->nsoc_tot), 256, 0, st>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot,
-                                                            lay->d_doff.as<int64_t>(), lay->d_soc.as<StreamSoc>(), b);
-        if (ndense > 0)
-            k_stream_dense<<<(unsigned)p->nsoc_tot, 128, 0, st>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot,
-                                                                  lay->d_doff.as<int64_t>(), p->d_psd.as<double>(),
-                                                                  lay->d_dense.as<df>(), b);
+    if (!p->d_dpi_off.p) {  // no such blocks: every offset -1
+        std::vector<int64_t> none((size_t)std::max<int64_t>(p->nsoc_tot, 1), -1);
+        QCP_TRY(up(p->d_dpi_off, none.data(), sizeof(int64_t) * none.size()));
     }
+    QCP_TRY(lay->d_soc.alloc(sizeof(StreamSoc) * (size_t)std::max<int64_t>(p->nsoc_tot, 1)));
+    if (p->nsoc_tot > 0)
+        k_stream_soc<<<grid_of(p->nsoc_tot), 256, 0, st>>>(p->d_blocks.as<SocBlock>(), p->nsoc_tot,
+                                                            p->d_dpi_off.as<int64_t>(), lay->d_soc.as<StreamSoc>(), b);
     QCP_CUDA(cudaGetLastError());
     // per-system workspace: CTAs per system up to the number resident at once
     int dev = 0, nsm = 0, occ = 0;
@@ -470,7 +504,7 @@ static StreamArgs stream_args(qcp_plan* p, const StreamLayout* lay, int scaled) 
     a.zy = lay->d_zy.as<df>();
     a.flag = p->d_flag.as<int8_t>();
     a.soc = lay->d_soc.as<StreamSoc>();
-    a.dense = lay->d_dense.as<df>();
+    a.dense = p->d_dpi.as<df>();
     a.rwd = p->d_rw.as<double>();
     a.cdd = p->d_cd.as<double>();
     a.sys = p->d_sys.as<Sys>();

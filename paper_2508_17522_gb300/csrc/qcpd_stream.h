@@ -12,6 +12,15 @@ namespace qcpd {
 // qcp_last_error says why.
 int stream_ready(qcp_plan* p, bool* ok);
 
+// Builds once the dense D Pi of the plan's exponential, power and PSD blocks
+// as df64 matrices (p->d_dpi, row-major, at p->d_dpi_off[block] for each
+// coupled block, -1 for SOC blocks): exponential and power blocks copy
+// their stored 3 x 3, a PSD block applies the pass engine's map to each unit
+// vector of its entries.  *ok false (p->dpi_why says why) for a PSD block of
+// more than 256 entries, more than 2 GB of matrices, or an entry above the
+// double-float range.  The stream and cluster engines apply them.
+int dense_dpi_ready(qcp_plan* p, bool* ok);
+
 // Runs the remaining LSQR iterations of systems [s0, s0 + ns) in one mode
 // (0 JVP, 1 VJP), the range's active counter at `active`: converts the
 // Krylov vectors to df64 pairs, iterates in chunks of check_every

@@ -3,8 +3,8 @@ dual cone made at plan time per block (Moreau: I - D Pi_K(-z); the
 exponential cone's nearest boundary ray by a scan and bisection and its
 derivative from the optimality conditions' Jacobian; the power cone's root
 r by bisection and the printed derivative formula) and applied as a dense
-3 x 3 per pass, on the pass, persistent and stream engines (the stream
-engine in double-float), against the CPU FP64 oracle (its own searches, pinned by membership, orthogonality and finite
+3 x 3 per pass, on the pass, persistent, stream and cluster engines (the
+last two in double-float), against the CPU FP64 oracle (its own searches, pinned by membership, orthogonality and finite
 differences)."""
 import numpy as np
 import pytest
@@ -42,21 +42,24 @@ def test_exp_jvp_vjp_match_oracle(q, name, mk, precond):
     rj = D.jvp_dense(prob, d, fac)[:3]
     rv = D.vjp_dense(prob, d, fac)[:4]
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
-    for engine in ("auto", "persistent", "stream"):
+    for engine in ("auto", "persistent", "stream", "cluster"):
         for solver in ("lsqr", "lsmr"):
+            if engine == "cluster" and solver == "lsmr":
+                continue  # the cluster engine runs LSQR
             opts = q.options(rtol=1e-11, precond=precond, engine=engine, solver=solver)
             jv, ji = gpu_jvp(q, plan, d, opts)
             vv, vi = gpu_vjp(q, plan, d, opts)
-            # auto: the stream engine (double-float, the cones' D Pi stored
-            # dense), the pass engine with the Jacobi scaling
-            want = {"persistent": "persistent", "stream": "stream"}.get(
-                engine, "stream" if precond != "jacobi" else "passes")
+            # auto: the cluster engine for LSQR (these problems fit it), the
+            # stream engine for LSMR (the pass engine with the Jacobi scaling);
+            # both apply the cones' D Pi as stored dense matrices in df64
+            auto = "cluster" if solver == "lsqr" else ("stream" if precond != "jacobi" else "passes")
+            want = {"persistent": "persistent", "stream": "stream", "cluster": "cluster"}.get(engine, auto)
             assert plan.last_engine() == want, (engine, solver, plan.last_engine())
             assert rel_err(jv, rj) < TOL64, (engine, solver, rel_err(jv, rj), ji)
             assert rel_err(vv, rv) < TOL64, (engine, solver, rel_err(vv, rv), vi)
             assert adjoint_gap(prob, d, jv, vv) < 1e-8
-    with pytest.raises(RuntimeError):
-        gpu_jvp(q, plan, d, q.options(engine="cluster"))
+    with pytest.raises(RuntimeError):  # the FP64 cluster kernel has no dense D Pi
+        gpu_jvp(q, plan, d, q.options(engine="cluster_fp64"))
     plan.close()
 
 

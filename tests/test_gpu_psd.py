@@ -1,7 +1,7 @@
 """The positive semidefinite cone (Appendix A) on the GPU: D Pi_psd = V (B o
 (V^T dZ V)) V^T with the eigendecomposition made at plan time, on the pass
-and persistent engines, and on the stream engine as the dense matrix of
-that map (made at plan time from the same V and B, applied in
+and persistent engines, and on the stream and cluster engines as the dense
+matrix of that map (made at plan time from the same V and B, applied in
 double-float), against the CPU FP64 oracle (which uses its own
 eigendecomposition and the same formula, and is pinned by finite
 differences of re-solves)."""
@@ -37,17 +37,20 @@ def test_psd_jvp_vjp_match_oracle(q, name, mk, precond):
     rj = D.jvp_dense(prob, d, fac)[:3]
     rv = D.vjp_dense(prob, d, fac)[:4]
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
-    for engine in ("auto", "persistent", "stream"):
+    for engine in ("auto", "persistent", "stream", "cluster"):
         for solver in ("lsqr", "lsmr"):
+            if engine == "cluster" and solver == "lsmr":
+                continue  # the cluster engine runs LSQR
             if engine == "stream" and precond == "jacobi":
                 continue  # the stream engine runs unscaled or equilibrated
             opts = q.options(rtol=1e-11, precond=precond, engine=engine, solver=solver)
             jv, ji = gpu_jvp(q, plan, d, opts)
             vv, vi = gpu_vjp(q, plan, d, opts)
-            # auto: the stream engine (double-float, the cones' D Pi stored
-            # dense), the pass engine with the Jacobi scaling
-            want = {"persistent": "persistent", "stream": "stream"}.get(
-                engine, "stream" if precond != "jacobi" else "passes")
+            # auto: the cluster engine for LSQR (these problems fit it), the
+            # stream engine for LSMR (the pass engine with the Jacobi scaling);
+            # both apply the cones' D Pi as stored dense matrices in df64
+            auto = "cluster" if solver == "lsqr" else ("stream" if precond != "jacobi" else "passes")
+            want = {"persistent": "persistent", "stream": "stream", "cluster": "cluster"}.get(engine, auto)
             assert plan.last_engine() == want, (engine, solver, plan.last_engine())
             assert rel_err(jv, rj) < TOL64, (engine, solver, rel_err(jv, rj), ji)
             assert rel_err(vv, rv) < TOL64, (engine, solver, rel_err(vv, rv), vi)
@@ -60,7 +63,7 @@ def test_psd_jvp_vjp_match_oracle(q, name, mk, precond):
 
 
 def test_psd_plan_rules(q):
-    """The cluster engines refuse PSD plans, the kink margin is the smallest
+    """The FP64 cluster kernel refuses PSD plans, the kink margin is the smallest
     |eigenvalue| of z_y on the PSD blocks (or a smaller R+/SOC margin), and
     malformed PSD sizes are rejected."""
     from oracle import cones as C
@@ -68,7 +71,7 @@ def test_psd_plan_rules(q):
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
     d = g.make_directions(prob, 3)
     with pytest.raises(RuntimeError):
-        gpu_jvp(q, plan, d, q.options(engine="cluster"))
+        gpu_jvp(q, plan, d, q.options(engine="cluster_fp64"))
     _, info = gpu_jvp(q, plan, d, q.options(rtol=1e-10))
     zy = prob.y - prob.s
     want = C.kink_margin(prob.cones, zy)
