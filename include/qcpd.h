@@ -168,15 +168,13 @@ typedef enum {
                                    memory and only hardware cluster barriers separate passes.
                                    Needs every system to fit (about 8 N + 60 N / C bytes per CTA
                                    for C CTAs); zero, R+ and SOC blocks, and PSD (order <= 22),
-                                   exponential and power blocks through their dense D Pi (the
-                                   double-float kernel only); LSQR only (any qcp_precond);
+                                   exponential and power blocks through their dense D Pi, and LSMR
+                                   (the last two on the double-float kernel only; any qcp_precond);
                                    QCP_ERR_ARG otherwise */
     QCP_ENGINE_AUTO = 3,        /* the plan's autotuned engine when qcp_plan_autotune has run, else
                                    QCP_ENGINE_CLUSTER; a cluster choice becomes STREAM when a system
                                    does not fit the cluster engine (PASSES where STREAM cannot run
-                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI); LSMR never runs on
-                                   the cluster engine, so it goes to STREAM where that can run the
-                                   plan, else PASSES */
+                                   the plan, and for QCP_PRECOND_DIAG / _JACOBI) */
     QCP_ENGINE_CLUSTER_FP64 = 4, /* QCP_ENGINE_CLUSTER with FP64 vector arithmetic.  The cluster engine
                                    otherwise computes its vector operations in double-float pairs of
                                    binary32 numbers (about 48 significant bits, on the FP32 pipes,
@@ -198,10 +196,10 @@ typedef enum {
 
 typedef struct {
     int32_t solver;           /* 0 = LSQR (Paige & Saunders 1982), 1 = LSMR (Fong & Saunders 2011; the
-                                 pass, persistent and stream engines: AUTO then runs the stream engine
-                                 where it can run the plan, else the pass engine; CLUSTER is an
-                                 error).  Both minimise the same ||Op x - b|| and stop on the same
-                                 estimate of ||r|| <= rtol ||b|| */
+                                 pass, persistent, stream and double-float cluster engines, AUTO
+                                 choosing as for LSQR; CLUSTER_FP64 is an error).  Both minimise
+                                 the same ||Op x - b|| and stop on the same estimate of
+                                 ||r|| <= rtol ||b|| */
     double rtol;              /* target for ||F dz + dN|| / ||dN|| (JVP) or ||F^T r + g|| / ||g|| (VJP) */
     int64_t maxiter;          /* iteration cap per system (counted over all restarts) */
     int32_t check_every;      /* iterations between host convergence checks; 0 = none */

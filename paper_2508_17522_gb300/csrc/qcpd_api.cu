@@ -376,8 +376,8 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
         set_error("solver must be 0 (LSQR) or 1 (LSMR)");
         return QCP_ERR_ARG;
     }
-    if (opts.solver == 1 && (opts.engine == QCP_ENGINE_CLUSTER || opts.engine == QCP_ENGINE_CLUSTER_FP64)) {
-        set_error("LSMR runs on the pass, persistent or stream engine");
+    if (opts.solver == 1 && opts.engine == QCP_ENGINE_CLUSTER_FP64) {
+        set_error("LSMR runs on the pass, persistent, stream or (double-float) cluster engine");
         return QCP_ERR_ARG;
     }
     if (opts.precond != QCP_PRECOND_NONE && opts.precond != QCP_PRECOND_EQUILIBRATE &&
@@ -421,16 +421,10 @@ static int solve(qcp_plan* p, const Seg<T>* segs, int nseg, const qcp_options* o
     // the stream engine takes no diagonal preconditioner: an autotuned choice of it becomes AUTO
     if (engine == QCP_ENGINE_STREAM && opts.engine == QCP_ENGINE_AUTO && opts.precond == QCP_PRECOND_DIAG)
         engine = QCP_ENGINE_AUTO;
-    if (opts.solver == 1 && engine == QCP_ENGINE_CLUSTER) engine = QCP_ENGINE_PASSES;
-    if (opts.solver == 1 && engine == QCP_ENGINE_AUTO) {
-        // LSMR: the cluster engine runs LSQR only; the stream engine where it can run the plan
-        bool sok = false;
-        if (opts.precond != QCP_PRECOND_DIAG) QCP_TRY(stream_ready(p, &sok));
-        engine = sok ? QCP_ENGINE_STREAM : QCP_ENGINE_PASSES;
-    }
+
     if (engine == QCP_ENGINE_CLUSTER || engine == QCP_ENGINE_AUTO || engine == QCP_ENGINE_CLUSTER_FP64) {
         bool fits = false;
-        QCP_TRY(cluster_ready(p, nsys, &fits));
+        QCP_TRY(cluster_ready(p, nsys, &fits, opts.solver == 1));
         if (fits) {
             engine = QCP_ENGINE_CLUSTER;
         } else if (engine != QCP_ENGINE_AUTO) {

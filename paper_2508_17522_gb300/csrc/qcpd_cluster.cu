@@ -190,6 +190,14 @@ static int cluster_smem_limit(size_t* out) {
     max_static_smem(k_cluster_df<0, true, float>, st);
     max_static_smem(k_cluster_df<1, false, float>, st);
     max_static_smem(k_cluster_df<1, true, float>, st);
+    max_static_smem(k_cluster_df<0, false, double, true>, st);
+    max_static_smem(k_cluster_df<0, true, double, true>, st);
+    max_static_smem(k_cluster_df<1, false, double, true>, st);
+    max_static_smem(k_cluster_df<1, true, double, true>, st);
+    max_static_smem(k_cluster_df<0, false, float, true>, st);
+    max_static_smem(k_cluster_df<0, true, float, true>, st);
+    max_static_smem(k_cluster_df<1, false, float, true>, st);
+    max_static_smem(k_cluster_df<1, true, float, true>, st);
     *out = (size_t)optin > st ? (size_t)optin - st : 0;
     return QCP_OK;
 }
@@ -473,10 +481,10 @@ static int get_layout(qcp_plan* p, int cap, ClusterLayout** out) {
 
 static int cap_for(const qcp_plan* p, int nsys) { return p->cluster_cap > 0 ? p->cluster_cap : auto_cap(nsys); }
 
-int cluster_ready(qcp_plan* p, int nsys, bool* ok) {
+int cluster_ready(qcp_plan* p, int nsys, bool* ok, bool need_df) {
     ClusterLayout* lay = nullptr;
     QCP_TRY(get_layout(p, cap_for(p, nsys), &lay));
-    *ok = lay->fits;
+    *ok = lay->fits && (!need_df || lay->df_ok);
     return QCP_OK;
 }
 
@@ -486,7 +494,8 @@ static auto cluster_kernel(bool scaled) -> void (*)(PlanView<T>, ClusterArgs) {
 }
 
 template <int MODE, typename T>
-static auto cluster_kernel_df(bool scaled) -> void (*)(PlanView<T>, ClusterArgs, ClusterDfArgs) {
+static auto cluster_kernel_df(bool scaled, bool lsmr) -> void (*)(PlanView<T>, ClusterArgs, ClusterDfArgs) {
+    if (lsmr) return scaled ? k_cluster_df<MODE, true, T, true> : k_cluster_df<MODE, false, T, true>;
     return scaled ? k_cluster_df<MODE, true, T> : k_cluster_df<MODE, false, T>;
 }
 
@@ -555,6 +564,10 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
         set_error("the FP64 cluster kernel applies D Pi to zero, R+ and SOC blocks only");
         return QCP_ERR_ARG;
     }
+    if (!use_df && opts.solver == 1) {
+        set_error("the FP64 cluster kernel runs LSQR only");
+        return QCP_ERR_ARG;
+    }
     if (use_df && p->d_bcast.bytes < bneed) QCP_TRY(p->d_bcast.alloc(bneed));
     QCP_CUDA(cudaMemcpyAsync(p->d_csys.p, p->h_csys.data(), sizeof(int32_t) * p->h_csys.size(),
                              cudaMemcpyHostToDevice, st));
@@ -620,7 +633,8 @@ int iterate_cluster(qcp_plan* p, const ClusterSeg* segs, int nseg, int nsys_call
             const bool dense = p->kpsd || p->ndense;
             da.dense = dense ? p->d_dpi.as<df>() : nullptr;
             da.doff = dense ? p->d_dpi_off.as<int64_t>() : nullptr;
-            auto fn = mode == 0 ? cluster_kernel_df<0, T>(vs.scaled != 0) : cluster_kernel_df<1, T>(vs.scaled != 0);
+            const bool ls = opts.solver == 1;
+            auto fn = mode == 0 ? cluster_kernel_df<0, T>(vs.scaled != 0, ls) : cluster_kernel_df<1, T>(vs.scaled != 0, ls);
             QCP_TRY(prepare_launch(fn, C, bytes, cfg));
             QCP_CUDA(cudaLaunchKernelEx(&cfg, fn, vs, ca, da));
         } else {

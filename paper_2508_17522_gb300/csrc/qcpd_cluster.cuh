@@ -116,7 +116,7 @@ __device__ __forceinline__ CSmem cluster_smem(double* base, int FN, int L) {
     return s;
 }
 
-enum TauSlot { TAU_U = 0, TAU_V = 1, TAU_W = 2, TAU_X = 3, TAU_XI = 4 };
+enum TauSlot { TAU_U = 0, TAU_V = 1, TAU_W = 2, TAU_X = 3, TAU_XI = 4, TAU_HB = 5 };  // TAU_HB: LSMR (df64 kernel)
 
 // What a pass leaves for the warp that finishes it during the next pass.
 struct Pending {

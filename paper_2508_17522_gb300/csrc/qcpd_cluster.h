@@ -8,8 +8,10 @@
 namespace qcpd {
 
 // Builds (once per requested cluster size) the cluster layouts of the plan's
-// problems; *ok tells whether every problem fits the shared-memory limit.
-int cluster_ready(qcp_plan* p, int nsys, bool* ok);
+// problems; *ok tells whether every problem fits the shared-memory limit
+// (and, with need_df, whether the double-float kernel can run the plan:
+// LSMR has no FP64 cluster kernel).
+int cluster_ready(qcp_plan* p, int nsys, bool* ok, bool need_df = false);
 
 // A range of systems [s0, s0 + ns) iterating one mode (0 JVP, 1 VJP);
 // seg is its index in the call (its active counter).

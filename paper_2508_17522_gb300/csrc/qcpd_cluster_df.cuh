@@ -54,8 +54,9 @@ struct ClusterDfArgs {
 
 // This pass's scalars: FP64 for the finisher, df64 for the vector work.
 struct PassScal {
-    double c1, c2, tin, tout, tt, wcoef, xcoef;
-    df dc1, dnc2, dnw, dxc, dtt;  // c1, -c2, -wcoef, xcoef, tt
+    double c1, c2, tin, tout, tt, wcoef, xcoef, hcoef;
+    df dc1, dnc2, dnw, dxc, dtt, dnhc;  // c1, -c2, -wcoef, xcoef, tt, -hcoef (LSMR)
+    int upd;                            // LSMR: this u-pass applies the deferred (hbar, x, h) updates
 };
 
 struct CCtxDf {
@@ -78,6 +79,7 @@ struct CCtxDf {
     const df* dense;  // the stored dense D Pi (offsets in bs[].w)
     df* W;  // the plan's w and x rows of this system, as df64 pairs
     df* X;
+    df* HB;  // LSMR: hbar (W holds h), as df64 pairs
     df* B;  // the system's broadcast buffers (bhalf entries each)
     int64_t bhalf;
     bool any_large;
@@ -237,7 +239,7 @@ __device__ __forceinline__ void sell_rowsums_df(const CCtxDf& c, const df* sval,
 }
 
 // Lane 0 of warp 0: this pass's scalars from the state and tau entries.
-template <int PASS, int ROLE, bool SC>
+template <int PASS, int ROLE, bool SC, bool LS>
 __device__ __forceinline__ void prep_scalars_df(const CCtxDf& c) {
     const LsqrState& st = *c.st;
     PassScal p;
@@ -253,12 +255,34 @@ __device__ __forceinline__ void prep_scalars_df(const CCtxDf& c) {
     p.dnw = df_from(-p.wcoef);
     p.dxc = df_from(p.xcoef);
     p.dtt = df_from(p.tt);
+    p.hcoef = LS ? st.hcoef : 0.0;
+    p.dnhc = df_from(-p.hcoef);
+    p.upd = LS && ROLE == ROLE_U ? st.upd : 0;
     *c.ps = p;
+}
+
+// LSMR's deferred updates of the tau entries (run_tile's lsmr_update):
+// hbar <- h - hcoef hbar, x <- x + xcoef hbar, h <- v / alpha - wcoef h.
+__device__ __forceinline__ void lsmr_tau_update(const CCtxDf& c, const PassScal& pd) {
+    const double h = c.tau[TAU_W];
+    const double hb = fma(-pd.hcoef, c.tau[TAU_HB], h);
+    c.tau[TAU_HB] = hb;
+    c.tau[TAU_X] = fma(pd.xcoef, hb, c.tau[TAU_X]);
+    c.tau[TAU_W] = fma(pd.tin, pd.c1, -pd.wcoef * h);
+}
+
+// LSMR's deferred updates of row r (the df64 form of lsmr_update).
+__device__ __forceinline__ void lsmr_row_update(const CCtxDf& c, int r, df iv, const PassScal& ps) {
+    const df h = c.W[r];
+    const df hb = df_fma(ps.dnhc, c.HB[r], h);
+    c.HB[r] = hb;
+    c.X[r] = df_fma(ps.dxc, hb, c.X[r]);
+    c.W[r] = df_fma(iv, ps.dc1, df_mul(ps.dnw, h));
 }
 
 // The end of the previous pass (kind PASS, ROLE) by warp 0, as in
 // cluster_finish, with the sums converted to FP64 once.
-template <int PASS, int ROLE, bool SC>
+template <int PASS, int ROLE, bool SC, bool LS>
 __device__ __forceinline__ void cluster_finish_df(const CCtxDf& c, const int par) {
     cg::cluster_group cl = cg::this_cluster();
     const int lane = threadIdx.x & 31;
@@ -300,7 +324,14 @@ __device__ __forceinline__ void cluster_finish_df(const CCtxDf& c, const int par
     const double nsq = fma(nvN, nvN, sa);
     double nrm, inv_nrm;
     norm_and_inverse(nsq, nrm, inv_nrm);
-    if (ROLE == ROLE_U) {
+    if (LS) {  // LSMR (Fong & Saunders 2011): the pass engine's recurrences
+        if (ROLE == ROLE_U) {
+            if (pd.upd) lsmr_tau_update(c, pd);
+            if (lsmr_step_u(&st, nrm, inv_nrm) && c.rank == 0) atomicSub(c.active, 1);
+        } else {
+            if (lsmr_step_v(&st, nrm, inv_nrm) && c.rank == 0) atomicSub(c.active, 1);
+        }
+    } else if (ROLE == ROLE_U) {
         c.tau[TAU_W] = pd.tin * pd.c1 - pd.wcoef * c.tau[TAU_W];
         lsqr_step_u(&st, nrm, inv_nrm, nsq);
     } else {
@@ -309,7 +340,7 @@ __device__ __forceinline__ void cluster_finish_df(const CCtxDf& c, const int par
     }
 }
 
-template <int PASS, int ROLE, bool SC>
+template <int PASS, int ROLE, bool SC, bool LS>
 __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, const bool pending) {
     constexpr int PPASS = (PASS == PASS_G) ? PASS_GT : PASS_G;
     constexpr int PROLE = (ROLE == ROLE_U) ? ROLE_V : ROLE_U;
@@ -317,8 +348,8 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
     const int tid = threadIdx.x;
     df* s0 = c.s0;
     if (tid < 32) {
-        if (pending) cluster_finish_df<PPASS, PROLE, SC>(c, par ^ 1);
-        if (tid == 0) prep_scalars_df<PASS, ROLE, SC>(c);
+        if (pending) cluster_finish_df<PPASS, PROLE, SC, LS>(c, par ^ 1);
+        if (tid == 0) prep_scalars_df<PASS, ROLE, SC, LS>(c);
     } else {
         if (pending) {
             // the previous pass's vector, from its broadcast buffer (L2)
@@ -349,14 +380,23 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
     const int status = st.status;
     if (status == S_DONE) return true;
     const PassScal ps = *c.ps;
-    if (ROLE == ROLE_V && status == S_FINAL) {
+    // a stopped system's last deferred update: LSQR's x-update in its
+    // v-pass, LSMR's (hbar, x, h) updates in its u-pass
+    if (status == S_FINAL && (ROLE == ROLE_V) == !LS) {
+        const df* vin = (ROLE == ROLE_U) ? c.V : c.U;
         for (int i = tid; i < c.L; i += kCThreads) {
             const int r = c.R0 + i;
-            c.X[r] = df_fma(ps.dxc, c.W[r], c.X[r]);
+            if (!LS) c.X[r] = df_fma(ps.dxc, c.W[r], c.X[r]);
+            else lsmr_row_update(c, r, vin[i], ps);
         }
         __syncthreads();
         if (tid == 0) {
-            c.tau[TAU_X] = fma(ps.xcoef, c.tau[TAU_W], c.tau[TAU_X]);
+            if (!LS) {
+                c.tau[TAU_X] = fma(ps.xcoef, c.tau[TAU_W], c.tau[TAU_X]);
+            } else {
+                lsmr_tau_update(c, ps);
+                st.upd = 0;  // applied: a continuation starts with a plain u-pass
+            }
             st.status = S_DONE;
             if (c.rank == 0) atomicSub(c.active, 1);
         }
@@ -386,7 +426,7 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             v.cd = SC ? c.cd[r] : df_zero();
             v.rw = SC ? c.rw[r] : df_zero();
             v.w = c.W[r];
-            v.x = ROLE == ROLE_V ? c.X[r] : df_zero();
+            v.x = ROLE == ROLE_V && !LS ? c.X[r] : df_zero();
             return v;
         };
         auto row = [&](int i, const RowIn& v) {
@@ -407,8 +447,12 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             out_s[i] = nv;
             bout[i] = nv;
             dfacc_fma(ss, nv, nv);
-            if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c1, df_mul(nw, v.w));
-            else c.X[r] = df_fma(xc, v.w, v.x);
+            if (ROLE == ROLE_U) {
+                if (!LS) c.W[r] = df_fma(iv, c1, df_mul(nw, v.w));
+                else if (ps.upd) lsmr_row_update(c, r, iv, ps);
+            } else if (!LS) {
+                c.X[r] = df_fma(xc, v.w, v.x);
+            }
         };
         for (int i = tid; i < L; i += kCThreads) row(i, load(i));
     } else {
@@ -436,8 +480,12 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
             out_s[i] = nv;
             s1[i] = nv;
             dfacc_fma(ss, nv, nv);
-            if (ROLE == ROLE_U) c.W[r] = df_fma(iv, c1, df_mul(nw, c.W[r]));
-            else c.X[r] = df_fma(xc, c.W[r], c.X[r]);
+            if (ROLE == ROLE_U) {
+                if (!LS) c.W[r] = df_fma(iv, c1, df_mul(nw, c.W[r]));
+                else if (ps.upd) lsmr_row_update(c, r, iv, ps);
+            } else if (!LS) {
+                c.X[r] = df_fma(xc, c.W[r], c.X[r]);
+            }
         }
         __syncthreads();
         apply_D_rows_df(c, s1, s2);
@@ -458,13 +506,13 @@ __device__ __forceinline__ bool cluster_pass_df(const CCtxDf& c, const int par, 
     return false;
 }
 
-template <int MODE, bool SC, typename T>
+template <int MODE, bool SC, typename T, bool LS = false>
 __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, ClusterArgs ca, ClusterDfArgs da) {
     extern __shared__ __align__(16) double csm[];
     __shared__ df scr[3 * kCThreads];
     __shared__ LsqrState st;
     __shared__ PassScal ps;
-    __shared__ double tau[5];
+    __shared__ double tau[6];
     __shared__ ClusterProb cp;
     __shared__ double s_scale;
     __shared__ int s_uscaled;
@@ -491,11 +539,13 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
         tau[TAU_W] = gW[rN];
         tau[TAU_X] = gX[rN];
         tau[TAU_XI] = gXI[rN];
+        tau[TAU_HB] = LS ? a.HB[sy.voff + rN] : 0.0;
         // scale the right-hand side to norm in [1/2, 1) by a power of two:
         // x, phibar, xcoef and bnorm are proportional to it, and so are u,
-        // beta and 1/uc2 before the first u-update
+        // beta and 1/uc2 before the first u-update (LSMR: no scaling, its
+        // recurrences carry many quantities proportional to ||b||)
         double s = 1.0;
-        if (st.bnorm > 0.0 && finite64(st.bnorm)) {
+        if (!LS && st.bnorm > 0.0 && finite64(st.bnorm)) {
             int e = 0;
             frexp(st.bnorm, &e);
             s = ldexp(1.0, -e);
@@ -550,6 +600,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
     c.dense = da.dense;
     c.W = reinterpret_cast<df*>(gW);
     c.X = reinterpret_cast<df*>(gX);
+    c.HB = reinterpret_cast<df*>(a.HB + sy.voff);
     c.B = da.bcast + (int64_t)(blockIdx.x / C) * 2 * da.bhalf;
     c.bhalf = da.bhalf;
     c.any_large = cp.nlarge[rank] > 0;
@@ -587,6 +638,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
             const double w = gW[r], x = gX[r] * sc;
             c.W[r] = df_from(w);
             c.X[r] = df_from(x);
+            if (LS) c.HB[r] = df_from(a.HB[sy.voff + r]);
             const int8_t f = c.flag[r];
             c.rowblk[i] = (r < c.n || f == RF_ONE) ? RB_ONE : (f == RF_SOC ? 0 : RB_ZERO);
         }
@@ -615,10 +667,10 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
         int par = 0;
         bool pending = false;
         for (int64_t pass = 0; pass < ca.max_passes; pass += 2) {
-            if (cluster_pass_df<PU, ROLE_U, SC>(c, par, pending)) break;
+            if (cluster_pass_df<PU, ROLE_U, SC, LS>(c, par, pending)) break;
             pending = true;
             par ^= 1;
-            if (cluster_pass_df<PV, ROLE_V, SC>(c, par, true)) break;
+            if (cluster_pass_df<PV, ROLE_V, SC, LS>(c, par, true)) break;
             par ^= 1;
         }
         // undo the scaling; back to FP64
@@ -632,6 +684,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
             const double w = df_to(c.W[r]), x = df_to(c.X[r]) * ix;
             gW[r] = w;
             gX[r] = x;
+            if (LS) a.HB[sy.voff + r] = df_to(c.HB[r]);
         }
         if (tid == 0 && rank == 0) {
             st.phibar *= ix;
@@ -646,6 +699,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cluster_df(PlanView<T> a, Clus
             gW[rN] = tau[TAU_W];
             gX[rN] = tau[TAU_X] * ix;
             gXI[rN] = tau[TAU_XI];
+            if (LS) a.HB[sy.voff + rN] = tau[TAU_HB];
             a.state[si] = st;
         }
     }

@@ -485,19 +485,27 @@ def test_lsmr_matches_oracle(q, name, mk, precond):
     pv, _ = gpu_vjp(q, plan, d, po)
     for a, b in zip(pj + pv, jv + vv):
         assert np.array_equal(a, b)
+    # the double-float cluster engine: the same recurrences, the oracle's results
+    co = q.options(rtol=1e-11, precond=precond, solver="lsmr", engine="cluster")
+    cj, cji = gpu_jvp(q, plan, d, co)
+    cv, cvi = gpu_vjp(q, plan, d, co)
+    assert plan.last_engine() == "cluster"
+    assert rel_err(cj, rj) < TOL64, (rel_err(cj, rj), cji)
+    assert rel_err(cv, rv) < TOL64, (rel_err(cv, rv), cvi)
     plan.close()
 
 
 def test_lsmr_config2_and_engine_rules(q, cfg2):
     """Configuration 2 with LSMR: four directions each way at rtol 1e-10;
-    auto runs LSMR on the stream engine (the cluster engines refuse it)."""
+    auto runs LSMR on the (double-float) cluster engine; the FP64 cluster
+    kernel refuses it."""
     prob, dirs, ref_j, ref_v = cfg2
     k = 4
     plan = _plan(q, prob, max_rhs=k)
     opts = q.options(rtol=1e-10, precond="equilibrate", solver="lsmr")
     cat = lambda name: np.concatenate([getattr(d, name) for d in dirs[:k]])
     dx, dy, ds, ji = q.qcp_derivative_jvp_multi(plan, k, cat("dP"), cat("dA"), cat("dq"), cat("db"), opts)
-    assert plan.last_engine() == "stream"
+    assert plan.last_engine() == "cluster"
     dx, dy, ds = to_np(dx, dy, ds)
     n, m = prob.n, prob.m
     for i in range(k):
@@ -509,10 +517,9 @@ def test_lsmr_config2_and_engine_rules(q, cfg2):
     for i in range(k):
         got = (gP[i * nP:(i + 1) * nP], gA[i * nA:(i + 1) * nA], gq[i * n:(i + 1) * n], gb[i * m:(i + 1) * m])
         assert rel_err(got, ref_v[i]) < TOL64, (i, rel_err(got, ref_v[i]), vi[i])
-    for engine in ("cluster", "cluster_fp64"):
-        with pytest.raises(RuntimeError):
-            q.qcp_derivative_jvp_multi(plan, 1, cat("dP")[:nP], cat("dA")[:nA], cat("dq")[:n], cat("db")[:m],
-                                       q.options(solver="lsmr", engine=engine))
+    with pytest.raises(RuntimeError):
+        q.qcp_derivative_jvp_multi(plan, 1, cat("dP")[:nP], cat("dA")[:nA], cat("dq")[:n], cat("db")[:m],
+                                   q.options(solver="lsmr", engine="cluster_fp64"))
     plan.close()
 
 
@@ -556,6 +563,6 @@ def test_jacobi_preconditioner(q, name, mk, solver):
     vv, vi = gpu_vjp(q, plan, d, opts)
     assert rel_err(jv, D.jvp_dense(prob, d, fac)[:3]) < TOL64, ji
     assert rel_err(vv, D.vjp_dense(prob, d, fac)[:4]) < TOL64, vi
-    # LSMR runs on the pass engine; LSQR with the Jacobi scaling on the cluster engine where it fits
-    assert plan.last_engine() in (("passes",) if solver == "lsmr" else ("cluster", "cluster_fp64")), plan.last_engine()
+    # either solver with the Jacobi scaling runs on the cluster engine where it fits
+    assert plan.last_engine() in ("cluster", "cluster_fp64"), plan.last_engine()
     plan.close()

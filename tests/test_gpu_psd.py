@@ -39,18 +39,15 @@ def test_psd_jvp_vjp_match_oracle(q, name, mk, precond):
     plan = q.qcp_plan_create(q.problem_tensors(prob, "cuda"), torch.float64)
     for engine in ("auto", "persistent", "stream", "cluster"):
         for solver in ("lsqr", "lsmr"):
-            if engine == "cluster" and solver == "lsmr":
-                continue  # the cluster engine runs LSQR
             if engine == "stream" and precond == "jacobi":
                 continue  # the stream engine runs unscaled or equilibrated
             opts = q.options(rtol=1e-11, precond=precond, engine=engine, solver=solver)
             jv, ji = gpu_jvp(q, plan, d, opts)
             vv, vi = gpu_vjp(q, plan, d, opts)
-            # auto: the cluster engine for LSQR (these problems fit it), the
-            # stream engine for LSMR (the pass engine with the Jacobi scaling);
-            # both apply the cones' D Pi as stored dense matrices in df64
-            auto = "cluster" if solver == "lsqr" else ("stream" if precond != "jacobi" else "passes")
-            want = {"persistent": "persistent", "stream": "stream", "cluster": "cluster"}.get(engine, auto)
+            # auto: the cluster engine (these problems fit it); the stream
+            # and cluster engines apply the cones' D Pi as stored dense
+            # matrices in df64
+            want = {"persistent": "persistent", "stream": "stream"}.get(engine, "cluster")
             assert plan.last_engine() == want, (engine, solver, plan.last_engine())
             assert rel_err(jv, rj) < TOL64, (engine, solver, rel_err(jv, rj), ji)
             assert rel_err(vv, rv) < TOL64, (engine, solver, rel_err(vv, rv), vi)
